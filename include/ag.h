@@ -1,0 +1,195 @@
+/* ag.h — C ABI of the GB300 multirotor fleet simulator (libaerialgb).
+ *
+ * One context simulates n_envs independent environments, each holding one
+ * multirotor (quad, hexa or octo) and up to AG_MAX_OBSTACLES static oriented
+ * boxes. The operations follow the problem statement of Kulkarni, Forgaard,
+ * Alexis, "Aerial Gym - Isaac Gym Simulator for Aerial Robots" (arXiv
+ * 2305.16510):
+ *   - Sec. III: a gym-style step / reset interface with access to each robot's
+ *     position, orientation, linear and angular velocity, and to the obstacle
+ *     state;
+ *   - Sec. IV-A (Eqs. 1-5) and IV-B (Eqs. 6-9): attitude and velocity command
+ *     interfaces of the parallel SE(3) geometric controller; Sec. I: position
+ *     tracking in the inertial frame;
+ *   - Sec. V: environments are reset with a fresh random draw.
+ *
+ * Conventions that hold for every entry point:
+ *   - World frame z up, g = (0, 0, -9.81) m/s^2. Quaternions are (w, x, y, z),
+ *     Hamilton, body -> world. Angular velocity is in the body frame.
+ *   - Arrays are structure-of-arrays over environments: field r of env i sits
+ *     at index r * n_envs + i, in float32 unless stated.
+ *   - Pointer arguments may point to host memory (pageable or pinned) or to
+ *     device memory of the context's device; the library copies with
+ *     cudaMemcpyAsync(cudaMemcpyDefault). The caller owns them; they are only
+ *     borrowed for the duration of the call, except that copies FROM a
+ *     pageable host buffer have completed when the call returns, and copies
+ *     INTO any buffer have completed once the context's stream has been
+ *     synchronised (ag_synchronize) — pinned/device destinations may still be
+ *     written after the call returns.
+ *   - Calls are asynchronous on the context's CUDA stream unless stated.
+ *   - Errors: AG_ERR_INVALID leaves the context unchanged. After a CUDA error
+ *     the context is failed and every later call except ag_last_error and
+ *     ag_destroy returns AG_ERR_STATE. No C++ exception crosses this ABI.
+ */
+#ifndef AG_H
+#define AG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AG_ABI_VERSION 1
+#define AG_MAX_OBSTACLES 64
+#define AG_STATE_DIM 13  /* p.xyz, v.xyz, q.wxyz, Omega.xyz */
+#define AG_MAX_ROTORS 8
+
+typedef struct ag_ctx ag_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  AG_OK = 0,
+  AG_ERR_INVALID = 1,     /* bad argument */
+  AG_ERR_OOM = 2,         /* device allocation failed or HBM budget exceeded */
+  AG_ERR_CUDA = 3,        /* a CUDA call failed; the context is now failed */
+  AG_ERR_STATE = 4,       /* the context failed earlier */
+  AG_ERR_TIMEOUT = 5,     /* a bounded wait expired */
+  AG_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} ag_status;
+
+/* Command interface of one environment (Sec. IV). Targets are four floats:
+ *   AG_MODE_POSITION   (p_d.x, p_d.y, p_d.z, psi_d)       world frame, yaw [rad]
+ *   AG_MODE_BODY_VEL   (v_d.x, v_d.y, v_d.z, psi_dot_d)   v_d in the yaw-aligned
+ *                                                        vehicle frame (Eq. 6)
+ *   AG_MODE_ATT_THRUST (phi_d, theta_d, psi_dot_d, f)     Eqs. 1-2, f in newtons
+ *   AG_MODE_WRENCH     (f, M_x, M_y, M_z)                 body wrench, bypasses the
+ *                                                        controller (still allocated,
+ *                                                        clamped and lagged) */
+typedef enum {
+  AG_MODE_POSITION = 0,
+  AG_MODE_BODY_VEL = 1,
+  AG_MODE_ATT_THRUST = 2,
+  AG_MODE_WRENCH = 3
+} ag_mode;
+
+typedef enum { AG_INTEG_SIE = 0 /* semi-implicit Euler */, AG_INTEG_RK4 = 1 } ag_integrator;
+
+typedef struct {
+  uint32_t n_envs;            /* >= 1 */
+  uint32_t substeps_per_step; /* controller + integrator updates per step (>= 1) */
+  uint32_t integrator;        /* ag_integrator */
+  uint32_t n_obstacles;       /* boxes per environment, 0..AG_MAX_OBSTACLES */
+  uint32_t n_quad, n_hexa, n_octo; /* contiguous type ranges in this order; sum == n_envs */
+  uint32_t reserved0;
+  float dt;          /* step length [s]; a substep is dt / substeps_per_step */
+  float motor_tau;   /* first-order motor time constant [s]; 0 = no lag */
+  float drag;        /* linear drag coefficient [N s / m], world frame */
+  float sphere_r;    /* collision radius of a vehicle [m] */
+  float u_max;       /* per-motor thrust limit [N] (lower limit 0) */
+  float arm;         /* rotor distance from the centre [m] */
+  float k_yaw;       /* rotor reaction torque per newton of thrust [m] */
+  float mass;        /* nominal mass [kg] written at create */
+  float inertia[3];  /* nominal diagonal inertia [kg m^2] written at create */
+  float kx[3], kv[3], kR[3], kW[3]; /* diagonal controller gains */
+  uint64_t seed;     /* Philox key for resets until ag_reset supplies another */
+  uint64_t hbm_budget_bytes; /* 0 = no limit; otherwise ag_create fails with
+                                AG_ERR_OOM if its buffers would exceed it */
+} ag_config;
+
+/* Fills *cfg with the defaults of a 1,024-quad fleet: dt 0.01, 1 substep,
+ * semi-implicit Euler, no obstacles, tau 0.03, no drag, r 0.2, u_max 5,
+ * arm 0.13, k_yaw 0.016, m 0.75, J diag(0.007, 0.007, 0.012),
+ * k_x (2,2,3), k_v (2,2,2), k_R (1.2,1.2,0.6), k_Omega (0.2,0.2,0.1), seed 1. */
+void ag_config_default(ag_config* cfg);
+
+/* Creates a context on the current CUDA device. `cuda_stream` is a
+ * cudaStream_t (NULL = the legacy default stream) that every later call is
+ * ordered on. Every environment starts at the origin, level, at rest, motors
+ * off, epoch 0, mode AG_MODE_WRENCH with zero targets; call ag_reset to draw
+ * initial states. Returns AG_ERR_INVALID for an inconsistent config and
+ * AG_ERR_OOM when the buffers do not fit. *out is NULL on failure. */
+ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out);
+
+/* Frees every buffer of the context (synchronises its stream first). NULL is
+ * accepted. */
+ag_status ag_destroy(ag_ctx* ctx);
+
+/* Copies the command of every environment: modes uint8[n_envs] (ag_mode
+ * values; any value above 3 acts as AG_MODE_WRENCH) and targets
+ * float[4][n_envs] as described at ag_mode. Either pointer may be NULL to
+ * keep the current one. */
+ag_status ag_set_commands(ag_ctx* ctx, const uint8_t* modes, const float* targets);
+
+/* Copies the static obstacles: float[n_obstacles][10][n_envs], per box the
+ * centre (3), half-extents (3, > 0) and a UNIT quaternion (4) of its
+ * orientation (Sec. V: the obstacle state is privileged information). */
+ag_status ag_set_obstacles(ag_ctx* ctx, const float* boxes);
+
+/* Copies per-environment rigid-body parameters float[4][n_envs]: mass and
+ * the diagonal inertia J_xx, J_yy, J_zz (all > 0). */
+ag_status ag_set_body(ag_ctx* ctx, const float* body);
+
+/* Advances every environment by n_substeps substeps (a positive multiple of
+ * substeps_per_step) in ONE fused kernel launch: per substep the controller
+ * of the environment's mode (Sec. IV), rotor allocation with per-motor clamp
+ * to [0, u_max] and first-order motor lag, and one integrator update with
+ * quaternion renormalisation; after the last substep of every step the
+ * vehicle sphere is tested against every box of its environment, and an
+ * environment that touches one is reset in place (epoch + 1, Philox draw of
+ * a new state, as ag_reset). Afterwards the collided flags mark environments
+ * that hit a box in any step of this call and the reset list holds each
+ * environment reset during this call once (order unspecified). */
+ag_status ag_step(ag_ctx* ctx, uint32_t n_substeps);
+
+/* Same results as ag_step, computed by one kernel launch per stage per
+ * substep (controller, allocation, integrator) and per step (collision,
+ * reset), with every intermediate written to and read back from device
+ * memory. It is the unfused comparison point; results agree with ag_step to
+ * float32 rounding. */
+ag_status ag_step_plain(ag_ctx* ctx, uint32_t n_substeps);
+
+/* Resets the environments whose mask byte is non-zero (mask NULL = all):
+ * epoch + 1, then position U[-2, 2)^3 m, attitude a rotation by U[0, pi/6)
+ * about a uniformly random axis, velocity N(0, 0.5^2) m/s per axis, zero body
+ * rate and every motor at hover thrust m g / n_rot. The draw is Philox4x32-10
+ * with key = seed and counter (env, epoch, slot, 0), transformed in strict
+ * binary32 arithmetic, so it is reproducible bit for bit. `seed` also becomes
+ * the key of later collision resets. Writes the reset list and clears the
+ * collided flags. */
+ag_status ag_reset(ag_ctx* ctx, const uint8_t* mask, uint64_t seed);
+
+/* Copies out the state float[13][n_envs] (p, v, q, Omega), the collided
+ * flags uint8[n_envs] and the reset list uint32[n_envs] (its first
+ * *n_reset entries are valid) of the last ag_step / ag_reset. Any pointer may
+ * be NULL. A non-NULL n_reset synchronises the stream. */
+ag_status ag_get_state(ag_ctx* ctx, float* state, uint8_t* collided, uint32_t* reset_ids, uint32_t* n_reset);
+
+/* Copies out the motor thrusts float[8][n_envs] (rows >= n_rot unused) and
+ * the reset epochs uint32[n_envs]. Either pointer may be NULL. */
+ag_status ag_get_motors(ag_ctx* ctx, float* motors, uint32_t* epoch);
+
+/* Overwrites the state float[13][n_envs]; motors float[8][n_envs] and
+ * epoch uint32[n_envs] may be NULL to keep the current values. With
+ * ag_get_state / ag_get_motors this checkpoints and resumes a fleet bit for
+ * bit. */
+ag_status ag_set_state(ag_ctx* ctx, const float* state, const float* motors, const uint32_t* epoch);
+
+/* Waits for all work queued on the context's stream. */
+ag_status ag_synchronize(ag_ctx* ctx);
+
+/* Number of environments / the configuration the context was created with. */
+ag_status ag_get_config(const ag_ctx* ctx, ag_config* out);
+
+/* Message of the last error of this context ("" if none); valid until the
+ * next call on the context. NULL ctx gives the last ag_create failure. */
+const char* ag_last_error(const ag_ctx* ctx);
+
+/* AG_ABI_VERSION of the loaded library. */
+int ag_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AG_H */

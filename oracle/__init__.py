@@ -64,7 +64,7 @@ def _declare(L: ctypes.CDLL) -> None:
     vp = ctypes.c_void_p
     L.orc_world_size.restype = ctypes.c_int
     L.orc_rollout.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp, _u8p, _dp, _dp, _u32p, ctypes.c_uint64, _u8p,
-                              _u32p, ctypes.c_int]
+                              _u32p, _u32p, ctypes.c_int]
     L.orc_reset.argtypes = [vp, _u8p, ctypes.c_uint64, _dp, _dp, _dp, _u32p]
     L.orc_hat.argtypes = [_dp, _dp]
     L.orc_vee.argtypes = [_dp, _dp]
@@ -193,9 +193,13 @@ def make_fleet(world: World, *, state=None, motors=None, body=None, modes=None, 
     return fl
 
 
-def rollout(world: World, fleet: Fleet, n_steps: int, n_threads: int = 1):
-    """Advances the fleet in place; returns (collided uint8[n], n_resets uint32[n])."""
+def rollout(world: World, fleet: Fleet, n_steps: int, n_threads: int = 1, env_ids=None):
+    """Advances the fleet in place; returns (collided uint8[n], n_resets uint32[n]).
+
+    env_ids: Philox environment number of each row (default: the row index).
+    """
     L = lib()
+    ids = None if env_ids is None else np.ascontiguousarray(np.asarray(env_ids, dtype=np.uint32))
     n = world.n_envs
     collided = np.zeros(n, dtype=np.uint8)
     resets = np.zeros(n, dtype=np.uint32)
@@ -204,7 +208,7 @@ def rollout(world: World, fleet: Fleet, n_steps: int, n_threads: int = 1):
     rc = L.orc_rollout(ctypes.byref(w), int(n_steps), _ptr(fleet.state, _dp), _ptr(fleet.motors, _dp),
                        _ptr(fleet.body, _dp), _ptr(fleet.modes, _u8p), _ptr(fleet.targets, _dp), _ptr(boxes, _dp),
                        _ptr(fleet.epoch, _u32p), ctypes.c_uint64(fleet.seed), _ptr(collided, _u8p),
-                       _ptr(resets, _u32p), int(n_threads))
+                       _ptr(resets, _u32p), _ptr(ids, _u32p), int(n_threads))
     if rc != 0:
         raise ValueError(f"orc_rollout failed ({rc})")
     return collided, resets

@@ -77,10 +77,11 @@ void substep(const Rotors& rot, int mode, const T tgt[4], const Body<T>& body, c
 }
 
 // Writes a fresh draw into environment i's state and motors (Sec. V reset).
+// `id` is the environment number in the Philox counter (normally i).
 void apply_reset(double* state, double* motors, const double* body, uint32_t* epoch, size_t n, size_t i, int n_rot,
-                 uint64_t seed) {
+                 uint64_t seed, uint32_t id) {
   epoch[i] += 1u;
-  ResetDraw d = sample_reset_f32(seed, (uint32_t)i, epoch[i]);
+  ResetDraw d = sample_reset_f32(seed, id, epoch[i]);
   double v[13] = {d.p[0], d.p[1], d.p[2], d.v[0], d.v[1], d.v[2], d.q[0], d.q[1], d.q[2], d.q[3], 0.0, 0.0, 0.0};
   for (int r = 0; r < 13; ++r) state[r * n + i] = v[r];
   float hover = hover_thrust_f32((float)body[0 * n + i], n_rot);
@@ -101,7 +102,8 @@ bool env_collides(const World& w, const double* boxes, size_t n, size_t i, Vec3<
 
 void rollout_range(const World& w, const Rotors rot[3], int n_steps, double* state, double* motors,
                    const double* body, const uint8_t* modes, const double* targets, const double* boxes,
-                   uint32_t* epoch, uint64_t seed, uint8_t* collided, uint32_t* n_resets, size_t i0, size_t i1) {
+                   uint32_t* epoch, uint64_t seed, uint8_t* collided, uint32_t* n_resets, const uint32_t* env_ids,
+                   size_t i0, size_t i1) {
   const size_t n = (size_t)w.n_envs;
   const double alpha = motor_alpha(w);
   const double h = w.dt / w.substeps_per_step;
@@ -123,7 +125,7 @@ void rollout_range(const World& w, const Rotors rot[3], int n_steps, double* sta
         any_hit = 1;
         resets += 1;
         store_state(s, state, n, i);
-        apply_reset(state, motors, body, epoch, n, i, n_rot, seed);
+        apply_reset(state, motors, body, epoch, n, i, n_rot, seed, env_ids ? env_ids[i] : (uint32_t)i);
         s = load_state<double>(state, n, i);
         for (int k = 0; k < 8; ++k) u[k] = motors[k * n + i];
       }
@@ -173,16 +175,20 @@ int orc_world_size(void) { return (int)sizeof(World); }
 // substeps_per_step substeps followed, when n_obs > 0, by the sphere-vs-box
 // test; an environment that hits any box is reset (epoch + 1, fresh draw).
 // collided[i] = 1 if env i hit a box in any step of this call; n_resets[i]
-// counts its resets. Work is split over n_threads host threads.
+// counts its resets. env_ids (may be NULL) gives the environment number
+// each row uses in the Philox counter, so a subset of a larger fleet draws
+// the same resets as in the full fleet. Work is split over n_threads host
+// threads.
 int orc_rollout(const void* world, int n_steps, double* state, double* motors, const double* body,
                 const uint8_t* modes, const double* targets, const double* boxes, uint32_t* epoch, uint64_t seed,
-                uint8_t* collided, uint32_t* n_resets, int n_threads) {
+                uint8_t* collided, uint32_t* n_resets, const uint32_t* env_ids, int n_threads) {
   World w = world_of(world);
   if (w.n_envs <= 0 || w.substeps_per_step <= 0 || n_steps < 0) return 1;
   Rotors rot[3] = {make_rotors(4, w.arm, w.k_yaw), make_rotors(6, w.arm, w.k_yaw), make_rotors(8, w.arm, w.k_yaw)};
   size_t n = (size_t)w.n_envs;
   if (n_threads <= 1) {
-    rollout_range(w, rot, n_steps, state, motors, body, modes, targets, boxes, epoch, seed, collided, n_resets, 0, n);
+    rollout_range(w, rot, n_steps, state, motors, body, modes, targets, boxes, epoch, seed, collided, n_resets, env_ids,
+                  0, n);
     return 0;
   }
   std::vector<std::thread> pool;
@@ -191,7 +197,7 @@ int orc_rollout(const void* world, int n_steps, double* state, double* motors, c
     size_t i0 = t * chunk, i1 = std::min(n, i0 + chunk);
     if (i0 >= i1) break;
     pool.emplace_back(rollout_range, std::cref(w), rot, n_steps, state, motors, body, modes, targets, boxes, epoch,
-                      seed, collided, n_resets, i0, i1);
+                      seed, collided, n_resets, env_ids, i0, i1);
   }
   for (auto& th : pool) th.join();
   return 0;
@@ -204,7 +210,7 @@ int orc_reset(const void* world, const uint8_t* mask, uint64_t seed, const doubl
   World w = world_of(world);
   size_t n = (size_t)w.n_envs;
   for (size_t i = 0; i < n; ++i)
-    if (!mask || mask[i]) apply_reset(state, motors, body, epoch, n, i, rotor_count(w, (int)i), seed);
+    if (!mask || mask[i]) apply_reset(state, motors, body, epoch, n, i, rotor_count(w, (int)i), seed, (uint32_t)i);
   return 0;
 }
 

@@ -1,0 +1,186 @@
+"""ctypes binding of include/ag.h — argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+simulation work: it converts Python arguments (ints, torch tensors, numpy
+arrays, None) to pointers, calls libaerialgb, and turns a non-zero ag_status
+into an AgError carrying ag_last_error(). The library must have been built
+(``paper_2305_16510_gb300.build.build()``); if it is missing this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+AG_OK, AG_ERR_INVALID, AG_ERR_OOM, AG_ERR_CUDA, AG_ERR_STATE, AG_ERR_TIMEOUT, AG_ERR_UNSUPPORTED = range(7)
+AG_MODE_POSITION, AG_MODE_BODY_VEL, AG_MODE_ATT_THRUST, AG_MODE_WRENCH = range(4)
+AG_INTEG_SIE, AG_INTEG_RK4 = 0, 1
+AG_MAX_OBSTACLES = 64
+STATUS_NAMES = {0: "AG_OK", 1: "AG_ERR_INVALID", 2: "AG_ERR_OOM", 3: "AG_ERR_CUDA", 4: "AG_ERR_STATE",
+                5: "AG_ERR_TIMEOUT", 6: "AG_ERR_UNSUPPORTED"}
+
+
+class AgError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where} -> {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ag_config(ctypes.Structure):
+    _fields_ = [("n_envs", ctypes.c_uint32), ("substeps_per_step", ctypes.c_uint32),
+                ("integrator", ctypes.c_uint32), ("n_obstacles", ctypes.c_uint32),
+                ("n_quad", ctypes.c_uint32), ("n_hexa", ctypes.c_uint32), ("n_octo", ctypes.c_uint32),
+                ("reserved0", ctypes.c_uint32),
+                ("dt", ctypes.c_float), ("motor_tau", ctypes.c_float), ("drag", ctypes.c_float),
+                ("sphere_r", ctypes.c_float), ("u_max", ctypes.c_float), ("arm", ctypes.c_float),
+                ("k_yaw", ctypes.c_float), ("mass", ctypes.c_float), ("inertia", ctypes.c_float * 3),
+                ("kx", ctypes.c_float * 3), ("kv", ctypes.c_float * 3), ("kR", ctypes.c_float * 3),
+                ("kW", ctypes.c_float * 3), ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# every symbol include/ag.h declares, with (restype, argtypes)
+_vp = ctypes.c_void_p
+SIGNATURES = {
+    "ag_abi_version": (ctypes.c_int, []),
+    "ag_config_default": (None, [ctypes.POINTER(ag_config)]),
+    "ag_create": (ctypes.c_int, [ctypes.POINTER(ag_config), _vp, ctypes.POINTER(_vp)]),
+    "ag_destroy": (ctypes.c_int, [_vp]),
+    "ag_set_commands": (ctypes.c_int, [_vp, _vp, _vp]),
+    "ag_set_obstacles": (ctypes.c_int, [_vp, _vp]),
+    "ag_set_body": (ctypes.c_int, [_vp, _vp]),
+    "ag_step": (ctypes.c_int, [_vp, ctypes.c_uint32]),
+    "ag_step_plain": (ctypes.c_int, [_vp, ctypes.c_uint32]),
+    "ag_reset": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
+    "ag_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),
+    "ag_get_motors": (ctypes.c_int, [_vp, _vp, _vp]),
+    "ag_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "ag_synchronize": (ctypes.c_int, [_vp]),
+    "ag_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(ag_config)]),
+    "ag_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libaerialgb.so (built in-tree). Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB_PATH
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: run paper_2305_16510_gb300.build.build() "
+                                   "(there is no CPU fallback)")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def ptr(x) -> int | None:
+    """Device or host address of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _check(rc: int, where: str, ctx) -> None:
+    if rc != AG_OK:
+        msg = lib().ag_last_error(ctx)
+        raise AgError(rc, where, msg.decode() if msg else "")
+
+
+def ag_abi_version() -> int:
+    return lib().ag_abi_version()
+
+
+def ag_config_default() -> ag_config:
+    c = ag_config()
+    lib().ag_config_default(ctypes.byref(c))
+    return c
+
+
+def ag_create(cfg: ag_config, stream: int | None = None) -> int:
+    out = _vp()
+    rc = lib().ag_create(ctypes.byref(cfg), stream, ctypes.byref(out))
+    _check(rc, "ag_create", None)
+    return out.value
+
+
+def ag_destroy(ctx: int) -> None:
+    _check(lib().ag_destroy(ctx), "ag_destroy", ctx)
+
+
+def ag_set_commands(ctx: int, modes, targets) -> None:
+    _check(lib().ag_set_commands(ctx, ptr(modes), ptr(targets)), "ag_set_commands", ctx)
+
+
+def ag_set_obstacles(ctx: int, boxes) -> None:
+    _check(lib().ag_set_obstacles(ctx, ptr(boxes)), "ag_set_obstacles", ctx)
+
+
+def ag_set_body(ctx: int, body) -> None:
+    _check(lib().ag_set_body(ctx, ptr(body)), "ag_set_body", ctx)
+
+
+def ag_step(ctx: int, n_substeps: int) -> None:
+    _check(lib().ag_step(ctx, int(n_substeps)), "ag_step", ctx)
+
+
+def ag_step_plain(ctx: int, n_substeps: int) -> None:
+    _check(lib().ag_step_plain(ctx, int(n_substeps)), "ag_step_plain", ctx)
+
+
+def ag_reset(ctx: int, mask, seed: int) -> None:
+    _check(lib().ag_reset(ctx, ptr(mask), int(seed) & (2**64 - 1)), "ag_reset", ctx)
+
+
+def ag_get_state(ctx: int, state=None, collided=None, reset_ids=None, want_count: bool = False) -> int | None:
+    cnt = ctypes.c_uint32(0)
+    rc = lib().ag_get_state(ctx, ptr(state), ptr(collided), ptr(reset_ids), ctypes.byref(cnt) if want_count else None)
+    _check(rc, "ag_get_state", ctx)
+    return cnt.value if want_count else None
+
+
+def ag_get_motors(ctx: int, motors=None, epoch=None) -> None:
+    _check(lib().ag_get_motors(ctx, ptr(motors), ptr(epoch)), "ag_get_motors", ctx)
+
+
+def ag_set_state(ctx: int, state, motors=None, epoch=None) -> None:
+    _check(lib().ag_set_state(ctx, ptr(state), ptr(motors), ptr(epoch)), "ag_set_state", ctx)
+
+
+def ag_synchronize(ctx: int) -> None:
+    _check(lib().ag_synchronize(ctx), "ag_synchronize", ctx)
+
+
+def ag_get_config(ctx: int) -> ag_config:
+    c = ag_config()
+    _check(lib().ag_get_config(ctx, ctypes.byref(c)), "ag_get_config", ctx)
+    return c
+
+
+def ag_last_error(ctx: int | None) -> str:
+    m = lib().ag_last_error(ctx)
+    return m.decode() if m else ""

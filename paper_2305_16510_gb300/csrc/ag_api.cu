@@ -1,0 +1,414 @@
+// ag_api.cu — the extern "C" entry points declared in include/ag.h.
+//
+// Host side of libaerialgb: argument validation, device buffers, the
+// per-context sticky error state, the FP64 rotor-allocation matrices, and
+// the stream-ordered copies and launches. Nothing here computes a vehicle
+// state; every step of the simulation runs in the kernels of
+// fleet_kernels.cu.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "ag.h"
+#include "fleet_internal.h"
+
+struct ag_ctx {
+  ag_config cfg;
+  cudaStream_t stream;
+  int device;
+  agk::FleetBuffers fb;
+  uint8_t* mask_dev;         // [n] staging for ag_reset masks
+  uint64_t seed;             // Philox key of collision resets
+  bool failed;
+  std::string err;
+  size_t bytes;              // device bytes held
+  float A[3][4][8], Ap[3][8][4];
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+ag_status fail_invalid(ag_ctx* ctx, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  else g_create_error = msg;
+  return AG_ERR_INVALID;
+}
+
+ag_status check_cuda(ag_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return AG_OK;
+  ctx->failed = true;
+  ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return AG_ERR_CUDA;
+}
+
+// Rotor allocation matrices in FP64. Rotor i of n sits at angle
+// beta_0 + 360 i / n degrees (beta_0 = 45 for a quad "X", 30 hexa, 22.5 octo)
+// at radius `arm`, thrusts along body +z and spins alternately (+, -, ...):
+// its column of A is (1, y_i, -x_i, s_i k_yaw). A^+ = A^T (A A^T)^-1.
+void rotor_matrices(int n, double arm, double k_yaw, float A[4][8], float Ap[8][4]) {
+  const double pi = 3.14159265358979323846;
+  const double start = n == 4 ? 45.0 : (n == 6 ? 30.0 : 22.5);
+  double a[4][8] = {};
+  for (int i = 0; i < n; ++i) {
+    double beta = (start + 360.0 * i / n) * pi / 180.0;
+    a[0][i] = 1.0;
+    a[1][i] = arm * std::sin(beta);
+    a[2][i] = -arm * std::cos(beta);
+    a[3][i] = (i % 2 == 0 ? 1.0 : -1.0) * k_yaw;
+  }
+  // M = A A^T, then solve M X = I by Gauss-Jordan with partial pivoting
+  double m[4][8];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += a[r][k] * a[c][k];
+      m[r][c] = s;
+      m[r][c + 4] = r == c ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < 4; ++c) {
+    int p = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (std::fabs(m[r][c]) > std::fabs(m[p][c])) p = r;
+    for (int k = 0; k < 8; ++k) std::swap(m[c][k], m[p][k]);
+    double d = m[c][c];
+    for (int k = 0; k < 8; ++k) m[c][k] /= d;
+    for (int r = 0; r < 4; ++r) {
+      if (r == c) continue;
+      double f = m[r][c];
+      for (int k = 0; k < 8; ++k) m[r][k] -= f * m[c][k];
+    }
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 8; ++c) A[r][c] = (float)a[r][c];
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 4; ++k) s += a[k][i] * m[k][j + 4];
+      Ap[i][j] = i < n ? (float)s : 0.f;
+    }
+}
+
+__global__ void k_fill_rows(float* dst, uint32_t n, float v0, float v1, float v2, float v3, int rows) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v[4] = {v0, v1, v2, v3};
+  for (int r = 0; r < rows; ++r) dst[(size_t)r * n + i] = v[r];
+}
+
+std::string validate(const ag_config* c) {
+  if (!c) return "config is NULL";
+  if (c->n_envs == 0) return "n_envs must be >= 1";
+  if (c->n_envs > (1u << 30)) return "n_envs must be <= 2^30";
+  if (c->substeps_per_step == 0) return "substeps_per_step must be >= 1";
+  if (c->integrator > 1) return "integrator must be 0 (semi-implicit Euler) or 1 (RK4)";
+  if (c->n_obstacles > AG_MAX_OBSTACLES) return "n_obstacles exceeds AG_MAX_OBSTACLES";
+  if ((uint64_t)c->n_quad + c->n_hexa + c->n_octo != c->n_envs) return "n_quad + n_hexa + n_octo must equal n_envs";
+  if (!(c->dt > 0.f) || !std::isfinite(c->dt)) return "dt must be > 0";
+  if (!(c->motor_tau >= 0.f)) return "motor_tau must be >= 0";
+  if (!(c->drag >= 0.f)) return "drag must be >= 0";
+  if (!(c->sphere_r >= 0.f)) return "sphere_r must be >= 0";
+  if (!(c->u_max > 0.f)) return "u_max must be > 0";
+  if (!(c->arm > 0.f)) return "arm must be > 0";
+  if (!(c->k_yaw > 0.f)) return "k_yaw must be > 0";
+  if (!(c->mass > 0.f) || !(c->inertia[0] > 0.f) || !(c->inertia[1] > 0.f) || !(c->inertia[2] > 0.f))
+    return "mass and inertia must be > 0";
+  return "";
+}
+
+size_t buffer_bytes(const ag_config* c) {
+  size_t n = c->n_envs;
+  size_t per = sizeof(float) * (13 + 8 + 4 + 4 + 4 + 4) + sizeof(uint32_t) * 3 + 3 /* modes, collided, hits */ + 1;
+  return n * per + (size_t)c->n_obstacles * 10 * n * sizeof(float) + sizeof(uint32_t);
+}
+
+agk::StepParams step_params(const ag_ctx* ctx) {
+  agk::StepParams P;
+  const ag_config& c = ctx->cfg;
+  for (int i = 0; i < 3; ++i) {
+    P.kx[i] = c.kx[i]; P.kv[i] = c.kv[i]; P.kR[i] = c.kR[i]; P.kW[i] = c.kW[i];
+  }
+  std::memcpy(P.A, ctx->A, sizeof(P.A));
+  std::memcpy(P.Ap, ctx->Ap, sizeof(P.Ap));
+  const double h = (double)c.dt / c.substeps_per_step;
+  P.h = (float)h;
+  P.alpha = c.motor_tau > 0.f ? (float)(1.0 - std::exp(-h / (double)c.motor_tau)) : 1.f;
+  P.drag = c.drag;
+  P.r2 = c.sphere_r * c.sphere_r;
+  P.u_max = c.u_max;
+  P.seed_lo = (uint32_t)(ctx->seed & 0xFFFFFFFFu);
+  P.seed_hi = (uint32_t)(ctx->seed >> 32);
+  return P;
+}
+
+// common prologue: NULL ctx, sticky failure, device selection
+ag_status enter(ag_ctx* ctx) {
+  if (!ctx) return AG_ERR_INVALID;
+  if (ctx->failed) return AG_ERR_STATE;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return check_cuda(ctx, e, "cudaSetDevice");
+  ctx->err.clear();
+  return AG_OK;
+}
+
+void free_all(ag_ctx* ctx) {
+  agk::FleetBuffers& f = ctx->fb;
+  void* ptrs[] = {f.state, f.motors, f.body, f.modes, f.targets, f.boxes, f.epoch, f.collided, f.reset_ids,
+                  f.n_reset, f.cmd, f.wrench, f.resets, f.hits, ctx->mask_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+template <class T> cudaError_t alloc(ag_ctx* ctx, T** p, size_t count) {
+  if (count == 0) { *p = nullptr; return cudaSuccess; }
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) ctx->bytes += count * sizeof(T);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ag_abi_version(void) { return AG_ABI_VERSION; }
+
+void ag_config_default(ag_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->n_envs = 1024;
+  c->substeps_per_step = 1;
+  c->integrator = AG_INTEG_SIE;
+  c->n_obstacles = 0;
+  c->n_quad = 1024;
+  c->dt = 0.01f;
+  c->motor_tau = 0.03f;
+  c->drag = 0.f;
+  c->sphere_r = 0.2f;
+  c->u_max = 5.f;
+  c->arm = 0.13f;
+  c->k_yaw = 0.016f;
+  c->mass = 0.75f;
+  c->inertia[0] = 0.007f; c->inertia[1] = 0.007f; c->inertia[2] = 0.012f;
+  const float kx[3] = {2.f, 2.f, 3.f}, kv[3] = {2.f, 2.f, 2.f}, kR[3] = {1.2f, 1.2f, 0.6f}, kW[3] = {0.2f, 0.2f, 0.1f};
+  for (int i = 0; i < 3; ++i) { c->kx[i] = kx[i]; c->kv[i] = kv[i]; c->kR[i] = kR[i]; c->kW[i] = kW[i]; }
+  c->seed = 1;
+  c->hbm_budget_bytes = 0;
+}
+
+ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
+  if (!out) return fail_invalid(nullptr, "out is NULL");
+  *out = nullptr;
+  std::string why = validate(cfg);
+  if (!why.empty()) return fail_invalid(nullptr, why);
+  if (cfg->hbm_budget_bytes && buffer_bytes(cfg) > cfg->hbm_budget_bytes) {
+    g_create_error = "buffers need " + std::to_string(buffer_bytes(cfg)) + " bytes, budget is " +
+                     std::to_string(cfg->hbm_budget_bytes);
+    return AG_ERR_OOM;
+  }
+  ag_ctx* ctx = new (std::nothrow) ag_ctx();
+  if (!ctx) { g_create_error = "host allocation failed"; return AG_ERR_OOM; }
+  ctx->cfg = *cfg;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->seed = cfg->seed;
+  std::memset(&ctx->fb, 0, sizeof(ctx->fb));
+  ctx->mask_dev = nullptr;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    g_create_error = "no CUDA device";
+    delete ctx;
+    return AG_ERR_CUDA;
+  }
+  for (int t = 0; t < 3; ++t) rotor_matrices(t == 0 ? 4 : (t == 1 ? 6 : 8), cfg->arm, cfg->k_yaw, ctx->A[t], ctx->Ap[t]);
+  const size_t n = cfg->n_envs;
+  agk::FleetBuffers& f = ctx->fb;
+  f.n = cfg->n_envs; f.n_quad = cfg->n_quad; f.n_hexa = cfg->n_hexa; f.n_octo = cfg->n_octo;
+  f.n_obs = cfg->n_obstacles;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = alloc(ctx, &f.state, 13 * n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.motors, 8 * n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.body, 4 * n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.modes, n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.targets, 4 * n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.boxes, (size_t)cfg->n_obstacles * 10 * n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.epoch, n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.collided, n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.reset_ids, n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.n_reset, 1);
+  if (e == cudaSuccess) e = alloc(ctx, &f.cmd, 4 * n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.wrench, 4 * n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.resets, n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.hits, n);
+  if (e == cudaSuccess) e = alloc(ctx, &ctx->mask_dev, n);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    free_all(ctx);
+    delete ctx;
+    return AG_ERR_OOM;
+  }
+  cudaStream_t st = ctx->stream;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.state, 0, 13 * n * sizeof(float), st);
+  if (e == cudaSuccess) { k_fill_rows<<<grid, 256, 0, st>>>(f.state + 6 * n, (uint32_t)n, 1.f, 0, 0, 0, 1); e = cudaGetLastError(); }
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.motors, 0, 8 * n * sizeof(float), st);
+  if (e == cudaSuccess) {
+    k_fill_rows<<<grid, 256, 0, st>>>(f.body, (uint32_t)n, cfg->mass, cfg->inertia[0], cfg->inertia[1], cfg->inertia[2], 4);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.modes, AG_MODE_WRENCH, n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.targets, 0, 4 * n * sizeof(float), st);
+  if (e == cudaSuccess && f.boxes) e = cudaMemsetAsync(f.boxes, 0, (size_t)cfg->n_obstacles * 10 * n * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.epoch, 0, n * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.collided, 0, n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.n_reset, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("initialisation failed: ") + cudaGetErrorString(e);
+    free_all(ctx);
+    delete ctx;
+    return AG_ERR_CUDA;
+  }
+  *out = ctx;
+  return AG_OK;
+}
+
+ag_status ag_destroy(ag_ctx* ctx) {
+  if (!ctx) return AG_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  delete ctx;
+  return AG_OK;
+}
+
+ag_status ag_set_commands(ag_ctx* ctx, const uint8_t* modes, const float* targets) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  const size_t n = ctx->cfg.n_envs;
+  if (modes) {
+    s = check_cuda(ctx, cudaMemcpyAsync(ctx->fb.modes, modes, n, cudaMemcpyDefault, ctx->stream), "copy modes");
+    if (s != AG_OK) return s;
+  }
+  if (targets)
+    s = check_cuda(ctx, cudaMemcpyAsync(ctx->fb.targets, targets, 4 * n * sizeof(float), cudaMemcpyDefault,
+                                        ctx->stream), "copy targets");
+  return s;
+}
+
+ag_status ag_set_obstacles(ag_ctx* ctx, const float* boxes) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!boxes) return fail_invalid(ctx, "boxes is NULL");
+  if (ctx->cfg.n_obstacles == 0) return AG_OK;
+  const size_t count = (size_t)ctx->cfg.n_obstacles * 10 * ctx->cfg.n_envs;
+  return check_cuda(ctx, cudaMemcpyAsync(ctx->fb.boxes, boxes, count * sizeof(float), cudaMemcpyDefault, ctx->stream),
+                    "copy boxes");
+}
+
+ag_status ag_set_body(ag_ctx* ctx, const float* body) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!body) return fail_invalid(ctx, "body is NULL");
+  return check_cuda(ctx, cudaMemcpyAsync(ctx->fb.body, body, 4 * ctx->cfg.n_envs * sizeof(float), cudaMemcpyDefault,
+                                         ctx->stream), "copy body");
+}
+
+static ag_status step_common(ag_ctx* ctx, uint32_t n_substeps, bool fused) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  const uint32_t sps = ctx->cfg.substeps_per_step;
+  if (n_substeps == 0 || n_substeps % sps != 0)
+    return fail_invalid(ctx, "n_substeps must be a positive multiple of substeps_per_step");
+  agk::StepParams P = step_params(ctx);
+  const int n_steps = (int)(n_substeps / sps);
+  cudaError_t e = fused ? agk::launch_fused_step(ctx->fb, P, (int)ctx->cfg.integrator, n_steps, (int)sps, ctx->stream)
+                        : agk::launch_plain_step(ctx->fb, P, (int)ctx->cfg.integrator, n_steps, (int)sps, ctx->stream);
+  return check_cuda(ctx, e, fused ? "fused step launch" : "plain step launch");
+}
+
+ag_status ag_step(ag_ctx* ctx, uint32_t n_substeps) { return step_common(ctx, n_substeps, true); }
+ag_status ag_step_plain(ag_ctx* ctx, uint32_t n_substeps) { return step_common(ctx, n_substeps, false); }
+
+ag_status ag_reset(ag_ctx* ctx, const uint8_t* mask, uint64_t seed) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  const uint8_t* mask_dev = nullptr;
+  if (mask) {
+    s = check_cuda(ctx, cudaMemcpyAsync(ctx->mask_dev, mask, ctx->cfg.n_envs, cudaMemcpyDefault, ctx->stream),
+                   "copy mask");
+    if (s != AG_OK) return s;
+    mask_dev = ctx->mask_dev;
+  }
+  ctx->seed = seed;
+  return check_cuda(ctx, agk::launch_reset(ctx->fb, mask_dev, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32),
+                                           ctx->stream), "reset launch");
+}
+
+ag_status ag_get_state(ag_ctx* ctx, float* state, uint8_t* collided, uint32_t* reset_ids, uint32_t* n_reset) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  const size_t n = ctx->cfg.n_envs;
+  cudaStream_t st = ctx->stream;
+  if (state && (s = check_cuda(ctx, cudaMemcpyAsync(state, ctx->fb.state, 13 * n * sizeof(float), cudaMemcpyDefault, st),
+                               "copy state out")) != AG_OK) return s;
+  if (collided && (s = check_cuda(ctx, cudaMemcpyAsync(collided, ctx->fb.collided, n, cudaMemcpyDefault, st),
+                                  "copy collided out")) != AG_OK) return s;
+  if (reset_ids && (s = check_cuda(ctx, cudaMemcpyAsync(reset_ids, ctx->fb.reset_ids, n * sizeof(uint32_t),
+                                                        cudaMemcpyDefault, st), "copy reset ids out")) != AG_OK) return s;
+  if (n_reset) {
+    uint32_t tmp = 0;
+    if ((s = check_cuda(ctx, cudaMemcpyAsync(&tmp, ctx->fb.n_reset, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                        "copy reset count out")) != AG_OK) return s;
+    if ((s = check_cuda(ctx, cudaStreamSynchronize(st), "synchronize")) != AG_OK) return s;
+    *n_reset = tmp;
+  }
+  return AG_OK;
+}
+
+ag_status ag_get_motors(ag_ctx* ctx, float* motors, uint32_t* epoch) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  const size_t n = ctx->cfg.n_envs;
+  if (motors && (s = check_cuda(ctx, cudaMemcpyAsync(motors, ctx->fb.motors, 8 * n * sizeof(float), cudaMemcpyDefault,
+                                                     ctx->stream), "copy motors out")) != AG_OK) return s;
+  if (epoch) s = check_cuda(ctx, cudaMemcpyAsync(epoch, ctx->fb.epoch, n * sizeof(uint32_t), cudaMemcpyDefault,
+                                                ctx->stream), "copy epoch out");
+  return s;
+}
+
+ag_status ag_set_state(ag_ctx* ctx, const float* state, const float* motors, const uint32_t* epoch) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!state) return fail_invalid(ctx, "state is NULL");
+  const size_t n = ctx->cfg.n_envs;
+  if ((s = check_cuda(ctx, cudaMemcpyAsync(ctx->fb.state, state, 13 * n * sizeof(float), cudaMemcpyDefault, ctx->stream),
+                      "copy state in")) != AG_OK) return s;
+  if (motors && (s = check_cuda(ctx, cudaMemcpyAsync(ctx->fb.motors, motors, 8 * n * sizeof(float), cudaMemcpyDefault,
+                                                     ctx->stream), "copy motors in")) != AG_OK) return s;
+  if (epoch) s = check_cuda(ctx, cudaMemcpyAsync(ctx->fb.epoch, epoch, n * sizeof(uint32_t), cudaMemcpyDefault,
+                                                ctx->stream), "copy epoch in");
+  return s;
+}
+
+ag_status ag_synchronize(ag_ctx* ctx) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "synchronize");
+}
+
+ag_status ag_get_config(const ag_ctx* ctx, ag_config* out) {
+  if (!ctx || !out) return AG_ERR_INVALID;
+  *out = ctx->cfg;
+  return AG_OK;
+}
+
+const char* ag_last_error(const ag_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

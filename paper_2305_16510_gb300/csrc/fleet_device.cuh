@@ -1,0 +1,300 @@
+// fleet_device.cuh — float32 device math of one multirotor substep.
+//
+// Everything a thread needs to advance ONE vehicle: the SE(3) geometric
+// controller (Kulkarni et al., arXiv 2305.16510, Sec. IV-A Eqs. 1-5, Sec. IV-B
+// Eqs. 6-9, and position tracking after Lee, Leok & McClamroch 2011 as
+// Sec. I states), rotor allocation with clamp and first-order lag, rigid-body
+// derivatives, semi-implicit Euler and RK4 updates, quaternion
+// renormalisation and the sphere-vs-oriented-box test.
+//
+// Differences from the paper's text that change no result beyond float32
+// rounding:
+//   * the yaw psi = atan2(R10, R00) is never formed: cos psi and sin psi are
+//     R00 / rho and R10 / rho with rho = sqrt(R00^2 + R10^2);
+//   * Eqs. 8-9 are evaluated without atan2/sin/cos: with a the commanded
+//     acceleration, cos(phi_d) = sqrt(a_x^2 + a_z^2) / |a|,
+//     sin(phi_d) = -a_y / |a|, cos(theta_d) = a_z / sqrt(a_x^2 + a_z^2),
+//     sin(theta_d) = a_x / sqrt(a_x^2 + a_z^2);
+//   * R_z(psi) R_y(theta_d) R_x(phi_d) is written out in those cosines and
+//     sines, and trig of commanded angles is taken once per launch;
+//   * e_R = 1/2 vee(E - E^T) and e_Omega = Omega - E^T Omega_d share one
+//     product E = R_d^T R;
+//   * the body z axis of a non-unit quaternion (RK4 stages) is the
+//     homogeneous quaternion form divided by |q|^2, which equals the axis of
+//     q / |q| exactly.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace agk {
+
+constexpr float kGravity = 9.81f;
+
+enum : int { kModePosition = 0, kModeBodyVel = 1, kModeAttThrust = 2, kModeWrench = 3 };
+enum : int { kIntegSIE = 0, kIntegRK4 = 1 };
+
+struct V3 { float x, y, z; };
+struct Q4 { float w, x, y, z; };
+struct VState { V3 p, v; Q4 q; V3 w; };
+struct Wrench4 { float f, mx, my, mz; };
+struct Body { float m, inv_m, jx, jy, jz, ijx, ijy, ijz; };
+
+// Gains, rotor matrices and integration constants of one launch; passed by
+// value as a kernel parameter (it lives in the constant bank).
+struct StepParams {
+  float kx[3], kv[3], kR[3], kW[3];
+  float A[3][4][8];   // wrench = A u for quad (0), hexa (1), octo (2)
+  float Ap[3][8][4];  // pseudo-inverse of A (FP64-computed, stored float32)
+  float h;            // substep length
+  float alpha;        // motor lag factor 1 - exp(-h / tau)
+  float drag;
+  float r2;           // squared collision radius
+  float u_max;
+  uint32_t seed_lo, seed_hi;
+};
+
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Rotation matrix of a unit quaternion (body -> world).
+__device__ __forceinline__ void rotation(const Q4& q, float R[3][3]) {
+  float xx = q.x * q.x, yy = q.y * q.y, zz = q.z * q.z;
+  float xy = q.x * q.y, xz = q.x * q.z, yz = q.y * q.z;
+  float wx = q.w * q.x, wy = q.w * q.y, wz = q.w * q.z;
+  R[0][0] = 1.f - 2.f * (yy + zz); R[0][1] = 2.f * (xy - wz);       R[0][2] = 2.f * (xz + wy);
+  R[1][0] = 2.f * (xy + wz);       R[1][1] = 1.f - 2.f * (xx + zz); R[1][2] = 2.f * (yz - wx);
+  R[2][0] = 2.f * (xz - wy);       R[2][1] = 2.f * (yz + wx);       R[2][2] = 1.f - 2.f * (xx + yy);
+}
+
+// Per-launch constants of an environment's command. Trig of commanded angles
+// is evaluated here once instead of every substep.
+//   position:   c = (p_d.x, p_d.y, p_d.z, cos psi_d, sin psi_d, -)
+//   body vel:   c = (v_d.x, v_d.y, v_d.z, psi_dot_d, -, -)
+//   att+thrust: c = (cos phi_d, sin phi_d, cos theta_d, sin theta_d, psi_dot_d, f)
+//   wrench:     c = (f, M_x, M_y, M_z, -, -)
+struct Command { int mode; float c[6]; };
+
+__device__ __forceinline__ Command prepare_command(int mode, float t0, float t1, float t2, float t3) {
+  Command cm;
+  cm.mode = mode > kModeWrench ? kModeWrench : mode;
+  cm.c[0] = t0; cm.c[1] = t1; cm.c[2] = t2; cm.c[3] = t3; cm.c[4] = 0.f; cm.c[5] = 0.f;
+  if (cm.mode == kModePosition) {
+    float s, c;
+    sincosf(t3, &s, &c);
+    cm.c[3] = c;
+    cm.c[4] = s;
+  } else if (cm.mode == kModeAttThrust) {
+    float sp, cp, st, ct;
+    sincosf(t0, &sp, &cp);
+    sincosf(t1, &st, &ct);
+    cm.c[0] = cp; cm.c[1] = sp; cm.c[2] = ct; cm.c[3] = st; cm.c[4] = t2; cm.c[5] = t3;
+  }
+  return cm;
+}
+
+// Geometric controller of one vehicle -> commanded (f, M).
+__device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm, const Body& b,
+                                              const StepParams& P) {
+  if (cm.mode == kModeWrench) return {cm.c[0], cm.c[1], cm.c[2], cm.c[3]};
+  float R[3][3];
+  rotation(s.q, R);
+  float Rd[3][3];
+  V3 Wd;
+  float f;
+  if (cm.mode == kModePosition) {
+    // Lee 2011: a = -k_x e_x - k_v e_v + g e3, b3d = a/|a|, b2d ~ b3d x b1c, b1d = b2d x b3d
+    V3 a = {-P.kx[0] * (s.p.x - cm.c[0]) - P.kv[0] * s.v.x,
+            -P.kx[1] * (s.p.y - cm.c[1]) - P.kv[1] * s.v.y,
+            -P.kx[2] * (s.p.z - cm.c[2]) - P.kv[2] * s.v.z + kGravity};
+    f = b.m * (a.x * R[0][2] + a.y * R[1][2] + a.z * R[2][2]);
+    float an2 = dot(a, a);
+    V3 b3d = an2 > 1e-18f ? rsqrtf(an2) * a : V3{0.f, 0.f, 1.f};
+    V3 b1c = {cm.c[3], cm.c[4], 0.f};
+    V3 c = cross(b3d, b1c);
+    float cn2 = dot(c, c);
+    if (!(cn2 > 1e-18f)) {
+      b1c = {-cm.c[4], cm.c[3], 0.f};
+      c = cross(b3d, b1c);
+      cn2 = dot(c, c);
+    }
+    V3 b2d = rsqrtf(cn2) * c;
+    V3 b1d = cross(b2d, b3d);
+    Rd[0][0] = b1d.x; Rd[0][1] = b2d.x; Rd[0][2] = b3d.x;
+    Rd[1][0] = b1d.y; Rd[1][1] = b2d.y; Rd[1][2] = b3d.y;
+    Rd[2][0] = b1d.z; Rd[2][1] = b2d.z; Rd[2][2] = b3d.z;
+    Wd = {0.f, 0.f, 0.f};
+  } else {
+    // current yaw of the body frame: (cos psi, sin psi) = (R00, R10) / rho
+    float rho2 = R[0][0] * R[0][0] + R[1][0] * R[1][0];
+    float cpsi = 1.f, spsi = 0.f;
+    if (rho2 > 0.f) {
+      float ir = rsqrtf(rho2);
+      cpsi = R[0][0] * ir;
+      spsi = R[1][0] * ir;
+    }
+    float cphi, sphi, cth, sth, rate;
+    if (cm.mode == kModeBodyVel) {
+      // Eq. 6 in the vehicle frame, Eq. 7 thrust, Eqs. 8-9 tilt (algebraic)
+      V3 vV = {cpsi * s.v.x + spsi * s.v.y, -spsi * s.v.x + cpsi * s.v.y, s.v.z};
+      V3 a = {P.kv[0] * (cm.c[0] - vV.x), P.kv[1] * (cm.c[1] - vV.y), P.kv[2] * (cm.c[2] - vV.z) + kGravity};
+      V3 b3V = {cpsi * R[0][2] + spsi * R[1][2], -spsi * R[0][2] + cpsi * R[1][2], R[2][2]};
+      f = b.m * dot(a, b3V);
+      float rxz2 = a.x * a.x + a.z * a.z;
+      float an2 = rxz2 + a.y * a.y;
+      cphi = 1.f; sphi = 0.f; cth = 1.f; sth = 0.f;
+      if (rxz2 > 0.f) {
+        float irxz = rsqrtf(rxz2);
+        cth = a.z * irxz;
+        sth = a.x * irxz;
+        float ian = rsqrtf(an2);
+        cphi = rxz2 * irxz * ian;
+        sphi = -a.y * ian;
+      } else if (an2 > 0.f) {
+        cphi = 0.f;
+        sphi = a.y > 0.f ? -1.f : 1.f;
+      }
+      rate = cm.c[3];
+    } else {
+      cphi = cm.c[0]; sphi = cm.c[1]; cth = cm.c[2]; sth = cm.c[3]; rate = cm.c[4];
+      f = cm.c[5];
+    }
+    // Eq. 1: R_d = R_z(psi) R_y(theta_d) R_x(phi_d)
+    float b01 = sth * sphi, b02 = sth * cphi, b21 = cth * sphi, b22 = cth * cphi;
+    Rd[0][0] = cpsi * cth;  Rd[0][1] = cpsi * b01 - spsi * cphi; Rd[0][2] = cpsi * b02 + spsi * sphi;
+    Rd[1][0] = spsi * cth;  Rd[1][1] = spsi * b01 + cpsi * cphi; Rd[1][2] = spsi * b02 - cpsi * sphi;
+    Rd[2][0] = -sth;        Rd[2][1] = b21;                      Rd[2][2] = b22;
+    // Eq. 2
+    Wd = {-sth * rate, b21 * rate, b22 * rate};
+  }
+  // Eqs. 3-5 with E = R_d^T R
+  float E[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) E[i][j] = Rd[0][i] * R[0][j] + Rd[1][i] * R[1][j] + Rd[2][i] * R[2][j];
+  V3 eR = {0.5f * (E[2][1] - E[1][2]), 0.5f * (E[0][2] - E[2][0]), 0.5f * (E[1][0] - E[0][1])};
+  V3 eW = {s.w.x - (E[0][0] * Wd.x + E[1][0] * Wd.y + E[2][0] * Wd.z),
+           s.w.y - (E[0][1] * Wd.x + E[1][1] * Wd.y + E[2][1] * Wd.z),
+           s.w.z - (E[0][2] * Wd.x + E[1][2] * Wd.y + E[2][2] * Wd.z)};
+  V3 JW = {b.jx * s.w.x, b.jy * s.w.y, b.jz * s.w.z};
+  V3 gyro = cross(s.w, JW);
+  return {f, -P.kR[0] * eR.x - P.kW[0] * eW.x + gyro.x, -P.kR[1] * eR.y - P.kW[1] * eW.y + gyro.y,
+          -P.kR[2] * eR.z - P.kW[2] * eW.z + gyro.z};
+}
+
+// Rotor allocation, per-motor clamp to [0, u_max], first-order lag; returns
+// the realised wrench A u.
+template <int NROT>
+__device__ __forceinline__ Wrench4 allocate(const Wrench4& cmd, float (&u)[NROT], const StepParams& P) {
+  constexpr int T = NROT == 4 ? 0 : (NROT == 6 ? 1 : 2);
+  Wrench4 W = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < NROT; ++i) {
+    float uc = P.Ap[T][i][0] * cmd.f + P.Ap[T][i][1] * cmd.mx + P.Ap[T][i][2] * cmd.my + P.Ap[T][i][3] * cmd.mz;
+    uc = fminf(fmaxf(uc, 0.f), P.u_max);
+    u[i] = u[i] + P.alpha * (uc - u[i]);
+    W.f += P.A[T][0][i] * u[i];
+    W.mx += P.A[T][1][i] * u[i];
+    W.my += P.A[T][2][i] * u[i];
+    W.mz += P.A[T][3][i] * u[i];
+  }
+  return W;
+}
+
+// Rigid-body derivatives under a fixed wrench.
+struct Deriv { V3 dp, dv; Q4 dq; V3 dw; };
+
+__device__ __forceinline__ Deriv derivatives(const VState& s, const Wrench4& W, const Body& b, float drag) {
+  const Q4& q = s.q;
+  float n2 = q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z;
+  float fs = W.f * b.inv_m * __fdividef(1.f, n2);
+  Deriv d;
+  d.dp = s.v;
+  float dm = drag * b.inv_m;
+  d.dv = {fs * 2.f * (q.x * q.z + q.w * q.y) - dm * s.v.x,
+          fs * 2.f * (q.y * q.z - q.w * q.x) - dm * s.v.y,
+          fs * (q.w * q.w - q.x * q.x - q.y * q.y + q.z * q.z) - dm * s.v.z - kGravity};
+  d.dq = {-0.5f * (q.x * s.w.x + q.y * s.w.y + q.z * s.w.z), 0.5f * (q.w * s.w.x + q.y * s.w.z - q.z * s.w.y),
+          0.5f * (q.w * s.w.y - q.x * s.w.z + q.z * s.w.x), 0.5f * (q.w * s.w.z + q.x * s.w.y - q.y * s.w.x)};
+  V3 JW = {b.jx * s.w.x, b.jy * s.w.y, b.jz * s.w.z};
+  V3 g = cross(s.w, JW);
+  d.dw = {b.ijx * (W.mx - g.x), b.ijy * (W.my - g.y), b.ijz * (W.mz - g.z)};
+  return d;
+}
+
+__device__ __forceinline__ void normalize(Q4& q) {
+  float r = rsqrtf(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+  q.w *= r; q.x *= r; q.y *= r; q.z *= r;
+}
+
+__device__ __forceinline__ VState advance(const VState& s, float h, const Deriv& d) {
+  VState r;
+  r.p = s.p + h * d.dp;
+  r.v = s.v + h * d.dv;
+  r.q = {s.q.w + h * d.dq.w, s.q.x + h * d.dq.x, s.q.y + h * d.dq.y, s.q.z + h * d.dq.z};
+  r.w = s.w + h * d.dw;
+  return r;
+}
+
+// Semi-implicit Euler: v, Omega from the derivatives; p, q from the updated
+// velocities; renormalise q.
+__device__ __forceinline__ void step_sie(VState& s, const Wrench4& W, const Body& b, float drag, float h) {
+  Deriv d = derivatives(s, W, b, drag);
+  s.v = s.v + h * d.dv;
+  s.w = s.w + h * d.dw;
+  s.p = s.p + h * s.v;
+  float hh = 0.5f * h;
+  Q4 q = s.q;
+  s.q = {q.w - hh * (q.x * s.w.x + q.y * s.w.y + q.z * s.w.z), q.x + hh * (q.w * s.w.x + q.y * s.w.z - q.z * s.w.y),
+         q.y + hh * (q.w * s.w.y - q.x * s.w.z + q.z * s.w.x), q.z + hh * (q.w * s.w.z + q.x * s.w.y - q.y * s.w.x)};
+  normalize(s.q);
+}
+
+// Classic RK4 with the wrench held over the stages; renormalise q.
+__device__ __forceinline__ void step_rk4(VState& s, const Wrench4& W, const Body& b, float drag, float h) {
+  float hh = 0.5f * h;
+  Deriv k = derivatives(s, W, b, drag);
+  Deriv acc = k;
+  k = derivatives(advance(s, hh, k), W, b, drag);
+  acc.dp = acc.dp + 2.f * k.dp; acc.dv = acc.dv + 2.f * k.dv; acc.dw = acc.dw + 2.f * k.dw;
+  acc.dq = {acc.dq.w + 2.f * k.dq.w, acc.dq.x + 2.f * k.dq.x, acc.dq.y + 2.f * k.dq.y, acc.dq.z + 2.f * k.dq.z};
+  k = derivatives(advance(s, hh, k), W, b, drag);
+  acc.dp = acc.dp + 2.f * k.dp; acc.dv = acc.dv + 2.f * k.dv; acc.dw = acc.dw + 2.f * k.dw;
+  acc.dq = {acc.dq.w + 2.f * k.dq.w, acc.dq.x + 2.f * k.dq.x, acc.dq.y + 2.f * k.dq.y, acc.dq.z + 2.f * k.dq.z};
+  k = derivatives(advance(s, h, k), W, b, drag);
+  acc.dp = acc.dp + k.dp; acc.dv = acc.dv + k.dv; acc.dw = acc.dw + k.dw;
+  acc.dq = {acc.dq.w + k.dq.w, acc.dq.x + k.dq.x, acc.dq.y + k.dq.y, acc.dq.z + k.dq.z};
+  s = advance(s, h * (1.f / 6.f), acc);
+  normalize(s.q);
+}
+
+template <int INTEG>
+__device__ __forceinline__ void integrate(VState& s, const Wrench4& W, const Body& b, const StepParams& P) {
+  if (INTEG == kIntegRK4)
+    step_rk4(s, W, b, P.drag, P.h);
+  else
+    step_sie(s, W, b, P.drag, P.h);
+}
+
+// Sphere of squared radius r2 at p versus the box (centre c, half-extents
+// hx, hy, hz, unit quaternion qb): p is taken into the box frame by the
+// conjugate rotation v - w t + u x t with t = 2 u x v, clamped to the box,
+// and the squared excess compared with r2 (touching counts).
+__device__ __forceinline__ bool sphere_hits_box(V3 p, float r2, V3 c, V3 hb, Q4 qb) {
+  V3 v = p - c;
+  V3 u = {qb.x, qb.y, qb.z};
+  V3 t = 2.f * cross(u, v);
+  V3 d = v - qb.w * t + cross(u, t);
+  float ex = d.x - fminf(fmaxf(d.x, -hb.x), hb.x);
+  float ey = d.y - fminf(fmaxf(d.y, -hb.y), hb.y);
+  float ez = d.z - fminf(fmaxf(d.z, -hb.z), hb.z);
+  return !(r2 < ex * ex + ey * ey + ez * ez);
+}
+
+}  // namespace agk

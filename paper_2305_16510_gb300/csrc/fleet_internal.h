@@ -1,0 +1,43 @@
+// fleet_internal.h — launch interface between the C-ABI layer and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fleet_device.cuh"
+
+namespace agk {
+
+// Device buffers of one fleet (all structure-of-arrays over n environments).
+struct FleetBuffers {
+  float* state;        // [13][n]  p, v, q, Omega
+  float* motors;       // [8][n]   rotor thrusts
+  float* body;         // [4][n]   m, Jxx, Jyy, Jzz
+  uint8_t* modes;      // [n]
+  float* targets;      // [4][n]
+  float* boxes;        // [n_obs][10][n]
+  uint32_t* epoch;     // [n]
+  uint8_t* collided;   // [n]     hit a box during the last call
+  uint32_t* reset_ids; // [n]     compact list of envs reset during the last call
+  uint32_t* n_reset;   // [1]     length of that list
+  // scratch of the unfused path (one launch per stage)
+  float* cmd;          // [4][n]  commanded wrench
+  float* wrench;       // [4][n]  realised wrench
+  uint32_t* resets;    // [n]     resets of this call per env
+  uint8_t* hits;       // [n]     collision of the current step
+  uint32_t n, n_quad, n_hexa, n_octo, n_obs;
+};
+
+// Launches return cudaGetLastError() of their launch.
+cudaError_t launch_fused_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,
+                              int substeps, cudaStream_t st);
+cudaError_t launch_reset(const FleetBuffers& fb, const uint8_t* mask, uint32_t seed_lo, uint32_t seed_hi,
+                         cudaStream_t st);
+cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,
+                              int substeps, cudaStream_t st);
+
+// Threads per block of the fused kernel for a given obstacle count (the
+// per-block shared-memory staging grows with it).
+int fused_block_size(int n_obs);
+
+}  // namespace agk

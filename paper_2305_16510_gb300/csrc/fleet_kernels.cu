@@ -1,0 +1,346 @@
+// fleet_kernels.cu — the fused fleet-step kernel, the reset kernel and the
+// unfused (one launch per stage) comparison path.
+//
+// Fused step (the hot path): one thread owns one environment for a whole
+// launch of n_steps steps. Its 13 state words, motor thrusts, body
+// parameters and command live in registers across every substep; its boxes
+// are staged once per launch in shared memory in a [box][field][thread]
+// layout, so a warp reading one field of one box touches 32 consecutive
+// words (no bank conflicts); global memory is touched only at the start and
+// the end of the launch (coalesced structure-of-arrays rows). Collision
+// resets happen in registers; the reset list is built with one
+// __ballot_sync + __popc prefix and one atomicAdd per warp.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fleet_internal.h"
+#include "reset_sampler.cuh"
+
+namespace agk {
+namespace {
+
+__device__ __forceinline__ int rotor_count(const FleetBuffers& fb, uint32_t env) {
+  if (env < fb.n_quad) return 4;
+  if (env < fb.n_quad + fb.n_hexa) return 6;
+  return 8;
+}
+
+__device__ __forceinline__ VState load_state(const float* st, uint32_t n, uint32_t i) {
+  VState s;
+  s.p = {st[0 * n + i], st[1 * n + i], st[2 * n + i]};
+  s.v = {st[3 * n + i], st[4 * n + i], st[5 * n + i]};
+  s.q = {st[6 * n + i], st[7 * n + i], st[8 * n + i], st[9 * n + i]};
+  s.w = {st[10 * n + i], st[11 * n + i], st[12 * n + i]};
+  return s;
+}
+
+__device__ __forceinline__ void store_state(float* st, uint32_t n, uint32_t i, const VState& s) {
+  st[0 * n + i] = s.p.x; st[1 * n + i] = s.p.y; st[2 * n + i] = s.p.z;
+  st[3 * n + i] = s.v.x; st[4 * n + i] = s.v.y; st[5 * n + i] = s.v.z;
+  st[6 * n + i] = s.q.w; st[7 * n + i] = s.q.x; st[8 * n + i] = s.q.y; st[9 * n + i] = s.q.z;
+  st[10 * n + i] = s.w.x; st[11 * n + i] = s.w.y; st[12 * n + i] = s.w.z;
+}
+
+__device__ __forceinline__ Body load_body(const float* bd, uint32_t n, uint32_t i) {
+  Body b;
+  b.m = bd[0 * n + i];
+  b.jx = bd[1 * n + i];
+  b.jy = bd[2 * n + i];
+  b.jz = bd[3 * n + i];
+  b.inv_m = 1.f / b.m;
+  b.ijx = 1.f / b.jx;
+  b.ijy = 1.f / b.jy;
+  b.ijz = 1.f / b.jz;
+  return b;
+}
+
+__device__ __forceinline__ Command load_command(const FleetBuffers& fb, uint32_t i) {
+  const uint32_t n = fb.n;
+  return prepare_command(fb.modes[i], fb.targets[0 * n + i], fb.targets[1 * n + i], fb.targets[2 * n + i],
+                         fb.targets[3 * n + i]);
+}
+
+// Overwrites one environment with its reset draw for `epoch`.
+template <int NROT>
+__device__ __forceinline__ void reset_in_registers(VState& s, float (&u)[NROT], float m, uint32_t env,
+                                                   uint32_t epoch, uint32_t seed_lo, uint32_t seed_hi) {
+  ResetValues r = draw_reset(seed_lo, seed_hi, env, epoch);
+  s.p = {r.p[0], r.p[1], r.p[2]};
+  s.v = {r.v[0], r.v[1], r.v[2]};
+  s.q = {r.q[0], r.q[1], r.q[2], r.q[3]};
+  s.w = {0.f, 0.f, 0.f};
+  float hv = hover_per_motor(m, NROT);
+#pragma unroll
+  for (int k = 0; k < NROT; ++k) u[k] = hv;
+}
+
+// Appends the envs whose predicate is set to the compact list: one ballot and
+// one atomicAdd per warp, ranks from __popc of the lower lanes. Every lane of
+// the warp must call it.
+__device__ __forceinline__ void append_compact(bool pred, uint32_t env, uint32_t* ids, uint32_t* count) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+  if (mask == 0u) return;
+  const int leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if ((int)lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (pred) ids[base + __popc(mask & ((1u << lane) - 1u))] = env;
+}
+
+// The per-vehicle body of the fused kernel, specialised on the rotor count.
+template <int NROT, int INTEG>
+__device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, int n_steps,
+                                         int substeps, const float* sm, int B, uint32_t& resets, bool& any_hit) {
+  const uint32_t n = fb.n;
+  VState s = load_state(fb.state, n, env);
+  normalize(s.q);
+  float u[NROT];
+#pragma unroll
+  for (int k = 0; k < NROT; ++k) u[k] = fb.motors[k * n + env];
+  const Body b = load_body(fb.body, n, env);
+  const Command cm = load_command(fb, env);
+  uint32_t epoch = fb.epoch[env];
+  const int n_obs = (int)fb.n_obs;
+  for (int step = 0; step < n_steps; ++step) {
+    for (int ss = 0; ss < substeps; ++ss) {
+      Wrench4 W = allocate<NROT>(controller(s, cm, b, P), u, P);
+      integrate<INTEG>(s, W, b, P);
+    }
+    if (n_obs > 0) {
+      bool hit = false;
+#pragma unroll 4
+      for (int k = 0; k < n_obs; ++k) {
+        const float* bx = sm + k * 10 * B;
+        hit |= sphere_hits_box(s.p, P.r2, V3{bx[0], bx[B], bx[2 * B]}, V3{bx[3 * B], bx[4 * B], bx[5 * B]},
+                               Q4{bx[6 * B], bx[7 * B], bx[8 * B], bx[9 * B]});
+      }
+      if (hit) {
+        any_hit = true;
+        resets += 1;
+        epoch += 1;
+        reset_in_registers<NROT>(s, u, b.m, env, epoch, P.seed_lo, P.seed_hi);
+      }
+    }
+  }
+  store_state(fb.state, n, env, s);
+#pragma unroll
+  for (int k = 0; k < NROT; ++k) fb.motors[k * n + env] = u[k];
+  fb.epoch[env] = epoch;
+}
+
+template <int INTEG, bool QUAD_ONLY>
+__global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
+  extern __shared__ float sm_boxes[];  // [n_obs][10][blockDim.x]
+  const int B = blockDim.x;
+  const uint32_t env = blockIdx.x * B + threadIdx.x;
+  const bool active = env < fb.n;
+  // Each thread stages its own environment's boxes (coalesced rows of the
+  // [box][field][env] global layout); it alone reads them back, so no
+  // barrier is needed.
+  float* my = sm_boxes + threadIdx.x;
+  if (active) {
+    const int rows = (int)fb.n_obs * 10;
+    for (int r = 0; r < rows; ++r) my[r * B] = fb.boxes[(size_t)r * fb.n + env];
+  }
+  uint32_t resets = 0;
+  bool any_hit = false;
+  if (active) {
+    const int nrot = QUAD_ONLY ? 4 : rotor_count(fb, env);
+    if (nrot == 4)
+      simulate<4, INTEG>(fb, P, env, n_steps, substeps, my, B, resets, any_hit);
+    else if (nrot == 6)
+      simulate<6, INTEG>(fb, P, env, n_steps, substeps, my, B, resets, any_hit);
+    else
+      simulate<8, INTEG>(fb, P, env, n_steps, substeps, my, B, resets, any_hit);
+    fb.collided[env] = any_hit ? 1 : 0;
+  }
+  append_compact(resets > 0u, env, fb.reset_ids, fb.n_reset);
+}
+
+// ag_reset: resample masked environments, clear collided flags, list them.
+__global__ void __launch_bounds__(256) k_reset(FleetBuffers fb, const uint8_t* mask, uint32_t seed_lo,
+                                               uint32_t seed_hi) {
+  const uint32_t env = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = fb.n;
+  const bool active = env < n;
+  const bool flag = active && (mask == nullptr || mask[env] != 0);
+  if (flag) {
+    const uint32_t epoch = fb.epoch[env] + 1u;
+    fb.epoch[env] = epoch;
+    ResetValues r = draw_reset(seed_lo, seed_hi, env, epoch);
+    float* st = fb.state;
+    st[0 * n + env] = r.p[0]; st[1 * n + env] = r.p[1]; st[2 * n + env] = r.p[2];
+    st[3 * n + env] = r.v[0]; st[4 * n + env] = r.v[1]; st[5 * n + env] = r.v[2];
+    st[6 * n + env] = r.q[0]; st[7 * n + env] = r.q[1]; st[8 * n + env] = r.q[2]; st[9 * n + env] = r.q[3];
+    st[10 * n + env] = 0.f; st[11 * n + env] = 0.f; st[12 * n + env] = 0.f;
+    const int nrot = rotor_count(fb, env);
+    const float hv = hover_per_motor(fb.body[env], nrot);
+    for (int k = 0; k < 8; ++k) fb.motors[k * n + env] = k < nrot ? hv : 0.f;
+  }
+  if (active) fb.collided[env] = 0;
+  append_compact(flag, env, fb.reset_ids, fb.n_reset);
+}
+
+// ------------------------------------------------ unfused comparison path --
+__global__ void __launch_bounds__(256) k_plain_controller(FleetBuffers fb, StepParams P) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= fb.n) return;
+  const uint32_t n = fb.n;
+  VState s = load_state(fb.state, n, i);
+  normalize(s.q);
+  Wrench4 c = controller(s, load_command(fb, i), load_body(fb.body, n, i), P);
+  fb.cmd[0 * n + i] = c.f; fb.cmd[1 * n + i] = c.mx; fb.cmd[2 * n + i] = c.my; fb.cmd[3 * n + i] = c.mz;
+}
+
+template <int NROT>
+__device__ __forceinline__ void plain_allocate_one(const FleetBuffers& fb, const StepParams& P, uint32_t i) {
+  const uint32_t n = fb.n;
+  float u[NROT];
+#pragma unroll
+  for (int k = 0; k < NROT; ++k) u[k] = fb.motors[k * n + i];
+  Wrench4 c = {fb.cmd[0 * n + i], fb.cmd[1 * n + i], fb.cmd[2 * n + i], fb.cmd[3 * n + i]};
+  Wrench4 W = allocate<NROT>(c, u, P);
+#pragma unroll
+  for (int k = 0; k < NROT; ++k) fb.motors[k * n + i] = u[k];
+  fb.wrench[0 * n + i] = W.f; fb.wrench[1 * n + i] = W.mx; fb.wrench[2 * n + i] = W.my; fb.wrench[3 * n + i] = W.mz;
+}
+
+__global__ void __launch_bounds__(256) k_plain_allocate(FleetBuffers fb, StepParams P) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= fb.n) return;
+  const int nrot = rotor_count(fb, i);
+  if (nrot == 4) plain_allocate_one<4>(fb, P, i);
+  else if (nrot == 6) plain_allocate_one<6>(fb, P, i);
+  else plain_allocate_one<8>(fb, P, i);
+}
+
+template <int INTEG>
+__global__ void __launch_bounds__(256) k_plain_integrate(FleetBuffers fb, StepParams P) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= fb.n) return;
+  const uint32_t n = fb.n;
+  VState s = load_state(fb.state, n, i);
+  Wrench4 W = {fb.wrench[0 * n + i], fb.wrench[1 * n + i], fb.wrench[2 * n + i], fb.wrench[3 * n + i]};
+  integrate<INTEG>(s, W, load_body(fb.body, n, i), P);
+  store_state(fb.state, n, i, s);
+}
+
+// Collision test of every environment against its boxes read from global
+// memory; the per-env hit byte goes to `collided_now`.
+__global__ void __launch_bounds__(256) k_plain_collide(FleetBuffers fb, StepParams P, uint8_t* collided_now) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= fb.n) return;
+  const uint32_t n = fb.n;
+  V3 p = {fb.state[0 * n + i], fb.state[1 * n + i], fb.state[2 * n + i]};
+  bool hit = false;
+  for (uint32_t k = 0; k < fb.n_obs; ++k) {
+    const float* bx = fb.boxes + (size_t)k * 10 * n + i;
+    hit |= sphere_hits_box(p, P.r2, V3{bx[0], bx[n], bx[2 * n]}, V3{bx[3 * n], bx[4 * n], bx[5 * n]},
+                           Q4{bx[6 * n], bx[7 * n], bx[8 * n], bx[9 * n]});
+  }
+  collided_now[i] = hit ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(256) k_plain_reset_hits(FleetBuffers fb, StepParams P, const uint8_t* collided_now) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= fb.n || collided_now[i] == 0) return;
+  const uint32_t n = fb.n;
+  const uint32_t epoch = fb.epoch[i] + 1u;
+  fb.epoch[i] = epoch;
+  fb.resets[i] += 1u;
+  fb.collided[i] = 1;
+  ResetValues r = draw_reset(P.seed_lo, P.seed_hi, i, epoch);
+  float* st = fb.state;
+  st[0 * n + i] = r.p[0]; st[1 * n + i] = r.p[1]; st[2 * n + i] = r.p[2];
+  st[3 * n + i] = r.v[0]; st[4 * n + i] = r.v[1]; st[5 * n + i] = r.v[2];
+  st[6 * n + i] = r.q[0]; st[7 * n + i] = r.q[1]; st[8 * n + i] = r.q[2]; st[9 * n + i] = r.q[3];
+  st[10 * n + i] = 0.f; st[11 * n + i] = 0.f; st[12 * n + i] = 0.f;
+  const int nrot = rotor_count(fb, i);
+  const float hv = hover_per_motor(fb.body[i], nrot);
+  for (int k = 0; k < nrot; ++k) fb.motors[k * n + i] = hv;
+}
+
+__global__ void __launch_bounds__(256) k_plain_compact(FleetBuffers fb) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool pred = i < fb.n && fb.resets[i] > 0u;
+  append_compact(pred, i, fb.reset_ids, fb.n_reset);
+}
+
+template <int INTEG, bool QUAD_ONLY>
+cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, cudaStream_t st) {
+  const int B = fused_block_size((int)fb.n_obs);
+  const size_t smem = (size_t)fb.n_obs * 10 * B * sizeof(float);
+  static bool attr_set = false;  // per instantiation; raise the dynamic shared-memory cap once
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_fused_step<INTEG, QUAD_ONLY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const unsigned grid = (fb.n + B - 1) / B;
+  k_fused_step<INTEG, QUAD_ONLY><<<grid, B, smem, st>>>(fb, P, n_steps, substeps);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int fused_block_size(int n_obs) {
+  // keep the per-block staging at or below ~100 KB so two blocks fit per SM
+  const int bytes_per_thread = n_obs * 10 * (int)sizeof(float);
+  if (bytes_per_thread == 0) return 128;
+  int b = (100 * 1024) / bytes_per_thread;
+  b = (b / 32) * 32;
+  if (b > 128) b = 128;
+  if (b < 32) b = 32;
+  return b;
+}
+
+cudaError_t launch_fused_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,
+                              int substeps, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(fb.n_reset, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const bool quad_only = fb.n_quad == fb.n;
+  if (integrator == kIntegRK4)
+    return quad_only ? launch_fused_t<kIntegRK4, true>(fb, P, n_steps, substeps, st)
+                     : launch_fused_t<kIntegRK4, false>(fb, P, n_steps, substeps, st);
+  return quad_only ? launch_fused_t<kIntegSIE, true>(fb, P, n_steps, substeps, st)
+                   : launch_fused_t<kIntegSIE, false>(fb, P, n_steps, substeps, st);
+}
+
+cudaError_t launch_reset(const FleetBuffers& fb, const uint8_t* mask, uint32_t seed_lo, uint32_t seed_hi,
+                         cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(fb.n_reset, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (fb.n + 255) / 256;
+  k_reset<<<grid, 256, 0, st>>>(fb, mask, seed_lo, seed_hi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,
+                              int substeps, cudaStream_t st) {
+  const unsigned grid = (fb.n + 255) / 256;
+  cudaError_t e = cudaMemsetAsync(fb.n_reset, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fb.resets, 0, sizeof(uint32_t) * fb.n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fb.collided, 0, fb.n, st);
+  if (e != cudaSuccess) return e;
+  uint8_t* hits = fb.hits;
+  for (int step = 0; step < n_steps; ++step) {
+    for (int ss = 0; ss < substeps; ++ss) {
+      k_plain_controller<<<grid, 256, 0, st>>>(fb, P);
+      k_plain_allocate<<<grid, 256, 0, st>>>(fb, P);
+      if (integrator == kIntegRK4)
+        k_plain_integrate<kIntegRK4><<<grid, 256, 0, st>>>(fb, P);
+      else
+        k_plain_integrate<kIntegSIE><<<grid, 256, 0, st>>>(fb, P);
+    }
+    if (fb.n_obs > 0) {
+      k_plain_collide<<<grid, 256, 0, st>>>(fb, P, hits);
+      k_plain_reset_hits<<<grid, 256, 0, st>>>(fb, P, hits);
+    }
+  }
+  k_plain_compact<<<grid, 256, 0, st>>>(fb);
+  return cudaGetLastError();
+}
+
+}  // namespace agk

@@ -1,0 +1,345 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle, element by element.
+
+Tolerances: the FP32 state after 100 semi-implicit-Euler steps must match
+the oracle within 1e-4 m in position and 1e-4 rad in attitude (the parity
+bar of the fleet-step workload); single-step comparisons use
+abs 2e-5 + rel 2e-6, the float32 rounding of one RK4 step with margin.
+Reset draws are compared bit for bit. Collision decisions whose squared
+distance margin lies within 1e-5 m^2 of the radius are near-ties that float32
+and float64 may decide differently; they are counted and excluded.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from harness import (attitude_error, box_margin, gpu_fleet, max_state_errors, oracle_fleet_from, oracle_world,
+                     subset)
+from paper_2305_16510_gb300 import _abi
+from paper_2305_16510_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2305_16510_gb300 import build
+    build.build()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _reset_pair(w, seed, inp=None):
+    inp = inp or W.make_inputs(w, seed)
+    fl = gpu_fleet(w, inp, seed)
+    fl.reset(None, seed)
+    orc = oracle_fleet_from(w, inp, np.zeros((13, w.n_envs)), np.zeros((8, w.n_envs)), np.zeros(w.n_envs, np.uint32),
+                            seed)
+    O.reset(oracle_world(w), orc, None, seed)
+    return fl, orc, inp
+
+
+# ------------------------------------------------------------------ resets --
+def test_reset_draws_bit_exact_mixed_fleet():
+    w = W.scaled(W.WORKLOADS["mixed"], 1000)
+    fl, orc, inp = _reset_pair(w, 2024)
+    st = _np(fl.state())
+    np.testing.assert_array_equal(st, orc.state.astype(np.float32))
+    mot = _np(fl.motors())
+    np.testing.assert_array_equal(mot, orc.motors.astype(np.float32))
+    np.testing.assert_array_equal(_np(fl.epoch()).astype(np.uint32), orc.epoch)
+    col, ids = fl.events()
+    assert sorted(_np(ids).tolist()) == list(range(w.n_envs))
+    assert int(_np(col).sum()) == 0
+    # a masked reset with another seed
+    mask = W.reset_mask(w.n_envs, 0.3, np.random.default_rng(5))
+    fl.reset(mask, 99)
+    O.reset(oracle_world(w), orc, mask, 99)
+    np.testing.assert_array_equal(_np(fl.state()), orc.state.astype(np.float32))
+    np.testing.assert_array_equal(_np(fl.motors()), orc.motors.astype(np.float32))
+    np.testing.assert_array_equal(_np(fl.epoch()).astype(np.uint32), orc.epoch)
+    _, ids = fl.events()
+    assert sorted(_np(ids).tolist()) == np.flatnonzero(mask).tolist()
+    fl.close()
+
+
+def test_reset_draws_bit_exact_one_million():
+    w = W.WORKLOADS["obstacles"]
+    n = w.n_envs
+    inp = W.Inputs(np.zeros(n, np.uint8), np.zeros((4, n), np.float32), W.body(w, np.random.default_rng(0)), None)
+    w0 = W.Workload(**{**w.__dict__, "n_obstacles": 0})
+    fl = gpu_fleet(w0, inp, 7)
+    fl.reset(None, 0x1234_5678_9ABC_DEF0)
+    fl.reset(W.reset_mask(n, 0.5, np.random.default_rng(1)), 0x1234_5678_9ABC_DEF0)
+    orc = oracle_fleet_from(w0, inp, np.zeros((13, n)), np.zeros((8, n)), np.zeros(n, np.uint32), 0)
+    O.reset(oracle_world(w0), orc, None, 0x1234_5678_9ABC_DEF0)
+    O.reset(oracle_world(w0), orc, W.reset_mask(n, 0.5, np.random.default_rng(1)), 0x1234_5678_9ABC_DEF0)
+    np.testing.assert_array_equal(_np(fl.state()), orc.state.astype(np.float32))
+    fl.close()
+
+
+# ---------------------------------------------------------- full rollouts --
+def test_parity_position_mode_1024_quads_100_steps():
+    w = W.WORKLOADS["parity"]
+    fl, orc, _ = _reset_pair(w, 1)
+    fl.step(100)
+    O.rollout(oracle_world(w), orc, 100, n_threads=8)
+    dp, dv, dang, dw = max_state_errors(_np(fl.state()), orc.state)
+    assert dp.max() <= 1e-4, dp.max()
+    assert dang.max() <= 1e-4, dang.max()
+    assert dv.max() <= 1e-3 and dw.max() <= 1e-2
+    # the oracle's controller really moved the fleet towards its targets
+    assert np.mean(np.abs(orc.state[0:3] - orc.targets[0:3])) < 2.0
+
+
+@pytest.mark.parametrize("mode_mix,integ,sub", [
+    ((W.MODE_POSITION,), 1, 4),
+    ((W.MODE_BODY_VEL,), 0, 1),
+    ((W.MODE_BODY_VEL,), 1, 4),
+    ((W.MODE_ATT_THRUST,), 0, 1),
+    ((W.MODE_ATT_THRUST,), 1, 2),
+    ((W.MODE_POSITION, W.MODE_BODY_VEL, W.MODE_ATT_THRUST), 1, 4),
+])
+def test_parity_each_mode_and_integrator(mode_mix, integ, sub):
+    # 1,000 envs: several 128-thread blocks and a ragged last block
+    w = W.Workload("modes", 1000, sub, integ, 0, 1000, 0, 0, mode_mix=mode_mix)
+    fl, orc, _ = _reset_pair(w, 11)
+    fl.step(100)
+    O.rollout(oracle_world(w), orc, 100, n_threads=8)
+    dp, dv, dang, dw = max_state_errors(_np(fl.state()), orc.state)
+    scale = 1.0 + np.max(np.abs(orc.state[0:3]), axis=0)
+    assert np.all(dp <= 1e-4 * scale), dp.max()
+    assert dang.max() <= 2e-4, dang.max()
+
+
+def test_parity_mixed_rotor_types_drag_and_random_bodies():
+    w = W.scaled(W.WORKLOADS["mixed"], 2000)
+    fl, orc, _ = _reset_pair(w, 3)
+    fl.step(60)
+    O.rollout(oracle_world(w), orc, 60, n_threads=8)
+    dp, dv, dang, dw = max_state_errors(_np(fl.state()), orc.state)
+    assert dp.max() <= 1e-4, dp.max()
+    assert dang.max() <= 1e-4, dang.max()
+    mot = _np(fl.motors())
+    np.testing.assert_allclose(mot, orc.motors, atol=2e-4)
+
+
+def test_wrench_mode_free_fall_and_hover_fixed_point():
+    n = 300
+    w = W.Workload("wrench", n, 1, 0, 0, n, 0, 0, mode_mix=(W.MODE_WRENCH,))
+    fl, orc, inp = _reset_pair(w, 5)
+    # zero commanded wrench: the motors spin down through the lag, then free fall
+    fl.step(50)
+    O.rollout(oracle_world(w), orc, 50)
+    np.testing.assert_allclose(_np(fl.state())[0:3], orc.state[0:3], atol=1e-4)
+    # hover: at the position target, level at the yaw target, at rest
+    tg = np.zeros((4, n), np.float32)
+    tg[0:3] = np.random.default_rng(1).uniform(-1, 1, (3, n))
+    st = np.zeros((13, n), np.float32)
+    st[0:3] = tg[0:3]
+    st[6] = 1.0
+    mot = np.zeros((8, n), np.float32)
+    mot[0:4] = np.float32(0.75 * 9.81 / 4)
+    fl.set_commands(np.zeros(n, np.uint8), tg)
+    fl.set_state(st, mot)
+    fl.step(100)
+    np.testing.assert_allclose(_np(fl.state()), st, atol=2e-5)
+    fl.close()
+
+
+# -------------------------------------------------------------- obstacles --
+def _teacher_forced_steps(w, seed, n_calls, plain=False):
+    """One step per call; after each call the oracle advances the GPU's
+    pre-call state by one step and the two are compared."""
+    fl, _, inp = _reset_pair(w, seed)
+    world = oracle_world(w)
+    world_free = oracle_world(W.Workload(**{**w.__dict__, "n_obstacles": 0}))
+    n_ambiguous = n_hits = 0
+    for _ in range(n_calls):
+        s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
+        (fl.step_plain if plain else fl.step)(1)
+        s1, col, ids = _np(fl.state()), *[_np(x) for x in fl.events()]
+        # oracle: the same step from the same float32 state
+        pre = oracle_fleet_from(w, inp, s0, m0, e0, seed)
+        pre.boxes = None
+        O.rollout(world_free, pre, 1)
+        amb = np.abs(box_margin(pre.state[0:3], inp.boxes.astype(np.float64))) < 1e-5
+        orc = oracle_fleet_from(w, inp, s0, m0, e0, seed)
+        ocol, _ = O.rollout(world, orc, 1)
+        ok = ~amb
+        n_ambiguous += int(amb.sum())
+        n_hits += int(ocol[ok].sum())
+        np.testing.assert_array_equal(col[ok], ocol[ok])
+        assert set(ids.tolist()) == set(np.flatnonzero(col).tolist())
+        hit = ok & (ocol == 1)
+        # a reset env holds its Philox draw bit for bit
+        np.testing.assert_array_equal(s1[:, hit], orc.state[:, hit].astype(np.float32))
+        free = ok & (ocol == 0)
+        dp, dv, dang, dw = max_state_errors(s1[:, free], orc.state[:, free])
+        scale = 1.0 + np.max(np.abs(orc.state[0:3, free]), axis=0)
+        assert np.all(dp <= 2e-5 * scale), dp.max()
+        assert dang.max() <= 2e-5, dang.max()
+    return n_hits, n_ambiguous
+
+
+def test_obstacle_collisions_and_resets_teacher_forced():
+    w = W.scaled(W.WORKLOADS["obstacles"], 2048)
+    hits, amb = _teacher_forced_steps(w, 21, 25)
+    assert hits > 20           # the workload does collide
+    assert amb <= 5
+
+
+def test_plain_path_matches_oracle_teacher_forced():
+    w = W.scaled(W.WORKLOADS["obstacles"], 1000)
+    hits, amb = _teacher_forced_steps(w, 22, 10, plain=True)
+    assert hits > 5 and amb <= 5
+
+
+def test_plain_and_fused_agree():
+    w = W.scaled(W.WORKLOADS["obstacles"], 3000)
+    inp = W.make_inputs(w, 8)
+    a, b = gpu_fleet(w, inp, 8), gpu_fleet(w, inp, 8)
+    a.reset(None, 8)
+    b.reset(None, 8)
+    a.step(20)
+    b.step_plain(20)
+    sa, sb = _np(a.state()), _np(b.state())
+    ca, ia = a.events()
+    cb, ib = b.events()
+    same = (_np(ca) == _np(cb)) & (_np(a.epoch()) == _np(b.epoch()))
+    assert same.mean() > 0.995          # rare float32 near-ties may differ
+    np.testing.assert_allclose(sa[:, same], sb[:, same], atol=1e-4, rtol=1e-5)
+    a.close()
+    b.close()
+
+
+def test_max_obstacles_and_single_env():
+    for n, n_obs in ((1, 3), (77, 64)):
+        w = W.Workload("maxobs", n, 2, 1, n_obs, n, 0, 0, mode_mix=(W.MODE_POSITION, W.MODE_ATT_THRUST))
+        inp = W.make_inputs(w, 4)
+        fl = gpu_fleet(w, inp, 4)
+        fl.reset(None, 4)
+        s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
+        fl.step(1)
+        orc = oracle_fleet_from(w, inp, s0, m0, e0, 4)
+        ocol, _ = O.rollout(oracle_world(w), orc, 1)
+        col, _ = fl.events()
+        np.testing.assert_array_equal(_np(col), ocol)
+        s1 = _np(fl.state())
+        dp, _, dang, _ = max_state_errors(s1, orc.state)
+        assert dp.max() <= 2e-5 and dang.max() <= 2e-5
+        fl.close()
+
+
+# --------------------------------------------- launch configuration checks --
+def test_one_call_of_many_steps_equals_single_step_calls():
+    w = W.scaled(W.WORKLOADS["obstacles"], 1500)
+    inp = W.make_inputs(w, 31)
+    a, b = gpu_fleet(w, inp, 31), gpu_fleet(w, inp, 31)
+    a.reset(None, 31)
+    b.reset(None, 31)
+    a.step(12)
+    for _ in range(12):
+        b.step(1)
+    same = _np(a.epoch()) == _np(b.epoch())
+    assert same.mean() > 0.995
+    np.testing.assert_allclose(_np(a.state())[:, same], _np(b.state())[:, same], atol=1e-5, rtol=1e-6)
+    a.close()
+    b.close()
+
+
+def test_checkpoint_resume_is_bit_exact():
+    w = W.scaled(W.WORKLOADS["obstacles"], 700)
+    inp = W.make_inputs(w, 12)
+    fl = gpu_fleet(w, inp, 12)
+    fl.reset(None, 12)
+    fl.step(5)
+    ck = (fl.state().clone(), fl.motors().clone(), fl.epoch().clone())
+    fl.step(10)
+    s1, e1 = _np(fl.state()), _np(fl.epoch())
+    fl.set_state(*ck)
+    fl.step(10)
+    np.testing.assert_array_equal(_np(fl.state()), s1)
+    np.testing.assert_array_equal(_np(fl.epoch()), e1)
+    fl.close()
+
+
+def test_host_buffers_round_trip_through_the_abi():
+    w = W.WORKLOADS["parity"]
+    inp = W.make_inputs(w, 2)
+    fl = gpu_fleet(w, inp, 2)
+    fl.reset(None, 2)
+    host = np.empty((13, w.n_envs), np.float32)
+    _abi.ag_get_state(fl.ctx, state=host)
+    fl.synchronize()
+    np.testing.assert_array_equal(host, _np(fl.state()))
+    host[0] += 1.0
+    _abi.ag_set_state(fl.ctx, host)
+    np.testing.assert_array_equal(_np(fl.state()), host)
+    fl.close()
+
+
+def test_invalid_arguments_leave_context_usable():
+    w = W.Workload("inv", 64, 4, 1, 0, 64, 0, 0)
+    inp = W.make_inputs(w, 1)
+    fl = gpu_fleet(w, inp, 1)
+    with pytest.raises(_abi.AgError) as e:
+        _abi.ag_step(fl.ctx, 3)
+    assert e.value.status == _abi.AG_ERR_INVALID
+    with pytest.raises(_abi.AgError):
+        _abi.ag_step(fl.ctx, 0)
+    fl.reset(None, 1)
+    fl.step(2)
+    assert np.isfinite(_np(fl.state())).all()
+    cfg = _abi.ag_config_default()
+    cfg.n_envs = 1 << 20
+    cfg.n_quad = 1 << 20
+    cfg.hbm_budget_bytes = 1 << 20
+    with pytest.raises(_abi.AgError) as e:
+        _abi.ag_create(cfg, torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == _abi.AG_ERR_OOM
+    fl.close()
+
+
+# ----------------------------------------- full size, sampled, bench launch --
+def test_full_size_obstacle_fleet_sampled_against_oracle():
+    """1,048,576 quads, 16 boxes each, one ag_step of 100 steps (the launch the
+    bench times); 384 sampled envs are re-simulated by the oracle step by step
+    from the same initial draw, near-tie envs excluded."""
+    w = W.WORKLOADS["obstacles"]
+    seed = 1
+    inp = W.make_inputs(w, seed)
+    fl = gpu_fleet(w, inp, seed)
+    fl.reset(None, seed)
+    s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
+    fl.step(100)
+    s1 = _np(fl.state())
+    col = _np(fl.events()[0])
+    e1 = _np(fl.epoch()).astype(np.uint32)
+    fl.close()
+    idx = np.sort(np.random.default_rng(0).choice(w.n_envs, 384, replace=False))
+    ws, ins = subset(w, inp, idx)
+    boxes = ins.boxes.astype(np.float64)
+    world, world_free = oracle_world(ws), oracle_world(W.Workload(**{**ws.__dict__, "n_obstacles": 0}))
+    orc = oracle_fleet_from(ws, ins, s0[:, idx], m0[:, idx], e0[idx], seed)
+    ok = np.ones(len(idx), bool)
+    any_hit = np.zeros(len(idx), np.uint8)
+    for _ in range(100):
+        # near-tie check on the pre-collision position of this step
+        pre = oracle_fleet_from(ws, ins, orc.state, orc.motors, orc.epoch, seed)
+        pre.boxes = None
+        O.rollout(world_free, pre, 1)
+        ok &= np.abs(box_margin(pre.state[0:3], boxes)) >= 1e-5
+        c, _ = O.rollout(world, orc, 1, env_ids=idx)    # resets draw with the global env id
+        any_hit |= c
+    assert ok.mean() > 0.97
+    np.testing.assert_array_equal(e1[idx][ok], orc.epoch[ok])
+    np.testing.assert_array_equal(col[idx][ok], any_hit[ok])
+    dp, dv, dang, dw = max_state_errors(s1[:, idx[ok]], orc.state[:, ok])
+    scale = 1.0 + np.max(np.abs(orc.state[0:3, ok]), axis=0)
+    assert np.all(dp <= 1e-4 * scale), dp.max()
+    assert dang.max() <= 1e-3, dang.max()
