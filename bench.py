@@ -1,0 +1,380 @@
+"""Fleet-step throughput bench: vehicle-steps/s of the fused kernel vs the
+unfused one-launch-per-stage path, on 1,048,576 quadrotors with mixed command
+modes, RK4 (4 substeps of 2.5 ms per 10 ms step) and 16 oriented boxes each.
+
+One bench step = one ag_step call that advances the whole fleet by
+STEPS_PER_CALL simulated steps (all stages: controller, allocation, motor
+lag, RK4, renormalisation, sphere-vs-box test, Philox resets, compaction).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--envs N_ENVS] [--steps-per-call C] [--parts fused,plain,e2e,paper]
+
+--envs / --steps-per-call / --parts run a reduced case of the same workload
+(for profiler captures); the default is the full workload and every part.
+
+Under torchrun each rank runs an independent replica on its own GPU (the
+environments are independent; there is no exchange step). Rank 0 prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vehicle-steps/s at 1M quads (fused vs plain step); serving p50/p99 ms"
+UNIT = "vehicle-steps/s"
+STEPS_PER_CALL = 1000          # the obstacle workload's horizon: one call = one full rollout
+WORKLOAD = "obstacles"
+WORKLOAD_TEXT = ("1,048,576 quadrotors; command mode uniform over position / body velocity / attitude+thrust; "
+                 "RK4, 4 substeps x 2.5 ms per 10 ms step; 16 random oriented boxes per env "
+                 "(half-extents U[0.1,1] m, centres U[-5,5]^3 m); r = 0.2 m sphere; collision -> Philox reset; "
+                 f"{STEPS_PER_CALL} steps per call")
+# Algorithmic FP32 operations per vehicle-step of this workload: the FP64
+# oracle run with an operation-counting scalar (adds, muls, divs, square
+# roots, transcendentals; comparisons excluded), averaged over the three
+# command modes, RK4 x 4 substeps + 16 boxes. tests/test_bench_constants.py
+# re-derives it.
+FLOP_PER_VEHICLE_STEP = 4588.0
+# GB300 FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2,070 MHz
+SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+ALU_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+# Algorithmic bytes of one fused launch per vehicle: state in+out (13 f32 x 2),
+# motors in+out (4 x 2), body (4), targets (4), mode (1 B), epoch in+out (2 x 4),
+# boxes (16 x 10 f32), collided flag (1 B), reset-list entry (4 B, upper bound)
+BYTES_PER_VEHICLE_LAUNCH = 4 * (26 + 8 + 4 + 4) + 1 + 8 + 4 * 160 + 1 + 4
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- GPU arm ----
+def make_fleet(w, inp, seed):
+    from paper_2305_16510_gb300.fleet import Fleet
+    fl = Fleet(w.n_envs, substeps_per_step=w.substeps_per_step, integrator=w.integrator, n_obstacles=w.n_obstacles,
+               n_hexa=w.n_hexa, n_octo=w.n_octo, dt=w.dt, motor_tau=w.motor_tau, drag=w.drag, seed=seed)
+    fl.set_body(inp.body)
+    fl.set_commands(inp.modes, inp.targets)
+    if inp.boxes is not None:
+        fl.set_obstacles(inp.boxes)
+    fl.reset(None, seed)
+    return fl
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_calls(fl, call, k: int, world: int):
+    """Times k calls with CUDA events on the fleet's stream; returns
+    (total seconds across ranks, per-call event durations in ms)."""
+    import torch
+    stream = fl.stream
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for a, b in evs:
+        a.record(stream)
+        call()
+        b.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    total_ms = t0.elapsed_time(t1)
+    per = [a.elapsed_time(b) for a, b in evs]
+    return max_over_ranks(total_ms / 1e3, world), per
+
+
+def gpu_arm(args) -> dict | None:
+    import torch
+    from paper_2305_16510_gb300 import build, workloads as W
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    w = W.WORKLOADS[WORKLOAD]
+    if args.envs:
+        w = W.scaled(w, args.envs)
+    C = args.steps_per_call
+    parts = set(args.parts.split(","))
+    seed = 1 + rank
+    inp = W.make_inputs(w, seed)
+    fl = make_fleet(w, inp, seed)
+    n_sub = C * w.substeps_per_step
+
+    # ---- fused (headline)
+    for _ in range(args.warmup):
+        fl.step(C)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        secs, per = time_calls(fl, lambda: fl.step(C), args.steps, world)
+    units = w.n_envs * C * args.steps * world
+    value = units / secs
+    ms_per_step = secs * 1e3 / args.steps
+    launch_ms = float(np.mean(per))
+    achieved_tflops = w.n_envs * C * FLOP_PER_VEHICLE_STEP / (launch_ms * 1e-3) / 1e12
+    _, n_reset = fl.events()
+    out = {}
+
+    # ---- unfused comparison path (same fleet, same call size)
+    if "plain" in parts:
+        k_plain = max(1, min(args.steps, 3))
+        fl.step_plain(C)
+        torch.cuda.synchronize()
+        secs_p, per_p = time_calls(fl, lambda: fl.step_plain(C), k_plain, world)
+        plain_value = w.n_envs * C * k_plain * world / secs_p
+        out["plain"] = {"value": plain_value, "unit": UNIT, "ms_per_step": secs_p * 1e3 / k_plain,
+                        "launches_per_step": C * (3 * w.substeps_per_step + 2) + 1,
+                        "fused_over_plain": value / plain_value}
+
+    # ---- end to end through the C-ABI with host buffers: per call, upload the
+    # commands from pinned host memory, step, read the state back
+    from paper_2305_16510_gb300 import _abi
+    modes_h = torch.from_numpy(inp.modes).pin_memory()
+    targets_h = torch.from_numpy(inp.targets).pin_memory()
+    state_h = torch.empty((13, w.n_envs), dtype=torch.float32).pin_memory()
+
+    def e2e_call():
+        _abi.ag_set_commands(fl.ctx, modes_h, targets_h)
+        _abi.ag_step(fl.ctx, n_sub)
+        _abi.ag_get_state(fl.ctx, state=state_h)
+
+    if "e2e" in parts:
+        e2e_call()
+        fl.synchronize()
+        k_e2e = max(1, min(args.steps, 5))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            e2e_call()
+            fl.synchronize()
+        e2e_secs = max_over_ranks(time.perf_counter() - t0, world)
+        e2e_value = w.n_envs * C * k_e2e * world / e2e_secs
+        h2d = inp.modes.nbytes + inp.targets.nbytes
+        d2h = state_h.numel() * 4
+        assert np.isfinite(state_h.numpy()).all()
+        out["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)}
+
+    # ---- the paper's own throughput shape (context only)
+    if "paper" in parts:
+        ws = W.WORKLOADS["paper_shape"]
+        inp_s = W.make_inputs(ws, seed)
+        fs = make_fleet(ws, inp_s, seed)
+        fs.step(100)
+        torch.cuda.synchronize()
+        secs_s, _ = time_calls(fs, lambda: fs.step(1000), 3, world)
+        out["paper_shape"] = {"value": ws.n_envs * 1000 * 3 * world / secs_s, "unit": UNIT,
+                              "workload": "131,072 quads, attitude/body-velocity commands, no obstacles, SIE, "
+                                          "1 substep",
+                              "paper_value": 3.8e6,
+                              "paper_hardware": "2x RTX 3090 + TR PRO 3975WX (Isaac Gym/PhysX)"}
+        fs.close()
+    fl.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    clocks = clk.summary()
+    wtext = WORKLOAD_TEXT if (w.n_envs == 1 << 20 and C == STEPS_PER_CALL) else \
+        f"reduced case of the same recipe: {w.n_envs} envs, {C} steps per call"
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded numpy commands and boxes; Philox initial states)",
+        "config": {"workload": wtext, "n_envs": w.n_envs, "steps_per_call": C,
+                   "substeps_per_step": w.substeps_per_step, "integrator": "rk4", "boxes_per_env": w.n_obstacles,
+                   "l2": "no flush: inputs exceed L2 (boxes 671 MB + state 55 MB per call)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / ALU_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_fused_step<RK4, quad>", "launch_ms": launch_ms,
+                     "flop_per_vehicle_step": FLOP_PER_VEHICLE_STEP,
+                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",
+                     "algorithmic_bytes_per_launch": BYTES_PER_VEHICLE_LAUNCH * w.n_envs},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "resets_last_call": int(n_reset.numel()),
+    }
+    res.update(out)
+    return res
+
+
+# ------------------------------------------------- CPU oracle (baseline) ----
+def oracle_rate(n_envs: int, n_steps: int, threads: int, seed: int = 1) -> tuple[float, float]:
+    """Times the FP64 oracle on the first n_envs envs of the workload for
+    n_steps steps; returns (vehicle-steps/s, seconds)."""
+    import oracle as O
+    from paper_2305_16510_gb300 import workloads as W
+    w = W.scaled(W.WORKLOADS[WORKLOAD], n_envs)
+    inp = W.make_inputs(w, seed)
+    world = O.World(n_envs=n_envs, substeps_per_step=w.substeps_per_step, integrator=w.integrator,
+                    n_obs=w.n_obstacles, dt=w.dt, motor_tau=w.motor_tau, drag=w.drag)
+    fl = O.make_fleet(world, body=inp.body.astype(np.float64), modes=inp.modes,
+                      targets=inp.targets.astype(np.float64), boxes=inp.boxes.astype(np.float64), seed=seed)
+    O.reset(world, fl, None, seed)
+    t0 = time.perf_counter()
+    O.rollout(world, fl, n_steps, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return n_envs * n_steps / dt, dt
+
+
+def cpu_baseline(target_s: float = 12.0) -> dict:
+    threads = os.cpu_count() or 1
+    n_envs = 8192
+    rate, _ = oracle_rate(n_envs, 20, threads)
+    n_steps = max(2, int(target_s * rate / n_envs))
+    rate, secs = oracle_rate(n_envs, n_steps, threads)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n_envs} envs x {n_steps} steps of the same workload ({secs:.1f} s, FP64, {threads} threads)"}
+
+
+def reference_arm(args) -> dict | None:
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    threads = os.cpu_count() or 1
+    n_envs = 4096
+    rate0, _ = oracle_rate(n_envs, 50, threads)
+    n_steps = max(1, int(4.0 * rate0 / n_envs))       # ~4 s of oracle work per bench step
+    for _ in range(args.warmup):
+        oracle_rate(n_envs, 1, threads)
+    total_units, total_s = 0, 0.0
+    for _ in range(args.steps):
+        r, s = oracle_rate(n_envs, n_steps, threads, seed=1)
+        total_units += n_envs * n_steps
+        total_s += s
+    value = total_units / total_s
+    sample = f"{n_envs} envs x {n_steps} steps per bench step (FP64 oracle, {threads} threads)"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT, "n_envs": 1 << 20, "steps_per_call": STEPS_PER_CALL,
+                       "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--envs", type=int, default=0, help="reduced fleet size (default: the full workload)")
+    ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
+    ap.add_argument("--parts", default="fused,plain,e2e,paper")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        out = reference_arm(args)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = gpu_arm(args)
+    if out is None:
+        return
+    world, _, _ = dist_env()
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
