@@ -175,6 +175,39 @@ ag_status ag_get_motors(ag_ctx* ctx, float* motors, uint32_t* epoch);
  * bit. */
 ag_status ag_set_state(ag_ctx* ctx, const float* state, const float* motors, const uint32_t* epoch);
 
+/* Allocation-free unfused step: the same computation as ag_step_plain,
+ * without a context and without allocating any device memory.
+ *
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc: for example a simulator embedded in a real-time
+ * control loop, where cudaMalloc's implicit device synchronisation and
+ * unbounded latency are forbidden once the loop runs, or a host application
+ * that owns the whole device-memory budget and does not let libraries
+ * allocate. The caller passes every input and output as device pointers in
+ * the layouts of ag_get_state / ag_get_motors / ag_set_commands /
+ * ag_set_obstacles / ag_set_body; state, motors and epoch are updated in
+ * place, collided / reset_ids / *n_reset (n_reset is a device pointer)
+ * describe this call, and `seed` keys the collision resets. The intermediate
+ * wrenches, hit bytes and reset counters live in a static device array sized
+ * for AG_NOALLOC_MAX_ENVS environments (2,424,832 bytes), which every GPU that
+ * loads the library holds until the process exits.
+ *   - n_envs > AG_NOALLOC_MAX_ENVS, an invalid config, an n_substeps that is
+ *     not a positive multiple of substeps_per_step, or a NULL / non-device
+ *     pointer returns AG_ERR_INVALID; a CUDA failure returns AG_ERR_CUDA.
+ *     The reason is written to err (err_len bytes, may be NULL).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture
+ *     begins.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; the call clears what must start at zero itself. Two calls whose
+ *     work overlaps on the GPU (for example on two streams) race on the array
+ *     and give undefined results: order them on one stream. */
+#define AG_NOALLOC_MAX_ENVS 65536
+ag_status ag_step_plain_noalloc(const ag_config* cfg, void* cuda_stream, uint32_t n_substeps, uint64_t seed,
+                                float* state, float* motors, const float* body, const uint8_t* modes,
+                                const float* targets, const float* boxes, uint32_t* epoch, uint8_t* collided,
+                                uint32_t* reset_ids, uint32_t* n_reset, char* err, size_t err_len);
+
 /* Waits for all work queued on the context's stream. */
 ag_status ag_synchronize(ag_ctx* ctx);
 

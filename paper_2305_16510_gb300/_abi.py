@@ -63,6 +63,9 @@ SIGNATURES = {
     "ag_synchronize": (ctypes.c_int, [_vp]),
     "ag_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(ag_config)]),
     "ag_last_error": (ctypes.c_char_p, [_vp]),
+    "ag_step_plain_noalloc": (ctypes.c_int, [ctypes.POINTER(ag_config), _vp, ctypes.c_uint32, ctypes.c_uint64,
+                                             _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_char_p,
+                                             ctypes.c_size_t]),
 }
 
 
@@ -184,3 +187,18 @@ def ag_get_config(ctx: int) -> ag_config:
 def ag_last_error(ctx: int | None) -> str:
     m = lib().ag_last_error(ctx)
     return m.decode() if m else ""
+
+
+AG_NOALLOC_MAX_ENVS = 65536
+
+
+def ag_step_plain_noalloc(cfg: ag_config, stream, n_substeps: int, seed: int, state, motors, body, modes, targets,
+                          boxes, epoch, collided, reset_ids, n_reset) -> None:
+    """Context-free unfused step that allocates no device memory (all buffers
+    are the caller's device buffers; see include/ag.h)."""
+    err = ctypes.create_string_buffer(256)
+    rc = lib().ag_step_plain_noalloc(ctypes.byref(cfg), stream, int(n_substeps), int(seed) & (2**64 - 1),
+                                     ptr(state), ptr(motors), ptr(body), ptr(modes), ptr(targets), ptr(boxes),
+                                     ptr(epoch), ptr(collided), ptr(reset_ids), ptr(n_reset), err, len(err))
+    if rc != AG_OK:
+        raise AgError(rc, "ag_step_plain_noalloc", err.value.decode())
