@@ -23,6 +23,7 @@ struct ag_ctx {
   int device;
   agk::FleetBuffers fb;
   uint8_t* mask_dev;         // [n] staging for ag_reset masks
+  uint32_t* order_scratch;   // [24] key counts and cursors of the grouping permutation
   uint64_t seed;             // Philox key of collision resets
   bool failed;
   std::string err;
@@ -124,7 +125,7 @@ const char* validate(const ag_config* c) {
 
 size_t buffer_bytes(const ag_config* c) {
   size_t n = c->n_envs;
-  size_t per = sizeof(float) * (13 + 8 + 4 + 4 + 4 + 4) + sizeof(uint32_t) * 3 + 3 /* modes, collided, hits */ + 1;
+  size_t per = sizeof(float) * (13 + 8 + 4 + 4 + 4 + 4) + sizeof(uint32_t) * 4 + 3 /* modes, collided, hits */ + 1;
   return n * per + (size_t)c->n_obstacles * 10 * n * sizeof(float) + sizeof(uint32_t);
 }
 
@@ -160,7 +161,7 @@ ag_status enter(ag_ctx* ctx) {
 void free_all(ag_ctx* ctx) {
   agk::FleetBuffers& f = ctx->fb;
   void* ptrs[] = {f.state, f.motors, f.body, f.modes, f.targets, f.boxes, f.epoch, f.collided, f.reset_ids,
-                  f.n_reset, f.cmd, f.wrench, f.resets, f.hits, ctx->mask_dev};
+                  f.n_reset, f.cmd, f.wrench, f.resets, f.hits, f.order, ctx->mask_dev, ctx->order_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -218,6 +219,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   ctx->seed = cfg->seed;
   std::memset(&ctx->fb, 0, sizeof(ctx->fb));
   ctx->mask_dev = nullptr;
+  ctx->order_scratch = nullptr;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     g_create_error = "no CUDA device";
     delete ctx;
@@ -244,6 +246,8 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = alloc(ctx, &f.resets, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.hits, n);
   if (e == cudaSuccess) e = alloc(ctx, &ctx->mask_dev, n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.order, n);
+  if (e == cudaSuccess) e = alloc(ctx, &ctx->order_scratch, 24);
   if (e != cudaSuccess) {
     g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
     cudaGetLastError();
@@ -266,6 +270,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(f.epoch, 0, n * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.collided, 0, n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.n_reset, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = agk::launch_build_order(f, ctx->order_scratch, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     g_create_error = std::string("initialisation failed: ") + cudaGetErrorString(e);
@@ -292,6 +297,8 @@ ag_status ag_set_commands(ag_ctx* ctx, const uint8_t* modes, const float* target
   const size_t n = ctx->cfg.n_envs;
   if (modes) {
     s = check_cuda(ctx, cudaMemcpyAsync(ctx->fb.modes, modes, n, cudaMemcpyDefault, ctx->stream), "copy modes");
+    if (s != AG_OK) return s;
+    s = check_cuda(ctx, agk::launch_build_order(ctx->fb, ctx->order_scratch, ctx->stream), "build order");
     if (s != AG_OK) return s;
   }
   if (targets)

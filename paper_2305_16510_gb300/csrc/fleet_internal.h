@@ -25,6 +25,7 @@ struct FleetBuffers {
   float* wrench;       // [4][n]  realised wrench
   uint32_t* resets;    // [n]     resets of this call per env
   uint8_t* hits;       // [n]     collision of the current step
+  uint32_t* order;     // [n]     thread slot -> env, grouped by rotor type and mode (NULL = identity)
   uint32_t n, n_quad, n_hexa, n_octo, n_obs;
 };
 
@@ -36,8 +37,19 @@ cudaError_t launch_reset(const FleetBuffers& fb, const uint8_t* mask, uint32_t s
 cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,
                               int substeps, cudaStream_t st);
 
+// Builds fb.order from the current modes and rotor types (3 small launches;
+// scratch24 is 24 words of device scratch).
+cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch24, cudaStream_t st);
+
 // Threads per block of the fused kernel for a given obstacle count (the
 // per-block shared-memory staging grows with it).
 int fused_block_size(int n_obs);
+
+// Launch choices of the fused kernel. Defaults: boxes staged in shared
+// memory, mode-grouped order, fused_block_size(). Tuning overrides (read at
+// each launch): AG_FUSED_STAGING=l1 reads the boxes from global memory,
+// AG_FUSED_ORDER=identity runs env i in slot i, AG_FUSED_BLOCK=32..128.
+struct FusedTuning { bool smem, sorted; int block; };
+FusedTuning fused_tuning_from_env(int n_obs);
 
 }  // namespace agk

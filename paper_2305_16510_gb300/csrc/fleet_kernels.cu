@@ -11,6 +11,8 @@
 // resets happen in registers; the reset list is built with one
 // __ballot_sync + __popc prefix and one atomicAdd per warp.
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "fleet_internal.h"
@@ -89,9 +91,12 @@ __device__ __forceinline__ void append_compact(bool pred, uint32_t env, uint32_t
 }
 
 // The per-vehicle body of the fused kernel, specialised on the rotor count.
+// Box field f of box k sits at bx[(k * 10 + f) * stride]: the thread's
+// shared-memory column (stride = block size) or its global column (stride = n).
 template <int NROT, int INTEG>
 __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, int n_steps,
-                                         int substeps, const float* sm, int B, uint32_t& resets, bool& any_hit) {
+                                         int substeps, const float* __restrict__ bx0, int stride, uint32_t& resets,
+                                         bool& any_hit) {
   const uint32_t n = fb.n;
   VState s = load_state(fb.state, n, env);
   normalize(s.q);
@@ -111,9 +116,10 @@ __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParam
       bool hit = false;
 #pragma unroll 4
       for (int k = 0; k < n_obs; ++k) {
-        const float* bx = sm + k * 10 * B;
-        hit |= sphere_hits_box(s.p, P.r2, V3{bx[0], bx[B], bx[2 * B]}, V3{bx[3 * B], bx[4 * B], bx[5 * B]},
-                               Q4{bx[6 * B], bx[7 * B], bx[8 * B], bx[9 * B]});
+        const float* bx = bx0 + (size_t)k * 10 * stride;
+        hit |= sphere_hits_box(s.p, P.r2, V3{bx[0], bx[stride], bx[2 * stride]},
+                               V3{bx[3 * stride], bx[4 * stride], bx[5 * stride]},
+                               Q4{bx[6 * stride], bx[7 * stride], bx[8 * stride], bx[9 * stride]});
       }
       if (hit) {
         any_hit = true;
@@ -129,33 +135,94 @@ __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParam
   fb.epoch[env] = epoch;
 }
 
-template <int INTEG, bool QUAD_ONLY>
+// Thread slot i of the launch simulates environment order[i] (a permutation
+// that groups environments of equal rotor count and command mode, so the
+// mode branches of the controller are warp-uniform), or environment i when
+// order is NULL. SMEM selects where the boxes are read during the steps:
+// staged once per launch in shared memory, or straight from global memory
+// through L1/L2.
+template <int INTEG, bool QUAD_ONLY, bool SMEM>
 __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
   extern __shared__ float sm_boxes[];  // [n_obs][10][blockDim.x]
   const int B = blockDim.x;
-  const uint32_t env = blockIdx.x * B + threadIdx.x;
-  const bool active = env < fb.n;
-  // Each thread stages its own environment's boxes (coalesced rows of the
-  // [box][field][env] global layout); it alone reads them back, so no
-  // barrier is needed.
-  float* my = sm_boxes + threadIdx.x;
-  if (active) {
-    const int rows = (int)fb.n_obs * 10;
-    for (int r = 0; r < rows; ++r) my[r * B] = fb.boxes[(size_t)r * fb.n + env];
+  const uint32_t slot = blockIdx.x * B + threadIdx.x;
+  const bool active = slot < fb.n;
+  const uint32_t env = active ? (fb.order ? fb.order[slot] : slot) : slot;
+  const float* bx0;
+  int stride;
+  if (SMEM) {
+    // Each thread stages its own environment's boxes; it alone reads them
+    // back, so no barrier is needed.
+    float* my = sm_boxes + threadIdx.x;
+    if (active) {
+      const int rows = (int)fb.n_obs * 10;
+      for (int r = 0; r < rows; ++r) my[r * B] = fb.boxes[(size_t)r * fb.n + env];
+    }
+    bx0 = my;
+    stride = B;
+  } else {
+    bx0 = fb.boxes + env;
+    stride = (int)fb.n;
   }
   uint32_t resets = 0;
   bool any_hit = false;
   if (active) {
     const int nrot = QUAD_ONLY ? 4 : rotor_count(fb, env);
     if (nrot == 4)
-      simulate<4, INTEG>(fb, P, env, n_steps, substeps, my, B, resets, any_hit);
+      simulate<4, INTEG>(fb, P, env, n_steps, substeps, bx0, stride, resets, any_hit);
     else if (nrot == 6)
-      simulate<6, INTEG>(fb, P, env, n_steps, substeps, my, B, resets, any_hit);
+      simulate<6, INTEG>(fb, P, env, n_steps, substeps, bx0, stride, resets, any_hit);
     else
-      simulate<8, INTEG>(fb, P, env, n_steps, substeps, my, B, resets, any_hit);
+      simulate<8, INTEG>(fb, P, env, n_steps, substeps, bx0, stride, resets, any_hit);
     fb.collided[env] = any_hit ? 1 : 0;
   }
   append_compact(resets > 0u, env, fb.reset_ids, fb.n_reset);
+}
+
+// Grouping permutation: key = rotor-type index * 4 + mode (12 keys). Pass 1
+// counts keys, pass 2 turns the counts into start offsets, pass 3 scatters
+// every env to its key's range (order inside a range is arbitrary; each env
+// appears exactly once).
+__device__ __forceinline__ uint32_t order_key(const FleetBuffers& fb, uint32_t i) {
+  const int nrot = rotor_count(fb, i);
+  const uint32_t m = fb.modes[i] > 3 ? 3u : fb.modes[i];
+  return (uint32_t)(nrot == 4 ? 0 : (nrot == 6 ? 1 : 2)) * 4u + m;
+}
+
+__global__ void __launch_bounds__(256) k_order_count(FleetBuffers fb, uint32_t* counts) {
+  __shared__ uint32_t h[12];
+  if (threadIdx.x < 12) h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < fb.n) atomicAdd(&h[order_key(fb, i)], 1u);
+  __syncthreads();
+  if (threadIdx.x < 12 && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_order_offsets(uint32_t* counts, uint32_t* cursor) {
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < 12; ++k) {
+      cursor[k] = run;
+      run += counts[k];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_order_scatter(FleetBuffers fb, uint32_t* cursor) {
+  __shared__ uint32_t h[12], base[12];
+  if (threadIdx.x < 12) h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t key = 0, rank = 0;
+  if (i < fb.n) {
+    key = order_key(fb, i);
+    rank = atomicAdd(&h[key], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 12 && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], h[threadIdx.x]);
+  __syncthreads();
+  if (i < fb.n) fb.order[base[key] + rank] = i;
 }
 
 // ag_reset: resample masked environments, clear collided flags, list them.
@@ -267,20 +334,27 @@ __global__ void __launch_bounds__(256) k_plain_compact(FleetBuffers fb) {
   append_compact(pred, i, fb.reset_ids, fb.n_reset);
 }
 
-template <int INTEG, bool QUAD_ONLY>
-cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, cudaStream_t st) {
-  const int B = fused_block_size((int)fb.n_obs);
-  const size_t smem = (size_t)fb.n_obs * 10 * B * sizeof(float);
+template <int INTEG, bool QUAD_ONLY, bool SMEM>
+cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
+                           cudaStream_t st) {
+  const size_t smem = SMEM ? (size_t)fb.n_obs * 10 * B * sizeof(float) : 0;
   static bool attr_set = false;  // per instantiation; raise the dynamic shared-memory cap once
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_step<INTEG, QUAD_ONLY>,
+  if (SMEM && !attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_fused_step<INTEG, QUAD_ONLY, SMEM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const unsigned grid = (fb.n + B - 1) / B;
-  k_fused_step<INTEG, QUAD_ONLY><<<grid, B, smem, st>>>(fb, P, n_steps, substeps);
+  k_fused_step<INTEG, QUAD_ONLY, SMEM><<<grid, B, smem, st>>>(fb, P, n_steps, substeps);
   return cudaGetLastError();
+}
+
+template <int INTEG, bool QUAD_ONLY>
+cudaError_t launch_fused_s(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, bool smem, int B,
+                           cudaStream_t st) {
+  return smem ? launch_fused_t<INTEG, QUAD_ONLY, true>(fb, P, n_steps, substeps, B, st)
+              : launch_fused_t<INTEG, QUAD_ONLY, false>(fb, P, n_steps, substeps, B, st);
 }
 
 }  // namespace
@@ -296,16 +370,44 @@ int fused_block_size(int n_obs) {
   return b;
 }
 
-cudaError_t launch_fused_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,
+FusedTuning fused_tuning_from_env(int n_obs) {
+  FusedTuning t;
+  t.smem = true;
+  t.sorted = true;
+  t.block = fused_block_size(n_obs);
+  if (const char* v = std::getenv("AG_FUSED_STAGING")) t.smem = std::strcmp(v, "l1") != 0;
+  if (const char* v = std::getenv("AG_FUSED_ORDER")) t.sorted = std::strcmp(v, "identity") != 0;
+  if (const char* v = std::getenv("AG_FUSED_BLOCK")) {
+    int b = std::atoi(v);
+    if (b >= 32 && b <= 128 && b % 32 == 0 && (size_t)n_obs * 40 * b <= 200 * 1024) t.block = b;
+  }
+  return t;
+}
+
+cudaError_t launch_fused_step(const FleetBuffers& fb_in, const StepParams& P, int integrator, int n_steps,
                               int substeps, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(fb.n_reset, 0, sizeof(uint32_t), st);
+  cudaError_t e = cudaMemsetAsync(fb_in.n_reset, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
+  const FusedTuning t = fused_tuning_from_env((int)fb_in.n_obs);
+  FleetBuffers fb = fb_in;
+  if (!t.sorted) fb.order = nullptr;
+  const bool smem = t.smem && fb.n_obs > 0;
   const bool quad_only = fb.n_quad == fb.n;
   if (integrator == kIntegRK4)
-    return quad_only ? launch_fused_t<kIntegRK4, true>(fb, P, n_steps, substeps, st)
-                     : launch_fused_t<kIntegRK4, false>(fb, P, n_steps, substeps, st);
-  return quad_only ? launch_fused_t<kIntegSIE, true>(fb, P, n_steps, substeps, st)
-                   : launch_fused_t<kIntegSIE, false>(fb, P, n_steps, substeps, st);
+    return quad_only ? launch_fused_s<kIntegRK4, true>(fb, P, n_steps, substeps, smem, t.block, st)
+                     : launch_fused_s<kIntegRK4, false>(fb, P, n_steps, substeps, smem, t.block, st);
+  return quad_only ? launch_fused_s<kIntegSIE, true>(fb, P, n_steps, substeps, smem, t.block, st)
+                   : launch_fused_s<kIntegSIE, false>(fb, P, n_steps, substeps, smem, t.block, st);
+}
+
+cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch24, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(scratch24, 0, 24 * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (fb.n + 255) / 256;
+  k_order_count<<<grid, 256, 0, st>>>(fb, scratch24);
+  k_order_offsets<<<1, 32, 0, st>>>(scratch24, scratch24 + 12);
+  k_order_scatter<<<grid, 256, 0, st>>>(fb, scratch24 + 12);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reset(const FleetBuffers& fb, const uint8_t* mask, uint32_t seed_lo, uint32_t seed_hi,
