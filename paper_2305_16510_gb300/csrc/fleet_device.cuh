@@ -17,8 +17,15 @@
 //     sin(theta_d) = a_x / sqrt(a_x^2 + a_z^2);
 //   * R_z(psi) R_y(theta_d) R_x(phi_d) is written out in those cosines and
 //     sines, and trig of commanded angles is taken once per launch;
-//   * e_R = 1/2 vee(E - E^T) and e_Omega = Omega - E^T Omega_d share one
-//     product E = R_d^T R;
+//   * e_R = 1/2 vee(E - E^T) needs only the off-diagonal entries of
+//     E = R_d^T R;
+//   * Eq. 2 is Omega_d = R_d^T (0, 0, psi_dot_d) (the body rate of a pure
+//     world-z yaw rate seen from R_d = R_z R_y R_x), so R_d Omega_d =
+//     psi_dot_d e_3 and Eq. 4 becomes e_Omega = Omega - psi_dot_d R^T e_3,
+//     i.e. the third row of R times the commanded yaw rate (zero in position
+//     mode, where Omega_d = 0);
+//   * the first derivative evaluation of a substep reuses the controller's
+//     R e_3 (q is unit there: it was renormalised after the last substep);
 //   * the body z axis of a non-unit quaternion (RK4 stages) is the
 //     homogeneous quaternion form divided by |q|^2, which equals the axis of
 //     q / |q| exactly.
@@ -98,14 +105,16 @@ __device__ __forceinline__ Command prepare_command(int mode, float t0, float t1,
   return cm;
 }
 
-// Geometric controller of one vehicle -> commanded (f, M).
+// Geometric controller of one vehicle -> commanded (f, M). Also returns the
+// body z axis R e_3 of the (unit) attitude, which the integrator reuses.
 __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm, const Body& b,
-                                              const StepParams& P) {
-  if (cm.mode == kModeWrench) return {cm.c[0], cm.c[1], cm.c[2], cm.c[3]};
+                                              const StepParams& P, V3& b3) {
   float R[3][3];
   rotation(s.q, R);
+  b3 = {R[0][2], R[1][2], R[2][2]};
+  if (cm.mode == kModeWrench) return {cm.c[0], cm.c[1], cm.c[2], cm.c[3]};
   float Rd[3][3];
-  V3 Wd;
+  float rate;  // commanded yaw rate: R_d Omega_d = rate e_3
   float f;
   if (cm.mode == kModePosition) {
     // Lee 2011: a = -k_x e_x - k_v e_v + g e3, b3d = a/|a|, b2d ~ b3d x b1c, b1d = b2d x b3d
@@ -128,7 +137,7 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
     Rd[0][0] = b1d.x; Rd[0][1] = b2d.x; Rd[0][2] = b3d.x;
     Rd[1][0] = b1d.y; Rd[1][1] = b2d.y; Rd[1][2] = b3d.y;
     Rd[2][0] = b1d.z; Rd[2][1] = b2d.z; Rd[2][2] = b3d.z;
-    Wd = {0.f, 0.f, 0.f};
+    rate = 0.f;
   } else {
     // current yaw of the body frame: (cos psi, sin psi) = (R00, R10) / rho
     float rho2 = R[0][0] * R[0][0] + R[1][0] * R[1][0];
@@ -138,7 +147,7 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
       cpsi = R[0][0] * ir;
       spsi = R[1][0] * ir;
     }
-    float cphi, sphi, cth, sth, rate;
+    float cphi, sphi, cth, sth;
     if (cm.mode == kModeBodyVel) {
       // Eq. 6 in the vehicle frame, Eq. 7 thrust, Eqs. 8-9 tilt (algebraic)
       V3 vV = {cpsi * s.v.x + spsi * s.v.y, -spsi * s.v.x + cpsi * s.v.y, s.v.z};
@@ -169,19 +178,12 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
     Rd[0][0] = cpsi * cth;  Rd[0][1] = cpsi * b01 - spsi * cphi; Rd[0][2] = cpsi * b02 + spsi * sphi;
     Rd[1][0] = spsi * cth;  Rd[1][1] = spsi * b01 + cpsi * cphi; Rd[1][2] = spsi * b02 - cpsi * sphi;
     Rd[2][0] = -sth;        Rd[2][1] = b21;                      Rd[2][2] = b22;
-    // Eq. 2
-    Wd = {-sth * rate, b21 * rate, b22 * rate};
   }
-  // Eqs. 3-5 with E = R_d^T R
-  float E[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) E[i][j] = Rd[0][i] * R[0][j] + Rd[1][i] * R[1][j] + Rd[2][i] * R[2][j];
-  V3 eR = {0.5f * (E[2][1] - E[1][2]), 0.5f * (E[0][2] - E[2][0]), 0.5f * (E[1][0] - E[0][1])};
-  V3 eW = {s.w.x - (E[0][0] * Wd.x + E[1][0] * Wd.y + E[2][0] * Wd.z),
-           s.w.y - (E[0][1] * Wd.x + E[1][1] * Wd.y + E[2][1] * Wd.z),
-           s.w.z - (E[0][2] * Wd.x + E[1][2] * Wd.y + E[2][2] * Wd.z)};
+  // Eq. 3: e_R = 1/2 vee(E - E^T), E = R_d^T R (off-diagonal entries only)
+  auto Eij = [&](int i, int j) { return Rd[0][i] * R[0][j] + Rd[1][i] * R[1][j] + Rd[2][i] * R[2][j]; };
+  V3 eR = {0.5f * (Eij(2, 1) - Eij(1, 2)), 0.5f * (Eij(0, 2) - Eij(2, 0)), 0.5f * (Eij(1, 0) - Eij(0, 1))};
+  // Eq. 4 with R^T R_d Omega_d = rate R^T e_3
+  V3 eW = {s.w.x - rate * R[2][0], s.w.y - rate * R[2][1], s.w.z - rate * R[2][2]};
   V3 JW = {b.jx * s.w.x, b.jy * s.w.y, b.jz * s.w.z};
   V3 gyro = cross(s.w, JW);
   return {f, -P.kR[0] * eR.x - P.kW[0] * eW.x + gyro.x, -P.kR[1] * eR.y - P.kW[1] * eW.y + gyro.y,
@@ -207,25 +209,40 @@ __device__ __forceinline__ Wrench4 allocate(const Wrench4& cmd, float (&u)[NROT]
   return W;
 }
 
-// Rigid-body derivatives under a fixed wrench.
+// Rigid-body derivatives under a fixed wrench, given the body z axis b3 of
+// the attitude (R(q / |q|) e_3). DRAG = false drops the (zero) drag terms.
 struct Deriv { V3 dp, dv; Q4 dq; V3 dw; };
 
-__device__ __forceinline__ Deriv derivatives(const VState& s, const Wrench4& W, const Body& b, float drag) {
+template <bool DRAG>
+__device__ __forceinline__ Deriv derivatives_b3(const VState& s, V3 b3, const Wrench4& W, const Body& b, float drag) {
   const Q4& q = s.q;
-  float n2 = q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z;
-  float fs = W.f * b.inv_m * __fdividef(1.f, n2);
+  const float fm = W.f * b.inv_m;
   Deriv d;
   d.dp = s.v;
-  float dm = drag * b.inv_m;
-  d.dv = {fs * 2.f * (q.x * q.z + q.w * q.y) - dm * s.v.x,
-          fs * 2.f * (q.y * q.z - q.w * q.x) - dm * s.v.y,
-          fs * (q.w * q.w - q.x * q.x - q.y * q.y + q.z * q.z) - dm * s.v.z - kGravity};
+  d.dv = {fm * b3.x, fm * b3.y, fm * b3.z - kGravity};
+  if (DRAG) {
+    const float dm = drag * b.inv_m;
+    d.dv = {d.dv.x - dm * s.v.x, d.dv.y - dm * s.v.y, d.dv.z - dm * s.v.z};
+  }
   d.dq = {-0.5f * (q.x * s.w.x + q.y * s.w.y + q.z * s.w.z), 0.5f * (q.w * s.w.x + q.y * s.w.z - q.z * s.w.y),
           0.5f * (q.w * s.w.y - q.x * s.w.z + q.z * s.w.x), 0.5f * (q.w * s.w.z + q.x * s.w.y - q.y * s.w.x)};
   V3 JW = {b.jx * s.w.x, b.jy * s.w.y, b.jz * s.w.z};
   V3 g = cross(s.w, JW);
   d.dw = {b.ijx * (W.mx - g.x), b.ijy * (W.my - g.y), b.ijz * (W.mz - g.z)};
   return d;
+}
+
+// Body z axis of a possibly non-unit quaternion: the homogeneous form over |q|^2.
+__device__ __forceinline__ V3 body_z(const Q4& q) {
+  float n2 = q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z;
+  float inv = __fdividef(1.f, n2);
+  return {inv * 2.f * (q.x * q.z + q.w * q.y), inv * 2.f * (q.y * q.z - q.w * q.x),
+          inv * (q.w * q.w - q.x * q.x - q.y * q.y + q.z * q.z)};
+}
+
+template <bool DRAG>
+__device__ __forceinline__ Deriv derivatives(const VState& s, const Wrench4& W, const Body& b, float drag) {
+  return derivatives_b3<DRAG>(s, body_z(s.q), W, b, drag);
 }
 
 __device__ __forceinline__ void normalize(Q4& q) {
@@ -243,9 +260,10 @@ __device__ __forceinline__ VState advance(const VState& s, float h, const Deriv&
 }
 
 // Semi-implicit Euler: v, Omega from the derivatives; p, q from the updated
-// velocities; renormalise q.
-__device__ __forceinline__ void step_sie(VState& s, const Wrench4& W, const Body& b, float drag, float h) {
-  Deriv d = derivatives(s, W, b, drag);
+// velocities; renormalise q. b3 is R e_3 of the (unit) start attitude.
+template <bool DRAG>
+__device__ __forceinline__ void step_sie(VState& s, V3 b3, const Wrench4& W, const Body& b, float drag, float h) {
+  Deriv d = derivatives_b3<DRAG>(s, b3, W, b, drag);
   s.v = s.v + h * d.dv;
   s.w = s.w + h * d.dw;
   s.p = s.p + h * s.v;
@@ -256,44 +274,47 @@ __device__ __forceinline__ void step_sie(VState& s, const Wrench4& W, const Body
   normalize(s.q);
 }
 
-// Classic RK4 with the wrench held over the stages; renormalise q.
-__device__ __forceinline__ void step_rk4(VState& s, const Wrench4& W, const Body& b, float drag, float h) {
+// Classic RK4 with the wrench held over the stages; renormalise q. The
+// first stage uses the start attitude's b3 (unit q).
+template <bool DRAG>
+__device__ __forceinline__ void step_rk4(VState& s, V3 b3, const Wrench4& W, const Body& b, float drag, float h) {
   float hh = 0.5f * h;
-  Deriv k = derivatives(s, W, b, drag);
+  Deriv k = derivatives_b3<DRAG>(s, b3, W, b, drag);
   Deriv acc = k;
-  k = derivatives(advance(s, hh, k), W, b, drag);
+  k = derivatives<DRAG>(advance(s, hh, k), W, b, drag);
   acc.dp = acc.dp + 2.f * k.dp; acc.dv = acc.dv + 2.f * k.dv; acc.dw = acc.dw + 2.f * k.dw;
   acc.dq = {acc.dq.w + 2.f * k.dq.w, acc.dq.x + 2.f * k.dq.x, acc.dq.y + 2.f * k.dq.y, acc.dq.z + 2.f * k.dq.z};
-  k = derivatives(advance(s, hh, k), W, b, drag);
+  k = derivatives<DRAG>(advance(s, hh, k), W, b, drag);
   acc.dp = acc.dp + 2.f * k.dp; acc.dv = acc.dv + 2.f * k.dv; acc.dw = acc.dw + 2.f * k.dw;
   acc.dq = {acc.dq.w + 2.f * k.dq.w, acc.dq.x + 2.f * k.dq.x, acc.dq.y + 2.f * k.dq.y, acc.dq.z + 2.f * k.dq.z};
-  k = derivatives(advance(s, h, k), W, b, drag);
+  k = derivatives<DRAG>(advance(s, h, k), W, b, drag);
   acc.dp = acc.dp + k.dp; acc.dv = acc.dv + k.dv; acc.dw = acc.dw + k.dw;
   acc.dq = {acc.dq.w + k.dq.w, acc.dq.x + k.dq.x, acc.dq.y + k.dq.y, acc.dq.z + k.dq.z};
   s = advance(s, h * (1.f / 6.f), acc);
   normalize(s.q);
 }
 
-template <int INTEG>
-__device__ __forceinline__ void integrate(VState& s, const Wrench4& W, const Body& b, const StepParams& P) {
+template <int INTEG, bool DRAG>
+__device__ __forceinline__ void integrate(VState& s, V3 b3, const Wrench4& W, const Body& b, const StepParams& P) {
   if (INTEG == kIntegRK4)
-    step_rk4(s, W, b, P.drag, P.h);
+    step_rk4<DRAG>(s, b3, W, b, P.drag, P.h);
   else
-    step_sie(s, W, b, P.drag, P.h);
+    step_sie<DRAG>(s, b3, W, b, P.drag, P.h);
 }
 
 // Sphere of squared radius r2 at p versus the box (centre c, half-extents
 // hx, hy, hz, unit quaternion qb): p is taken into the box frame by the
-// conjugate rotation v - w t + u x t with t = 2 u x v, clamped to the box,
-// and the squared excess compared with r2 (touching counts).
+// conjugate rotation v - w t + u x t with t = 2 u x v; the distance to the
+// box is the norm of max(|d| - h, 0) per axis (equal to |d - clamp(d, -h, h)|);
+// touching counts.
 __device__ __forceinline__ bool sphere_hits_box(V3 p, float r2, V3 c, V3 hb, Q4 qb) {
   V3 v = p - c;
   V3 u = {qb.x, qb.y, qb.z};
   V3 t = 2.f * cross(u, v);
   V3 d = v - qb.w * t + cross(u, t);
-  float ex = d.x - fminf(fmaxf(d.x, -hb.x), hb.x);
-  float ey = d.y - fminf(fmaxf(d.y, -hb.y), hb.y);
-  float ez = d.z - fminf(fmaxf(d.z, -hb.z), hb.z);
+  float ex = fmaxf(fabsf(d.x) - hb.x, 0.f);
+  float ey = fmaxf(fabsf(d.y) - hb.y, 0.f);
+  float ez = fmaxf(fabsf(d.z) - hb.z, 0.f);
   return !(r2 < ex * ex + ey * ey + ez * ez);
 }
 

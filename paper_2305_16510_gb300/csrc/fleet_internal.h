@@ -45,11 +45,11 @@ cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch24, cuda
 // per-block shared-memory staging grows with it).
 int fused_block_size(int n_obs);
 
-// Launch choices of the fused kernel. Defaults: boxes staged in shared
-// memory, mode-grouped order, fused_block_size(). Tuning overrides (read at
-// each launch): AG_FUSED_STAGING=l1 reads the boxes from global memory,
-// AG_FUSED_ORDER=identity runs env i in slot i, AG_FUSED_BLOCK=32..128.
-struct FusedTuning { bool smem, sorted; int block; };
+// Launch choices of the fused kernel. Defaults: mode-grouped order and
+// fused_block_size(). Tuning overrides (read at each launch):
+// AG_FUSED_ORDER=identity runs env i in slot i (the ungrouped ablation),
+// AG_FUSED_BLOCK=32..128 (multiple of 32) sets the block size.
+struct FusedTuning { bool sorted; int block; };
 FusedTuning fused_tuning_from_env(int n_obs);
 
 }  // namespace agk

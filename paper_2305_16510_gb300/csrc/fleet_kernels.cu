@@ -91,11 +91,11 @@ __device__ __forceinline__ void append_compact(bool pred, uint32_t env, uint32_t
 }
 
 // The per-vehicle body of the fused kernel, specialised on the rotor count.
-// Box field f of box k sits at bx[(k * 10 + f) * stride]: the thread's
-// shared-memory column (stride = block size) or its global column (stride = n).
-template <int NROT, int INTEG>
+// sm points at this thread's staged boxes: box k occupies the 10 floats at
+// sm + k * box_stride (c, h, q), read as five 8-byte loads.
+template <int NROT, int INTEG, bool DRAG>
 __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, int n_steps,
-                                         int substeps, const float* __restrict__ bx0, int stride, uint32_t& resets,
+                                         int substeps, const float* sm, int box_stride, uint32_t& resets,
                                          bool& any_hit) {
   const uint32_t n = fb.n;
   VState s = load_state(fb.state, n, env);
@@ -109,17 +109,17 @@ __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParam
   const int n_obs = (int)fb.n_obs;
   for (int step = 0; step < n_steps; ++step) {
     for (int ss = 0; ss < substeps; ++ss) {
-      Wrench4 W = allocate<NROT>(controller(s, cm, b, P), u, P);
-      integrate<INTEG>(s, W, b, P);
+      V3 b3;
+      Wrench4 W = allocate<NROT>(controller(s, cm, b, P, b3), u, P);
+      integrate<INTEG, DRAG>(s, b3, W, b, P);
     }
     if (n_obs > 0) {
       bool hit = false;
 #pragma unroll 4
       for (int k = 0; k < n_obs; ++k) {
-        const float* bx = bx0 + (size_t)k * 10 * stride;
-        hit |= sphere_hits_box(s.p, P.r2, V3{bx[0], bx[stride], bx[2 * stride]},
-                               V3{bx[3 * stride], bx[4 * stride], bx[5 * stride]},
-                               Q4{bx[6 * stride], bx[7 * stride], bx[8 * stride], bx[9 * stride]});
+        const float2* bx = reinterpret_cast<const float2*>(sm + k * box_stride);
+        const float2 a0 = bx[0], a1 = bx[1], a2 = bx[2], a3 = bx[3], a4 = bx[4];
+        hit |= sphere_hits_box(s.p, P.r2, V3{a0.x, a0.y, a1.x}, V3{a1.y, a2.x, a2.y}, Q4{a3.x, a3.y, a4.x, a4.y});
       }
       if (hit) {
         any_hit = true;
@@ -138,42 +138,33 @@ __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParam
 // Thread slot i of the launch simulates environment order[i] (a permutation
 // that groups environments of equal rotor count and command mode, so the
 // mode branches of the controller are warp-uniform), or environment i when
-// order is NULL. SMEM selects where the boxes are read during the steps:
-// staged once per launch in shared memory, or straight from global memory
-// through L1/L2.
-template <int INTEG, bool QUAD_ONLY, bool SMEM>
+// order is NULL. Each thread stages its environment's boxes once per launch
+// in shared memory as [box][thread][10 floats]: 40-byte records, so the
+// five 8-byte loads of a warp hit 32 distinct bank pairs per phase. A thread
+// reads only what it wrote, so no barrier is needed.
+template <int INTEG, bool QUAD_ONLY, bool DRAG>
 __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
-  extern __shared__ float sm_boxes[];  // [n_obs][10][blockDim.x]
+  extern __shared__ float sm_boxes[];  // [n_obs][blockDim.x][10]
   const int B = blockDim.x;
   const uint32_t slot = blockIdx.x * B + threadIdx.x;
   const bool active = slot < fb.n;
   const uint32_t env = active ? (fb.order ? fb.order[slot] : slot) : slot;
-  const float* bx0;
-  int stride;
-  if (SMEM) {
-    // Each thread stages its own environment's boxes; it alone reads them
-    // back, so no barrier is needed.
-    float* my = sm_boxes + threadIdx.x;
-    if (active) {
-      const int rows = (int)fb.n_obs * 10;
-      for (int r = 0; r < rows; ++r) my[r * B] = fb.boxes[(size_t)r * fb.n + env];
-    }
-    bx0 = my;
-    stride = B;
-  } else {
-    bx0 = fb.boxes + env;
-    stride = (int)fb.n;
+  float* my = sm_boxes + threadIdx.x * 10;
+  if (active) {
+    for (int k = 0; k < (int)fb.n_obs; ++k)
+#pragma unroll
+      for (int f = 0; f < 10; ++f) my[k * B * 10 + f] = fb.boxes[((size_t)k * 10 + f) * fb.n + env];
   }
   uint32_t resets = 0;
   bool any_hit = false;
   if (active) {
     const int nrot = QUAD_ONLY ? 4 : rotor_count(fb, env);
     if (nrot == 4)
-      simulate<4, INTEG>(fb, P, env, n_steps, substeps, bx0, stride, resets, any_hit);
+      simulate<4, INTEG, DRAG>(fb, P, env, n_steps, substeps, my, B * 10, resets, any_hit);
     else if (nrot == 6)
-      simulate<6, INTEG>(fb, P, env, n_steps, substeps, bx0, stride, resets, any_hit);
+      simulate<6, INTEG, DRAG>(fb, P, env, n_steps, substeps, my, B * 10, resets, any_hit);
     else
-      simulate<8, INTEG>(fb, P, env, n_steps, substeps, bx0, stride, resets, any_hit);
+      simulate<8, INTEG, DRAG>(fb, P, env, n_steps, substeps, my, B * 10, resets, any_hit);
     fb.collided[env] = any_hit ? 1 : 0;
   }
   append_compact(resets > 0u, env, fb.reset_ids, fb.n_reset);
@@ -256,7 +247,8 @@ __global__ void __launch_bounds__(256) k_plain_controller(FleetBuffers fb, StepP
   const uint32_t n = fb.n;
   VState s = load_state(fb.state, n, i);
   normalize(s.q);
-  Wrench4 c = controller(s, load_command(fb, i), load_body(fb.body, n, i), P);
+  V3 b3;
+  Wrench4 c = controller(s, load_command(fb, i), load_body(fb.body, n, i), P, b3);
   fb.cmd[0 * n + i] = c.f; fb.cmd[1 * n + i] = c.mx; fb.cmd[2 * n + i] = c.my; fb.cmd[3 * n + i] = c.mz;
 }
 
@@ -282,14 +274,14 @@ __global__ void __launch_bounds__(256) k_plain_allocate(FleetBuffers fb, StepPar
   else plain_allocate_one<8>(fb, P, i);
 }
 
-template <int INTEG>
+template <int INTEG, bool DRAG>
 __global__ void __launch_bounds__(256) k_plain_integrate(FleetBuffers fb, StepParams P) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= fb.n) return;
   const uint32_t n = fb.n;
   VState s = load_state(fb.state, n, i);
   Wrench4 W = {fb.wrench[0 * n + i], fb.wrench[1 * n + i], fb.wrench[2 * n + i], fb.wrench[3 * n + i]};
-  integrate<INTEG>(s, W, load_body(fb.body, n, i), P);
+  integrate<INTEG, DRAG>(s, body_z(s.q), W, load_body(fb.body, n, i), P);
   store_state(fb.state, n, i, s);
 }
 
@@ -334,48 +326,58 @@ __global__ void __launch_bounds__(256) k_plain_compact(FleetBuffers fb) {
   append_compact(pred, i, fb.reset_ids, fb.n_reset);
 }
 
-template <int INTEG, bool QUAD_ONLY, bool SMEM>
+template <int INTEG, bool QUAD_ONLY, bool DRAG>
 cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
                            cudaStream_t st) {
-  const size_t smem = SMEM ? (size_t)fb.n_obs * 10 * B * sizeof(float) : 0;
+  const size_t smem = (size_t)fb.n_obs * 10 * B * sizeof(float);
   static bool attr_set = false;  // per instantiation; raise the dynamic shared-memory cap once
-  if (SMEM && !attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_step<INTEG, QUAD_ONLY, SMEM>,
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_fused_step<INTEG, QUAD_ONLY, DRAG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const unsigned grid = (fb.n + B - 1) / B;
-  k_fused_step<INTEG, QUAD_ONLY, SMEM><<<grid, B, smem, st>>>(fb, P, n_steps, substeps);
+  k_fused_step<INTEG, QUAD_ONLY, DRAG><<<grid, B, smem, st>>>(fb, P, n_steps, substeps);
   return cudaGetLastError();
 }
 
-template <int INTEG, bool QUAD_ONLY>
-cudaError_t launch_fused_s(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, bool smem, int B,
+template <int INTEG>
+cudaError_t launch_fused_i(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
                            cudaStream_t st) {
-  return smem ? launch_fused_t<INTEG, QUAD_ONLY, true>(fb, P, n_steps, substeps, B, st)
-              : launch_fused_t<INTEG, QUAD_ONLY, false>(fb, P, n_steps, substeps, B, st);
+  const bool quad_only = fb.n_quad == fb.n;
+  const bool drag = P.drag != 0.f;
+  if (quad_only)
+    return drag ? launch_fused_t<INTEG, true, true>(fb, P, n_steps, substeps, B, st)
+                : launch_fused_t<INTEG, true, false>(fb, P, n_steps, substeps, B, st);
+  return drag ? launch_fused_t<INTEG, false, true>(fb, P, n_steps, substeps, B, st)
+              : launch_fused_t<INTEG, false, false>(fb, P, n_steps, substeps, B, st);
 }
 
 }  // namespace
 
 int fused_block_size(int n_obs) {
-  // keep the per-block staging at or below ~100 KB so two blocks fit per SM
-  const int bytes_per_thread = n_obs * 10 * (int)sizeof(float);
-  if (bytes_per_thread == 0) return 128;
-  int b = (100 * 1024) / bytes_per_thread;
-  b = (b / 32) * 32;
-  if (b > 128) b = 128;
-  if (b < 32) b = 32;
-  return b;
+  // Largest block in {128, 96, 64, 32} that maximises resident warps per SM
+  // under 228 KB of shared memory (1 KB reserved per block) and ~96
+  // registers per thread.
+  const int per_thread = n_obs * 10 * (int)sizeof(float);
+  int best_b = 128, best_warps = -1;
+  for (int b = 128; b >= 32; b -= 32) {
+    const int smem_blocks = per_thread ? 233472 / (per_thread * b + 1024) : 32;
+    const int reg_blocks = 65536 / (96 * b);
+    int blocks = smem_blocks < reg_blocks ? smem_blocks : reg_blocks;
+    if (blocks > 32) blocks = 32;
+    if (per_thread * b > 200 * 1024) blocks = 0;
+    const int warps = blocks * b / 32;
+    if (warps > best_warps) { best_warps = warps; best_b = b; }
+  }
+  return best_b;
 }
 
 FusedTuning fused_tuning_from_env(int n_obs) {
   FusedTuning t;
-  t.smem = true;
   t.sorted = true;
   t.block = fused_block_size(n_obs);
-  if (const char* v = std::getenv("AG_FUSED_STAGING")) t.smem = std::strcmp(v, "l1") != 0;
   if (const char* v = std::getenv("AG_FUSED_ORDER")) t.sorted = std::strcmp(v, "identity") != 0;
   if (const char* v = std::getenv("AG_FUSED_BLOCK")) {
     int b = std::atoi(v);
@@ -391,13 +393,8 @@ cudaError_t launch_fused_step(const FleetBuffers& fb_in, const StepParams& P, in
   const FusedTuning t = fused_tuning_from_env((int)fb_in.n_obs);
   FleetBuffers fb = fb_in;
   if (!t.sorted) fb.order = nullptr;
-  const bool smem = t.smem && fb.n_obs > 0;
-  const bool quad_only = fb.n_quad == fb.n;
-  if (integrator == kIntegRK4)
-    return quad_only ? launch_fused_s<kIntegRK4, true>(fb, P, n_steps, substeps, smem, t.block, st)
-                     : launch_fused_s<kIntegRK4, false>(fb, P, n_steps, substeps, smem, t.block, st);
-  return quad_only ? launch_fused_s<kIntegSIE, true>(fb, P, n_steps, substeps, smem, t.block, st)
-                   : launch_fused_s<kIntegSIE, false>(fb, P, n_steps, substeps, smem, t.block, st);
+  return integrator == kIntegRK4 ? launch_fused_i<kIntegRK4>(fb, P, n_steps, substeps, t.block, st)
+                                 : launch_fused_i<kIntegSIE>(fb, P, n_steps, substeps, t.block, st);
 }
 
 cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch24, cudaStream_t st) {
@@ -431,10 +428,14 @@ cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int i
     for (int ss = 0; ss < substeps; ++ss) {
       k_plain_controller<<<grid, 256, 0, st>>>(fb, P);
       k_plain_allocate<<<grid, 256, 0, st>>>(fb, P);
-      if (integrator == kIntegRK4)
-        k_plain_integrate<kIntegRK4><<<grid, 256, 0, st>>>(fb, P);
-      else
-        k_plain_integrate<kIntegSIE><<<grid, 256, 0, st>>>(fb, P);
+      const bool drag = P.drag != 0.f;
+      if (integrator == kIntegRK4) {
+        if (drag) k_plain_integrate<kIntegRK4, true><<<grid, 256, 0, st>>>(fb, P);
+        else k_plain_integrate<kIntegRK4, false><<<grid, 256, 0, st>>>(fb, P);
+      } else {
+        if (drag) k_plain_integrate<kIntegSIE, true><<<grid, 256, 0, st>>>(fb, P);
+        else k_plain_integrate<kIntegSIE, false><<<grid, 256, 0, st>>>(fb, P);
+      }
     }
     if (fb.n_obs > 0) {
       k_plain_collide<<<grid, 256, 0, st>>>(fb, P, hits);
