@@ -81,7 +81,7 @@ typedef struct {
   uint32_t integrator;        /* ag_integrator */
   uint32_t n_obstacles;       /* boxes per environment, 0..AG_MAX_OBSTACLES */
   uint32_t n_quad, n_hexa, n_octo; /* contiguous type ranges in this order; sum == n_envs */
-  uint32_t reserved0;
+  uint32_t record_every;      /* checkpoint interval K of ag_rollout_loss (0 = 32 steps) */
   float dt;          /* step length [s]; a substep is dt / substeps_per_step */
   float motor_tau;   /* first-order motor time constant [s]; 0 = no lag */
   float drag;        /* linear drag coefficient [N s / m], world frame */
@@ -207,6 +207,39 @@ ag_status ag_step_plain_noalloc(const ag_config* cfg, void* cuda_stream, uint32_
                                 float* state, float* motors, const float* body, const uint8_t* modes,
                                 const float* targets, const float* boxes, uint32_t* epoch, uint8_t* collided,
                                 uint32_t* reset_ids, uint32_t* n_reset, char* err, size_t err_len);
+
+/* Sets the 12 diagonal controller gains (k_x, k_v, k_R, k_Omega, three each,
+ * in that order) used by every later launch. gains12 may be a host or device
+ * pointer (the call synchronises the copy). */
+ag_status ag_set_gains(ag_ctx* ctx, const float* gains12);
+
+/* Differentiable rollout, forward half. Advances every environment n_steps
+ * steps from its current state with the position-tracking controller (Sec. I,
+ * after Lee et al. 2011; attitude law Sec. IV-A Eqs. 3-5), allocation with
+ * clamp and lag, and semi-implicit Euler, without collision tests; records a
+ * checkpoint (state + motors) every record_every steps; and writes
+ *   loss[i] = sum_{t=1..n_steps} w_pos |p_t - p_goal_i|^2 + w_omega |Omega_t|^2
+ * (x_t = the state after step t; p_goal float[3][n_envs]). saturated (may be
+ * NULL) flags environments in which some motor command was clamped during
+ * the rollout; there the gradient uses the clamp's subgradient 0. Requires
+ * every environment in AG_MODE_POSITION, semi-implicit Euler, one substep per
+ * step and no obstacles (else AG_ERR_UNSUPPORTED). Synchronises once (mode
+ * check). Commands, body parameters and gains must not change until
+ * ag_backward has run. */
+ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos, float w_omega, const float* p_goal,
+                          float* loss, uint8_t* saturated);
+
+/* Differentiable rollout, reverse half: the hand-written adjoint of the last
+ * ag_rollout_loss. With weights c_i = loss_weights[i] (NULL = all 1), writes
+ * the gradient of sum_i c_i loss[i] with respect to each environment's
+ * initial state float[13][n_envs] (grad_x0), with respect to the 12 gains
+ * float[12] (grad_gains, the fleet sum, reduced in a fixed order so repeated
+ * calls give identical bits) and, optionally, each environment's share
+ * float[12][n_envs] (grad_gains_per_env). Any output may be NULL. The
+ * gradient with respect to the initial quaternion is that of the loss as a
+ * function of q_0 / |q_0|. Returns AG_ERR_STATE if nothing was recorded. */
+ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, float* grad_gains,
+                      float* grad_gains_per_env);
 
 /* Waits for all work queued on the context's stream. */
 ag_status ag_synchronize(ag_ctx* ctx);

@@ -33,7 +33,7 @@ class ag_config(ctypes.Structure):
     _fields_ = [("n_envs", ctypes.c_uint32), ("substeps_per_step", ctypes.c_uint32),
                 ("integrator", ctypes.c_uint32), ("n_obstacles", ctypes.c_uint32),
                 ("n_quad", ctypes.c_uint32), ("n_hexa", ctypes.c_uint32), ("n_octo", ctypes.c_uint32),
-                ("reserved0", ctypes.c_uint32),
+                ("record_every", ctypes.c_uint32),
                 ("dt", ctypes.c_float), ("motor_tau", ctypes.c_float), ("drag", ctypes.c_float),
                 ("sphere_r", ctypes.c_float), ("u_max", ctypes.c_float), ("arm", ctypes.c_float),
                 ("k_yaw", ctypes.c_float), ("mass", ctypes.c_float), ("inertia", ctypes.c_float * 3),
@@ -63,6 +63,9 @@ SIGNATURES = {
     "ag_synchronize": (ctypes.c_int, [_vp]),
     "ag_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(ag_config)]),
     "ag_last_error": (ctypes.c_char_p, [_vp]),
+    "ag_set_gains": (ctypes.c_int, [_vp, _vp]),
+    "ag_rollout_loss": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
+    "ag_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "ag_step_plain_noalloc": (ctypes.c_int, [ctypes.POINTER(ag_config), _vp, ctypes.c_uint32, ctypes.c_uint64,
                                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_char_p,
                                              ctypes.c_size_t]),
@@ -182,6 +185,20 @@ def ag_get_config(ctx: int) -> ag_config:
     c = ag_config()
     _check(lib().ag_get_config(ctx, ctypes.byref(c)), "ag_get_config", ctx)
     return c
+
+
+def ag_set_gains(ctx: int, gains12) -> None:
+    _check(lib().ag_set_gains(ctx, ptr(gains12)), "ag_set_gains", ctx)
+
+
+def ag_rollout_loss(ctx: int, n_steps: int, w_pos: float, w_omega: float, p_goal, loss, saturated=None) -> None:
+    _check(lib().ag_rollout_loss(ctx, int(n_steps), float(w_pos), float(w_omega), ptr(p_goal), ptr(loss),
+                                 ptr(saturated)), "ag_rollout_loss", ctx)
+
+
+def ag_backward(ctx: int, loss_weights=None, grad_x0=None, grad_gains=None, grad_gains_per_env=None) -> None:
+    _check(lib().ag_backward(ctx, ptr(loss_weights), ptr(grad_x0), ptr(grad_gains), ptr(grad_gains_per_env)),
+           "ag_backward", ctx)
 
 
 def ag_last_error(ctx: int | None) -> str:

@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 
+#include "adjoint_internal.h"
 #include "ag.h"
 #include "fleet_internal.h"
 
@@ -29,6 +30,13 @@ struct ag_ctx {
   std::string err;
   size_t bytes;              // device bytes held
   float A[3][4][8], Ap[3][8][4];
+  // differentiable rollout (allocated at the first ag_rollout_loss)
+  agk::AdjointBuffers adj;
+  size_t adj_ckpt_cap;       // checkpoints the ckpt buffer holds
+  int adj_tape_cap;          // steps the tape holds
+  uint32_t* adj_count;       // [1] device scratch
+  bool adj_recorded;
+  agk::StepParams adj_P;     // parameters of the recorded rollout
 };
 
 namespace {
@@ -126,7 +134,7 @@ const char* validate(const ag_config* c) {
 size_t buffer_bytes(const ag_config* c) {
   size_t n = c->n_envs;
   size_t per = sizeof(float) * (13 + 8 + 4 + 4 + 4 + 4) + sizeof(uint32_t) * 4 + 3 /* modes, collided, hits */ + 1;
-  return n * per + (size_t)c->n_obstacles * 10 * n * sizeof(float) + sizeof(uint32_t);
+  return n * per + 2 * (size_t)c->n_obstacles * 10 * n * sizeof(float) + sizeof(uint32_t);
 }
 
 agk::StepParams step_params(const ag_ctx* ctx) {
@@ -158,10 +166,20 @@ ag_status enter(ag_ctx* ctx) {
   return AG_OK;
 }
 
+void free_adjoint(ag_ctx* ctx) {
+  agk::AdjointBuffers& a = ctx->adj;
+  void* ptrs[] = {(void*)a.p_goal, a.ckpt, a.tape, a.loss, a.saturated, (void*)a.loss_weights, a.grad_x0,
+                  a.grad_gains_env, a.partial, a.grad_gains, ctx->adj_count};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
 void free_all(ag_ctx* ctx) {
+  free_adjoint(ctx);
   agk::FleetBuffers& f = ctx->fb;
   void* ptrs[] = {f.state, f.motors, f.body, f.modes, f.targets, f.boxes, f.epoch, f.collided, f.reset_ids,
-                  f.n_reset, f.cmd, f.wrench, f.resets, f.hits, f.order, ctx->mask_dev, ctx->order_scratch};
+                  f.n_reset, f.cmd, f.wrench, f.resets, f.hits, f.order, f.boxes_slot, ctx->mask_dev,
+                  ctx->order_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -220,6 +238,11 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   std::memset(&ctx->fb, 0, sizeof(ctx->fb));
   ctx->mask_dev = nullptr;
   ctx->order_scratch = nullptr;
+  std::memset(&ctx->adj, 0, sizeof(ctx->adj));
+  ctx->adj_ckpt_cap = 0;
+  ctx->adj_tape_cap = 0;
+  ctx->adj_count = nullptr;
+  ctx->adj_recorded = false;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     g_create_error = "no CUDA device";
     delete ctx;
@@ -237,6 +260,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = alloc(ctx, &f.modes, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.targets, 4 * n);
   if (e == cudaSuccess) e = alloc(ctx, &f.boxes, (size_t)cfg->n_obstacles * 10 * n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.boxes_slot, (size_t)cfg->n_obstacles * 10 * n);
   if (e == cudaSuccess) e = alloc(ctx, &f.epoch, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.collided, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.reset_ids, n);
@@ -267,6 +291,8 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(f.modes, AG_MODE_WRENCH, n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.targets, 0, 4 * n * sizeof(float), st);
   if (e == cudaSuccess && f.boxes) e = cudaMemsetAsync(f.boxes, 0, (size_t)cfg->n_obstacles * 10 * n * sizeof(float), st);
+  if (e == cudaSuccess && f.boxes_slot)
+    e = cudaMemsetAsync(f.boxes_slot, 0, (size_t)cfg->n_obstacles * 10 * n * sizeof(float), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.epoch, 0, n * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.collided, 0, n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.n_reset, 0, sizeof(uint32_t), st);
@@ -313,8 +339,10 @@ ag_status ag_set_obstacles(ag_ctx* ctx, const float* boxes) {
   if (!boxes) return fail_invalid(ctx, "boxes is NULL");
   if (ctx->cfg.n_obstacles == 0) return AG_OK;
   const size_t count = (size_t)ctx->cfg.n_obstacles * 10 * ctx->cfg.n_envs;
-  return check_cuda(ctx, cudaMemcpyAsync(ctx->fb.boxes, boxes, count * sizeof(float), cudaMemcpyDefault, ctx->stream),
-                    "copy boxes");
+  s = check_cuda(ctx, cudaMemcpyAsync(ctx->fb.boxes, boxes, count * sizeof(float), cudaMemcpyDefault, ctx->stream),
+                 "copy boxes");
+  if (s != AG_OK) return s;
+  return check_cuda(ctx, agk::launch_permute_boxes(ctx->fb, ctx->stream), "permute boxes");
 }
 
 ag_status ag_set_body(ag_ctx* ctx, const float* body) {
@@ -420,6 +448,132 @@ const char* ag_last_error(const ag_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Differentiable rollout: gains, recorded forward, adjoint.
+namespace {
+
+// Grows the adjoint buffers for a record of n_steps steps with interval K.
+ag_status ensure_adjoint(ag_ctx* ctx, int n_steps, int K) {
+  agk::AdjointBuffers& a = ctx->adj;
+  const size_t n = ctx->cfg.n_envs;
+  const size_t n_ckpt = (size_t)(n_steps + K - 1) / K;
+  cudaError_t e = cudaSuccess;
+  if (!a.loss) {
+    float* pg = nullptr; float* lw = nullptr;
+    if (e == cudaSuccess) e = alloc(ctx, &pg, 3 * n);
+    if (e == cudaSuccess) e = alloc(ctx, &a.loss, n);
+    if (e == cudaSuccess) e = alloc(ctx, &a.saturated, n);
+    if (e == cudaSuccess) e = alloc(ctx, &lw, n);
+    if (e == cudaSuccess) e = alloc(ctx, &a.grad_x0, 13 * n);
+    if (e == cudaSuccess) e = alloc(ctx, &a.grad_gains_env, 12 * n);
+    if (e == cudaSuccess) e = alloc(ctx, &a.partial, 12 * (size_t)agk::kReduceParts);
+    if (e == cudaSuccess) e = alloc(ctx, &a.grad_gains, 12);
+    if (e == cudaSuccess) e = alloc(ctx, &ctx->adj_count, 1);
+    a.p_goal = pg;
+    a.loss_weights = lw;
+    if (e != cudaSuccess) { cudaGetLastError(); ctx->err = "adjoint buffers do not fit"; return AG_ERR_OOM; }
+  }
+  if (n_ckpt > ctx->adj_ckpt_cap) {
+    if (a.ckpt) { cudaStreamSynchronize(ctx->stream); cudaFree(a.ckpt); a.ckpt = nullptr; }
+    e = alloc(ctx, &a.ckpt, n_ckpt * 21 * n);
+    if (e != cudaSuccess) { cudaGetLastError(); ctx->adj_ckpt_cap = 0; ctx->err = "checkpoints do not fit"; return AG_ERR_OOM; }
+    ctx->adj_ckpt_cap = n_ckpt;
+  }
+  if (K > ctx->adj_tape_cap) {
+    if (a.tape) { cudaStreamSynchronize(ctx->stream); cudaFree(a.tape); a.tape = nullptr; }
+    e = alloc(ctx, &a.tape, (size_t)K * 21 * n);
+    if (e != cudaSuccess) { cudaGetLastError(); ctx->adj_tape_cap = 0; ctx->err = "tape does not fit"; return AG_ERR_OOM; }
+    ctx->adj_tape_cap = K;
+  }
+  return AG_OK;
+}
+
+}  // namespace
+
+extern "C" ag_status ag_set_gains(ag_ctx* ctx, const float* gains12) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!gains12) return fail_invalid(ctx, "gains is NULL");
+  float g[12];
+  if ((s = check_cuda(ctx, cudaMemcpy(g, gains12, sizeof(g), cudaMemcpyDefault), "copy gains")) != AG_OK) return s;
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(g[i])) return fail_invalid(ctx, "gains must be finite");
+  for (int i = 0; i < 3; ++i) {
+    ctx->cfg.kx[i] = g[i]; ctx->cfg.kv[i] = g[3 + i]; ctx->cfg.kR[i] = g[6 + i]; ctx->cfg.kW[i] = g[9 + i];
+  }
+  return AG_OK;
+}
+
+extern "C" ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos, float w_omega, const float* p_goal,
+                                     float* loss, uint8_t* saturated) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  const ag_config& c = ctx->cfg;
+  if (c.integrator != AG_INTEG_SIE || c.substeps_per_step != 1 || c.n_obstacles != 0) {
+    ctx->err = "the differentiable rollout needs semi-implicit Euler, 1 substep per step and no obstacles";
+    return AG_ERR_UNSUPPORTED;
+  }
+  if (n_steps == 0 || !p_goal || !loss) return fail_invalid(ctx, "n_steps must be >= 1; p_goal and loss are required");
+  const size_t n = c.n_envs;
+  const int K = c.record_every ? (int)c.record_every : 32;
+  if ((s = ensure_adjoint(ctx, (int)n_steps, K)) != AG_OK) return s;
+  // every environment must be in position mode
+  uint32_t bad = 0;
+  if ((s = check_cuda(ctx, agk::launch_count_non_position(ctx->fb.modes, (uint32_t)n, ctx->adj_count, ctx->stream),
+                      "mode check")) != AG_OK) return s;
+  if ((s = check_cuda(ctx, cudaMemcpyAsync(&bad, ctx->adj_count, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream),
+                      "mode check copy")) != AG_OK) return s;
+  if ((s = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "synchronize")) != AG_OK) return s;
+  if (bad) {
+    ctx->err = "the differentiable rollout supports position mode only (" + std::to_string(bad) + " envs are not)";
+    return AG_ERR_UNSUPPORTED;
+  }
+  agk::AdjointBuffers& a = ctx->adj;
+  if ((s = check_cuda(ctx, cudaMemcpyAsync((void*)a.p_goal, p_goal, 3 * n * sizeof(float), cudaMemcpyDefault,
+                                           ctx->stream), "copy goals")) != AG_OK) return s;
+  a.state = ctx->fb.state; a.motors = ctx->fb.motors; a.body = ctx->fb.body; a.targets = ctx->fb.targets;
+  a.n = c.n_envs; a.n_quad = c.n_quad; a.n_hexa = c.n_hexa; a.n_octo = c.n_octo;
+  a.n_steps = (int)n_steps; a.K = K; a.w_pos = w_pos; a.w_omega = w_omega;
+  ctx->adj_P = step_params(ctx);
+  ctx->adj_recorded = false;
+  if ((s = check_cuda(ctx, agk::launch_record(a, ctx->adj_P, ctx->stream), "record launch")) != AG_OK) return s;
+  ctx->adj_recorded = true;
+  if ((s = check_cuda(ctx, cudaMemcpyAsync(loss, a.loss, n * sizeof(float), cudaMemcpyDefault, ctx->stream),
+                      "copy loss out")) != AG_OK) return s;
+  if (saturated)
+    s = check_cuda(ctx, cudaMemcpyAsync(saturated, a.saturated, n, cudaMemcpyDefault, ctx->stream), "copy flags out");
+  return s;
+}
+
+extern "C" ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, float* grad_gains,
+                                 float* grad_gains_per_env) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!ctx->adj_recorded) {
+    ctx->err = "ag_backward needs a rollout recorded by ag_rollout_loss";
+    return AG_ERR_STATE;
+  }
+  if (!grad_x0 && !grad_gains && !grad_gains_per_env) return AG_OK;
+  agk::AdjointBuffers a = ctx->adj;
+  const size_t n = ctx->cfg.n_envs;
+  if (loss_weights) {
+    if ((s = check_cuda(ctx, cudaMemcpyAsync((void*)a.loss_weights, loss_weights, n * sizeof(float),
+                                             cudaMemcpyDefault, ctx->stream), "copy weights")) != AG_OK) return s;
+  } else {
+    a.loss_weights = nullptr;
+  }
+  if ((s = check_cuda(ctx, agk::launch_adjoint(a, ctx->adj_P, ctx->stream), "adjoint launch")) != AG_OK) return s;
+  cudaStream_t st = ctx->stream;
+  if (grad_x0 && (s = check_cuda(ctx, cudaMemcpyAsync(grad_x0, a.grad_x0, 13 * n * sizeof(float), cudaMemcpyDefault,
+                                                      st), "copy grad x0")) != AG_OK) return s;
+  if (grad_gains && (s = check_cuda(ctx, cudaMemcpyAsync(grad_gains, a.grad_gains, 12 * sizeof(float),
+                                                         cudaMemcpyDefault, st), "copy grad gains")) != AG_OK) return s;
+  if (grad_gains_per_env)
+    s = check_cuda(ctx, cudaMemcpyAsync(grad_gains_per_env, a.grad_gains_env, 12 * n * sizeof(float),
+                                        cudaMemcpyDefault, st), "copy per-env grad gains");
+  return s;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free unfused step (ag_step_plain_noalloc).

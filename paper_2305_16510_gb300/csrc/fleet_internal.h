@@ -26,6 +26,7 @@ struct FleetBuffers {
   uint32_t* resets;    // [n]     resets of this call per env
   uint8_t* hits;       // [n]     collision of the current step
   uint32_t* order;     // [n]     thread slot -> env, grouped by rotor type and mode (NULL = identity)
+  float* boxes_slot;   // [n_obs][10][n] the boxes in slot order (boxes_slot[r][i] = boxes[r][order[i]])
   uint32_t n, n_quad, n_hexa, n_octo, n_obs;
 };
 
@@ -38,8 +39,11 @@ cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int i
                               int substeps, cudaStream_t st);
 
 // Builds fb.order from the current modes and rotor types (3 small launches;
-// scratch24 is 24 words of device scratch).
+// scratch24 is 24 words of device scratch), then refreshes fb.boxes_slot.
 cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch24, cudaStream_t st);
+
+// Refreshes fb.boxes_slot from fb.boxes and fb.order (after the boxes change).
+cudaError_t launch_permute_boxes(const FleetBuffers& fb, cudaStream_t st);
 
 // Threads per block of the fused kernel for a given obstacle count (the
 // per-block shared-memory staging grows with it).

@@ -151,9 +151,11 @@ __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams 
   const uint32_t env = active ? (fb.order ? fb.order[slot] : slot) : slot;
   float* my = sm_boxes + threadIdx.x * 10;
   if (active) {
+    // slot-ordered copy when grouped (coalesced rows); env == slot otherwise
+    const float* src = fb.order ? fb.boxes_slot : fb.boxes;
     for (int k = 0; k < (int)fb.n_obs; ++k)
 #pragma unroll
-      for (int f = 0; f < 10; ++f) my[k * B * 10 + f] = fb.boxes[((size_t)k * 10 + f) * fb.n + env];
+      for (int f = 0; f < 10; ++f) my[k * B * 10 + f] = src[((size_t)k * 10 + f) * fb.n + slot];
   }
   uint32_t resets = 0;
   bool any_hit = false;
@@ -198,6 +200,14 @@ __global__ void k_order_offsets(uint32_t* counts, uint32_t* cursor) {
       run += counts[k];
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_permute_boxes(FleetBuffers fb) {
+  const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= fb.n) return;
+  const uint32_t env = fb.order[slot];
+  const size_t rows = (size_t)fb.n_obs * 10;
+  for (size_t r = 0; r < rows; ++r) fb.boxes_slot[r * fb.n + slot] = fb.boxes[r * fb.n + env];
 }
 
 __global__ void __launch_bounds__(256) k_order_scatter(FleetBuffers fb, uint32_t* cursor) {
@@ -404,6 +414,14 @@ cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch24, cuda
   k_order_count<<<grid, 256, 0, st>>>(fb, scratch24);
   k_order_offsets<<<1, 32, 0, st>>>(scratch24, scratch24 + 12);
   k_order_scatter<<<grid, 256, 0, st>>>(fb, scratch24 + 12);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_permute_boxes(fb, st);
+}
+
+cudaError_t launch_permute_boxes(const FleetBuffers& fb, cudaStream_t st) {
+  if (fb.n_obs == 0 || !fb.order || !fb.boxes_slot) return cudaSuccess;
+  k_permute_boxes<<<(fb.n + 255) / 256, 256, 0, st>>>(fb);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,9 @@ Recipes (sizes and distributions of the fleet workloads):
               U[-1, 1], 1 % Bernoulli reset mask every 50 steps
   paper_shape 131,072 quads, attitude or body-velocity command, no obstacles,
               1 substep (the fleet size of the paper's throughput figure)
+  adjoint     65,536 quads, position mode (targets as in parity), semi-implicit
+              Euler, 1 substep, horizon 256 steps, goals = the position
+              targets, checkpoint every 32 steps
 Targets per mode: position U[-3, 3]^3 and yaw U[-pi, pi); body velocity
 U[-2, 2]^3 and yaw rate U[-1, 1]; attitude roll and pitch U[-30, 30] deg,
 yaw rate U[-1, 1], collective thrust U[0.5, 1.5] m g.
@@ -64,6 +67,7 @@ WORKLOADS = {
                       mode_mix=(MODE_BODY_VEL,), reset_every=50, reset_prob=0.01),
     "paper_shape": Workload("paper_shape", 1 << 17, 1, 0, 0, 1 << 17, 0, 0, horizon=100,
                             mode_mix=(MODE_BODY_VEL, MODE_ATT_THRUST)),
+    "adjoint": Workload("adjoint", 65536, 1, 0, 0, 65536, 0, 0, horizon=256, mode_mix=(MODE_POSITION,)),
 }
 
 
