@@ -241,6 +241,90 @@ ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos, float w_om
 ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, float* grad_gains,
                       float* grad_gains_per_env);
 
+/* ------------------------------------------------------------------------
+ * Continuous-batching rollout server.
+ *
+ * A server owns one device slab of hbm_budget_bytes (allocated once at
+ * creation) and a persistent host thread. Each submitted request is a whole
+ * rollout of an independent quadrotor fleet (its own size, horizon, command
+ * mode per environment, obstacle count and Philox seed). The thread admits
+ * requests first-in first-out while a slot (max_active) and slab memory are
+ * free, draws their initial states (as ag_reset), and advances ALL active
+ * requests together: one kernel launch covers every environment of every
+ * active request for chunk_steps steps (fewer for a request's last chunk),
+ * with the same per-step computation as ag_step (controller, allocation,
+ * integrator, collision test, Philox reset). Requests that arrive while
+ * others run join at the next launch; their state stays on the device until
+ * they finish. A finished request's final state and reset epochs are kept
+ * on the host until ag_server_wait collects them. Chunk boundaries are
+ * counted from each request's own first launch, so a request's result is
+ * bit-identical alone or in any mix. max_active = 1 makes the same loop run
+ * one request per launch (the unbatched comparison point). Physics settings
+ * (integrator, substeps, dt, gains, motor model, radius) come from `physics`;
+ * its fleet-size fields are ignored. */
+#define AG_SERVER_MAX_ACTIVE 4096
+
+typedef struct ag_server ag_server;
+
+typedef struct {
+  ag_config physics;         /* per-step physics of every request */
+  uint32_t max_active;       /* requests on the device at once, 1..AG_SERVER_MAX_ACTIVE */
+  uint32_t chunk_steps;      /* steps per launch (>= 1) */
+  uint64_t hbm_budget_bytes; /* device memory for request buffers (>= 1 MiB) */
+} ag_server_config;
+
+typedef struct {
+  uint32_t n_envs;           /* quadrotors in this request (>= 1) */
+  uint32_t n_steps;          /* horizon in steps (>= 1) */
+  uint32_t n_obstacles;      /* boxes per environment, 0..AG_MAX_OBSTACLES */
+  uint32_t reserved;
+  uint64_t seed;             /* Philox key of its initial draw and collision resets */
+  const uint8_t* modes;      /* [n_envs] ag_mode values */
+  const float* targets;      /* [4][pitch]: first n_envs of each row used */
+  const float* body;         /* [4][pitch] m, J diagonal; NULL = the physics' nominal body */
+  const float* boxes;        /* [n_obstacles * 10][pitch] as ag_set_obstacles; NULL if none */
+  uint64_t pitch;            /* row stride of targets/body/boxes in elements (0 = n_envs) */
+} ag_request;
+
+typedef struct {
+  uint64_t launches;         /* chunk launches so far */
+  uint64_t completed;        /* requests finished */
+  uint64_t pending;          /* waiting for admission */
+  uint64_t active;           /* on the device */
+  double vehicle_steps;      /* environment-steps computed */
+  double gpu_ms;             /* summed device time of the launches (CUDA events) */
+  uint64_t hbm_used_bytes;   /* slab bytes held by active requests */
+} ag_server_stats;
+
+/* Defaults: RK4 with 4 substeps of 2.5 ms, the ag_config_default body,
+ * motor model and gains, max_active 1024, chunk_steps 50, a 40 GiB budget. */
+void ag_server_config_default(ag_server_config* cfg);
+
+/* Creates a server on the current CUDA device and starts its loop thread.
+ * AG_ERR_INVALID for a bad config, AG_ERR_OOM if the slab does not fit. */
+ag_status ag_server_create(const ag_server_config* cfg, ag_server** out);
+
+/* Queues a request (thread-safe, non-blocking) and returns its id. The input
+ * arrays (host or device) must stay valid until ag_server_wait has returned
+ * for this id. AG_ERR_INVALID for a malformed request, AG_ERR_OOM if it could
+ * never fit the budget, AG_ERR_STATE if the server has failed. */
+ag_status ag_server_submit(ag_server* s, const ag_request* req, uint64_t* id);
+
+/* Blocks until request `id` finishes or timeout_s seconds pass
+ * (AG_ERR_TIMEOUT; the request stays queued and can be waited for again).
+ * On success copies its final state float[13][n_envs] and reset epochs
+ * uint32[n_envs] into HOST buffers (either may be NULL), writes its latency
+ * from submission to completion in milliseconds, and forgets the request. */
+ag_status ag_server_wait(ag_server* s, uint64_t id, double timeout_s, float* final_state, uint32_t* epoch,
+                         double* latency_ms);
+
+/* Snapshot of the server's counters. */
+ag_status ag_server_get_stats(ag_server* s, ag_server_stats* out);
+
+/* Stops the loop after the requests on the device finish, abandons queued
+ * ones, and frees everything. */
+ag_status ag_server_destroy(ag_server* s);
+
 /* Waits for all work queued on the context's stream. */
 ag_status ag_synchronize(ag_ctx* ctx);
 

@@ -41,6 +41,24 @@ class ag_config(ctypes.Structure):
                 ("kW", ctypes.c_float * 3), ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64)]
 
 
+class ag_server_config(ctypes.Structure):
+    _fields_ = [("physics", ag_config), ("max_active", ctypes.c_uint32), ("chunk_steps", ctypes.c_uint32),
+                ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class ag_request(ctypes.Structure):
+    _fields_ = [("n_envs", ctypes.c_uint32), ("n_steps", ctypes.c_uint32), ("n_obstacles", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("modes", ctypes.c_void_p),
+                ("targets", ctypes.c_void_p), ("body", ctypes.c_void_p), ("boxes", ctypes.c_void_p),
+                ("pitch", ctypes.c_uint64)]
+
+
+class ag_server_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("pending", ctypes.c_uint64),
+                ("active", ctypes.c_uint64), ("vehicle_steps", ctypes.c_double), ("gpu_ms", ctypes.c_double),
+                ("hbm_used_bytes", ctypes.c_uint64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -66,6 +84,13 @@ SIGNATURES = {
     "ag_set_gains": (ctypes.c_int, [_vp, _vp]),
     "ag_rollout_loss": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
     "ag_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ag_server_config_default": (None, [ctypes.POINTER(ag_server_config)]),
+    "ag_server_create": (ctypes.c_int, [ctypes.POINTER(ag_server_config), ctypes.POINTER(_vp)]),
+    "ag_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(ag_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "ag_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, _vp, _vp,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "ag_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ag_server_stats)]),
+    "ag_server_destroy": (ctypes.c_int, [_vp]),
     "ag_step_plain_noalloc": (ctypes.c_int, [ctypes.POINTER(ag_config), _vp, ctypes.c_uint32, ctypes.c_uint64,
                                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_char_p,
                                              ctypes.c_size_t]),
@@ -199,6 +224,49 @@ def ag_rollout_loss(ctx: int, n_steps: int, w_pos: float, w_omega: float, p_goal
 def ag_backward(ctx: int, loss_weights=None, grad_x0=None, grad_gains=None, grad_gains_per_env=None) -> None:
     _check(lib().ag_backward(ctx, ptr(loss_weights), ptr(grad_x0), ptr(grad_gains), ptr(grad_gains_per_env)),
            "ag_backward", ctx)
+
+
+def ag_server_config_default() -> ag_server_config:
+    c = ag_server_config()
+    lib().ag_server_config_default(ctypes.byref(c))
+    return c
+
+
+def ag_server_create(cfg: ag_server_config) -> int:
+    out = _vp()
+    rc = lib().ag_server_create(ctypes.byref(cfg), ctypes.byref(out))
+    if rc != AG_OK:
+        raise AgError(rc, "ag_server_create", "")
+    return out.value
+
+
+def ag_server_submit(server: int, req: ag_request) -> int:
+    rid = ctypes.c_uint64()
+    rc = lib().ag_server_submit(server, ctypes.byref(req), ctypes.byref(rid))
+    if rc != AG_OK:
+        raise AgError(rc, "ag_server_submit", "")
+    return rid.value
+
+
+def ag_server_wait(server: int, rid: int, timeout_s: float, final_state=None, epoch=None) -> float:
+    """Returns the request's latency in ms (final_state / epoch: host arrays or None)."""
+    lat = ctypes.c_double()
+    rc = lib().ag_server_wait(server, int(rid), float(timeout_s), ptr(final_state), ptr(epoch), ctypes.byref(lat))
+    if rc != AG_OK:
+        raise AgError(rc, "ag_server_wait", "")
+    return lat.value
+
+
+def ag_server_get_stats(server: int) -> ag_server_stats:
+    st = ag_server_stats()
+    rc = lib().ag_server_get_stats(server, ctypes.byref(st))
+    if rc not in (AG_OK, AG_ERR_STATE):
+        raise AgError(rc, "ag_server_get_stats", "")
+    return st
+
+
+def ag_server_destroy(server: int) -> None:
+    lib().ag_server_destroy(server)
 
 
 def ag_last_error(ctx: int | None) -> str:

@@ -137,6 +137,27 @@ size_t buffer_bytes(const ag_config* c) {
   return n * per + 2 * (size_t)c->n_obstacles * 10 * n * sizeof(float) + sizeof(uint32_t);
 }
 
+}  // namespace
+
+agk::StepParams agk::step_params_for(const ag_config& c, uint64_t seed) {
+  agk::StepParams P;
+  for (int i = 0; i < 3; ++i) {
+    P.kx[i] = c.kx[i]; P.kv[i] = c.kv[i]; P.kR[i] = c.kR[i]; P.kW[i] = c.kW[i];
+  }
+  for (int t = 0; t < 3; ++t) rotor_matrices(t == 0 ? 4 : (t == 1 ? 6 : 8), c.arm, c.k_yaw, P.A[t], P.Ap[t]);
+  const double h = (double)c.dt / c.substeps_per_step;
+  P.h = (float)h;
+  P.alpha = c.motor_tau > 0.f ? (float)(1.0 - std::exp(-h / (double)c.motor_tau)) : 1.f;
+  P.drag = c.drag;
+  P.r2 = c.sphere_r * c.sphere_r;
+  P.u_max = c.u_max;
+  P.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
+  P.seed_hi = (uint32_t)(seed >> 32);
+  return P;
+}
+
+namespace {
+
 agk::StepParams step_params(const ag_ctx* ctx) {
   agk::StepParams P;
   const ag_config& c = ctx->cfg;

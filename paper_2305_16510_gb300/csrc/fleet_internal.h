@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ag.h"
 #include "fleet_device.cuh"
 
 namespace agk {
@@ -29,6 +30,11 @@ struct FleetBuffers {
   float* boxes_slot;   // [n_obs][10][n] the boxes in slot order (boxes_slot[r][i] = boxes[r][order[i]])
   uint32_t n, n_quad, n_hexa, n_octo, n_obs;
 };
+
+// Launch constants of a configuration: gains, FP64-computed allocation
+// matrices of the three rotor types, substep length, motor-lag factor,
+// drag, squared collision radius, thrust limit and the reset key.
+StepParams step_params_for(const ag_config& c, uint64_t seed);
 
 // Launches return cudaGetLastError() of their launch.
 cudaError_t launch_fused_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,

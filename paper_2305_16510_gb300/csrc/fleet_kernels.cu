@@ -16,124 +16,11 @@
 #include <cuda_runtime.h>
 
 #include "fleet_internal.h"
+#include "fleet_sim.cuh"
 #include "reset_sampler.cuh"
 
 namespace agk {
 namespace {
-
-__device__ __forceinline__ int rotor_count(const FleetBuffers& fb, uint32_t env) {
-  if (env < fb.n_quad) return 4;
-  if (env < fb.n_quad + fb.n_hexa) return 6;
-  return 8;
-}
-
-__device__ __forceinline__ VState load_state(const float* st, uint32_t n, uint32_t i) {
-  VState s;
-  s.p = {st[0 * n + i], st[1 * n + i], st[2 * n + i]};
-  s.v = {st[3 * n + i], st[4 * n + i], st[5 * n + i]};
-  s.q = {st[6 * n + i], st[7 * n + i], st[8 * n + i], st[9 * n + i]};
-  s.w = {st[10 * n + i], st[11 * n + i], st[12 * n + i]};
-  return s;
-}
-
-__device__ __forceinline__ void store_state(float* st, uint32_t n, uint32_t i, const VState& s) {
-  st[0 * n + i] = s.p.x; st[1 * n + i] = s.p.y; st[2 * n + i] = s.p.z;
-  st[3 * n + i] = s.v.x; st[4 * n + i] = s.v.y; st[5 * n + i] = s.v.z;
-  st[6 * n + i] = s.q.w; st[7 * n + i] = s.q.x; st[8 * n + i] = s.q.y; st[9 * n + i] = s.q.z;
-  st[10 * n + i] = s.w.x; st[11 * n + i] = s.w.y; st[12 * n + i] = s.w.z;
-}
-
-__device__ __forceinline__ Body load_body(const float* bd, uint32_t n, uint32_t i) {
-  Body b;
-  b.m = bd[0 * n + i];
-  b.jx = bd[1 * n + i];
-  b.jy = bd[2 * n + i];
-  b.jz = bd[3 * n + i];
-  b.inv_m = 1.f / b.m;
-  b.ijx = 1.f / b.jx;
-  b.ijy = 1.f / b.jy;
-  b.ijz = 1.f / b.jz;
-  return b;
-}
-
-__device__ __forceinline__ Command load_command(const FleetBuffers& fb, uint32_t i) {
-  const uint32_t n = fb.n;
-  return prepare_command(fb.modes[i], fb.targets[0 * n + i], fb.targets[1 * n + i], fb.targets[2 * n + i],
-                         fb.targets[3 * n + i]);
-}
-
-// Overwrites one environment with its reset draw for `epoch`.
-template <int NROT>
-__device__ __forceinline__ void reset_in_registers(VState& s, float (&u)[NROT], float m, uint32_t env,
-                                                   uint32_t epoch, uint32_t seed_lo, uint32_t seed_hi) {
-  ResetValues r = draw_reset(seed_lo, seed_hi, env, epoch);
-  s.p = {r.p[0], r.p[1], r.p[2]};
-  s.v = {r.v[0], r.v[1], r.v[2]};
-  s.q = {r.q[0], r.q[1], r.q[2], r.q[3]};
-  s.w = {0.f, 0.f, 0.f};
-  float hv = hover_per_motor(m, NROT);
-#pragma unroll
-  for (int k = 0; k < NROT; ++k) u[k] = hv;
-}
-
-// Appends the envs whose predicate is set to the compact list: one ballot and
-// one atomicAdd per warp, ranks from __popc of the lower lanes. Every lane of
-// the warp must call it.
-__device__ __forceinline__ void append_compact(bool pred, uint32_t env, uint32_t* ids, uint32_t* count) {
-  const unsigned lane = threadIdx.x & 31u;
-  const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
-  if (mask == 0u) return;
-  const int leader = __ffs(mask) - 1;
-  uint32_t base = 0;
-  if ((int)lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
-  base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  if (pred) ids[base + __popc(mask & ((1u << lane) - 1u))] = env;
-}
-
-// The per-vehicle body of the fused kernel, specialised on the rotor count.
-// sm points at this thread's staged boxes: box k occupies the 10 floats at
-// sm + k * box_stride (c, h, q), read as five 8-byte loads.
-template <int NROT, int INTEG, bool DRAG>
-__device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, int n_steps,
-                                         int substeps, const float* sm, int box_stride, uint32_t& resets,
-                                         bool& any_hit) {
-  const uint32_t n = fb.n;
-  VState s = load_state(fb.state, n, env);
-  normalize(s.q);
-  float u[NROT];
-#pragma unroll
-  for (int k = 0; k < NROT; ++k) u[k] = fb.motors[k * n + env];
-  const Body b = load_body(fb.body, n, env);
-  const Command cm = load_command(fb, env);
-  uint32_t epoch = fb.epoch[env];
-  const int n_obs = (int)fb.n_obs;
-  for (int step = 0; step < n_steps; ++step) {
-    for (int ss = 0; ss < substeps; ++ss) {
-      V3 b3;
-      Wrench4 W = allocate<NROT>(controller(s, cm, b, P, b3), u, P);
-      integrate<INTEG, DRAG>(s, b3, W, b, P);
-    }
-    if (n_obs > 0) {
-      bool hit = false;
-#pragma unroll 4
-      for (int k = 0; k < n_obs; ++k) {
-        const float2* bx = reinterpret_cast<const float2*>(sm + k * box_stride);
-        const float2 a0 = bx[0], a1 = bx[1], a2 = bx[2], a3 = bx[3], a4 = bx[4];
-        hit |= sphere_hits_box(s.p, P.r2, V3{a0.x, a0.y, a1.x}, V3{a1.y, a2.x, a2.y}, Q4{a3.x, a3.y, a4.x, a4.y});
-      }
-      if (hit) {
-        any_hit = true;
-        resets += 1;
-        epoch += 1;
-        reset_in_registers<NROT>(s, u, b.m, env, epoch, P.seed_lo, P.seed_hi);
-      }
-    }
-  }
-  store_state(fb.state, n, env, s);
-#pragma unroll
-  for (int k = 0; k < NROT; ++k) fb.motors[k * n + env] = u[k];
-  fb.epoch[env] = epoch;
-}
 
 // Thread slot i of the launch simulates environment order[i] (a permutation
 // that groups environments of equal rotor count and command mode, so the
@@ -161,12 +48,14 @@ __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams 
   bool any_hit = false;
   if (active) {
     const int nrot = QUAD_ONLY ? 4 : rotor_count(fb, env);
+    const SmemBoxes bx{my, B * 10};
+    const int n_obs = (int)fb.n_obs;
     if (nrot == 4)
-      simulate<4, INTEG, DRAG>(fb, P, env, n_steps, substeps, my, B * 10, resets, any_hit);
+      simulate<4, INTEG, DRAG>(fb, P, env, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
     else if (nrot == 6)
-      simulate<6, INTEG, DRAG>(fb, P, env, n_steps, substeps, my, B * 10, resets, any_hit);
+      simulate<6, INTEG, DRAG>(fb, P, env, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
     else
-      simulate<8, INTEG, DRAG>(fb, P, env, n_steps, substeps, my, B * 10, resets, any_hit);
+      simulate<8, INTEG, DRAG>(fb, P, env, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
     fb.collided[env] = any_hit ? 1 : 0;
   }
   append_compact(resets > 0u, env, fb.reset_ids, fb.n_reset);

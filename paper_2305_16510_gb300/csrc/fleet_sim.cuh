@@ -1,0 +1,159 @@
+// fleet_sim.cuh — the per-vehicle loop shared by the fused kernels.
+//
+// Loading one environment into registers, running its steps (controller,
+// allocation, integrator, collision test, in-register Philox reset) and
+// storing it back; plus the warp-level compaction of reset ids. Used by the
+// single-fleet fused kernel and by the multi-request serving kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fleet_device.cuh"
+#include "fleet_internal.h"
+#include "reset_sampler.cuh"
+
+namespace agk {
+
+__device__ __forceinline__ int rotor_count(const FleetBuffers& fb, uint32_t env) {
+  if (env < fb.n_quad) return 4;
+  if (env < fb.n_quad + fb.n_hexa) return 6;
+  return 8;
+}
+
+__device__ __forceinline__ VState load_state(const float* st, uint32_t n, uint32_t i) {
+  VState s;
+  s.p = {st[0 * n + i], st[1 * n + i], st[2 * n + i]};
+  s.v = {st[3 * n + i], st[4 * n + i], st[5 * n + i]};
+  s.q = {st[6 * n + i], st[7 * n + i], st[8 * n + i], st[9 * n + i]};
+  s.w = {st[10 * n + i], st[11 * n + i], st[12 * n + i]};
+  return s;
+}
+
+__device__ __forceinline__ void store_state(float* st, uint32_t n, uint32_t i, const VState& s) {
+  st[0 * n + i] = s.p.x; st[1 * n + i] = s.p.y; st[2 * n + i] = s.p.z;
+  st[3 * n + i] = s.v.x; st[4 * n + i] = s.v.y; st[5 * n + i] = s.v.z;
+  st[6 * n + i] = s.q.w; st[7 * n + i] = s.q.x; st[8 * n + i] = s.q.y; st[9 * n + i] = s.q.z;
+  st[10 * n + i] = s.w.x; st[11 * n + i] = s.w.y; st[12 * n + i] = s.w.z;
+}
+
+__device__ __forceinline__ Body load_body(const float* bd, uint32_t n, uint32_t i) {
+  Body b;
+  b.m = bd[0 * n + i];
+  b.jx = bd[1 * n + i];
+  b.jy = bd[2 * n + i];
+  b.jz = bd[3 * n + i];
+  b.inv_m = 1.f / b.m;
+  b.ijx = 1.f / b.jx;
+  b.ijy = 1.f / b.jy;
+  b.ijz = 1.f / b.jz;
+  return b;
+}
+
+__device__ __forceinline__ Command load_command(const FleetBuffers& fb, uint32_t i) {
+  const uint32_t n = fb.n;
+  return prepare_command(fb.modes[i], fb.targets[0 * n + i], fb.targets[1 * n + i], fb.targets[2 * n + i],
+                         fb.targets[3 * n + i]);
+}
+
+// Overwrites one environment with its reset draw for `epoch`.
+template <int NROT>
+__device__ __forceinline__ void reset_in_registers(VState& s, float (&u)[NROT], float m, uint32_t env,
+                                                   uint32_t epoch, uint32_t seed_lo, uint32_t seed_hi) {
+  ResetValues r = draw_reset(seed_lo, seed_hi, env, epoch);
+  s.p = {r.p[0], r.p[1], r.p[2]};
+  s.v = {r.v[0], r.v[1], r.v[2]};
+  s.q = {r.q[0], r.q[1], r.q[2], r.q[3]};
+  s.w = {0.f, 0.f, 0.f};
+  float hv = hover_per_motor(m, NROT);
+#pragma unroll
+  for (int k = 0; k < NROT; ++k) u[k] = hv;
+}
+
+// Appends the envs whose predicate is set to the compact list: one ballot and
+// one atomicAdd per warp, ranks from __popc of the lower lanes. Every lane of
+// the warp must call it.
+__device__ __forceinline__ void append_compact(bool pred, uint32_t env, uint32_t* ids, uint32_t* count) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+  if (mask == 0u) return;
+  const int leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if ((int)lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (pred) ids[base + __popc(mask & ((1u << lane) - 1u))] = env;
+}
+
+// Box accessors of the per-vehicle loop. SmemBoxes reads the thread's
+// staged record (box k = 10 floats at sm + k * stride, five 8-byte loads);
+// GlobalBoxes reads structure-of-arrays rows [k * 10 + f][n] at one index.
+struct SmemBoxes {
+  const float* sm;
+  int stride;
+  __device__ __forceinline__ void get(int k, V3& c, V3& h, Q4& q) const {
+    const float2* bx = reinterpret_cast<const float2*>(sm + k * stride);
+    const float2 a0 = bx[0], a1 = bx[1], a2 = bx[2], a3 = bx[3], a4 = bx[4];
+    c = {a0.x, a0.y, a1.x};
+    h = {a1.y, a2.x, a2.y};
+    q = {a3.x, a3.y, a4.x, a4.y};
+  }
+};
+
+struct GlobalBoxes {
+  const float* __restrict__ rows;  // [n_obs * 10][n]
+  uint32_t n, idx;
+  __device__ __forceinline__ float at(int r) const { return __ldg(rows + (size_t)r * n + idx); }
+  __device__ __forceinline__ void get(int k, V3& c, V3& h, Q4& q) const {
+    const int r = k * 10;
+    c = {at(r), at(r + 1), at(r + 2)};
+    h = {at(r + 3), at(r + 4), at(r + 5)};
+    q = {at(r + 6), at(r + 7), at(r + 8), at(r + 9)};
+  }
+};
+
+// The per-vehicle body of the fused kernels, specialised on the rotor count:
+// n_steps steps of `substeps` substeps, then the sphere-vs-box test against
+// n_obs boxes and, on a hit, the Philox reset keyed (seed_lo, seed_hi).
+template <int NROT, int INTEG, bool DRAG, class Boxes>
+__device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, int n_steps,
+                                         int substeps, int n_obs, const Boxes& boxes, uint32_t seed_lo,
+                                         uint32_t seed_hi, uint32_t& resets, bool& any_hit) {
+  const uint32_t n = fb.n;
+  VState s = load_state(fb.state, n, env);
+  normalize(s.q);
+  float u[NROT];
+#pragma unroll
+  for (int k = 0; k < NROT; ++k) u[k] = fb.motors[k * n + env];
+  const Body b = load_body(fb.body, n, env);
+  const Command cm = load_command(fb, env);
+  uint32_t epoch = fb.epoch[env];
+  for (int step = 0; step < n_steps; ++step) {
+    for (int ss = 0; ss < substeps; ++ss) {
+      V3 b3;
+      Wrench4 W = allocate<NROT>(controller(s, cm, b, P, b3), u, P);
+      integrate<INTEG, DRAG>(s, b3, W, b, P);
+    }
+    if (n_obs > 0) {
+      bool hit = false;
+#pragma unroll 4
+      for (int k = 0; k < n_obs; ++k) {
+        V3 c, h;
+        Q4 q;
+        boxes.get(k, c, h, q);
+        hit |= sphere_hits_box(s.p, P.r2, c, h, q);
+      }
+      if (hit) {
+        any_hit = true;
+        resets += 1;
+        epoch += 1;
+        reset_in_registers<NROT>(s, u, b.m, env, epoch, seed_lo, seed_hi);
+      }
+    }
+  }
+  store_state(fb.state, n, env, s);
+#pragma unroll
+  for (int k = 0; k < NROT; ++k) fb.motors[k * n + env] = u[k];
+  fb.epoch[env] = epoch;
+}
+
+}  // namespace agk
