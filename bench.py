@@ -7,7 +7,7 @@ STEPS_PER_CALL simulated steps (all stages: controller, allocation, motor
 lag, RK4, renormalisation, sphere-vs-box test, Philox resets, compaction).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--envs N_ENVS] [--steps-per-call C] [--parts fused,plain,e2e,paper]
+                    [--envs N_ENVS] [--steps-per-call C] [--parts fused,plain,e2e,paper,adjoint,serve]
 
 --envs / --steps-per-call / --parts run a reduced case of the same workload
 (for profiler captures); the default is the full workload and every part.
@@ -264,6 +264,10 @@ def gpu_arm(args) -> dict | None:
                               "paper_hardware": "2x RTX 3090 + TR PRO 3975WX (Isaac Gym/PhysX)"}
         fs.close()
     fl.close()
+    if "adjoint" in parts:
+        out["adjoint"] = adjoint_part(seed, world)
+    if "serve" in parts:
+        out["serving"] = serving_part(seed)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -292,6 +296,140 @@ def gpu_arm(args) -> dict | None:
     }
     res.update(out)
     return res
+
+
+# ----------------------------------------------------------------- adjoint --
+def adjoint_part(seed: int, world: int) -> dict:
+    """Differentiable rollout at 65,536 quads x 256 steps (position mode, SIE,
+    checkpoint every 32): recorded forward + hand-written adjoint."""
+    import torch
+    from paper_2305_16510_gb300 import _abi, workloads as W
+    w = W.WORKLOADS["adjoint"]
+    inp = W.make_inputs(w, seed)
+    fl = make_fleet(w, inp, seed)
+    n, H = w.n_envs, w.horizon
+    goal = torch.from_numpy(np.ascontiguousarray(inp.targets[0:3])).cuda()
+    loss = torch.empty(n, device="cuda")
+    gx = torch.empty((13, n), device="cuda")
+    gg = torch.empty(12, device="cuda")
+    x0, m0 = fl.state().clone(), fl.motors().clone()
+
+    def fwd_bwd():
+        fl.set_state(x0, m0)
+        _abi.ag_rollout_loss(fl.ctx, H, 1.0, 0.01, goal, loss)
+        _abi.ag_backward(fl.ctx, None, gx, gg, None)
+
+    for _ in range(3):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = 10
+    for _ in range(k):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    secs = max_over_ranks(time.perf_counter() - t0, world)
+    fl.close()
+    return {"value": n * H * k * world / secs, "unit": "vehicle-steps/s (forward + adjoint)",
+            "ms_per_rollout": secs * 1e3 / k,
+            "workload": "65,536 quads, position mode, SIE, horizon 256, checkpoint every 32 steps, "
+                        "gradients w.r.t. x0 (13/vehicle) and 12 gains"}
+
+
+# ----------------------------------------------------------------- serving --
+SERVE_LAMBDA = 200.0           # requests per second (Poisson arrivals)
+SERVE_REQUESTS = 2200          # 200 warm-up + 2,000 measured
+SERVE_WARMUP = 200
+SERVE_POOL = 1 << 19           # pool of environments requests take slices of
+SERVE_BUDGET = 40 << 30
+
+
+def serve_trace(n_req: int, seed: int = 7):
+    """Seeded request trace: exponential inter-arrivals, fleet log-uniform in
+    [256, 262144], horizon uniform in {50..2000}, obstacles from {0, 8, 32}."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / SERVE_LAMBDA, size=n_req))
+    n = np.floor(np.exp(rng.uniform(np.log(256), np.log(262144), size=n_req))).astype(int)
+    h = rng.integers(50, 2001, size=n_req)
+    obs = rng.choice([0, 8, 32], size=n_req)
+    off = (rng.uniform(size=n_req) * (SERVE_POOL - n)).astype(int)
+    return [dict(t=float(t[i]), n=int(n[i]), h=int(h[i]), obs=int(obs[i]), off=int(off[i]), seed=1000 + i)
+            for i in range(n_req)]
+
+
+def run_trace(server, pool, trace, warm: int, cap_s: float) -> dict:
+    """Replays the trace in real time against one server; returns latency and
+    throughput of the requests after the warm-up that completed within cap_s."""
+    t0 = time.perf_counter() + 0.2
+    ids = [None] * len(trace)
+    stop = threading.Event()
+
+    def submitter():
+        for i, r in enumerate(trace):
+            delay = t0 + r["t"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if stop.is_set() or time.perf_counter() - t0 > cap_s:
+                break
+            ids[i] = server.submit(pool.request(r["n"], r["h"], r["obs"], r["seed"], r["off"]))
+
+    th = threading.Thread(target=submitter, daemon=True)
+    th.start()
+    lat, done_at = {}, {}
+    for i in range(len(trace)):
+        while ids[i] is None and th.is_alive():
+            time.sleep(0.0002)
+        if ids[i] is None:
+            break
+        left = cap_s - (time.perf_counter() - t0)
+        if left <= 0:
+            break
+        try:
+            _, _, l = server.wait(ids[i], timeout_s=left, want_state=False)
+        except Exception:
+            break
+        lat[i] = l
+        done_at[i] = time.perf_counter() - t0
+    stop.set()
+    th.join()
+    meas = [i for i in range(warm, len(trace)) if i in lat]
+    submitted = sum(1 for x in ids if x is not None)
+    if not meas:
+        return {"completed": 0, "submitted": submitted}
+    t_begin = trace[warm]["t"]
+    t_end = max(done_at[i] for i in meas)
+    work = sum(trace[i]["n"] * trace[i]["h"] for i in meas)
+    L = np.array([lat[i] for i in meas])
+    return {"value": work / (t_end - t_begin), "unit": UNIT, "p50_ms": float(np.percentile(L, 50)),
+            "p99_ms": float(np.percentile(L, 99)), "mean_ms": float(L.mean()), "completed": len(meas),
+            "measured_of": len(trace) - warm, "submitted": submitted, "window_s": t_end - t_begin}
+
+
+def serving_part(seed: int) -> dict:
+    from paper_2305_16510_gb300 import workloads as W
+    from paper_2305_16510_gb300.serving import RequestPool, Server
+    w = W.Workload("pool", SERVE_POOL, 4, 1, 32, SERVE_POOL, 0, 0,
+                   mode_mix=(W.MODE_POSITION, W.MODE_BODY_VEL, W.MODE_ATT_THRUST))
+    inp = W.make_inputs(w, seed)
+    pool = RequestPool(inp.modes, inp.targets, inp.boxes.reshape(32 * 10, SERVE_POOL))
+    del inp
+    trace = serve_trace(SERVE_REQUESTS)
+    out = {"workload": (f"Poisson {SERVE_LAMBDA:.0f} req/s, {SERVE_REQUESTS} requests ({SERVE_WARMUP} warm-up), "
+                        "fleet log-uniform [256, 262144] quads, horizon U{50..2000} steps, modes mixed, "
+                        "obstacles {0, 8, 32}, RK4 4 substeps, 40 GB budget, 50 steps per launch"),
+           "offered_vehicle_steps_per_s": sum(r["n"] * r["h"] for r in trace) / trace[-1]["t"]}
+    with Server(max_active=1024, chunk_steps=50, hbm_budget_bytes=SERVE_BUDGET) as srv:
+        out["batched"] = run_trace(srv, pool, trace, SERVE_WARMUP, cap_s=120.0)
+        st = srv.stats()
+        out["batched"]["launches"] = int(st.launches)
+        out["batched"]["gpu_busy_s"] = st.gpu_ms / 1e3
+    with Server(max_active=1, chunk_steps=50, hbm_budget_bytes=SERVE_BUDGET) as srv:
+        out["one_per_launch"] = run_trace(srv, pool, trace, SERVE_WARMUP, cap_s=30.0)
+        st = srv.stats()
+        out["one_per_launch"]["launches"] = int(st.launches)
+    b, o = out["batched"], out["one_per_launch"]
+    if b.get("value") and o.get("value"):
+        out["batched_over_one_per_launch"] = b["value"] / o["value"]
+    return out
 
 
 # ------------------------------------------------- CPU oracle (baseline) ----
@@ -358,7 +496,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--envs", type=int, default=0, help="reduced fleet size (default: the full workload)")
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
-    ap.add_argument("--parts", default="fused,plain,e2e,paper")
+    ap.add_argument("--parts", default="fused,plain,e2e,paper,adjoint,serve")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
