@@ -299,10 +299,7 @@ __device__ __forceinline__ void store_x(float* st, float* mot, uint32_t n, uint3
 }
 
 __device__ __forceinline__ Body body_at(const float* bd, uint32_t n, uint32_t i) {
-  Body b;
-  b.m = bd[i]; b.jx = bd[n + i]; b.jy = bd[2 * n + i]; b.jz = bd[3 * n + i];
-  b.inv_m = 1.f / b.m; b.ijx = 1.f / b.jx; b.ijy = 1.f / b.jy; b.ijz = 1.f / b.jz;
-  return b;
+  return make_body(bd[i], bd[n + i], bd[2 * n + i], bd[3 * n + i]);
 }
 
 __device__ __forceinline__ int rotors_of(const AdjointBuffers& ab, uint32_t i) {

@@ -28,7 +28,12 @@
 //     R e_3 (q is unit there: it was renormalised after the last substep);
 //   * the body z axis of a non-unit quaternion (RK4 stages) is the
 //     homogeneous quaternion form divided by |q|^2, which equals the axis of
-//     q / |q| exactly.
+//     q / |q| exactly;
+//   * with the diagonal inertia, Omega x J Omega is written in principal
+//     axes, ((Jz - Jy) wy wz, (Jx - Jz) wz wx, (Jy - Jx) wx wy), and J^-1 M is
+//     formed once per substep (the wrench is held over the RK4 stages);
+//   * the factor 1/2 of q' = 1/2 q (x) (0, Omega) is folded into the RK4
+//     stage weights (multiplications by powers of two are exact).
 #pragma once
 
 #include <cstdint>
@@ -45,7 +50,19 @@ struct V3 { float x, y, z; };
 struct Q4 { float w, x, y, z; };
 struct VState { V3 p, v; Q4 q; V3 w; };
 struct Wrench4 { float f, mx, my, mz; };
-struct Body { float m, inv_m, jx, jy, jz, ijx, ijy, ijz; };
+// Rigid-body parameters of one vehicle. With a diagonal inertia the
+// gyroscopic term is Omega x J Omega = (gx wy wz, gy wz wx, gz wx wy), where
+// (gx, gy, gz) = (Jz - Jy, Jx - Jz, Jy - Jx); (ex, ey, ez) = g / J.
+struct Body { float m, inv_m, jx, jy, jz, ijx, ijy, ijz, gx, gy, gz, ex, ey, ez; };
+
+__device__ __forceinline__ Body make_body(float m, float jx, float jy, float jz) {
+  Body b;
+  b.m = m; b.jx = jx; b.jy = jy; b.jz = jz;
+  b.inv_m = 1.f / m; b.ijx = 1.f / jx; b.ijy = 1.f / jy; b.ijz = 1.f / jz;
+  b.gx = jz - jy; b.gy = jx - jz; b.gz = jy - jx;
+  b.ex = b.gx * b.ijx; b.ey = b.gy * b.ijy; b.ez = b.gz * b.ijz;
+  return b;
+}
 
 // Gains, rotor matrices and integration constants of one launch; passed by
 // value as a kernel parameter (it lives in the constant bank).
@@ -184,8 +201,8 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
   V3 eR = {0.5f * (Eij(2, 1) - Eij(1, 2)), 0.5f * (Eij(0, 2) - Eij(2, 0)), 0.5f * (Eij(1, 0) - Eij(0, 1))};
   // Eq. 4 with R^T R_d Omega_d = rate R^T e_3
   V3 eW = {s.w.x - rate * R[2][0], s.w.y - rate * R[2][1], s.w.z - rate * R[2][2]};
-  V3 JW = {b.jx * s.w.x, b.jy * s.w.y, b.jz * s.w.z};
-  V3 gyro = cross(s.w, JW);
+  // Eq. 5's Omega x J Omega in principal axes
+  const V3 gyro = {b.gx * (s.w.y * s.w.z), b.gy * (s.w.z * s.w.x), b.gz * (s.w.x * s.w.y)};
   return {f, -P.kR[0] * eR.x - P.kW[0] * eW.x + gyro.x, -P.kR[1] * eR.y - P.kW[1] * eW.y + gyro.y,
           -P.kR[2] * eR.z - P.kW[2] * eW.z + gyro.z};
 }
@@ -209,40 +226,13 @@ __device__ __forceinline__ Wrench4 allocate(const Wrench4& cmd, float (&u)[NROT]
   return W;
 }
 
-// Rigid-body derivatives under a fixed wrench, given the body z axis b3 of
-// the attitude (R(q / |q|) e_3). DRAG = false drops the (zero) drag terms.
-struct Deriv { V3 dp, dv; Q4 dq; V3 dw; };
-
-template <bool DRAG>
-__device__ __forceinline__ Deriv derivatives_b3(const VState& s, V3 b3, const Wrench4& W, const Body& b, float drag) {
-  const Q4& q = s.q;
-  const float fm = W.f * b.inv_m;
-  Deriv d;
-  d.dp = s.v;
-  d.dv = {fm * b3.x, fm * b3.y, fm * b3.z - kGravity};
-  if (DRAG) {
-    const float dm = drag * b.inv_m;
-    d.dv = {d.dv.x - dm * s.v.x, d.dv.y - dm * s.v.y, d.dv.z - dm * s.v.z};
-  }
-  d.dq = {-0.5f * (q.x * s.w.x + q.y * s.w.y + q.z * s.w.z), 0.5f * (q.w * s.w.x + q.y * s.w.z - q.z * s.w.y),
-          0.5f * (q.w * s.w.y - q.x * s.w.z + q.z * s.w.x), 0.5f * (q.w * s.w.z + q.x * s.w.y - q.y * s.w.x)};
-  V3 JW = {b.jx * s.w.x, b.jy * s.w.y, b.jz * s.w.z};
-  V3 g = cross(s.w, JW);
-  d.dw = {b.ijx * (W.mx - g.x), b.ijy * (W.my - g.y), b.ijz * (W.mz - g.z)};
-  return d;
-}
-
 // Body z axis of a possibly non-unit quaternion: the homogeneous form over |q|^2.
 __device__ __forceinline__ V3 body_z(const Q4& q) {
   float n2 = q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z;
   float inv = __fdividef(1.f, n2);
-  return {inv * 2.f * (q.x * q.z + q.w * q.y), inv * 2.f * (q.y * q.z - q.w * q.x),
+  float inv2 = 2.f * inv;
+  return {inv2 * (q.x * q.z + q.w * q.y), inv2 * (q.y * q.z - q.w * q.x),
           inv * (q.w * q.w - q.x * q.x - q.y * q.y + q.z * q.z)};
-}
-
-template <bool DRAG>
-__device__ __forceinline__ Deriv derivatives(const VState& s, const Wrench4& W, const Body& b, float drag) {
-  return derivatives_b3<DRAG>(s, body_z(s.q), W, b, drag);
 }
 
 __device__ __forceinline__ void normalize(Q4& q) {
@@ -250,47 +240,89 @@ __device__ __forceinline__ void normalize(Q4& q) {
   q.w *= r; q.x *= r; q.y *= r; q.z *= r;
 }
 
-__device__ __forceinline__ VState advance(const VState& s, float h, const Deriv& d) {
-  VState r;
-  r.p = s.p + h * d.dp;
-  r.v = s.v + h * d.dv;
-  r.q = {s.q.w + h * d.dq.w, s.q.x + h * d.dq.x, s.q.y + h * d.dq.y, s.q.z + h * d.dq.z};
-  r.w = s.w + h * d.dw;
-  return r;
+// q (x) (0, w): twice the quaternion rate q' = 1/2 q (x) (0, Omega)
+__device__ __forceinline__ Q4 quat_rate2(const Q4& q, const V3& w) {
+  return {-(q.x * w.x + q.y * w.y + q.z * w.z), q.w * w.x + q.y * w.z - q.z * w.y, q.w * w.y - q.x * w.z + q.z * w.x,
+          q.w * w.z + q.x * w.y - q.y * w.x};
 }
 
-// Semi-implicit Euler: v, Omega from the derivatives; p, q from the updated
+// The rigid-body rates under the wrench held over a substep:
+//   v' = fm b3 - (c/m) v + g,  Omega' = J^-1 M - e (wy wz, wz wx, wx wy)
+// with fm = f / m and aw = J^-1 M computed once per substep (Euler's
+// equations in principal axes).
+template <bool DRAG>
+__device__ __forceinline__ V3 accel(V3 b3, V3 v, float fm, float dm) {
+  V3 a = {fm * b3.x, fm * b3.y, fm * b3.z - kGravity};
+  if (DRAG) a = {a.x - dm * v.x, a.y - dm * v.y, a.z - dm * v.z};
+  return a;
+}
+
+__device__ __forceinline__ V3 ang_accel(V3 w, V3 aw, const Body& b) {
+  return {aw.x - b.ex * (w.y * w.z), aw.y - b.ey * (w.z * w.x), aw.z - b.ez * (w.x * w.y)};
+}
+
+// Semi-implicit Euler: v, Omega from the rates; p, q from the updated
 // velocities; renormalise q. b3 is R e_3 of the (unit) start attitude.
 template <bool DRAG>
 __device__ __forceinline__ void step_sie(VState& s, V3 b3, const Wrench4& W, const Body& b, float drag, float h) {
-  Deriv d = derivatives_b3<DRAG>(s, b3, W, b, drag);
-  s.v = s.v + h * d.dv;
-  s.w = s.w + h * d.dw;
+  const float fm = W.f * b.inv_m, dm = drag * b.inv_m;
+  const V3 aw = {b.ijx * W.mx, b.ijy * W.my, b.ijz * W.mz};
+  const V3 dv = accel<DRAG>(b3, s.v, fm, dm);
+  const V3 dw = ang_accel(s.w, aw, b);
+  s.v = s.v + h * dv;
+  s.w = s.w + h * dw;
   s.p = s.p + h * s.v;
-  float hh = 0.5f * h;
-  Q4 q = s.q;
-  s.q = {q.w - hh * (q.x * s.w.x + q.y * s.w.y + q.z * s.w.z), q.x + hh * (q.w * s.w.x + q.y * s.w.z - q.z * s.w.y),
-         q.y + hh * (q.w * s.w.y - q.x * s.w.z + q.z * s.w.x), q.z + hh * (q.w * s.w.z + q.x * s.w.y - q.y * s.w.x)};
+  const float hh = 0.5f * h;
+  const Q4 r = quat_rate2(s.q, s.w);
+  s.q = {s.q.w + hh * r.w, s.q.x + hh * r.x, s.q.y + hh * r.y, s.q.z + hh * r.z};
   normalize(s.q);
 }
 
-// Classic RK4 with the wrench held over the stages; renormalise q. The
-// first stage uses the start attitude's b3 (unit q).
+// Classic RK4 on (p, v, q, Omega) with the wrench held over the stages;
+// renormalise q. The first stage uses the start attitude's b3 (unit q). The
+// factor 1/2 of the quaternion rate is folded into the stage weights.
 template <bool DRAG>
 __device__ __forceinline__ void step_rk4(VState& s, V3 b3, const Wrench4& W, const Body& b, float drag, float h) {
-  float hh = 0.5f * h;
-  Deriv k = derivatives_b3<DRAG>(s, b3, W, b, drag);
-  Deriv acc = k;
-  k = derivatives<DRAG>(advance(s, hh, k), W, b, drag);
-  acc.dp = acc.dp + 2.f * k.dp; acc.dv = acc.dv + 2.f * k.dv; acc.dw = acc.dw + 2.f * k.dw;
-  acc.dq = {acc.dq.w + 2.f * k.dq.w, acc.dq.x + 2.f * k.dq.x, acc.dq.y + 2.f * k.dq.y, acc.dq.z + 2.f * k.dq.z};
-  k = derivatives<DRAG>(advance(s, hh, k), W, b, drag);
-  acc.dp = acc.dp + 2.f * k.dp; acc.dv = acc.dv + 2.f * k.dv; acc.dw = acc.dw + 2.f * k.dw;
-  acc.dq = {acc.dq.w + 2.f * k.dq.w, acc.dq.x + 2.f * k.dq.x, acc.dq.y + 2.f * k.dq.y, acc.dq.z + 2.f * k.dq.z};
-  k = derivatives<DRAG>(advance(s, h, k), W, b, drag);
-  acc.dp = acc.dp + k.dp; acc.dv = acc.dv + k.dv; acc.dw = acc.dw + k.dw;
-  acc.dq = {acc.dq.w + k.dq.w, acc.dq.x + k.dq.x, acc.dq.y + k.dq.y, acc.dq.z + k.dq.z};
-  s = advance(s, h * (1.f / 6.f), acc);
+  const float fm = W.f * b.inv_m, dm = drag * b.inv_m;
+  const V3 aw = {b.ijx * W.mx, b.ijy * W.my, b.ijz * W.mz};
+  const float h2 = 0.5f * h, h4 = 0.25f * h;
+  // stage 1; the accumulators collect k1 + 2 k2 + 2 k3 + k4
+  V3 a = accel<DRAG>(b3, s.v, fm, dm);
+  V3 al = ang_accel(s.w, aw, b);
+  Q4 r = quat_rate2(s.q, s.w);
+  V3 sp = s.v, sv = a, sw = al;
+  Q4 sq = r;
+  // stages 2 and 3 (t + h/2, each from the previous stage's rates)
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const V3 v = s.v + h2 * a, w = s.w + h2 * al;
+    const Q4 q = {s.q.w + h4 * r.w, s.q.x + h4 * r.x, s.q.y + h4 * r.y, s.q.z + h4 * r.z};
+    a = accel<DRAG>(body_z(q), v, fm, dm);
+    al = ang_accel(w, aw, b);
+    r = quat_rate2(q, w);
+    sp = sp + 2.f * v;
+    sv = sv + 2.f * a;
+    sw = sw + 2.f * al;
+    sq = {sq.w + 2.f * r.w, sq.x + 2.f * r.x, sq.y + 2.f * r.y, sq.z + 2.f * r.z};
+  }
+  // stage 4 (t + h, from stage 3's rates)
+  {
+    const V3 v = s.v + h * a, w = s.w + h * al;
+    const Q4 q = {s.q.w + h2 * r.w, s.q.x + h2 * r.x, s.q.y + h2 * r.y, s.q.z + h2 * r.z};
+    a = accel<DRAG>(body_z(q), v, fm, dm);
+    al = ang_accel(w, aw, b);
+    r = quat_rate2(q, w);
+    sp = sp + v;
+    sv = sv + a;
+    sw = sw + al;
+    sq = {sq.w + r.w, sq.x + r.x, sq.y + r.y, sq.z + r.z};
+  }
+  // x + h/6 (k1 + 2 k2 + 2 k3 + k4); p' = v, q' = r / 2
+  const float h6 = h * (1.f / 6.f), h12 = h * (1.f / 12.f);
+  s.p = s.p + h6 * sp;
+  s.v = s.v + h6 * sv;
+  s.w = s.w + h6 * sw;
+  s.q = {s.q.w + h12 * sq.w, s.q.x + h12 * sq.x, s.q.y + h12 * sq.y, s.q.z + h12 * sq.z};
   normalize(s.q);
 }
 

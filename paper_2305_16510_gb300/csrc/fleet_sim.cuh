@@ -38,16 +38,7 @@ __device__ __forceinline__ void store_state(float* st, uint32_t n, uint32_t i, c
 }
 
 __device__ __forceinline__ Body load_body(const float* bd, uint32_t n, uint32_t i) {
-  Body b;
-  b.m = bd[0 * n + i];
-  b.jx = bd[1 * n + i];
-  b.jy = bd[2 * n + i];
-  b.jz = bd[3 * n + i];
-  b.inv_m = 1.f / b.m;
-  b.ijx = 1.f / b.jx;
-  b.ijy = 1.f / b.jy;
-  b.ijz = 1.f / b.jz;
-  return b;
+  return make_body(bd[0 * n + i], bd[1 * n + i], bd[2 * n + i], bd[3 * n + i]);
 }
 
 __device__ __forceinline__ Command load_command(const FleetBuffers& fb, uint32_t i) {
