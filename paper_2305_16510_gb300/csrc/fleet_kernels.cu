@@ -31,24 +31,32 @@ namespace {
 // reads only what it wrote, so no barrier is needed.
 template <int INTEG, bool QUAD_ONLY, bool DRAG>
 __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
-  extern __shared__ float sm_boxes[];  // [n_obs][blockDim.x][10]
+  extern __shared__ float2 sm_pairs[];  // [ceil(n_obs / 2)][10][blockDim.x] box pairs
   const int B = blockDim.x;
   const uint32_t slot = blockIdx.x * B + threadIdx.x;
   const bool active = slot < fb.n;
   const uint32_t env = active ? (fb.order ? fb.order[slot] : slot) : slot;
-  float* my = sm_boxes + threadIdx.x * 10;
+  float2* my = sm_pairs + threadIdx.x;
   if (active) {
     // slot-ordered copy when grouped (coalesced rows); env == slot otherwise
     const float* src = fb.order ? fb.boxes_slot : fb.boxes;
-    for (int k = 0; k < (int)fb.n_obs; ++k)
+    const int n_obs = (int)fb.n_obs;
+    for (int j = 0; j < (n_obs + 1) / 2; ++j) {
+      const int k0 = 2 * j, k1 = 2 * j + 1;
 #pragma unroll
-      for (int f = 0; f < 10; ++f) my[k * B * 10 + f] = src[((size_t)k * 10 + f) * fb.n + slot];
+      for (int f = 0; f < 10; ++f) {
+        const float a = src[((size_t)k0 * 10 + f) * fb.n + slot];
+        // padding box: centre 1e30, zero extents, identity orientation
+        const float b = k1 < n_obs ? src[((size_t)k1 * 10 + f) * fb.n + slot] : (f < 3 ? 1e30f : (f == 6 ? 1.f : 0.f));
+        my[(j * 10 + f) * B] = make_float2(a, b);
+      }
+    }
   }
   uint32_t resets = 0;
   bool any_hit = false;
   if (active) {
     const int nrot = QUAD_ONLY ? 4 : rotor_count(fb, env);
-    const SmemBoxes bx{my, B * 10};
+    const SmemBoxPairs bx{my, B};
     const int n_obs = (int)fb.n_obs;
     if (nrot == 4)
       simulate<4, INTEG, DRAG>(fb, P, env, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(256) k_plain_compact(FleetBuffers fb) {
 template <int INTEG, bool QUAD_ONLY, bool DRAG>
 cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
                            cudaStream_t st) {
-  const size_t smem = (size_t)fb.n_obs * 10 * B * sizeof(float);
+  const size_t smem = (size_t)((fb.n_obs + 1) / 2) * 10 * B * sizeof(float2);
   static bool attr_set = false;  // per instantiation; raise the dynamic shared-memory cap once
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_fused_step<INTEG, QUAD_ONLY, DRAG>,
@@ -259,7 +267,7 @@ int fused_block_size(int n_obs) {
   // Largest block in {128, 96, 64, 32} that maximises resident warps per SM
   // under 228 KB of shared memory (1 KB reserved per block) and ~96
   // registers per thread.
-  const int per_thread = n_obs * 10 * (int)sizeof(float);
+  const int per_thread = ((n_obs + 1) / 2) * 10 * (int)sizeof(float2);
   int best_b = 128, best_warps = -1;
   for (int b = 128; b >= 32; b -= 32) {
     const int smem_blocks = per_thread ? 233472 / (per_thread * b + 1024) : 32;
@@ -280,7 +288,7 @@ FusedTuning fused_tuning_from_env(int n_obs) {
   if (const char* v = std::getenv("AG_FUSED_ORDER")) t.sorted = std::strcmp(v, "identity") != 0;
   if (const char* v = std::getenv("AG_FUSED_BLOCK")) {
     int b = std::atoi(v);
-    if (b >= 32 && b <= 128 && b % 32 == 0 && (size_t)n_obs * 40 * b <= 200 * 1024) t.block = b;
+    if (b >= 32 && b <= 128 && b % 32 == 0 && (size_t)((n_obs + 1) / 2) * 80 * b <= 200 * 1024) t.block = b;
   }
   return t;
 }

@@ -75,30 +75,68 @@ __device__ __forceinline__ void append_compact(bool pred, uint32_t env, uint32_t
   if (pred) ids[base + __popc(mask & ((1u << lane) - 1u))] = env;
 }
 
-// Box accessors of the per-vehicle loop. SmemBoxes reads the thread's
-// staged record (box k = 10 floats at sm + k * stride, five 8-byte loads);
-// GlobalBoxes reads structure-of-arrays rows [k * 10 + f][n] at one index.
-struct SmemBoxes {
-  const float* sm;
-  int stride;
-  __device__ __forceinline__ void get(int k, V3& c, V3& h, Q4& q) const {
-    const float2* bx = reinterpret_cast<const float2*>(sm + k * stride);
-    const float2 a0 = bx[0], a1 = bx[1], a2 = bx[2], a3 = bx[3], a4 = bx[4];
-    c = {a0.x, a0.y, a1.x};
-    h = {a1.y, a2.x, a2.y};
-    q = {a3.x, a3.y, a4.x, a4.y};
+// Box sources of the per-vehicle loop; any_hit(p, r2, n_obs) runs the
+// sphere-vs-box test against all boxes of the environment.
+//
+// SmemBoxPairs: the thread's boxes staged in shared memory in pairs, laid out
+// as float2 [pair][field][thread] (field f of boxes 2j and 2j+1 side by side),
+// so one conflict-free 8-byte load fetches a field of two boxes and the test
+// runs on both at once with Blackwell's packed FP32x2 arithmetic. An odd box
+// count is padded with a box at 1e30 that cannot be touched.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+struct SmemBoxPairs {
+  const float2* sm;  // this thread's column: element (j * 10 + f) * B
+  int B;
+  __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
+    const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
+    bool hit = false;
+    const int pairs = (n_obs + 1) >> 1;
+#pragma unroll 2
+    for (int j = 0; j < pairs; ++j) {
+      const float2* f = sm + (size_t)j * 10 * B;
+      const float2 cx = f[0], cy = f[B], cz = f[2 * B], hx = f[3 * B], hy = f[4 * B], hz = f[5 * B];
+      const float2 qw = f[6 * B], ux = f[7 * B], uy = f[8 * B], uz = f[9 * B];
+      // v = p - c;  t = 2 u x v;  d = v - w t + u x t  (R_b^T (p - c))
+      const float2 vx = add2(px, neg2(cx)), vy = add2(py, neg2(cy)), vz = add2(pz, neg2(cz));
+      const float2 tx = mul2(dup2(2.f), fma2(uy, vz, neg2(mul2(uz, vy))));
+      const float2 ty = mul2(dup2(2.f), fma2(uz, vx, neg2(mul2(ux, vz))));
+      const float2 tz = mul2(dup2(2.f), fma2(ux, vy, neg2(mul2(uy, vx))));
+      const float2 dx = add2(fma2(neg2(qw), tx, vx), fma2(uy, tz, neg2(mul2(uz, ty))));
+      const float2 dy = add2(fma2(neg2(qw), ty, vy), fma2(uz, tx, neg2(mul2(ux, tz))));
+      const float2 dz = add2(fma2(neg2(qw), tz, vz), fma2(ux, ty, neg2(mul2(uy, tx))));
+      // excess over the half-extents, clamped at 0
+      const float2 ex = add2(make_float2(fabsf(dx.x), fabsf(dx.y)), neg2(hx));
+      const float2 ey = add2(make_float2(fabsf(dy.x), fabsf(dy.y)), neg2(hy));
+      const float2 ez = add2(make_float2(fabsf(dz.x), fabsf(dz.y)), neg2(hz));
+      const float2 mx = make_float2(fmaxf(ex.x, 0.f), fmaxf(ex.y, 0.f));
+      const float2 my = make_float2(fmaxf(ey.x, 0.f), fmaxf(ey.y, 0.f));
+      const float2 mz = make_float2(fmaxf(ez.x, 0.f), fmaxf(ez.y, 0.f));
+      const float2 e2 = fma2(mz, mz, fma2(my, my, mul2(mx, mx)));
+      hit |= !(r2 < e2.x) | !(r2 < e2.y);
+    }
+    return hit;
   }
 };
 
+// GlobalBoxes: structure-of-arrays rows [k * 10 + f][n] read at one index.
 struct GlobalBoxes {
   const float* __restrict__ rows;  // [n_obs * 10][n]
   uint32_t n, idx;
   __device__ __forceinline__ float at(int r) const { return __ldg(rows + (size_t)r * n + idx); }
-  __device__ __forceinline__ void get(int k, V3& c, V3& h, Q4& q) const {
-    const int r = k * 10;
-    c = {at(r), at(r + 1), at(r + 2)};
-    h = {at(r + 3), at(r + 4), at(r + 5)};
-    q = {at(r + 6), at(r + 7), at(r + 8), at(r + 9)};
+  __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
+    bool hit = false;
+#pragma unroll 4
+    for (int k = 0; k < n_obs; ++k) {
+      const int r = k * 10;
+      hit |= sphere_hits_box(p, r2, V3{at(r), at(r + 1), at(r + 2)}, V3{at(r + 3), at(r + 4), at(r + 5)},
+                             Q4{at(r + 6), at(r + 7), at(r + 8), at(r + 9)});
+    }
+    return hit;
   }
 };
 
@@ -125,14 +163,7 @@ __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParam
       integrate<INTEG, DRAG>(s, b3, W, b, P);
     }
     if (n_obs > 0) {
-      bool hit = false;
-#pragma unroll 4
-      for (int k = 0; k < n_obs; ++k) {
-        V3 c, h;
-        Q4 q;
-        boxes.get(k, c, h, q);
-        hit |= sphere_hits_box(s.p, P.r2, c, h, q);
-      }
+      const bool hit = boxes.any_hit(s.p, P.r2, n_obs);
       if (hit) {
         any_hit = true;
         resets += 1;
