@@ -24,7 +24,7 @@ struct ag_ctx {
   int device;
   agk::FleetBuffers fb;
   uint8_t* mask_dev;         // [n] staging for ag_reset masks
-  uint32_t* order_scratch;   // [24] key counts and cursors of the grouping permutation
+  uint32_t* order_scratch;   // per-block key counts / offsets of the grouping permutation
   uint64_t seed;             // Philox key of collision resets
   bool failed;
   std::string err;
@@ -292,7 +292,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = alloc(ctx, &f.hits, n);
   if (e == cudaSuccess) e = alloc(ctx, &ctx->mask_dev, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.order, n);
-  if (e == cudaSuccess) e = alloc(ctx, &ctx->order_scratch, 24);
+  if (e == cudaSuccess) e = alloc(ctx, &ctx->order_scratch, agk::order_scratch_words(cfg->n_envs));
   if (e != cudaSuccess) {
     g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
     cudaGetLastError();

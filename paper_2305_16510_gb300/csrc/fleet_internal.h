@@ -45,8 +45,9 @@ cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int i
                               int substeps, cudaStream_t st);
 
 // Builds fb.order from the current modes and rotor types (3 small launches;
-// scratch24 is 24 words of device scratch), then refreshes fb.boxes_slot.
-cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch24, cudaStream_t st);
+// scratch holds order_scratch_words(n) words), then refreshes fb.boxes_slot.
+cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch, cudaStream_t st);
+size_t order_scratch_words(uint32_t n);
 
 // Refreshes fb.boxes_slot from fb.boxes and fb.order (after the boxes change).
 cudaError_t launch_permute_boxes(const FleetBuffers& fb, cudaStream_t st);

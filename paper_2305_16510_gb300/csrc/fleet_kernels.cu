@@ -69,34 +69,96 @@ __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams 
   append_compact(resets > 0u, env, fb.reset_ids, fb.n_reset);
 }
 
-// Grouping permutation: key = rotor-type index * 4 + mode (12 keys). Pass 1
-// counts keys, pass 2 turns the counts into start offsets, pass 3 scatters
-// every env to its key's range (order inside a range is arbitrary; each env
-// appears exactly once).
+// Grouping permutation: key = rotor-type index * 4 + mode (12 keys), a
+// stable partition of the environments by key (inside a key the env ids
+// stay increasing, so a warp of slots touches few cache lines). Pass 1
+// counts each key per 256-env block; pass 2 (one block) turns the counts into
+// each block's start offset per key, keys in order and blocks in order; pass 3
+// ranks each env inside its warp with __match_any_sync, adds the preceding
+// warps' counts and writes order[position] = env.
+constexpr int kOrderBlock = 256;
+
 __device__ __forceinline__ uint32_t order_key(const FleetBuffers& fb, uint32_t i) {
   const int nrot = rotor_count(fb, i);
   const uint32_t m = fb.modes[i] > 3 ? 3u : fb.modes[i];
   return (uint32_t)(nrot == 4 ? 0 : (nrot == 6 ? 1 : 2)) * 4u + m;
 }
 
-__global__ void __launch_bounds__(256) k_order_count(FleetBuffers fb, uint32_t* counts) {
+__global__ void __launch_bounds__(kOrderBlock) k_order_count(FleetBuffers fb, uint32_t* counts) {
   __shared__ uint32_t h[12];
   if (threadIdx.x < 12) h[threadIdx.x] = 0;
   __syncthreads();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < fb.n) atomicAdd(&h[order_key(fb, i)], 1u);
   __syncthreads();
-  if (threadIdx.x < 12 && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+  if (threadIdx.x < 12) counts[(size_t)blockIdx.x * 12 + threadIdx.x] = h[threadIdx.x];
 }
 
-__global__ void k_order_offsets(uint32_t* counts, uint32_t* cursor) {
-  if (threadIdx.x == 0) {
+// One block of kScanThreads threads: thread t owns a contiguous run of env blocks.
+constexpr int kScanThreads = 512;
+
+__global__ void __launch_bounds__(kScanThreads) k_order_offsets(uint32_t* counts, uint32_t n_blocks) {
+  __shared__ uint32_t part[kScanThreads][12];
+  __shared__ uint32_t key_base[12];
+  const uint32_t per = (n_blocks + kScanThreads - 1) / kScanThreads;
+  const uint32_t b0 = threadIdx.x * per, b1 = min(n_blocks, b0 + per);
+  uint32_t sum[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) sum[k] = 0;
+  for (uint32_t b = b0; b < b1; ++b)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sum[k] += counts[(size_t)b * 12 + k];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) part[threadIdx.x][k] = sum[k];
+  __syncthreads();
+  if (threadIdx.x < 12) {  // exclusive scan of the partial sums of key k
+    const int k = threadIdx.x;
+    uint32_t run = 0;
+    for (int t = 0; t < kScanThreads; ++t) {
+      const uint32_t c = part[t][k];
+      part[t][k] = run;
+      run += c;
+    }
+    key_base[k] = run;  // total of key k
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // keys in order
     uint32_t run = 0;
     for (int k = 0; k < 12; ++k) {
-      cursor[k] = run;
-      run += counts[k];
+      const uint32_t c = key_base[k];
+      key_base[k] = run;
+      run += c;
     }
   }
+  __syncthreads();
+  uint32_t run[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) run[k] = key_base[k] + part[threadIdx.x][k];
+  for (uint32_t b = b0; b < b1; ++b)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const uint32_t c = counts[(size_t)b * 12 + k];
+      counts[(size_t)b * 12 + k] = run[k];
+      run[k] += c;
+    }
+}
+
+__global__ void __launch_bounds__(kOrderBlock) k_order_scatter(FleetBuffers fb, const uint32_t* offsets) {
+  __shared__ uint32_t warp_count[kOrderBlock / 32][12];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool active = i < fb.n;
+  const uint32_t key = active ? order_key(fb, i) : 12u;
+  const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
+  const uint32_t rank = __popc(same & ((1u << lane) - 1u));
+  if (lane < 12) warp_count[warp][lane] = 0;
+  __syncwarp();
+  if (active && rank == 0) warp_count[warp][key] = __popc(same);
+  __syncthreads();
+  if (!active) return;
+  uint32_t before = 0;
+  for (int w = 0; w < warp; ++w) before += warp_count[w][key];
+  fb.order[offsets[(size_t)blockIdx.x * 12 + key] + before + rank] = i;
 }
 
 __global__ void __launch_bounds__(256) k_permute_boxes(FleetBuffers fb) {
@@ -105,22 +167,6 @@ __global__ void __launch_bounds__(256) k_permute_boxes(FleetBuffers fb) {
   const uint32_t env = fb.order[slot];
   const size_t rows = (size_t)fb.n_obs * 10;
   for (size_t r = 0; r < rows; ++r) fb.boxes_slot[r * fb.n + slot] = fb.boxes[r * fb.n + env];
-}
-
-__global__ void __launch_bounds__(256) k_order_scatter(FleetBuffers fb, uint32_t* cursor) {
-  __shared__ uint32_t h[12], base[12];
-  if (threadIdx.x < 12) h[threadIdx.x] = 0;
-  __syncthreads();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t key = 0, rank = 0;
-  if (i < fb.n) {
-    key = order_key(fb, i);
-    rank = atomicAdd(&h[key], 1u);
-  }
-  __syncthreads();
-  if (threadIdx.x < 12 && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], h[threadIdx.x]);
-  __syncthreads();
-  if (i < fb.n) fb.order[base[key] + rank] = i;
 }
 
 // ag_reset: resample masked environments, clear collided flags, list them.
@@ -304,17 +350,17 @@ cudaError_t launch_fused_step(const FleetBuffers& fb_in, const StepParams& P, in
                                  : launch_fused_i<kIntegSIE>(fb, P, n_steps, substeps, t.block, st);
 }
 
-cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch24, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(scratch24, 0, 24 * sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
-  const unsigned grid = (fb.n + 255) / 256;
-  k_order_count<<<grid, 256, 0, st>>>(fb, scratch24);
-  k_order_offsets<<<1, 32, 0, st>>>(scratch24, scratch24 + 12);
-  k_order_scatter<<<grid, 256, 0, st>>>(fb, scratch24 + 12);
-  e = cudaGetLastError();
+cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch, cudaStream_t st) {
+  const unsigned grid = (fb.n + kOrderBlock - 1) / kOrderBlock;
+  k_order_count<<<grid, kOrderBlock, 0, st>>>(fb, scratch);
+  k_order_offsets<<<1, kScanThreads, 0, st>>>(scratch, grid);
+  k_order_scatter<<<grid, kOrderBlock, 0, st>>>(fb, scratch);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_permute_boxes(fb, st);
 }
+
+size_t order_scratch_words(uint32_t n) { return (size_t)((n + kOrderBlock - 1) / kOrderBlock) * 12; }
 
 cudaError_t launch_permute_boxes(const FleetBuffers& fb, cudaStream_t st) {
   if (fb.n_obs == 0 || !fb.order || !fb.boxes_slot) return cudaSuccess;

@@ -130,7 +130,7 @@ size_t request_bytes(size_t n, size_t n_obs) {
   size_t b = 0;
   b += align256(13 * n * 4) + align256(8 * n * 4) + align256(4 * n * 4) + align256(4 * n * 4);
   b += align256(n) + align256(n * 4) + align256(n) + align256(n * 4) + align256(4) + align256(n * 4);
-  b += 2 * align256(n_obs * 10 * n * 4) + align256(24 * 4);
+  b += 2 * align256(n_obs * 10 * n * 4) + align256(order_scratch_words((uint32_t)n) * 4);
   return b;
 }
 
@@ -204,7 +204,7 @@ void carve(ag_server* s, ServeRequest* r) {
   f.order = (uint32_t*)take(n * 4);
   f.boxes = (float*)take(n_obs * 10 * n * 4);
   f.boxes_slot = (float*)take(n_obs * 10 * n * 4);
-  r->order_scratch = (uint32_t*)take(24 * 4);
+  r->order_scratch = (uint32_t*)take(agk::order_scratch_words((uint32_t)n) * 4);
   f.n = (uint32_t)n;
   f.n_quad = (uint32_t)n;
   f.n_obs = (uint32_t)n_obs;
