@@ -44,8 +44,8 @@ cudaError_t launch_reset(const FleetBuffers& fb, const uint8_t* mask, uint32_t s
 cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,
                               int substeps, cudaStream_t st);
 
-// Builds fb.order from the current modes and rotor types (3 small launches;
-// scratch holds order_scratch_words(n) words), then refreshes fb.boxes_slot.
+// Builds fb.order from the current modes and rotor types (one launch; scratch
+// holds order_scratch_words(n) words), then refreshes fb.boxes_slot.
 cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch, cudaStream_t st);
 size_t order_scratch_words(uint32_t n);
 

@@ -69,14 +69,16 @@ __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams 
   append_compact(resets > 0u, env, fb.reset_ids, fb.n_reset);
 }
 
-// Grouping permutation: key = rotor-type index * 4 + mode (12 keys), a
-// stable partition of the environments by key (inside a key the env ids
-// stay increasing, so a warp of slots touches few cache lines). Pass 1
-// counts each key per 256-env block; pass 2 (one block) turns the counts into
-// each block's start offset per key, keys in order and blocks in order; pass 3
-// ranks each env inside its warp with __match_any_sync, adds the preceding
-// warps' counts and writes order[position] = env.
-constexpr int kOrderBlock = 256;
+// Grouping permutation: key = rotor-type index * 4 + mode (12 keys). Slots
+// [w * W, (w + 1) * W) hold the environments of the same window, stably
+// partitioned by key: inside a window the controller's mode branches become
+// warp-uniform (at most one mixed warp per key boundary), and since a window's
+// envs are loaded by blocks that run at the same time, the sectors their
+// gathers share are served from L2 instead of being fetched again from DRAM.
+// One block per window: each env is ranked inside its warp with
+// __match_any_sync, then offset by the counts of lower keys in the window and
+// of its key in the preceding warps.
+constexpr int kOrderWindow = 1024;
 
 __device__ __forceinline__ uint32_t order_key(const FleetBuffers& fb, uint32_t i) {
   const int nrot = rotor_count(fb, i);
@@ -84,67 +86,9 @@ __device__ __forceinline__ uint32_t order_key(const FleetBuffers& fb, uint32_t i
   return (uint32_t)(nrot == 4 ? 0 : (nrot == 6 ? 1 : 2)) * 4u + m;
 }
 
-__global__ void __launch_bounds__(kOrderBlock) k_order_count(FleetBuffers fb, uint32_t* counts) {
-  __shared__ uint32_t h[12];
-  if (threadIdx.x < 12) h[threadIdx.x] = 0;
-  __syncthreads();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < fb.n) atomicAdd(&h[order_key(fb, i)], 1u);
-  __syncthreads();
-  if (threadIdx.x < 12) counts[(size_t)blockIdx.x * 12 + threadIdx.x] = h[threadIdx.x];
-}
-
-// One block of kScanThreads threads: thread t owns a contiguous run of env blocks.
-constexpr int kScanThreads = 512;
-
-__global__ void __launch_bounds__(kScanThreads) k_order_offsets(uint32_t* counts, uint32_t n_blocks) {
-  __shared__ uint32_t part[kScanThreads][12];
-  __shared__ uint32_t key_base[12];
-  const uint32_t per = (n_blocks + kScanThreads - 1) / kScanThreads;
-  const uint32_t b0 = threadIdx.x * per, b1 = min(n_blocks, b0 + per);
-  uint32_t sum[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) sum[k] = 0;
-  for (uint32_t b = b0; b < b1; ++b)
-#pragma unroll
-    for (int k = 0; k < 12; ++k) sum[k] += counts[(size_t)b * 12 + k];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) part[threadIdx.x][k] = sum[k];
-  __syncthreads();
-  if (threadIdx.x < 12) {  // exclusive scan of the partial sums of key k
-    const int k = threadIdx.x;
-    uint32_t run = 0;
-    for (int t = 0; t < kScanThreads; ++t) {
-      const uint32_t c = part[t][k];
-      part[t][k] = run;
-      run += c;
-    }
-    key_base[k] = run;  // total of key k
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {  // keys in order
-    uint32_t run = 0;
-    for (int k = 0; k < 12; ++k) {
-      const uint32_t c = key_base[k];
-      key_base[k] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  uint32_t run[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) run[k] = key_base[k] + part[threadIdx.x][k];
-  for (uint32_t b = b0; b < b1; ++b)
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const uint32_t c = counts[(size_t)b * 12 + k];
-      counts[(size_t)b * 12 + k] = run[k];
-      run[k] += c;
-    }
-}
-
-__global__ void __launch_bounds__(kOrderBlock) k_order_scatter(FleetBuffers fb, const uint32_t* offsets) {
-  __shared__ uint32_t warp_count[kOrderBlock / 32][12];
+__global__ void __launch_bounds__(kOrderWindow) k_order_window(FleetBuffers fb) {
+  __shared__ uint32_t warp_count[kOrderWindow / 32][12];
+  __shared__ uint32_t key_start[12];
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool active = i < fb.n;
@@ -155,10 +99,18 @@ __global__ void __launch_bounds__(kOrderBlock) k_order_scatter(FleetBuffers fb, 
   __syncwarp();
   if (active && rank == 0) warp_count[warp][key] = __popc(same);
   __syncthreads();
+  if (threadIdx.x == 0) {  // start of each key inside the window, keys in order
+    uint32_t run = 0;
+    for (int k = 0; k < 12; ++k) {
+      key_start[k] = run;
+      for (int w = 0; w < kOrderWindow / 32; ++w) run += warp_count[w][k];
+    }
+  }
+  __syncthreads();
   if (!active) return;
-  uint32_t before = 0;
+  uint32_t before = key_start[key];
   for (int w = 0; w < warp; ++w) before += warp_count[w][key];
-  fb.order[offsets[(size_t)blockIdx.x * 12 + key] + before + rank] = i;
+  fb.order[blockIdx.x * kOrderWindow + before + rank] = i;
 }
 
 __global__ void __launch_bounds__(256) k_permute_boxes(FleetBuffers fb) {
@@ -351,16 +303,17 @@ cudaError_t launch_fused_step(const FleetBuffers& fb_in, const StepParams& P, in
 }
 
 cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch, cudaStream_t st) {
-  const unsigned grid = (fb.n + kOrderBlock - 1) / kOrderBlock;
-  k_order_count<<<grid, kOrderBlock, 0, st>>>(fb, scratch);
-  k_order_offsets<<<1, kScanThreads, 0, st>>>(scratch, grid);
-  k_order_scatter<<<grid, kOrderBlock, 0, st>>>(fb, scratch);
+  (void)scratch;
+  k_order_window<<<(fb.n + kOrderWindow - 1) / kOrderWindow, kOrderWindow, 0, st>>>(fb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_permute_boxes(fb, st);
 }
 
-size_t order_scratch_words(uint32_t n) { return (size_t)((n + kOrderBlock - 1) / kOrderBlock) * 12; }
+size_t order_scratch_words(uint32_t n) {
+  (void)n;
+  return 1;
+}
 
 cudaError_t launch_permute_boxes(const FleetBuffers& fb, cudaStream_t st) {
   if (fb.n_obs == 0 || !fb.order || !fb.boxes_slot) return cudaSuccess;
