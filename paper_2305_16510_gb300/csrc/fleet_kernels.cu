@@ -70,15 +70,17 @@ __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams 
 }
 
 // Grouping permutation: key = rotor-type index * 4 + mode (12 keys). Slots
-// [w * W, (w + 1) * W) hold the environments of the same window, stably
+// [w * W, (w + 1) * W), W = 4,096, hold the environments of the same window, stably
 // partitioned by key: inside a window the controller's mode branches become
 // warp-uniform (at most one mixed warp per key boundary), and since a window's
 // envs are loaded by blocks that run at the same time, the sectors their
 // gathers share are served from L2 instead of being fetched again from DRAM.
-// One block per window: each env is ranked inside its warp with
-// __match_any_sync, then offset by the counts of lower keys in the window and
-// of its key in the preceding warps.
-constexpr int kOrderWindow = 1024;
+// One block per window: the key totals give each key's start; then, 1,024
+// envs at a time, each env is ranked inside its warp with __match_any_sync and
+// offset by its key's running position and the preceding warps' counts.
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderSub = 4;                                  // sub-windows per window
+constexpr int kOrderWindow = kOrderThreads * kOrderSub;       // 4,096 envs
 
 __device__ __forceinline__ uint32_t order_key(const FleetBuffers& fb, uint32_t i) {
   const int nrot = rotor_count(fb, i);
@@ -86,31 +88,52 @@ __device__ __forceinline__ uint32_t order_key(const FleetBuffers& fb, uint32_t i
   return (uint32_t)(nrot == 4 ? 0 : (nrot == 6 ? 1 : 2)) * 4u + m;
 }
 
-__global__ void __launch_bounds__(kOrderWindow) k_order_window(FleetBuffers fb) {
-  __shared__ uint32_t warp_count[kOrderWindow / 32][12];
-  __shared__ uint32_t key_start[12];
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kOrderThreads) k_order_window(FleetBuffers fb) {
+  __shared__ uint32_t warp_count[kOrderThreads / 32][12];
+  __shared__ uint32_t key_next[12];  // next free position of each key in the window
+  const uint32_t base = blockIdx.x * kOrderWindow;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool active = i < fb.n;
-  const uint32_t key = active ? order_key(fb, i) : 12u;
-  const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
-  const uint32_t rank = __popc(same & ((1u << lane) - 1u));
-  if (lane < 12) warp_count[warp][lane] = 0;
-  __syncwarp();
-  if (active && rank == 0) warp_count[warp][key] = __popc(same);
+  // pass 1: totals per key over the window -> start position of each key
+  if (threadIdx.x < 12) key_next[threadIdx.x] = 0;
   __syncthreads();
-  if (threadIdx.x == 0) {  // start of each key inside the window, keys in order
+  for (int sub = 0; sub < kOrderSub; ++sub) {
+    const uint32_t i = base + sub * kOrderThreads + threadIdx.x;
+    if (i < fb.n) atomicAdd(&key_next[order_key(fb, i)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     uint32_t run = 0;
     for (int k = 0; k < 12; ++k) {
-      key_start[k] = run;
-      for (int w = 0; w < kOrderWindow / 32; ++w) run += warp_count[w][k];
+      const uint32_t c = key_next[k];
+      key_next[k] = run;
+      run += c;
     }
   }
   __syncthreads();
-  if (!active) return;
-  uint32_t before = key_start[key];
-  for (int w = 0; w < warp; ++w) before += warp_count[w][key];
-  fb.order[blockIdx.x * kOrderWindow + before + rank] = i;
+  // pass 2: sub-window by sub-window, stable ranks inside each key
+  for (int sub = 0; sub < kOrderSub; ++sub) {
+    const uint32_t i = base + sub * kOrderThreads + threadIdx.x;
+    const bool active = i < fb.n;
+    const uint32_t key = active ? order_key(fb, i) : 12u;
+    const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
+    const uint32_t rank = __popc(same & ((1u << lane) - 1u));
+    if (lane < 12) warp_count[warp][lane] = 0;
+    __syncwarp();
+    if (active && rank == 0) warp_count[warp][key] = __popc(same);
+    __syncthreads();
+    if (active) {
+      uint32_t pos = key_next[key] + rank;
+      for (int w = 0; w < warp; ++w) pos += warp_count[w][key];
+      fb.order[base + pos] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {  // advance each key by its count in this sub-window
+      uint32_t c = 0;
+      for (int w = 0; w < kOrderThreads / 32; ++w) c += warp_count[w][threadIdx.x];
+      key_next[threadIdx.x] += c;
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(256) k_permute_boxes(FleetBuffers fb) {
@@ -304,7 +327,7 @@ cudaError_t launch_fused_step(const FleetBuffers& fb_in, const StepParams& P, in
 
 cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch, cudaStream_t st) {
   (void)scratch;
-  k_order_window<<<(fb.n + kOrderWindow - 1) / kOrderWindow, kOrderWindow, 0, st>>>(fb);
+  k_order_window<<<(fb.n + kOrderWindow - 1) / kOrderWindow, kOrderThreads, 0, st>>>(fb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_permute_boxes(fb, st);
