@@ -53,6 +53,11 @@ ALU_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # motors in+out (4 x 2), body (4), targets (4), mode (1 B), epoch in+out (2 x 4),
 # boxes (16 x 10 f32), collided flag (1 B), reset-list entry (4 B, upper bound)
 BYTES_PER_VEHICLE_LAUNCH = 4 * (26 + 8 + 4 + 4) + 1 + 8 + 4 * 160 + 1 + 4
+# DRAM traffic of one full-size fused launch (1,048,576 envs, 1,000 steps):
+# dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu capture of
+# exactly this launch (794.94 MB + 69.43 MB). It scales with the fleet size
+# (each env is loaded and stored once per launch), not with the step count.
+TRAFFIC_BYTES_FULL_LAUNCH = 794.94e6 + 69.43e6
 
 
 def dist_env():
@@ -285,7 +290,8 @@ def gpu_arm(args) -> dict | None:
                    "l2": "no flush: inputs exceed L2 (boxes 671 MB + state 55 MB per call)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / ALU_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved_tflops / ALU_PEAK_TFLOPS,
+                     "traffic": TRAFFIC_BYTES_FULL_LAUNCH if w.n_envs == 1 << 20 else None,
                      "kernel": "k_fused_step<RK4, quad>", "launch_ms": launch_ms,
                      "flop_per_vehicle_step": FLOP_PER_VEHICLE_STEP,
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",
