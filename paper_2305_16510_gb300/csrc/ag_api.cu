@@ -134,7 +134,8 @@ const char* validate(const ag_config* c) {
 size_t buffer_bytes(const ag_config* c) {
   size_t n = c->n_envs;
   size_t per = sizeof(float) * (13 + 8 + 4 + 4 + 4 + 4) + sizeof(uint32_t) * 4 + 3 /* modes, collided, hits */ + 1;
-  return n * per + 2 * (size_t)c->n_obstacles * 10 * n * sizeof(float) + sizeof(uint32_t);
+  return n * per + (size_t)c->n_obstacles * 10 * n * sizeof(float) +
+         agk::box_pair_elems(n, c->n_obstacles) * sizeof(float2) + sizeof(uint32_t);
 }
 
 }  // namespace
@@ -281,7 +282,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = alloc(ctx, &f.modes, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.targets, 4 * n);
   if (e == cudaSuccess) e = alloc(ctx, &f.boxes, (size_t)cfg->n_obstacles * 10 * n);
-  if (e == cudaSuccess) e = alloc(ctx, &f.boxes_slot, (size_t)cfg->n_obstacles * 10 * n);
+  if (e == cudaSuccess) e = alloc(ctx, &f.boxes_slot, agk::box_pair_elems(n, cfg->n_obstacles));
   if (e == cudaSuccess) e = alloc(ctx, &f.epoch, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.collided, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.reset_ids, n);
@@ -313,7 +314,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(f.targets, 0, 4 * n * sizeof(float), st);
   if (e == cudaSuccess && f.boxes) e = cudaMemsetAsync(f.boxes, 0, (size_t)cfg->n_obstacles * 10 * n * sizeof(float), st);
   if (e == cudaSuccess && f.boxes_slot)
-    e = cudaMemsetAsync(f.boxes_slot, 0, (size_t)cfg->n_obstacles * 10 * n * sizeof(float), st);
+    e = cudaMemsetAsync(f.boxes_slot, 0, agk::box_pair_elems(n, cfg->n_obstacles) * sizeof(float2), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.epoch, 0, n * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.collided, 0, n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.n_reset, 0, sizeof(uint32_t), st);

@@ -27,7 +27,8 @@ struct FleetBuffers {
   uint32_t* resets;    // [n]     resets of this call per env
   uint8_t* hits;       // [n]     collision of the current step
   uint32_t* order;     // [n]     thread slot -> env, grouped by rotor type and mode (NULL = identity)
-  float* boxes_slot;   // [n_obs][10][n] the boxes in slot order (boxes_slot[r][i] = boxes[r][order[i]])
+  float2* boxes_slot;  // [ceil(n_obs/2)][10][n] the boxes in slot order, in pairs: element
+                       // (j*10 + f)*n + i = (field f of box 2j, of box 2j+1) of env order[i]
   uint32_t n, n_quad, n_hexa, n_octo, n_obs;
 };
 
@@ -48,8 +49,11 @@ cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int i
 // holds order_scratch_words(n) words), then refreshes fb.boxes_slot.
 cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch, cudaStream_t st);
 size_t order_scratch_words(uint32_t n);
+// Elements (float2) of fb.boxes_slot for n envs with n_obs boxes each.
+inline size_t box_pair_elems(size_t n, size_t n_obs) { return (n_obs + 1) / 2 * 10 * n; }
 
 // Refreshes fb.boxes_slot from fb.boxes and fb.order (after the boxes change).
+// An odd box count is padded with a box at 1e30 that no sphere can touch.
 cudaError_t launch_permute_boxes(const FleetBuffers& fb, cudaStream_t st);
 
 // Threads per block of the fused kernel for a given obstacle count (the

@@ -38,17 +38,21 @@ __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams 
   const uint32_t env = active ? (fb.order ? fb.order[slot] : slot) : slot;
   float2* my = sm_pairs + threadIdx.x;
   if (active) {
-    // slot-ordered copy when grouped (coalesced rows); env == slot otherwise
-    const float* src = fb.order ? fb.boxes_slot : fb.boxes;
     const int n_obs = (int)fb.n_obs;
-    for (int j = 0; j < (n_obs + 1) / 2; ++j) {
-      const int k0 = 2 * j, k1 = 2 * j + 1;
+    const int pairs = (n_obs + 1) / 2;
+    if (fb.order) {
+      // the slot-ordered pair copy: coalesced 8-byte rows
+      for (int r = 0; r < pairs * 10; ++r) my[r * B] = fb.boxes_slot[(size_t)r * fb.n + slot];
+    } else {
+      // ungrouped (env == slot): pair up the env-ordered rows here
+      for (int j = 0; j < pairs; ++j) {
+        const int k0 = 2 * j, k1 = 2 * j + 1;
 #pragma unroll
-      for (int f = 0; f < 10; ++f) {
-        const float a = src[((size_t)k0 * 10 + f) * fb.n + slot];
-        // padding box: centre 1e30, zero extents, identity orientation
-        const float b = k1 < n_obs ? src[((size_t)k1 * 10 + f) * fb.n + slot] : (f < 3 ? 1e30f : (f == 6 ? 1.f : 0.f));
-        my[(j * 10 + f) * B] = make_float2(a, b);
+        for (int f = 0; f < 10; ++f) {
+          const float a = fb.boxes[((size_t)k0 * 10 + f) * fb.n + slot];
+          const float b = k1 < n_obs ? fb.boxes[((size_t)k1 * 10 + f) * fb.n + slot] : box_pad_field(f);
+          my[(j * 10 + f) * B] = make_float2(a, b);
+        }
       }
     }
   }
@@ -140,8 +144,16 @@ __global__ void __launch_bounds__(256) k_permute_boxes(FleetBuffers fb) {
   const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= fb.n) return;
   const uint32_t env = fb.order[slot];
-  const size_t rows = (size_t)fb.n_obs * 10;
-  for (size_t r = 0; r < rows; ++r) fb.boxes_slot[r * fb.n + slot] = fb.boxes[r * fb.n + env];
+  const int n_obs = (int)fb.n_obs;
+  for (int j = 0; j < (n_obs + 1) / 2; ++j) {
+    const int k0 = 2 * j, k1 = 2 * j + 1;
+#pragma unroll
+    for (int f = 0; f < 10; ++f) {
+      const float a = fb.boxes[((size_t)k0 * 10 + f) * fb.n + env];
+      const float b = k1 < n_obs ? fb.boxes[((size_t)k1 * 10 + f) * fb.n + env] : box_pad_field(f);
+      fb.boxes_slot[(size_t)(j * 10 + f) * fb.n + slot] = make_float2(a, b);
+    }
+  }
 }
 
 // ag_reset: resample masked environments, clear collided flags, list them.

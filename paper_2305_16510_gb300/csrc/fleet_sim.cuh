@@ -89,6 +89,34 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// Field f of the padding box that completes an odd box count: centre at
+// 1e30, zero extents, identity orientation (no sphere can touch it).
+__device__ __forceinline__ float box_pad_field(int f) { return f < 3 ? 1e30f : (f == 6 ? 1.f : 0.f); }
+
+// Sphere (squared radius r2, centre p) against two boxes at once; the ten
+// float2 hold (box a, box b) of: centre x y z, half-extents x y z, q w x y z.
+__device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float r2, float2 cx, float2 cy, float2 cz,
+                                          float2 hx, float2 hy, float2 hz, float2 qw, float2 ux, float2 uy,
+                                          float2 uz) {
+  // v = p - c;  t = 2 u x v;  d = v - w t + u x t  (R_b^T (p - c))
+  const float2 vx = add2(px, neg2(cx)), vy = add2(py, neg2(cy)), vz = add2(pz, neg2(cz));
+  const float2 tx = mul2(dup2(2.f), fma2(uy, vz, neg2(mul2(uz, vy))));
+  const float2 ty = mul2(dup2(2.f), fma2(uz, vx, neg2(mul2(ux, vz))));
+  const float2 tz = mul2(dup2(2.f), fma2(ux, vy, neg2(mul2(uy, vx))));
+  const float2 dx = add2(fma2(neg2(qw), tx, vx), fma2(uy, tz, neg2(mul2(uz, ty))));
+  const float2 dy = add2(fma2(neg2(qw), ty, vy), fma2(uz, tx, neg2(mul2(ux, tz))));
+  const float2 dz = add2(fma2(neg2(qw), tz, vz), fma2(ux, ty, neg2(mul2(uy, tx))));
+  // excess over the half-extents, clamped at 0
+  const float2 ex = add2(make_float2(fabsf(dx.x), fabsf(dx.y)), neg2(hx));
+  const float2 ey = add2(make_float2(fabsf(dy.x), fabsf(dy.y)), neg2(hy));
+  const float2 ez = add2(make_float2(fabsf(dz.x), fabsf(dz.y)), neg2(hz));
+  const float2 mx = make_float2(fmaxf(ex.x, 0.f), fmaxf(ex.y, 0.f));
+  const float2 my = make_float2(fmaxf(ey.x, 0.f), fmaxf(ey.y, 0.f));
+  const float2 mz = make_float2(fmaxf(ez.x, 0.f), fmaxf(ez.y, 0.f));
+  const float2 e2 = fma2(mz, mz, fma2(my, my, mul2(mx, mx)));
+  return !(r2 < e2.x) | !(r2 < e2.y);
+}
+
 struct SmemBoxPairs {
   const float2* sm;  // this thread's column: element (j * 10 + f) * B
   int B;
@@ -99,42 +127,28 @@ struct SmemBoxPairs {
 #pragma unroll 2
     for (int j = 0; j < pairs; ++j) {
       const float2* f = sm + (size_t)j * 10 * B;
-      const float2 cx = f[0], cy = f[B], cz = f[2 * B], hx = f[3 * B], hy = f[4 * B], hz = f[5 * B];
-      const float2 qw = f[6 * B], ux = f[7 * B], uy = f[8 * B], uz = f[9 * B];
-      // v = p - c;  t = 2 u x v;  d = v - w t + u x t  (R_b^T (p - c))
-      const float2 vx = add2(px, neg2(cx)), vy = add2(py, neg2(cy)), vz = add2(pz, neg2(cz));
-      const float2 tx = mul2(dup2(2.f), fma2(uy, vz, neg2(mul2(uz, vy))));
-      const float2 ty = mul2(dup2(2.f), fma2(uz, vx, neg2(mul2(ux, vz))));
-      const float2 tz = mul2(dup2(2.f), fma2(ux, vy, neg2(mul2(uy, vx))));
-      const float2 dx = add2(fma2(neg2(qw), tx, vx), fma2(uy, tz, neg2(mul2(uz, ty))));
-      const float2 dy = add2(fma2(neg2(qw), ty, vy), fma2(uz, tx, neg2(mul2(ux, tz))));
-      const float2 dz = add2(fma2(neg2(qw), tz, vz), fma2(ux, ty, neg2(mul2(uy, tx))));
-      // excess over the half-extents, clamped at 0
-      const float2 ex = add2(make_float2(fabsf(dx.x), fabsf(dx.y)), neg2(hx));
-      const float2 ey = add2(make_float2(fabsf(dy.x), fabsf(dy.y)), neg2(hy));
-      const float2 ez = add2(make_float2(fabsf(dz.x), fabsf(dz.y)), neg2(hz));
-      const float2 mx = make_float2(fmaxf(ex.x, 0.f), fmaxf(ex.y, 0.f));
-      const float2 my = make_float2(fmaxf(ey.x, 0.f), fmaxf(ey.y, 0.f));
-      const float2 mz = make_float2(fmaxf(ez.x, 0.f), fmaxf(ez.y, 0.f));
-      const float2 e2 = fma2(mz, mz, fma2(my, my, mul2(mx, mx)));
-      hit |= !(r2 < e2.x) | !(r2 < e2.y);
+      hit |= pair_hits(px, py, pz, r2, f[0], f[B], f[2 * B], f[3 * B], f[4 * B], f[5 * B], f[6 * B], f[7 * B],
+                       f[8 * B], f[9 * B]);
     }
     return hit;
   }
 };
 
-// GlobalBoxes: structure-of-arrays rows [k * 10 + f][n] read at one index.
-struct GlobalBoxes {
-  const float* __restrict__ rows;  // [n_obs * 10][n]
+// GlobalBoxPairs: the slot-ordered pair copy in global memory, element
+// (j * 10 + f) * n + idx, read through the read-only cache.
+struct GlobalBoxPairs {
+  const float2* __restrict__ rows;
   uint32_t n, idx;
-  __device__ __forceinline__ float at(int r) const { return __ldg(rows + (size_t)r * n + idx); }
+  __device__ __forceinline__ float2 at(int r) const { return __ldg(rows + (size_t)r * n + idx); }
   __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
+    const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
     bool hit = false;
-#pragma unroll 4
-    for (int k = 0; k < n_obs; ++k) {
-      const int r = k * 10;
-      hit |= sphere_hits_box(p, r2, V3{at(r), at(r + 1), at(r + 2)}, V3{at(r + 3), at(r + 4), at(r + 5)},
-                             Q4{at(r + 6), at(r + 7), at(r + 8), at(r + 9)});
+    const int pairs = (n_obs + 1) >> 1;
+#pragma unroll 2
+    for (int j = 0; j < pairs; ++j) {
+      const int r = j * 10;
+      hit |= pair_hits(px, py, pz, r2, at(r), at(r + 1), at(r + 2), at(r + 3), at(r + 4), at(r + 5), at(r + 6),
+                       at(r + 7), at(r + 8), at(r + 9));
     }
     return hit;
   }

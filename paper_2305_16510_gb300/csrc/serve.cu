@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kServeBlock) k_serve_step(const ServeDesc* __r
   const uint32_t slot = (blockIdx.x - d.block_begin) * blockDim.x + threadIdx.x;
   if (slot >= d.fb.n || d.steps <= 0) return;
   const uint32_t env = d.fb.order[slot];
-  const GlobalBoxes bx{d.fb.boxes_slot, d.fb.n, slot};
+  const GlobalBoxPairs bx{d.fb.boxes_slot, d.fb.n, slot};
   uint32_t resets = 0;
   bool hit = false;
   simulate<4, INTEG, DRAG>(d.fb, P, env, d.steps, substeps, (int)d.fb.n_obs, bx, d.seed_lo, d.seed_hi, resets, hit);
@@ -130,7 +130,8 @@ size_t request_bytes(size_t n, size_t n_obs) {
   size_t b = 0;
   b += align256(13 * n * 4) + align256(8 * n * 4) + align256(4 * n * 4) + align256(4 * n * 4);
   b += align256(n) + align256(n * 4) + align256(n) + align256(n * 4) + align256(4) + align256(n * 4);
-  b += 2 * align256(n_obs * 10 * n * 4) + align256(order_scratch_words((uint32_t)n) * 4);
+  b += align256(n_obs * 10 * n * 4) + align256(box_pair_elems(n, n_obs) * 8) +
+       align256(order_scratch_words((uint32_t)n) * 4);
   return b;
 }
 
@@ -203,7 +204,7 @@ void carve(ag_server* s, ServeRequest* r) {
   f.n_reset = (uint32_t*)take(4);
   f.order = (uint32_t*)take(n * 4);
   f.boxes = (float*)take(n_obs * 10 * n * 4);
-  f.boxes_slot = (float*)take(n_obs * 10 * n * 4);
+  f.boxes_slot = (float2*)take(agk::box_pair_elems(n, n_obs) * 8);
   r->order_scratch = (uint32_t*)take(agk::order_scratch_words((uint32_t)n) * 4);
   f.n = (uint32_t)n;
   f.n_quad = (uint32_t)n;
