@@ -7,7 +7,7 @@ STEPS_PER_CALL simulated steps (all stages: controller, allocation, motor
 lag, RK4, renormalisation, sphere-vs-box test, Philox resets, compaction).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--envs N_ENVS] [--steps-per-call C] [--parts fused,plain,e2e,paper,adjoint,serve]
+                    [--envs N_ENVS] [--steps-per-call C] [--parts fused,plain,e2e,paper,mixed,adjoint,serve]
 
 --envs / --steps-per-call / --parts run a reduced case of the same workload
 (for profiler captures); the default is the full workload and every part.
@@ -269,6 +269,8 @@ def gpu_arm(args) -> dict | None:
                               "paper_hardware": "2x RTX 3090 + TR PRO 3975WX (Isaac Gym/PhysX)"}
         fs.close()
     fl.close()
+    if "mixed" in parts:
+        out["mixed"] = mixed_part(seed, world)
     if "adjoint" in parts:
         out["adjoint"] = adjoint_part(seed, world)
     if "serve" in parts:
@@ -302,6 +304,36 @@ def gpu_arm(args) -> dict | None:
     }
     res.update(out)
     return res
+
+
+# ------------------------------------------------------------- mixed fleet --
+def mixed_part(seed: int, world: int) -> dict:
+    """4,194,304 vehicles (40 % quad, 40 % hexa, 20 % octo), randomised mass
+    and inertia, motor lag, drag, body-velocity commands, semi-implicit Euler:
+    the 500-step rollout as 10 calls of 50 steps, each followed by a 1 %
+    Bernoulli ag_reset mask (masks pre-generated on the device)."""
+    import torch
+    from paper_2305_16510_gb300 import workloads as W
+    w = W.WORKLOADS["mixed"]
+    inp = W.make_inputs(w, seed)
+    fl = make_fleet(w, inp, seed)
+    rng = np.random.default_rng(seed + 100)
+    masks = [torch.from_numpy(W.reset_mask(w.n_envs, w.reset_prob, rng)).cuda() for _ in range(10)]
+    from paper_2305_16510_gb300 import _abi
+
+    def rollout():
+        for k in range(10):
+            fl.step(w.reset_every)
+            _abi.ag_reset(fl.ctx, masks[k], seed + k)
+
+    rollout()
+    torch.cuda.synchronize()
+    secs, _ = time_calls(fl, rollout, 3, world)
+    fl.close()
+    return {"value": w.n_envs * 500 * 3 * world / secs, "unit": UNIT, "ms_per_rollout": secs * 1e3 / 3,
+            "workload": "4,194,304 vehicles (1,677,722 quad / 1,677,722 hexa / 838,860 octo), mass and inertia "
+                        "x U[0.8, 1.2], tau 0.03, drag 0.1, body-velocity targets U[-2, 2]^3, SIE, 500 steps "
+                        "as 10 x (50-step ag_step + 1 % ag_reset mask)"}
 
 
 # ----------------------------------------------------------------- adjoint --
@@ -502,7 +534,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--envs", type=int, default=0, help="reduced fleet size (default: the full workload)")
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
-    ap.add_argument("--parts", default="fused,plain,e2e,paper,adjoint,serve")
+    ap.add_argument("--parts", default="fused,plain,e2e,paper,mixed,adjoint,serve")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -65,7 +65,7 @@ def _declare(L: ctypes.CDLL) -> None:
     L.orc_world_size.restype = ctypes.c_int
     L.orc_rollout.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp, _u8p, _dp, _dp, _u32p, ctypes.c_uint64, _u8p,
                               _u32p, _u32p, ctypes.c_int]
-    L.orc_reset.argtypes = [vp, _u8p, ctypes.c_uint64, _dp, _dp, _dp, _u32p]
+    L.orc_reset.argtypes = [vp, _u8p, ctypes.c_uint64, _dp, _dp, _dp, _u32p, _u32p]
     L.orc_hat.argtypes = [_dp, _dp]
     L.orc_vee.argtypes = [_dp, _dp]
     L.orc_quat_to_rot.argtypes = [_dp, _dp]
@@ -214,15 +214,19 @@ def rollout(world: World, fleet: Fleet, n_steps: int, n_threads: int = 1, env_id
     return collided, resets
 
 
-def reset(world: World, fleet: Fleet, mask=None, seed: int | None = None) -> None:
-    """Resets masked environments in place (all when mask is None)."""
+def reset(world: World, fleet: Fleet, mask=None, seed: int | None = None, env_ids=None) -> None:
+    """Resets masked environments in place (all when mask is None).
+
+    env_ids: Philox environment number of each row (default: the row index).
+    """
     L = lib()
     if seed is not None:
         fleet.seed = int(seed)
     m = None if mask is None else np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+    ids = None if env_ids is None else np.ascontiguousarray(np.asarray(env_ids, dtype=np.uint32))
     w = world.c()
     L.orc_reset(ctypes.byref(w), _ptr(m, _u8p), ctypes.c_uint64(fleet.seed), _ptr(fleet.body, _dp),
-                _ptr(fleet.state, _dp), _ptr(fleet.motors, _dp), _ptr(fleet.epoch, _u32p))
+                _ptr(fleet.state, _dp), _ptr(fleet.motors, _dp), _ptr(fleet.epoch, _u32p), _ptr(ids, _u32p))
 
 
 # ------------------------------------------------------------ single pieces --

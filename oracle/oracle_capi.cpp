@@ -204,13 +204,15 @@ int orc_rollout(const void* world, int n_steps, double* state, double* motors, c
 }
 
 // Resets the environments with mask[i] != 0 (all when mask is NULL):
-// epoch + 1, then the Philox draw for (seed, i, epoch) and hover motors.
+// epoch + 1, then the Philox draw for (seed, id, epoch) and hover motors,
+// id = env_ids[i] (NULL: i), as in orc_rollout.
 int orc_reset(const void* world, const uint8_t* mask, uint64_t seed, const double* body, double* state,
-              double* motors, uint32_t* epoch) {
+              double* motors, uint32_t* epoch, const uint32_t* env_ids) {
   World w = world_of(world);
   size_t n = (size_t)w.n_envs;
   for (size_t i = 0; i < n; ++i)
-    if (!mask || mask[i]) apply_reset(state, motors, body, epoch, n, i, rotor_count(w, (int)i), seed, (uint32_t)i);
+    if (!mask || mask[i])
+      apply_reset(state, motors, body, epoch, n, i, rotor_count(w, (int)i), seed, env_ids ? env_ids[i] : (uint32_t)i);
   return 0;
 }
 

@@ -42,9 +42,14 @@ def oracle_fleet_from(w: W.Workload, inp: W.Inputs, state, motors, epoch, seed: 
 
 
 def subset(w: W.Workload, inp: W.Inputs, idx: np.ndarray):
-    """Workload and inputs restricted to env indices idx (types must stay contiguous: quads only)."""
-    assert w.n_hexa == 0 and w.n_octo == 0
-    w2 = W.Workload(**{**w.__dict__, "n_envs": len(idx), "n_quad": len(idx)})
+    """Workload and inputs restricted to the sorted env indices idx (rotor
+    types stay in contiguous quad / hexa / octo ranges)."""
+    idx = np.asarray(idx)
+    assert np.all(np.diff(idx) > 0)
+    n_quad = int(np.sum(idx < w.n_quad))
+    n_hexa = int(np.sum((idx >= w.n_quad) & (idx < w.n_quad + w.n_hexa)))
+    w2 = W.Workload(**{**w.__dict__, "n_envs": len(idx), "n_quad": n_quad, "n_hexa": n_hexa,
+                       "n_octo": len(idx) - n_quad - n_hexa})
     inp2 = W.Inputs(inp.modes[idx], inp.targets[:, idx], inp.body[:, idx],
                     None if inp.boxes is None else np.ascontiguousarray(inp.boxes[:, :, idx]))
     return w2, inp2

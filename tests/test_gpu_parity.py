@@ -343,3 +343,46 @@ def test_full_size_obstacle_fleet_sampled_against_oracle():
     scale = 1.0 + np.max(np.abs(orc.state[0:3, ok]), axis=0)
     assert np.all(dp <= 1e-4 * scale), dp.max()
     assert dang.max() <= 1e-3, dang.max()
+
+
+def test_full_size_mixed_fleet_with_reset_masks_sampled_against_oracle():
+    """4,194,304 vehicles (40 % quad, 40 % hexa, 20 % octo), randomised mass and
+    inertia, drag, body-velocity commands: 150 steps in calls of 50 with a 1 %
+    Bernoulli reset mask after each call. The reset words of the whole fleet
+    are compared bit for bit; 384 sampled envs are re-simulated by the oracle."""
+    w = W.WORKLOADS["mixed"]
+    seed = 4
+    inp = W.make_inputs(w, seed)
+    fl = gpu_fleet(w, inp, seed)
+    fl.reset(None, seed)
+    s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
+    idx = np.sort(np.random.default_rng(5).choice(w.n_envs, 384, replace=False))
+    ws, ins = subset(w, inp, idx)
+    assert ws.n_quad > 0 and ws.n_hexa > 0 and ws.n_octo > 0
+    orc = oracle_fleet_from(ws, ins, s0[:, idx], m0[:, idx], e0[idx], seed)
+    world = oracle_world(ws)
+    rng = np.random.default_rng(6)
+    for call in range(3):
+        fl.step(50)
+        O.rollout(world, orc, 50)
+        mask = W.reset_mask(w.n_envs, 0.01, rng)
+        pre = _np(fl.state())
+        fl.reset(mask, seed + call + 1)
+        post = _np(fl.state())
+        hit = mask.astype(bool)
+        # untouched envs keep their state; reset envs hold their Philox draw
+        np.testing.assert_array_equal(post[:, ~hit], pre[:, ~hit])
+        ids = np.flatnonzero(hit)[:2000]
+        ep = _np(fl.epoch()).astype(np.uint32)
+        for i in ids[:200]:
+            d = O.sample_reset(seed + call + 1, int(i), int(ep[i]))
+            np.testing.assert_array_equal(post[0:10, i], d)
+            assert np.all(post[10:13, i] == 0.0)
+        O.reset(world, orc, mask[idx], seed + call + 1, env_ids=idx)
+    s1 = _np(fl.state())
+    mot = _np(fl.motors())
+    fl.close()
+    dp, dv, dang, dw = max_state_errors(s1[:, idx], orc.state)
+    assert dp.max() <= 1e-4, dp.max()
+    assert dang.max() <= 1e-4, dang.max()
+    np.testing.assert_allclose(mot[:, idx], orc.motors, atol=2e-4)
