@@ -65,7 +65,10 @@ def _declare(L: ctypes.CDLL) -> None:
     L.orc_world_size.restype = ctypes.c_int
     L.orc_rollout.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp, _u8p, _dp, _dp, _u32p, ctypes.c_uint64, _u8p,
                               _u32p, _u32p, ctypes.c_int]
-    L.orc_reset.argtypes = [vp, _u8p, ctypes.c_uint64, _dp, _dp, _dp, _u32p, _u32p]
+    L.orc_reset.argtypes = [vp, _u8p, ctypes.c_uint64, _dp, _dp, _dp, _u32p, _u32p, _dp]
+    L.orc_box_rand_size.restype = ctypes.c_int
+    L.orc_sample_box_pose.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp, _fp,
+                                      _fp, _fp]
     L.orc_hat.argtypes = [_dp, _dp]
     L.orc_vee.argtypes = [_dp, _dp]
     L.orc_quat_to_rot.argtypes = [_dp, _dp]
@@ -104,7 +107,28 @@ class _World(ctypes.Structure):
                 ("sphere_r", ctypes.c_double), ("u_max", ctypes.c_double), ("arm", ctypes.c_double),
                 ("k_yaw", ctypes.c_double),
                 ("kx", ctypes.c_double * 3), ("kv", ctypes.c_double * 3), ("kR", ctypes.c_double * 3),
-                ("kW", ctypes.c_double * 3)]
+                ("kW", ctypes.c_double * 3), ("box_rand", ctypes.c_void_p)]
+
+
+class BoxRand(ctypes.Structure):
+    """Re-draw spec of one obstacle (mirrors the oracle's C struct)."""
+    _fields_ = [("pos_min", ctypes.c_float * 3), ("pos_max", ctypes.c_float * 3),
+                ("euler_min", ctypes.c_float * 3), ("euler_max", ctypes.c_float * 3),
+                ("lock", ctypes.c_uint32), ("fixed", ctypes.c_float * 6)]
+
+
+class _BoxRandSpec(ctypes.Structure):
+    _fields_ = [("env_min", ctypes.c_float * 3), ("env_max", ctypes.c_float * 3), ("per_box", ctypes.c_void_p)]
+
+
+def box_rand(pos_min=(0, 0, 0), pos_max=(1, 1, 1), euler_min=(0, 0, 0), euler_max=(0, 0, 0), lock=0,
+             fixed=(0, 0, 0, 0, 0, 0)) -> BoxRand:
+    r = BoxRand()
+    r.pos_min[:], r.pos_max[:] = list(pos_min), list(pos_max)
+    r.euler_min[:], r.euler_max[:] = list(euler_min), list(euler_max)
+    r.lock = lock
+    r.fixed[:] = list(fixed)
+    return r
 
 
 @dataclass
@@ -128,6 +152,9 @@ class World:
     kv: tuple = (2.0, 2.0, 2.0)
     kR: tuple = (1.2, 1.2, 0.6)
     kW: tuple = (0.2, 0.2, 0.1)
+    env_min: tuple | None = None       # obstacle re-draw on reset: environment bounds
+    env_max: tuple | None = None
+    box_specs: list | None = None      # one BoxRand per obstacle (None: obstacles keep their poses)
 
     def c(self) -> _World:
         n_quad = self.n_envs - self.n_hexa - self.n_octo if self.n_quad is None else self.n_quad
@@ -138,6 +165,13 @@ class World:
         w.kv[:] = list(self.kv)
         w.kR[:] = list(self.kR)
         w.kW[:] = list(self.kW)
+        if self.box_specs:
+            arr = (BoxRand * len(self.box_specs))(*self.box_specs)
+            spec = _BoxRandSpec()
+            spec.env_min[:], spec.env_max[:] = list(self.env_min), list(self.env_max)
+            spec.per_box = ctypes.addressof(arr)
+            w.box_rand = ctypes.addressof(spec)
+            w._keep = (arr, spec)       # keep the structures alive with the World
         assert ctypes.sizeof(w) == lib().orc_world_size()
         return w
 
@@ -226,7 +260,8 @@ def reset(world: World, fleet: Fleet, mask=None, seed: int | None = None, env_id
     ids = None if env_ids is None else np.ascontiguousarray(np.asarray(env_ids, dtype=np.uint32))
     w = world.c()
     L.orc_reset(ctypes.byref(w), _ptr(m, _u8p), ctypes.c_uint64(fleet.seed), _ptr(fleet.body, _dp),
-                _ptr(fleet.state, _dp), _ptr(fleet.motors, _dp), _ptr(fleet.epoch, _u32p), _ptr(ids, _u32p))
+                _ptr(fleet.state, _dp), _ptr(fleet.motors, _dp), _ptr(fleet.epoch, _u32p), _ptr(ids, _u32p),
+                _ptr(fleet.boxes, _dp))
 
 
 # ------------------------------------------------------------ single pieces --
@@ -309,6 +344,16 @@ def sample_reset(seed, env, epoch) -> np.ndarray:
     """float32[10]: p xyz, v xyz, q wxyz of the reset draw."""
     out = np.zeros(10, dtype=np.float32)
     lib().orc_sample_reset(ctypes.c_uint64(seed), int(env), int(epoch), _ptr(out, _fp))
+    return out
+
+
+def sample_box_pose(seed, env, epoch, k, spec: BoxRand, env_min, env_max) -> np.ndarray:
+    """float32[7]: centre xyz, q wxyz of one obstacle re-draw."""
+    lo = np.ascontiguousarray(np.asarray(env_min, dtype=np.float32))
+    hi = np.ascontiguousarray(np.asarray(env_max, dtype=np.float32))
+    out = np.zeros(7, dtype=np.float32)
+    lib().orc_sample_box_pose(ctypes.c_uint64(seed), int(env), int(epoch), int(k), ctypes.byref(spec),
+                              _ptr(lo, _fp), _ptr(hi, _fp), _ptr(out, _fp))
     return out
 
 

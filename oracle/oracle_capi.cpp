@@ -25,11 +25,19 @@ namespace {
 
 using namespace orc;
 
+// Obstacle re-draw on reset: environment bounds and one spec per box (NULL
+// when obstacles keep their poses).
+struct BoxRandSpec {
+  float env_min[3], env_max[3];
+  const BoxRand* per_box;  // n_obs entries
+};
+
 struct World {
   int32_t n_envs, substeps_per_step, integrator, n_obs;
   int32_t n_quad, n_hexa, n_octo, pad_;
   double dt, motor_tau, drag, sphere_r, u_max, arm, k_yaw;
   double kx[3], kv[3], kR[3], kW[3];
+  const BoxRandSpec* box_rand;
 };
 
 int rotor_count(const World& w, int env) {
@@ -77,15 +85,26 @@ void substep(const Rotors& rot, int mode, const T tgt[4], const Body<T>& body, c
 }
 
 // Writes a fresh draw into environment i's state and motors (Sec. V reset).
-// `id` is the environment number in the Philox counter (normally i).
-void apply_reset(double* state, double* motors, const double* body, uint32_t* epoch, size_t n, size_t i, int n_rot,
-                 uint64_t seed, uint32_t id) {
+// `id` is the environment number in the Philox counter (normally i). With a
+// box re-draw spec the environment's boxes get new poses (boxes may be NULL
+// when n_obs is 0).
+void apply_reset(const World& w, double* state, double* motors, const double* body, double* boxes, uint32_t* epoch,
+                 size_t n, size_t i, int n_rot, uint64_t seed, uint32_t id) {
   epoch[i] += 1u;
   ResetDraw d = sample_reset_f32(seed, id, epoch[i]);
   double v[13] = {d.p[0], d.p[1], d.p[2], d.v[0], d.v[1], d.v[2], d.q[0], d.q[1], d.q[2], d.q[3], 0.0, 0.0, 0.0};
   for (int r = 0; r < 13; ++r) state[r * n + i] = v[r];
   float hover = hover_thrust_f32((float)body[0 * n + i], n_rot);
   for (int k = 0; k < 8; ++k) motors[k * n + i] = k < n_rot ? (double)hover : 0.0;
+  if (w.box_rand && boxes) {
+    for (int k = 0; k < w.n_obs; ++k) {
+      BoxPose bp = sample_box_pose_f32(seed, id, epoch[i], (uint32_t)k, w.box_rand->per_box[k], w.box_rand->env_min,
+                                       w.box_rand->env_max);
+      double* bx = boxes + (size_t)k * 10 * n;
+      for (int f = 0; f < 3; ++f) bx[f * n + i] = bp.c[f];
+      for (int f = 0; f < 4; ++f) bx[(6 + f) * n + i] = bp.q[f];
+    }
+  }
 }
 
 bool env_collides(const World& w, const double* boxes, size_t n, size_t i, Vec3<double> p) {
@@ -101,7 +120,7 @@ bool env_collides(const World& w, const double* boxes, size_t n, size_t i, Vec3<
 }
 
 void rollout_range(const World& w, const Rotors rot[3], int n_steps, double* state, double* motors,
-                   const double* body, const uint8_t* modes, const double* targets, const double* boxes,
+                   const double* body, const uint8_t* modes, const double* targets, double* boxes,
                    uint32_t* epoch, uint64_t seed, uint8_t* collided, uint32_t* n_resets, const uint32_t* env_ids,
                    size_t i0, size_t i1) {
   const size_t n = (size_t)w.n_envs;
@@ -125,7 +144,7 @@ void rollout_range(const World& w, const Rotors rot[3], int n_steps, double* sta
         any_hit = 1;
         resets += 1;
         store_state(s, state, n, i);
-        apply_reset(state, motors, body, epoch, n, i, n_rot, seed, env_ids ? env_ids[i] : (uint32_t)i);
+        apply_reset(w, state, motors, body, boxes, epoch, n, i, n_rot, seed, env_ids ? env_ids[i] : (uint32_t)i);
         s = load_state<double>(state, n, i);
         for (int k = 0; k < 8; ++k) u[k] = motors[k * n + i];
       }
@@ -180,7 +199,7 @@ int orc_world_size(void) { return (int)sizeof(World); }
 // the same resets as in the full fleet. Work is split over n_threads host
 // threads.
 int orc_rollout(const void* world, int n_steps, double* state, double* motors, const double* body,
-                const uint8_t* modes, const double* targets, const double* boxes, uint32_t* epoch, uint64_t seed,
+                const uint8_t* modes, const double* targets, double* boxes, uint32_t* epoch, uint64_t seed,
                 uint8_t* collided, uint32_t* n_resets, const uint32_t* env_ids, int n_threads) {
   World w = world_of(world);
   if (w.n_envs <= 0 || w.substeps_per_step <= 0 || n_steps < 0) return 1;
@@ -207,13 +226,26 @@ int orc_rollout(const void* world, int n_steps, double* state, double* motors, c
 // epoch + 1, then the Philox draw for (seed, id, epoch) and hover motors,
 // id = env_ids[i] (NULL: i), as in orc_rollout.
 int orc_reset(const void* world, const uint8_t* mask, uint64_t seed, const double* body, double* state,
-              double* motors, uint32_t* epoch, const uint32_t* env_ids) {
+              double* motors, uint32_t* epoch, const uint32_t* env_ids, double* boxes) {
   World w = world_of(world);
   size_t n = (size_t)w.n_envs;
   for (size_t i = 0; i < n; ++i)
     if (!mask || mask[i])
-      apply_reset(state, motors, body, epoch, n, i, rotor_count(w, (int)i), seed, env_ids ? env_ids[i] : (uint32_t)i);
+      apply_reset(w, state, motors, body, boxes, epoch, n, i, rotor_count(w, (int)i), seed,
+                  env_ids ? env_ids[i] : (uint32_t)i);
   return 0;
+}
+
+int orc_box_rand_size(void) { return (int)sizeof(BoxRand); }
+
+// One box pose draw (tests of the sampler): out7 = centre xyz, q wxyz.
+void orc_sample_box_pose(uint64_t seed, uint32_t env, uint32_t epoch, uint32_t k, const void* spec,
+                         const float env_min[3], const float env_max[3], float out7[7]) {
+  BoxRand r;
+  std::memcpy(&r, spec, sizeof(r));
+  BoxPose b = sample_box_pose_f32(seed, env, epoch, k, r, env_min, env_max);
+  for (int i = 0; i < 3; ++i) out7[i] = b.c[i];
+  for (int i = 0; i < 4; ++i) out7[3 + i] = b.q[i];
 }
 
 // ---- single-function entry points used by the oracle's own pins ----------

@@ -168,6 +168,56 @@ inline ResetDraw sample_reset_f32(uint64_t seed, uint32_t env, uint32_t epoch) {
   return d;
 }
 
+// ---------------------------------------------- obstacle pose re-draw ----
+// On a reset the obstacles of the environment may be re-placed (Sec. V: the
+// asset manager samples a new position and orientation for every obstacle of
+// an environment that resets; position bounds are fractions of the
+// environment bounds, orientation bounds are Euler angles, and a dimension
+// can be held at a constant value). Box k of environment env at epoch e uses
+// two draws: counter (env, e, k, 1) -> x, y, z fractions and roll;
+// counter (env, e, k, 2) -> pitch, yaw. Half-extents are kept.
+struct BoxRand {
+  float pos_min[3], pos_max[3];      // fractions of the environment bounds
+  float euler_min[3], euler_max[3];  // roll, pitch, yaw [rad], within [-pi, pi]
+  uint32_t lock;                     // bit d: dimension d (x, y, z, roll, pitch, yaw) held at fixed[d]
+  float fixed[6];
+};
+
+struct BoxPose { float c[3], q[4]; };
+
+inline BoxPose sample_box_pose_f32(uint64_t seed, uint32_t env, uint32_t epoch, uint32_t k, const BoxRand& r,
+                                   const float env_min[3], const float env_max[3]) {
+  uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+  uint32_t w1[4], w2[4];
+  uint32_t c1[4] = {env, epoch, k, 1u}, c2[4] = {env, epoch, k, 2u};
+  philox4x32_10(c1, key, w1);
+  philox4x32_10(c2, key, w2);
+  BoxPose b;
+  for (int d = 0; d < 3; ++d) {
+    if (r.lock & (1u << d)) {
+      b.c[d] = r.fixed[d];
+    } else {
+      float f = r.pos_min[d] + (r.pos_max[d] - r.pos_min[d]) * u01_f32(w1[d]);
+      b.c[d] = env_min[d] + (env_max[d] - env_min[d]) * f;
+    }
+  }
+  const uint32_t words[3] = {w1[3], w2[0], w2[1]};
+  float s[3], c[3];  // sin, cos of the half roll, pitch, yaw
+  for (int a = 0; a < 3; ++a) {
+    float ang = (r.lock & (1u << (3 + a))) ? r.fixed[3 + a]
+                                            : r.euler_min[a] + (r.euler_max[a] - r.euler_min[a]) * u01_f32(words[a]);
+    sincos_poly_f32(0.5f * ang, &s[a], &c[a]);
+  }
+  // q = q_z(yaw) (x) q_y(pitch) (x) q_x(roll)
+  const float cr = c[0], sr = s[0], cp = c[1], sp = s[1], cy = c[2], sy = s[2];
+  const float cycp = cy * cp, sysp = sy * sp, cysp = cy * sp, sycp = sy * cp;
+  b.q[0] = cycp * cr + sysp * sr;
+  b.q[1] = cycp * sr - sysp * cr;
+  b.q[2] = cysp * cr + sycp * sr;
+  b.q[3] = sycp * cr - cysp * sr;
+  return b;
+}
+
 // Hover thrust per motor written on reset: (m * 9.81) / n_rot in binary32.
 inline float hover_thrust_f32(float m, int n_rot) { return (m * 9.81f) / (float)n_rot; }
 

@@ -559,3 +559,63 @@ def test_op_counts_are_plausible():
     assert tot(c_rk4) > 4 * tot(c_sie)
     per_box = (tot(c_obs) - tot(c_rk4)) / 16
     assert 20 < per_box < 120
+
+
+# ------------------------------------------------- obstacle pose re-draw --
+ENV_MIN, ENV_MAX = (-5.0, -4.0, 0.0), (5.0, 4.0, 3.0)
+
+
+def test_box_pose_locked_dimensions_and_euler_composition():
+    rng = np.random.default_rng(20)
+    for _ in range(20):
+        fixed = list(rng.uniform(-3, 3, 3)) + list(rng.uniform(-3.0, 3.0, 3))
+        spec = O.box_rand(lock=0b111111, fixed=fixed)
+        out = O.sample_box_pose(7, int(rng.integers(0, 1000)), 1, 0, spec, ENV_MIN, ENV_MAX)
+        np.testing.assert_array_equal(out[0:3], np.float32(fixed[0:3]))
+        q = quat_wxyz(Rotation.from_euler("ZYX", [fixed[5], fixed[4], fixed[3]]))
+        got = out[3:7].astype(np.float64)
+        if got @ q < 0:
+            got = -got
+        np.testing.assert_allclose(got, q, atol=2e-6)
+
+
+def test_box_pose_bounds_and_uniformity():
+    from scipy import stats
+    spec = O.box_rand(pos_min=(0.1, 0.0, 0.5), pos_max=(0.9, 0.5, 1.0), euler_min=(-0.3, -0.2, -3.0),
+                      euler_max=(0.3, 0.2, 3.0), lock=0b000100, fixed=(0, 0, 1.25, 0, 0, 0))
+    draws = np.stack([O.sample_box_pose(3, i, 1 + i % 4, i % 16, spec, ENV_MIN, ENV_MAX) for i in range(5000)])
+    lo = np.array(ENV_MIN) + (np.array(ENV_MAX) - np.array(ENV_MIN)) * np.array([0.1, 0.0, 0.5])
+    hi = np.array(ENV_MIN) + (np.array(ENV_MAX) - np.array(ENV_MIN)) * np.array([0.9, 0.5, 1.0])
+    assert np.all(draws[:, 0:2] >= lo[0:2] - 1e-6) and np.all(draws[:, 0:2] <= hi[0:2] + 1e-6)
+    assert np.all(draws[:, 2] == np.float32(1.25))                     # z is locked
+    for d in range(2):
+        assert stats.kstest(draws[:, d], stats.uniform(loc=lo[d], scale=hi[d] - lo[d]).cdf).pvalue > 1e-4
+    q = draws[:, 3:7].astype(np.float64)
+    np.testing.assert_allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-6)
+    ypr = Rotation.from_quat(np.stack([q[:, 1], q[:, 2], q[:, 3], q[:, 0]], 1)).as_euler("ZYX")
+    assert np.all(np.abs(ypr[:, 2]) <= 0.3 + 1e-5) and np.all(np.abs(ypr[:, 1]) <= 0.2 + 1e-5)
+    assert stats.kstest(ypr[:, 0], stats.uniform(loc=-3.0, scale=6.0).cdf).pvalue > 1e-4
+
+
+def test_collision_reset_redraws_the_environments_boxes():
+    spec = [O.box_rand(pos_min=(0, 0, 0), pos_max=(1, 1, 1), euler_min=(-1, -1, -1), euler_max=(1, 1, 1))] * 2
+    world = O.World(n_envs=2, n_obs=2, env_min=ENV_MIN, env_max=ENV_MAX, box_specs=spec)
+    st = np.zeros((13, 2))
+    st[6] = 1.0
+    st[0:3, 0] = [0.0, 0.0, 1.0]     # env 0 inside its first box, env 1 far from both
+    st[0:3, 1] = [50.0, 0.0, 0.0]
+    boxes = np.zeros((2, 10, 2))
+    boxes[:, 0:3, :] = [[0.0, 0.0], [0.0, 0.0], [1.0, 1.0]]
+    boxes[1, 0, :] = 30.0
+    boxes[:, 3:6, :] = 0.5
+    boxes[:, 6, :] = 1.0
+    before = boxes.copy()
+    fl = O.make_fleet(world, state=st, modes=[O.MODE_WRENCH] * 2, boxes=boxes, epoch=[2, 2], seed=5)
+    collided, _ = O.rollout(world, fl, 1)
+    assert list(collided) == [1, 0]
+    for k in range(2):
+        pose = O.sample_box_pose(5, 0, 3, k, spec[k], ENV_MIN, ENV_MAX)
+        np.testing.assert_array_equal(fl.boxes[k, 0:3, 0].astype(np.float32), pose[0:3])
+        np.testing.assert_array_equal(fl.boxes[k, 6:10, 0].astype(np.float32), pose[3:7])
+        np.testing.assert_array_equal(fl.boxes[k, 3:6, 0], before[k, 3:6, 0])    # extents kept
+    np.testing.assert_array_equal(fl.boxes[:, :, 1], before[:, :, 1])            # env 1 untouched
