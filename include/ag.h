@@ -126,6 +126,35 @@ ag_status ag_set_commands(ag_ctx* ctx, const uint8_t* modes, const float* target
  * orientation (Sec. V: the obstacle state is privileged information). */
 ag_status ag_set_obstacles(ag_ctx* ctx, const float* boxes);
 
+/* Copies out the current obstacles float[n_obstacles][10][n_envs] (layout of
+ * ag_set_obstacles); they change only when obstacle re-placement is on. */
+ag_status ag_get_obstacles(ag_ctx* ctx, float* boxes);
+
+/* Re-placement of one obstacle when its environment resets (Sec. V: the
+ * asset manager samples a new position and orientation for every obstacle of
+ * a resetting environment; position bounds are fractions of the environment
+ * bounds, orientation bounds are Euler angles, and chosen dimensions can be
+ * held at a constant value). */
+typedef struct {
+  float pos_min[3], pos_max[3];     /* fractions in [0, 1] of env_min..env_max, per axis */
+  float euler_min[3], euler_max[3]; /* roll, pitch, yaw bounds [rad], within [-pi, pi] */
+  uint32_t lock;                    /* bit d set: dimension d (x, y, z, roll, pitch, yaw) is held at fixed[d] */
+  float fixed[6];                   /* held values: centre [m] for d < 3, angle [rad] for d >= 3 */
+} ag_box_randomization;
+
+/* Enables (per_box non-NULL, n_obstacles host entries) or disables (NULL)
+ * the re-placement of obstacles on reset. While enabled, every reset of an
+ * environment (ag_reset and collision resets alike) gives each of its boxes k
+ * a new centre x_d = env_min_d + (env_max_d - env_min_d) * U[pos_min_d,
+ * pos_max_d) and orientation q_z(yaw) q_y(pitch) q_x(roll) with each angle
+ * ~ U[euler_min, euler_max), locked dimensions held at fixed[d]; the
+ * half-extents are kept. The draws are Philox4x32-10 keyed by the reset seed
+ * with counters (env, epoch, k, 1) and (env, epoch, k, 2), transformed in
+ * strict binary32, so they are reproducible bit for bit. Host pointers;
+ * AG_ERR_INVALID for bounds outside [0, 1] or angles outside [-pi, pi]. */
+ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], const float env_max[3],
+                                        const ag_box_randomization* per_box);
+
 /* Copies per-environment rigid-body parameters float[4][n_envs]: mass and
  * the diagonal inertia J_xx, J_yy, J_zz (all > 0). */
 ag_status ag_set_body(ag_ctx* ctx, const float* body);

@@ -41,6 +41,12 @@ class ag_config(ctypes.Structure):
                 ("kW", ctypes.c_float * 3), ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64)]
 
 
+class ag_box_randomization(ctypes.Structure):
+    _fields_ = [("pos_min", ctypes.c_float * 3), ("pos_max", ctypes.c_float * 3),
+                ("euler_min", ctypes.c_float * 3), ("euler_max", ctypes.c_float * 3),
+                ("lock", ctypes.c_uint32), ("fixed", ctypes.c_float * 6)]
+
+
 class ag_server_config(ctypes.Structure):
     _fields_ = [("physics", ag_config), ("max_active", ctypes.c_uint32), ("chunk_steps", ctypes.c_uint32),
                 ("hbm_budget_bytes", ctypes.c_uint64)]
@@ -72,6 +78,9 @@ SIGNATURES = {
     "ag_set_commands": (ctypes.c_int, [_vp, _vp, _vp]),
     "ag_set_obstacles": (ctypes.c_int, [_vp, _vp]),
     "ag_set_body": (ctypes.c_int, [_vp, _vp]),
+    "ag_get_obstacles": (ctypes.c_int, [_vp, _vp]),
+    "ag_set_obstacle_randomization": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float * 3),
+                                                     ctypes.POINTER(ctypes.c_float * 3), _vp]),
     "ag_step": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "ag_step_plain": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "ag_reset": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
@@ -173,6 +182,30 @@ def ag_set_obstacles(ctx: int, boxes) -> None:
 
 def ag_set_body(ctx: int, body) -> None:
     _check(lib().ag_set_body(ctx, ptr(body)), "ag_set_body", ctx)
+
+
+def ag_get_obstacles(ctx: int, boxes) -> None:
+    _check(lib().ag_get_obstacles(ctx, ptr(boxes)), "ag_get_obstacles", ctx)
+
+
+def ag_set_obstacle_randomization(ctx: int, env_min, env_max, per_box) -> None:
+    """per_box: a sequence of ag_box_randomization (one per obstacle) or None to disable."""
+    lo = (ctypes.c_float * 3)(*env_min) if env_min is not None else None
+    hi = (ctypes.c_float * 3)(*env_max) if env_max is not None else None
+    arr = None if per_box is None else (ag_box_randomization * len(per_box))(*per_box)
+    rc = lib().ag_set_obstacle_randomization(ctx, ctypes.byref(lo) if lo else None, ctypes.byref(hi) if hi else None,
+                                             ctypes.cast(arr, ctypes.c_void_p) if arr is not None else None)
+    _check(rc, "ag_set_obstacle_randomization", ctx)
+
+
+def box_randomization(pos_min=(0, 0, 0), pos_max=(1, 1, 1), euler_min=(0, 0, 0), euler_max=(0, 0, 0), lock=0,
+                      fixed=(0, 0, 0, 0, 0, 0)) -> ag_box_randomization:
+    r = ag_box_randomization()
+    r.pos_min[:], r.pos_max[:] = list(pos_min), list(pos_max)
+    r.euler_min[:], r.euler_max[:] = list(euler_min), list(euler_max)
+    r.lock = lock
+    r.fixed[:] = list(fixed)
+    return r
 
 
 def ag_step(ctx: int, n_substeps: int) -> None:

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -201,7 +202,7 @@ void free_all(ag_ctx* ctx) {
   agk::FleetBuffers& f = ctx->fb;
   void* ptrs[] = {f.state, f.motors, f.body, f.modes, f.targets, f.boxes, f.epoch, f.collided, f.reset_ids,
                   f.n_reset, f.cmd, f.wrench, f.resets, f.hits, f.order, f.boxes_slot, ctx->mask_dev,
-                  ctx->order_scratch};
+                  ctx->order_scratch, f.slot_of, (void*)f.box_rand};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -293,6 +294,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = alloc(ctx, &f.hits, n);
   if (e == cudaSuccess) e = alloc(ctx, &ctx->mask_dev, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.order, n);
+  if (e == cudaSuccess && cfg->n_obstacles) e = alloc(ctx, &f.slot_of, n);
   if (e == cudaSuccess) e = alloc(ctx, &ctx->order_scratch, agk::order_scratch_words(cfg->n_envs));
   if (e != cudaSuccess) {
     g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
@@ -365,6 +367,57 @@ ag_status ag_set_obstacles(ag_ctx* ctx, const float* boxes) {
                  "copy boxes");
   if (s != AG_OK) return s;
   return check_cuda(ctx, agk::launch_permute_boxes(ctx->fb, ctx->stream), "permute boxes");
+}
+
+ag_status ag_get_obstacles(ag_ctx* ctx, float* boxes) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!boxes) return fail_invalid(ctx, "boxes is NULL");
+  const size_t count = (size_t)ctx->cfg.n_obstacles * 10 * ctx->cfg.n_envs;
+  if (count == 0) return AG_OK;
+  return check_cuda(ctx, cudaMemcpyAsync(boxes, ctx->fb.boxes, count * sizeof(float), cudaMemcpyDefault, ctx->stream),
+                    "copy boxes out");
+}
+
+ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], const float env_max[3],
+                                        const ag_box_randomization* per_box) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  agk::FleetBuffers& f = ctx->fb;
+  const uint32_t n_obs = ctx->cfg.n_obstacles;
+  if (!per_box) {
+    f.box_rand = nullptr;
+    return AG_OK;
+  }
+  if (n_obs == 0) return fail_invalid(ctx, "the context has no obstacles");
+  if (!env_min || !env_max) return fail_invalid(ctx, "env_min and env_max are required");
+  const float pi = 3.14159265358979f;
+  std::vector<agk::BoxRandDev> spec(n_obs);
+  for (uint32_t k = 0; k < n_obs; ++k) {
+    const ag_box_randomization& r = per_box[k];
+    agk::BoxRandDev& d = spec[k];
+    for (int i = 0; i < 3; ++i) {
+      if (!(r.pos_min[i] >= 0.f && r.pos_max[i] <= 1.f && r.pos_min[i] <= r.pos_max[i]))
+        return fail_invalid(ctx, "position fractions must satisfy 0 <= pos_min <= pos_max <= 1");
+      if (!(r.euler_min[i] >= -pi && r.euler_max[i] <= pi && r.euler_min[i] <= r.euler_max[i]))
+        return fail_invalid(ctx, "Euler bounds must satisfy -pi <= euler_min <= euler_max <= pi");
+      if ((r.lock & (1u << (3 + i))) && !(r.fixed[3 + i] >= -pi && r.fixed[3 + i] <= pi))
+        return fail_invalid(ctx, "held angles must lie in [-pi, pi]");
+      if (!(env_min[i] <= env_max[i])) return fail_invalid(ctx, "env_min must not exceed env_max");
+      d.pos_min[i] = r.pos_min[i]; d.pos_max[i] = r.pos_max[i];
+      d.euler_min[i] = r.euler_min[i]; d.euler_max[i] = r.euler_max[i];
+      d.env_min[i] = env_min[i]; d.env_max[i] = env_max[i];
+    }
+    d.lock = r.lock;
+    for (int i = 0; i < 6; ++i) d.fixed[i] = r.fixed[i];
+  }
+  if (!f.box_rand) {
+    agk::BoxRandDev* p = nullptr;
+    if ((s = check_cuda(ctx, alloc(ctx, &p, n_obs), "allocate obstacle spec")) != AG_OK) return s;
+    f.box_rand = p;
+  }
+  return check_cuda(ctx, cudaMemcpy((void*)f.box_rand, spec.data(), n_obs * sizeof(agk::BoxRandDev),
+                                    cudaMemcpyHostToDevice), "copy obstacle spec");
 }
 
 ag_status ag_set_body(ag_ctx* ctx, const float* body) {

@@ -63,11 +63,11 @@ __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams 
     const SmemBoxPairs bx{my, B};
     const int n_obs = (int)fb.n_obs;
     if (nrot == 4)
-      simulate<4, INTEG, DRAG>(fb, P, env, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+      simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
     else if (nrot == 6)
-      simulate<6, INTEG, DRAG>(fb, P, env, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+      simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
     else
-      simulate<8, INTEG, DRAG>(fb, P, env, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+      simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
     fb.collided[env] = any_hit ? 1 : 0;
   }
   append_compact(resets > 0u, env, fb.reset_ids, fb.n_reset);
@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_window(FleetBuffers fb)
       uint32_t pos = key_next[key] + rank;
       for (int w = 0; w < warp; ++w) pos += warp_count[w][key];
       fb.order[base + pos] = i;
+      if (fb.slot_of) fb.slot_of[i] = base + pos;
     }
     __syncthreads();
     if (threadIdx.x < 12) {  // advance each key by its count in this sub-window
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(256) k_reset(FleetBuffers fb, const uint8_t* m
     const int nrot = rotor_count(fb, env);
     const float hv = hover_per_motor(fb.body[env], nrot);
     for (int k = 0; k < 8; ++k) fb.motors[k * n + env] = k < nrot ? hv : 0.f;
+    if (fb.box_rand) redraw_boxes(fb, env, fb.slot_of ? fb.slot_of[env] : env, epoch, seed_lo, seed_hi, NoBoxes{});
   }
   if (active) fb.collided[env] = 0;
   append_compact(flag, env, fb.reset_ids, fb.n_reset);
@@ -258,6 +260,7 @@ __global__ void __launch_bounds__(256) k_plain_reset_hits(FleetBuffers fb, StepP
   const int nrot = rotor_count(fb, i);
   const float hv = hover_per_motor(fb.body[i], nrot);
   for (int k = 0; k < nrot; ++k) fb.motors[k * n + i] = hv;
+  if (fb.box_rand) redraw_boxes(fb, i, fb.slot_of ? fb.slot_of[i] : i, epoch, P.seed_lo, P.seed_hi, NoBoxes{});
 }
 
 __global__ void __launch_bounds__(256) k_plain_compact(FleetBuffers fb) {

@@ -118,8 +118,13 @@ __device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float
 }
 
 struct SmemBoxPairs {
-  const float2* sm;  // this thread's column: element (j * 10 + f) * B
+  float2* sm;  // this thread's column: element (j * 10 + f) * B
   int B;
+  // replace field f of box k (a re-drawn pose)
+  __device__ __forceinline__ void set(int k, int f, float v) const {
+    float2& e = sm[(size_t)((k >> 1) * 10 + f) * B];
+    if (k & 1) e.y = v; else e.x = v;
+  }
   __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
     const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
     bool hit = false;
@@ -134,11 +139,18 @@ struct SmemBoxPairs {
   }
 };
 
+// No staged copy (kernels that only update the global boxes).
+struct NoBoxes {
+  __device__ __forceinline__ void set(int, int, float) const {}
+};
+
 // GlobalBoxPairs: the slot-ordered pair copy in global memory, element
 // (j * 10 + f) * n + idx, read through the read-only cache.
 struct GlobalBoxPairs {
   const float2* __restrict__ rows;
   uint32_t n, idx;
+  // the global copy is refreshed by the caller of a re-draw; nothing cached here
+  __device__ __forceinline__ void set(int, int, float) const {}
   __device__ __forceinline__ float2 at(int r) const { return __ldg(rows + (size_t)r * n + idx); }
   __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
     const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
@@ -157,9 +169,33 @@ struct GlobalBoxPairs {
 // The per-vehicle body of the fused kernels, specialised on the rotor count:
 // n_steps steps of `substeps` substeps, then the sphere-vs-box test against
 // n_obs boxes and, on a hit, the Philox reset keyed (seed_lo, seed_hi).
+// New poses for every box of environment env (slot = its thread slot):
+// written to the env-ordered boxes, to the slot-ordered pair copy and to the
+// caller's box source (the thread's staged copy).
+template <class Boxes>
+__device__ __noinline__ void redraw_boxes(const FleetBuffers& fb, uint32_t env, uint32_t slot, uint32_t epoch,
+                                          uint32_t seed_lo, uint32_t seed_hi, const Boxes& boxes) {
+  const uint32_t n = fb.n;
+  for (int k = 0; k < (int)fb.n_obs; ++k) {
+    float c[3], q[4];
+    draw_box_pose(seed_lo, seed_hi, env, epoch, (uint32_t)k, fb.box_rand[k], c, q);
+    const float v[7] = {c[0], c[1], c[2], q[0], q[1], q[2], q[3]};
+    const int field[7] = {0, 1, 2, 6, 7, 8, 9};
+    for (int m = 0; m < 7; ++m) {
+      const int f = field[m];
+      fb.boxes[((size_t)k * 10 + f) * n + env] = v[m];
+      if (fb.boxes_slot) {
+        float2& e = fb.boxes_slot[(size_t)((k >> 1) * 10 + f) * n + slot];
+        if (k & 1) e.y = v[m]; else e.x = v[m];
+      }
+      boxes.set(k, f, v[m]);
+    }
+  }
+}
+
 template <int NROT, int INTEG, bool DRAG, class Boxes>
-__device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, int n_steps,
-                                         int substeps, int n_obs, const Boxes& boxes, uint32_t seed_lo,
+__device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, uint32_t slot,
+                                         int n_steps, int substeps, int n_obs, const Boxes& boxes, uint32_t seed_lo,
                                          uint32_t seed_hi, uint32_t& resets, bool& any_hit) {
   const uint32_t n = fb.n;
   VState s = load_state(fb.state, n, env);
@@ -183,6 +219,7 @@ __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParam
         resets += 1;
         epoch += 1;
         reset_in_registers<NROT>(s, u, b.m, env, epoch, seed_lo, seed_hi);
+        if (fb.box_rand) redraw_boxes(fb, env, slot, epoch, seed_lo, seed_hi, boxes);
       }
     }
   }

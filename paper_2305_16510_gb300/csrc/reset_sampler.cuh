@@ -127,6 +127,51 @@ __device__ __forceinline__ ResetValues draw_reset(uint32_t seed_lo, uint32_t see
   return r;
 }
 
+// Re-draw spec of one obstacle (the layout of ag_box_randomization) with the
+// environment bounds appended.
+struct BoxRandDev {
+  float pos_min[3], pos_max[3];      // fractions of the environment bounds
+  float euler_min[3], euler_max[3];  // roll, pitch, yaw [rad]
+  uint32_t lock;                     // bit d: dimension d (x, y, z, roll, pitch, yaw) held at fixed[d]
+  float fixed[6];
+  float env_min[3], env_max[3];
+};
+
+// New pose of box k of environment env at epoch (Sec. V: obstacles are
+// re-placed when their environment resets). Counter (env, epoch, k, 1) gives
+// the x, y, z fractions and the roll; (env, epoch, k, 2) the pitch and yaw.
+// q = q_z(yaw) (x) q_y(pitch) (x) q_x(roll) from half-angle sines and cosines.
+__device__ __forceinline__ void draw_box_pose(uint32_t seed_lo, uint32_t seed_hi, uint32_t env, uint32_t epoch,
+                                              uint32_t k, const BoxRandDev& r, float c[3], float q[4]) {
+  const uint4 w1 = philox4x32_10(make_uint4(env, epoch, k, 1u), seed_lo, seed_hi);
+  const uint4 w2 = philox4x32_10(make_uint4(env, epoch, k, 2u), seed_lo, seed_hi);
+  const uint32_t wp[3] = {w1.x, w1.y, w1.z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (r.lock & (1u << d)) {
+      c[d] = r.fixed[d];
+    } else {
+      const float f = __fadd_rn(r.pos_min[d], __fmul_rn(__fsub_rn(r.pos_max[d], r.pos_min[d]), unit24(wp[d])));
+      c[d] = __fadd_rn(r.env_min[d], __fmul_rn(__fsub_rn(r.env_max[d], r.env_min[d]), f));
+    }
+  }
+  const uint32_t wa[3] = {w1.w, w2.x, w2.y};
+  float sn[3], cs[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float ang = (r.lock & (1u << (3 + a)))
+                          ? r.fixed[3 + a]
+                          : __fadd_rn(r.euler_min[a], __fmul_rn(__fsub_rn(r.euler_max[a], r.euler_min[a]), unit24(wa[a])));
+    sincos_taylor(__fmul_rn(0.5f, ang), &sn[a], &cs[a]);
+  }
+  const float cr = cs[0], sr = sn[0], cp = cs[1], sp = sn[1], cy = cs[2], sy = sn[2];
+  const float cycp = __fmul_rn(cy, cp), sysp = __fmul_rn(sy, sp), cysp = __fmul_rn(cy, sp), sycp = __fmul_rn(sy, cp);
+  q[0] = __fadd_rn(__fmul_rn(cycp, cr), __fmul_rn(sysp, sr));
+  q[1] = __fsub_rn(__fmul_rn(cycp, sr), __fmul_rn(sysp, cr));
+  q[2] = __fadd_rn(__fmul_rn(cysp, cr), __fmul_rn(sycp, sr));
+  q[3] = __fsub_rn(__fmul_rn(sycp, cr), __fmul_rn(cysp, sr));
+}
+
 __device__ __forceinline__ float hover_per_motor(float m, int n_rot) {
   return __fdiv_rn(__fmul_rn(m, 9.81f), __int2float_rn(n_rot));
 }

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(kServeBlock) k_serve_step(const ServeDesc* __r
   const GlobalBoxPairs bx{d.fb.boxes_slot, d.fb.n, slot};
   uint32_t resets = 0;
   bool hit = false;
-  simulate<4, INTEG, DRAG>(d.fb, P, env, d.steps, substeps, (int)d.fb.n_obs, bx, d.seed_lo, d.seed_hi, resets, hit);
+  simulate<4, INTEG, DRAG>(d.fb, P, env, slot, d.steps, substeps, (int)d.fb.n_obs, bx, d.seed_lo, d.seed_hi, resets,
+                           hit);
 }
 
 // First-fit allocator over [0, size) with coalescing frees (host bookkeeping

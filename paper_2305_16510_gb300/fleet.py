@@ -73,6 +73,15 @@ class Fleet:
         _abi.ag_set_obstacles(self.ctx, b)
         self._keep_boxes = b
 
+    def obstacles(self) -> torch.Tensor:
+        out = torch.empty((self.cfg.n_obstacles, 10, self.n), dtype=torch.float32, device=self.device)
+        _abi.ag_get_obstacles(self.ctx, out)
+        return out
+
+    def set_obstacle_randomization(self, env_min, env_max, per_box) -> None:
+        """per_box: list of _abi.ag_box_randomization (one per obstacle), or None to disable."""
+        _abi.ag_set_obstacle_randomization(self.ctx, env_min, env_max, per_box)
+
     def set_body(self, body) -> None:
         b = self._dev(body, torch.float32)
         _abi.ag_set_body(self.ctx, b)

@@ -1,0 +1,119 @@
+"""Obstacle re-placement on reset (ag_set_obstacle_randomization) vs the oracle.
+
+Sec. V: an environment that resets gets new obstacle poses within position
+bounds (fractions of the environment bounds) and Euler-angle bounds, with
+chosen dimensions held constant. The re-drawn box words must equal the
+oracle's bit for bit, after ag_reset and after collision resets inside a
+fused or an unfused step.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from harness import box_margin, gpu_fleet, max_state_errors, oracle_fleet_from, oracle_world
+from paper_2305_16510_gb300 import _abi
+from paper_2305_16510_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+ENV_MIN, ENV_MAX = (-5.0, -5.0, -5.0), (5.0, 5.0, 5.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2305_16510_gb300 import build
+    build.build()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _specs(n_obs):
+    out_gpu, out_orc = [], []
+    rng = np.random.default_rng(n_obs)
+    for k in range(n_obs):
+        lo = rng.uniform(0.0, 0.4, 3)
+        hi = lo + rng.uniform(0.2, 0.6, 3)
+        emin = -rng.uniform(0.0, 3.0, 3)
+        emax = rng.uniform(0.0, 3.0, 3)
+        lock = int(rng.integers(0, 64)) if k % 3 == 0 else 0
+        fixed = list(rng.uniform(-4, 4, 3)) + list(rng.uniform(-3, 3, 3))
+        kw = dict(pos_min=lo, pos_max=hi, euler_min=emin, euler_max=emax, lock=lock, fixed=fixed)
+        out_gpu.append(_abi.box_randomization(**kw))
+        out_orc.append(O.box_rand(**kw))
+    return out_gpu, out_orc
+
+
+def _pair(w, seed):
+    inp = W.make_inputs(w, seed)
+    fl = gpu_fleet(w, inp, seed)
+    sg, so = _specs(w.n_obstacles)
+    fl.set_obstacle_randomization(ENV_MIN, ENV_MAX, sg)
+    world = O.World(**{**oracle_world(w).__dict__, "env_min": ENV_MIN, "env_max": ENV_MAX, "box_specs": so})
+    return fl, inp, world
+
+
+def test_reset_redraws_boxes_bit_exact():
+    w = W.Workload("redraw", 3000, 4, 1, 7, 3000, 0, 0, mode_mix=(0, 1, 2))
+    fl, inp, world = _pair(w, 31)
+    fl.reset(None, 31)
+    orc = oracle_fleet_from(w, inp, np.zeros((13, w.n_envs)), np.zeros((8, w.n_envs)), np.zeros(w.n_envs, np.uint32),
+                            31)
+    O.reset(world, orc, None, 31)
+    np.testing.assert_array_equal(_np(fl.state()), orc.state.astype(np.float32))
+    np.testing.assert_array_equal(_np(fl.obstacles()), orc.boxes.astype(np.float32))
+    mask = W.reset_mask(w.n_envs, 0.25, np.random.default_rng(2))
+    fl.reset(mask, 77)
+    O.reset(world, orc, mask, 77)
+    np.testing.assert_array_equal(_np(fl.obstacles()), orc.boxes.astype(np.float32))
+    np.testing.assert_array_equal(_np(fl.state()), orc.state.astype(np.float32))
+    fl.close()
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_collision_resets_redraw_boxes_teacher_forced(plain):
+    w = W.Workload("redraw", 2500, 4, 1, 16, 2500, 0, 0, mode_mix=(0, 1, 2))
+    fl, inp, world = _pair(w, 41)
+    fl.reset(None, 41)
+    world_free = O.World(**{**world.__dict__, "n_obs": 0, "box_specs": None})
+    hits = 0
+    for _ in range(12):
+        s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
+        b0 = _np(fl.obstacles())
+        (fl.step_plain if plain else fl.step)(1)
+        s1, b1 = _np(fl.state()), _np(fl.obstacles())
+        col = _np(fl.events()[0])
+        cur = W.Inputs(inp.modes, inp.targets, inp.body, b0)
+        pre = oracle_fleet_from(w, cur, s0, m0, e0, 41)
+        pre.boxes = None
+        O.rollout(world_free, pre, 1)
+        ok = np.abs(box_margin(pre.state[0:3], b0.astype(np.float64))) >= 1e-5
+        orc = oracle_fleet_from(w, cur, s0, m0, e0, 41)
+        ocol, _ = O.rollout(world, orc, 1)
+        np.testing.assert_array_equal(col[ok], ocol[ok])
+        hit = ok & (ocol == 1)
+        hits += int(hit.sum())
+        np.testing.assert_array_equal(b1[:, :, ok], orc.boxes[:, :, ok].astype(np.float32))
+        np.testing.assert_array_equal(s1[:, hit], orc.state[:, hit].astype(np.float32))
+        free = ok & (ocol == 0)
+        dp, _, dang, _ = max_state_errors(s1[:, free], orc.state[:, free])
+        assert dp.max() <= 2e-5 * (1 + np.abs(orc.state[0:3, free]).max()) and dang.max() <= 2e-5
+    assert hits > 10
+    fl.close()
+
+
+def test_disable_keeps_boxes():
+    w = W.Workload("redraw", 500, 1, 0, 4, 500, 0, 0)
+    fl, inp, world = _pair(w, 3)
+    fl.set_obstacle_randomization(None, None, None)
+    fl.reset(None, 3)
+    np.testing.assert_array_equal(_np(fl.obstacles()), inp.boxes)
+    with pytest.raises(_abi.AgError) as e:
+        bad, _ = _specs(4)
+        bad[0].pos_max[0] = 1.5
+        fl.set_obstacle_randomization(ENV_MIN, ENV_MAX, bad)
+    assert e.value.status == _abi.AG_ERR_INVALID
+    fl.close()
