@@ -155,6 +155,22 @@ typedef struct {
 ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], const float env_max[3],
                                         const ag_box_randomization* per_box);
 
+/* Depth images of n_cams vehicle-mounted pinhole cameras, rendered by ray
+ * casting against each environment's boxes (the paper's depth cameras,
+ * Sec. III, and its kernel-based ray casting, Sec. VII). Camera j belongs to
+ * environment env_ids[j] (host or device array; NULL = environments 0 ..
+ * n_cams-1), sits at p + R cam_offset (host float[3] in the body frame, NULL
+ * = the centre of mass) and looks along body +x with body +z up. Pixel
+ * (row r, column c) of a width x height image with horizontal field of view
+ * hfov [rad] sees along R (1, -(c + 0.5 - width/2) / f, -(r + 0.5 - height/2)
+ * / f) with f = (width/2) / tan(hfov/2); its value is the distance along the
+ * optical axis to the nearest box surface in front of the camera (0 inside a
+ * box), or max_range if none is closer. depth: float[n_cams][height][width],
+ * host or device. AG_ERR_INVALID for an empty image, hfov outside (0, pi),
+ * max_range <= 0 or an environment id out of range (host arrays only). */
+ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
+                          const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth);
+
 /* Copies per-environment rigid-body parameters float[4][n_envs]: mass and
  * the diagonal inertia J_xx, J_yy, J_zz (all > 0). */
 ag_status ag_set_body(ag_ctx* ctx, const float* body);

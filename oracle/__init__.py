@@ -67,6 +67,8 @@ def _declare(L: ctypes.CDLL) -> None:
                               _u32p, _u32p, ctypes.c_int]
     L.orc_reset.argtypes = [vp, _u8p, ctypes.c_uint64, _dp, _dp, _dp, _u32p, _u32p, _dp]
     L.orc_box_rand_size.restype = ctypes.c_int
+    L.orc_render_depth.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, _u32p, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]
     L.orc_sample_box_pose.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp, _fp,
                                       _fp, _fp]
     L.orc_hat.argtypes = [_dp, _dp]
@@ -354,6 +356,19 @@ def sample_box_pose(seed, env, epoch, k, spec: BoxRand, env_min, env_max) -> np.
     out = np.zeros(7, dtype=np.float32)
     lib().orc_sample_box_pose(ctypes.c_uint64(seed), int(env), int(epoch), int(k), ctypes.byref(spec),
                               _ptr(lo, _fp), _ptr(hi, _fp), _ptr(out, _fp))
+    return out
+
+
+def render_depth(state, boxes, env_ids, width, height, hfov, max_range, cam_offset=(0.0, 0.0, 0.0)):
+    """float64 [n_cams, H, W] depth images (see ray_box_depth for the camera model)."""
+    st = _f64(state)
+    n = st.shape[1]
+    bx = _f64(boxes) if boxes is not None and np.asarray(boxes).size else np.zeros(1)
+    n_obs = 0 if boxes is None else np.asarray(boxes).shape[0]
+    ids = np.ascontiguousarray(np.asarray(env_ids, dtype=np.uint32))
+    out = np.zeros((len(ids), height, width))
+    lib().orc_render_depth(int(n), int(n_obs), _ptr(st, _dp), _ptr(bx, _dp), len(ids), _ptr(ids, _u32p), int(width),
+                           int(height), float(hfov), float(max_range), _ptr(_f64(cam_offset), _dp), _ptr(out, _dp))
     return out
 
 

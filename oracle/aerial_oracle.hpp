@@ -538,4 +538,40 @@ bool sphere_hits_box(Vec3<T> p, T r, Vec3<T> c, Vec3<T> h, Quat<T> qb) {
   return !(r * r < dot(e, e));
 }
 
+// ------------------------------------------------------------ depth camera --
+// Depth image of a pinhole camera against the oriented boxes of one
+// environment (the paper renders depth through Isaac Gym's camera sensors,
+// Sec. III, and names kernel-based ray casting as its next step, Sec. VII).
+// Reading: the camera sits at p + R o_b (o_b its offset in the body frame) and
+// looks along body +x with body +z up; pixel (row r, column c) of a W x H
+// image with horizontal field of view hfov has the camera-frame ray
+//   d = (1, -(c + 0.5 - W/2) / f, -(r + 0.5 - H/2) / f),  f = (W/2) / tan(hfov/2)
+// (x forward, y left, z up); the depth of the pixel is the smallest t >= 0
+// with o + t R d inside some box, which is the distance along the optical
+// axis because d has unit forward component; max_range when nothing is hit
+// closer. A ray enters the box {|x_i| <= h_i} (box frame) by the slab method:
+// t_in = max_i min(t_i-, t_i+), t_out = min_i max(t_i-, t_i+) with
+// t_i-+ = (-+h_i - o_i) / d_i, and hits it iff t_out >= max(t_in, 0).
+template <class T>
+T ray_box_depth(Vec3<T> o, Vec3<T> d, Vec3<T> c, Vec3<T> h, Quat<T> qb, T max_range) {
+  Mat3<T> Rt = transpose(unit_quat_to_rot(qb));
+  Vec3<T> ob = matvec(Rt, o - c);
+  Vec3<T> db = matvec(Rt, d);
+  T oi[3] = {ob.x, ob.y, ob.z}, di[3] = {db.x, db.y, db.z}, hi[3] = {h.x, h.y, h.z};
+  T t_in = T(-1e300), t_out = T(1e300);
+  for (int i = 0; i < 3; ++i) {
+    if (di[i] == T(0)) {
+      if (oi[i] < -hi[i] || hi[i] < oi[i]) return max_range;  // parallel to the slab and outside it
+      continue;
+    }
+    T t1 = (-hi[i] - oi[i]) / di[i], t2 = (hi[i] - oi[i]) / di[i];
+    T lo = t1 < t2 ? t1 : t2, up = t1 < t2 ? t2 : t1;
+    if (t_in < lo) t_in = lo;
+    if (up < t_out) t_out = up;
+  }
+  T t0 = t_in < T(0) ? T(0) : t_in;
+  if (t_out < t0) return max_range;
+  return t0 < max_range ? t0 : max_range;
+}
+
 }  // namespace orc

@@ -238,6 +238,34 @@ int orc_reset(const void* world, const uint8_t* mask, uint64_t seed, const doubl
 
 int orc_box_rand_size(void) { return (int)sizeof(BoxRand); }
 
+// Depth images of n_cams cameras (row-major [cam][H][W]); camera j belongs to
+// environment env_ids[j] of a fleet with `n` environments (state double[13][n],
+// boxes double[n_obs][10][n]). See ray_box_depth for the camera model.
+void orc_render_depth(int n, int n_obs, const double* state, const double* boxes, int n_cams, const uint32_t* env_ids,
+                      int W, int H, double hfov, double max_range, const double cam_offset[3], double* out) {
+  const double f = 0.5 * W / std::tan(0.5 * hfov);
+  for (int j = 0; j < n_cams; ++j) {
+    const size_t i = env_ids[j];
+    State<double> s = load_state<double>(state, (size_t)n, i);
+    Mat3<double> R = quat_to_rot(s.q);
+    Vec3<double> o = s.p + matvec(R, Vec3<double>{cam_offset[0], cam_offset[1], cam_offset[2]});
+    for (int r = 0; r < H; ++r)
+      for (int c = 0; c < W; ++c) {
+        Vec3<double> dc = {1.0, -(c + 0.5 - 0.5 * W) / f, -(r + 0.5 - 0.5 * H) / f};
+        Vec3<double> d = matvec(R, dc);
+        double best = max_range;
+        for (int k = 0; k < n_obs; ++k) {
+          const double* bx = boxes + (size_t)k * 10 * n;
+          double t = ray_box_depth(o, d, Vec3<double>{bx[0 * n + i], bx[1 * n + i], bx[2 * n + i]},
+                                   Vec3<double>{bx[3 * n + i], bx[4 * n + i], bx[5 * n + i]},
+                                   Quat<double>{bx[6 * n + i], bx[7 * n + i], bx[8 * n + i], bx[9 * n + i]}, max_range);
+          if (t < best) best = t;
+        }
+        out[((size_t)j * H + r) * W + c] = best;
+      }
+  }
+}
+
 // One box pose draw (tests of the sampler): out7 = centre xyz, q wxyz.
 void orc_sample_box_pose(uint64_t seed, uint32_t env, uint32_t epoch, uint32_t k, const void* spec,
                          const float env_min[3], const float env_max[3], float out7[7]) {

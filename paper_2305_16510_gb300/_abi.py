@@ -79,6 +79,8 @@ SIGNATURES = {
     "ag_set_obstacles": (ctypes.c_int, [_vp, _vp]),
     "ag_set_body": (ctypes.c_int, [_vp, _vp]),
     "ag_get_obstacles": (ctypes.c_int, [_vp, _vp]),
+    "ag_render_depth": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
+                                       ctypes.POINTER(ctypes.c_float * 3), _vp, ctypes.c_uint32, _vp]),
     "ag_set_obstacle_randomization": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float * 3),
                                                      ctypes.POINTER(ctypes.c_float * 3), _vp]),
     "ag_step": (ctypes.c_int, [_vp, ctypes.c_uint32]),
@@ -186,6 +188,14 @@ def ag_set_body(ctx: int, body) -> None:
 
 def ag_get_obstacles(ctx: int, boxes) -> None:
     _check(lib().ag_get_obstacles(ctx, ptr(boxes)), "ag_get_obstacles", ctx)
+
+
+def ag_render_depth(ctx: int, width: int, height: int, hfov: float, max_range: float, cam_offset, env_ids,
+                    n_cams: int, depth) -> None:
+    off = None if cam_offset is None else (ctypes.c_float * 3)(*cam_offset)
+    rc = lib().ag_render_depth(ctx, int(width), int(height), float(hfov), float(max_range),
+                               ctypes.byref(off) if off is not None else None, ptr(env_ids), int(n_cams), ptr(depth))
+    _check(rc, "ag_render_depth", ctx)
 
 
 def ag_set_obstacle_randomization(ctx: int, env_min, env_max, per_box) -> None:

@@ -17,6 +17,7 @@
 
 #include "adjoint_internal.h"
 #include "ag.h"
+#include "depth_internal.h"
 #include "fleet_internal.h"
 
 struct ag_ctx {
@@ -38,6 +39,10 @@ struct ag_ctx {
   uint32_t* adj_count;       // [1] device scratch
   bool adj_recorded;
   agk::StepParams adj_P;     // parameters of the recorded rollout
+  // depth rendering staging (allocated on first use, grown as needed)
+  uint32_t* cam_ids;         // [n_envs]
+  float* depth_stage;        // device staging when the caller's buffer is on the host
+  size_t depth_stage_cap;    // floats
 };
 
 namespace {
@@ -199,6 +204,8 @@ void free_adjoint(ag_ctx* ctx) {
 
 void free_all(ag_ctx* ctx) {
   free_adjoint(ctx);
+  if (ctx->cam_ids) cudaFree(ctx->cam_ids);
+  if (ctx->depth_stage) cudaFree(ctx->depth_stage);
   agk::FleetBuffers& f = ctx->fb;
   void* ptrs[] = {f.state, f.motors, f.body, f.modes, f.targets, f.boxes, f.epoch, f.collided, f.reset_ids,
                   f.n_reset, f.cmd, f.wrench, f.resets, f.hits, f.order, f.boxes_slot, ctx->mask_dev,
@@ -266,6 +273,9 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   ctx->adj_tape_cap = 0;
   ctx->adj_count = nullptr;
   ctx->adj_recorded = false;
+  ctx->cam_ids = nullptr;
+  ctx->depth_stage = nullptr;
+  ctx->depth_stage_cap = 0;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     g_create_error = "no CUDA device";
     delete ctx;
@@ -377,6 +387,67 @@ ag_status ag_get_obstacles(ag_ctx* ctx, float* boxes) {
   if (count == 0) return AG_OK;
   return check_cuda(ctx, cudaMemcpyAsync(boxes, ctx->fb.boxes, count * sizeof(float), cudaMemcpyDefault, ctx->stream),
                     "copy boxes out");
+}
+
+ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
+                          const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  const uint32_t n = ctx->cfg.n_envs;
+  if (width == 0 || height == 0 || (uint64_t)width * height > (1u << 30))
+    return fail_invalid(ctx, "image size must be positive and at most 2^30 pixels");
+  if (!(hfov > 0.f && hfov < 3.14159f)) return fail_invalid(ctx, "hfov must lie in (0, pi)");
+  if (!(max_range > 0.f)) return fail_invalid(ctx, "max_range must be > 0");
+  if (n_cams == 0 || !depth) return fail_invalid(ctx, "n_cams must be >= 1 and depth non-NULL");
+  if (!env_ids && n_cams > n) return fail_invalid(ctx, "n_cams exceeds n_envs");
+  if (env_ids && n_cams > n) return fail_invalid(ctx, "at most n_envs cameras per call");
+  cudaStream_t st = ctx->stream;
+  const uint32_t* ids_dev = nullptr;
+  if (env_ids) {
+    cudaPointerAttributes pa;
+    const bool on_device = cudaPointerGetAttributes(&pa, env_ids) == cudaSuccess &&
+                           (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (!on_device)
+      for (uint32_t j = 0; j < n_cams; ++j)
+        if (env_ids[j] >= n) return fail_invalid(ctx, "environment id out of range");
+    if (!ctx->cam_ids && (s = check_cuda(ctx, alloc(ctx, &ctx->cam_ids, n), "allocate camera ids")) != AG_OK) return s;
+    if ((s = check_cuda(ctx, cudaMemcpyAsync(ctx->cam_ids, env_ids, n_cams * sizeof(uint32_t), cudaMemcpyDefault, st),
+                        "copy camera ids")) != AG_OK) return s;
+    ids_dev = ctx->cam_ids;
+  }
+  const size_t count = (size_t)n_cams * width * height;
+  cudaPointerAttributes pa;
+  const bool out_on_device = cudaPointerGetAttributes(&pa, depth) == cudaSuccess &&
+                             (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  float* out = depth;
+  if (!out_on_device) {
+    if (count > ctx->depth_stage_cap) {
+      if (ctx->depth_stage) { cudaStreamSynchronize(st); cudaFree(ctx->depth_stage); ctx->depth_stage = nullptr; }
+      ctx->depth_stage_cap = 0;
+      if ((s = check_cuda(ctx, alloc(ctx, &ctx->depth_stage, count), "allocate depth staging")) != AG_OK) return s;
+      ctx->depth_stage_cap = count;
+    }
+    out = ctx->depth_stage;
+  }
+  agk::DepthArgs a;
+  a.state = ctx->fb.state;
+  a.boxes = ctx->fb.boxes;
+  a.env_ids = ids_dev;
+  a.out = out;
+  a.n = n;
+  a.n_obs = ctx->cfg.n_obstacles;
+  a.n_cams = n_cams;
+  a.width = width;
+  a.height = height;
+  a.inv_f = (float)(std::tan(0.5 * (double)hfov) / (0.5 * width));
+  a.max_range = max_range;
+  for (int i = 0; i < 3; ++i) a.offset[i] = cam_offset ? cam_offset[i] : 0.f;
+  if ((s = check_cuda(ctx, agk::launch_render_depth(a, st), "depth launch")) != AG_OK) return s;
+  if (!out_on_device)
+    s = check_cuda(ctx, cudaMemcpyAsync(depth, out, count * sizeof(float), cudaMemcpyDeviceToHost, st), "copy depth out");
+  return s;
 }
 
 ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], const float env_max[3],

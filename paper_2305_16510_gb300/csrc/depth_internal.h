@@ -1,0 +1,24 @@
+// depth_internal.h — launch interface of the depth ray caster.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fleet_device.cuh"
+
+namespace agk {
+
+struct DepthArgs {
+  const float* state;      // [13][n]
+  const float* boxes;      // [n_obs][10][n]
+  const uint32_t* env_ids; // [n_cams] or NULL (camera j = env j)
+  float* out;              // [n_cams][height][width]
+  uint32_t n, n_obs, n_cams, width, height;
+  float inv_f;             // tan(hfov / 2) / (width / 2)
+  float max_range;
+  float offset[3];         // camera position in the body frame
+};
+
+cudaError_t launch_render_depth(const DepthArgs& a, cudaStream_t st);
+
+}  // namespace agk

@@ -82,6 +82,17 @@ class Fleet:
         """per_box: list of _abi.ag_box_randomization (one per obstacle), or None to disable."""
         _abi.ag_set_obstacle_randomization(self.ctx, env_min, env_max, per_box)
 
+    def render_depth(self, width: int, height: int, hfov: float, max_range: float, cam_offset=None,
+                     env_ids=None, n_cams: int | None = None, out=None) -> torch.Tensor:
+        """float32 [n_cams, height, width] depth images (see ag_render_depth)."""
+        ids = None if env_ids is None else self._dev(env_ids, torch.int32)
+        n_cams = (self.n if ids is None else ids.numel()) if n_cams is None else n_cams
+        if out is None:
+            out = torch.empty((n_cams, height, width), dtype=torch.float32, device=self.device)
+        _abi.ag_render_depth(self.ctx, width, height, hfov, max_range, cam_offset, ids, n_cams, out)
+        self._keep_ids = ids
+        return out
+
     def set_body(self, body) -> None:
         b = self._dev(body, torch.float32)
         _abi.ag_set_body(self.ctx, b)

@@ -619,3 +619,76 @@ def test_collision_reset_redraws_the_environments_boxes():
         np.testing.assert_array_equal(fl.boxes[k, 6:10, 0].astype(np.float32), pose[3:7])
         np.testing.assert_array_equal(fl.boxes[k, 3:6, 0], before[k, 3:6, 0])    # extents kept
     np.testing.assert_array_equal(fl.boxes[:, :, 1], before[:, :, 1])            # env 1 untouched
+
+
+# ------------------------------------------------------------ depth camera --
+def _cam_state(p=(0, 0, 0), rot=None):
+    q = (1, 0, 0, 0) if rot is None else quat_wxyz(rot)
+    return state13(p=p, q=q)[:, None]
+
+
+def test_depth_axis_aligned_wall_closed_form():
+    # a wide box whose near face is the plane x = 3: every pixel sees depth 3
+    # (distance along the optical axis), or max_range outside the face
+    boxes = np.zeros((1, 10, 1))
+    boxes[0, 0:3, 0] = [4.0, 0.0, 0.0]
+    boxes[0, 3:6, 0] = [1.0, 50.0, 50.0]
+    boxes[0, 6, 0] = 1.0
+    img = O.render_depth(_cam_state(), boxes, [0], 16, 12, math.radians(90), 20.0)
+    np.testing.assert_allclose(img, 3.0, atol=1e-12)
+    # camera offset along body x moves the face closer; yaw by 180 deg looks away
+    img = O.render_depth(_cam_state(), boxes, [0], 16, 12, math.radians(90), 20.0, cam_offset=(0.5, 0, 0))
+    np.testing.assert_allclose(img, 2.5, atol=1e-12)
+    img = O.render_depth(_cam_state(rot=Rotation.from_euler("Z", math.pi)), boxes, [0], 8, 6, 1.0, 20.0)
+    np.testing.assert_allclose(img, 20.0)
+
+
+def test_depth_pixel_geometry_and_inside_box():
+    # a thin post at (5, 0, 0): only the central columns see it; the column
+    # angle follows the pinhole model with f = (W/2) / tan(hfov/2)
+    W, H, hfov = 64, 8, math.radians(60)
+    boxes = np.zeros((1, 10, 1))
+    boxes[0, 0:3, 0] = [5.0, 0.0, 0.0]
+    boxes[0, 3:6, 0] = [0.1, 0.1, 10.0]
+    boxes[0, 6, 0] = 1.0
+    img = O.render_depth(_cam_state(), boxes, [0], W, H, hfov, 30.0)
+    f = 0.5 * W / math.tan(0.5 * hfov)
+    for c in range(W):
+        y = -(c + 0.5 - 0.5 * W) / f             # ray slope to the left
+        hits = abs(y * 4.9) <= 0.1 or abs(y * 5.1) <= 0.1
+        assert (img[0, 0, c] < 30.0) == hits
+    # a camera inside a box sees depth 0
+    boxes[0, 0:3, 0] = [0.0, 0.0, 0.0]
+    img = O.render_depth(_cam_state(), boxes, [0], 4, 4, 1.0, 30.0)
+    np.testing.assert_array_equal(img, 0.0)
+
+
+def test_depth_brute_force_ray_march():
+    # rotated boxes and a rotated camera: the depth of sampled pixels equals
+    # the first point of a fine march along the ray that lies in a box
+    rng = np.random.default_rng(21)
+    n_obs = 5
+    boxes = np.zeros((n_obs, 10, 1))
+    for k in range(n_obs):
+        boxes[k, 0:3, 0] = rng.uniform([2, -3, -2], [8, 3, 2])
+        boxes[k, 3:6, 0] = rng.uniform(0.2, 1.0, 3)
+        boxes[k, 6:10, 0] = quat_wxyz(Rotation.random(random_state=rng))
+    rot = Rotation.from_euler("ZYX", [0.2, -0.1, 0.15])
+    W, H, hfov, rmax = 20, 12, math.radians(80), 12.0
+    img = O.render_depth(_cam_state(rot=rot), boxes, [0], W, H, hfov, rmax)
+    f = 0.5 * W / math.tan(0.5 * hfov)
+    ts = np.linspace(0, rmax, 24001)
+    checked = 0
+    for r in range(0, H, 3):
+        for c in range(0, W, 2):
+            d = rot.apply([1.0, -(c + 0.5 - 0.5 * W) / f, -(r + 0.5 - 0.5 * H) / f])
+            pts = ts[:, None] * d[None, :]
+            inside = np.zeros(len(ts), bool)
+            for k in range(n_obs):
+                rb = Rotation.from_quat(np.roll(boxes[k, 6:10, 0], -1))
+                loc = rb.inv().apply(pts - boxes[k, 0:3, 0])
+                inside |= np.all(np.abs(loc) <= boxes[k, 3:6, 0], axis=1)
+            t_march = ts[np.argmax(inside)] if inside.any() else rmax
+            assert abs(img[0, r, c] - t_march) <= 1.5 * (ts[1] - ts[0]) * np.linalg.norm(d), (r, c)
+            checked += 1
+    assert checked > 30
