@@ -33,7 +33,6 @@ def _np(t):
 def _compare(gpu, orc, max_bad_frac):
     close = np.abs(gpu.astype(np.float64) - orc) <= 1e-4 * np.maximum(1.0, orc)
     assert close.mean() >= 1.0 - max_bad_frac, close.mean()
-    assert np.any(orc < orc.max())       # the cameras really see boxes
 
 
 def test_depth_matches_oracle_small_images():
@@ -47,6 +46,7 @@ def test_depth_matches_oracle_small_images():
     img = _np(fl.render_depth(96, 64, hfov, rng_max, cam_offset=(0.1, 0.0, 0.05), env_ids=ids))
     ref = O.render_depth(_np(fl.state()), _np(fl.obstacles()), ids, 96, 64, hfov, rng_max, (0.1, 0.0, 0.05))
     _compare(img, ref, 0.002)
+    assert (ref < rng_max).mean() > 0.05          # the cameras really see boxes
     # host destination and default camera ids
     host = np.empty((8, 32, 48), np.float32)
     _abi.ag_render_depth(fl.ctx, 48, 32, hfov, rng_max, None, None, 8, host)
@@ -71,6 +71,7 @@ def test_depth_paper_resolution_1024_robots_sampled():
     fl.step(10)
     img = fl.render_depth(480, 270, math.radians(87), 10.0)
     assert img.shape == (1024, 270, 480)
+    assert (img < 10.0).float().mean().item() > 0.05
     st, bx = _np(fl.state()), _np(fl.obstacles())
     for j in (0, 511, 1023):
         ref = O.render_depth(st, bx, [j], 480, 270, math.radians(87), 10.0)
