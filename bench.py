@@ -7,7 +7,7 @@ STEPS_PER_CALL simulated steps (all stages: controller, allocation, motor
 lag, RK4, renormalisation, sphere-vs-box test, Philox resets, compaction).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--envs N_ENVS] [--steps-per-call C] [--parts fused,plain,e2e,paper,mixed,adjoint,serve]
+                    [--envs N_ENVS] [--steps-per-call C] [--parts fused,plain,e2e,paper,mixed,depth,adjoint,serve]
 
 --envs / --steps-per-call / --parts run a reduced case of the same workload
 (for profiler captures); the default is the full workload and every part.
@@ -271,6 +271,8 @@ def gpu_arm(args) -> dict | None:
     fl.close()
     if "mixed" in parts:
         out["mixed"] = mixed_part(seed, world)
+    if "depth" in parts:
+        out["depth"] = depth_part(seed, world)
     if "adjoint" in parts:
         out["adjoint"] = adjoint_part(seed, world)
     if "serve" in parts:
@@ -334,6 +336,35 @@ def mixed_part(seed: int, world: int) -> dict:
             "workload": "4,194,304 vehicles (1,677,722 quad / 1,677,722 hexa / 838,860 octo), mass and inertia "
                         "x U[0.8, 1.2], tau 0.03, drag 0.1, body-velocity targets U[-2, 2]^3, SIE, 500 steps "
                         "as 10 x (50-step ag_step + 1 % ag_reset mask)"}
+
+
+# ------------------------------------------------------------------- depth --
+def depth_part(seed: int, world: int) -> dict:
+    """2^10 robots, each a 270 x 480 depth camera (87 deg horizontal field of
+    view, 10 m range) ray-cast against its environment's 16 boxes."""
+    import math
+    import torch
+    from paper_2305_16510_gb300 import workloads as W
+    w = W.scaled(W.WORKLOADS[WORKLOAD], 1024)
+    inp = W.make_inputs(w, seed)
+    fl = make_fleet(w, inp, seed)
+    fl.step(10)
+    out = torch.empty((1024, 270, 480), dtype=torch.float32, device="cuda")
+
+    def render():
+        fl.render_depth(480, 270, math.radians(87), 10.0, out=out)
+
+    for _ in range(3):
+        render()
+    torch.cuda.synchronize()
+    k = 20
+    secs, per = time_calls(fl, render, k, world)
+    fl.close()
+    frames = 1024 * k * world
+    return {"value": frames / secs, "unit": "depth frames/s", "ms_per_1024_frames": float(np.mean(per)),
+            "ray_box_tests_per_s": frames * 270 * 480 * 16 / secs,
+            "workload": "1,024 robots x 270 x 480 depth camera, 16 oriented boxes per environment, 87 deg hfov",
+            "paper_value": 1800.0, "paper_hardware": "2x RTX 3090, Isaac Gym camera sensors (graphics renderer)"}
 
 
 # ----------------------------------------------------------------- adjoint --
@@ -534,7 +565,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--envs", type=int, default=0, help="reduced fleet size (default: the full workload)")
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
-    ap.add_argument("--parts", default="fused,plain,e2e,paper,mixed,adjoint,serve")
+    ap.add_argument("--parts", default="fused,plain,e2e,paper,mixed,depth,adjoint,serve")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
