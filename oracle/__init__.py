@@ -67,6 +67,8 @@ def _declare(L: ctypes.CDLL) -> None:
                               _u32p, _u32p, ctypes.c_int]
     L.orc_reset.argtypes = [vp, _u8p, ctypes.c_uint64, _dp, _dp, _dp, _u32p, _u32p, _dp]
     L.orc_box_rand_size.restype = ctypes.c_int
+    L.orc_reach_task.argtypes = [ctypes.c_int, _dp, _dp, _u8p, _u32p, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_uint32, _dp, _dp, _u8p]
     L.orc_render_depth.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, _u32p, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]
     L.orc_sample_box_pose.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp, _fp,
@@ -370,6 +372,19 @@ def render_depth(state, boxes, env_ids, width, height, hfov, max_range, cam_offs
     lib().orc_render_depth(int(n), int(n_obs), _ptr(st, _dp), _ptr(bx, _dp), len(ids), _ptr(ids, _u32p), int(width),
                            int(height), float(hfov), float(max_range), _ptr(_f64(cam_offset), _dp), _ptr(out, _dp))
     return out
+
+
+def reach_task(state, goals, collided, steps, w_v=0.1, w_w=0.01, crash=10.0, max_dist=8.0, max_steps=500):
+    """(obs [13, n], reward [n], done [n]) of the reach-a-setpoint task."""
+    st, g = _f64(state), _f64(goals)
+    n = st.shape[1]
+    col = np.ascontiguousarray(np.asarray(collided, dtype=np.uint8))
+    stp = np.ascontiguousarray(np.asarray(steps, dtype=np.uint32))
+    obs, rew, done = np.zeros((13, n)), np.zeros(n), np.zeros(n, np.uint8)
+    lib().orc_reach_task(int(n), _ptr(st, _dp), _ptr(g, _dp), _ptr(col, _u8p), _ptr(stp, _u32p), float(w_v),
+                         float(w_w), float(crash), float(max_dist), int(max_steps), _ptr(obs, _dp), _ptr(rew, _dp),
+                         _ptr(done, _u8p))
+    return obs, rew, done
 
 
 def hover_thrust(m, n_rot) -> np.float32:

@@ -238,6 +238,34 @@ int orc_reset(const void* world, const uint8_t* mask, uint64_t seed, const doubl
 
 int orc_box_rand_size(void) { return (int)sizeof(BoxRand); }
 
+// Reach-a-setpoint task (Sec. I: robots learn to reach a target setpoint
+// through the attitude command interface). Reading of its observation, reward
+// and termination, per environment i with goal g_i:
+//   obs    = (p - g, v, q (w >= 0 hemisphere), Omega)            13 numbers
+//   reward = -crash                                 if the vehicle collided
+//            -|p - g| - w_v |v| - w_w |Omega|       otherwise
+//   done   = collided  or  |p - g| > max_dist  or  steps >= max_steps
+// (a collided vehicle was already re-drawn by the step, so its reward carries
+// no distance term; steps counts the episode's steps including this one).
+void orc_reach_task(int n, const double* state, const double* goals, const uint8_t* collided, const uint32_t* steps,
+                    double w_v, double w_w, double crash, double max_dist, uint32_t max_steps, double* obs,
+                    double* reward, uint8_t* done) {
+  for (int i = 0; i < n; ++i) {
+    double s[13];
+    for (int r = 0; r < 13; ++r) s[r] = state[(size_t)r * n + i];
+    double e[3] = {s[0] - goals[i], s[1] - goals[(size_t)n + i], s[2] - goals[2 * (size_t)n + i]};
+    const double sign = s[6] < 0.0 ? -1.0 : 1.0;
+    double o[13] = {e[0], e[1], e[2], s[3], s[4], s[5], sign * s[6], sign * s[7], sign * s[8], sign * s[9],
+                    s[10], s[11], s[12]};
+    for (int r = 0; r < 13; ++r) obs[(size_t)r * n + i] = o[r];
+    const double dist = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    const double speed = std::sqrt(s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+    const double rate = std::sqrt(s[10] * s[10] + s[11] * s[11] + s[12] * s[12]);
+    reward[i] = collided[i] ? -crash : -dist - w_v * speed - w_w * rate;
+    done[i] = (collided[i] || dist > max_dist || steps[i] >= max_steps) ? 1 : 0;
+  }
+}
+
 // Depth images of n_cams cameras (row-major [cam][H][W]); camera j belongs to
 // environment env_ids[j] of a fleet with `n` environments (state double[13][n],
 // boxes double[n_obs][10][n]). See ray_box_depth for the camera model.

@@ -692,3 +692,28 @@ def test_depth_brute_force_ray_march():
             assert abs(img[0, r, c] - t_march) <= 1.5 * (ts[1] - ts[0]) * np.linalg.norm(d), (r, c)
             checked += 1
     assert checked > 30
+
+
+# ------------------------------------------------------------ reach task --
+def test_reach_task_definition_cases():
+    n = 4
+    st = np.zeros((13, n))
+    st[6] = 1.0
+    st[0:3, 0] = [1.0, 2.0, 2.0]          # 3 m from the goal
+    st[3:6, 1] = [0.0, 3.0, 4.0]          # at the goal, moving at 5 m/s
+    st[6:10, 2] = [-1.0, 0.0, 0.0, 0.0]   # q and -q are the same attitude: obs keeps w >= 0
+    st[0, 2] = 3.0                        # collided: the crash penalty alone
+    st[0, 3] = 20.0                       # too far away
+    goals = np.zeros((3, n))
+    obs, rew, done = O.reach_task(st, goals, [0, 0, 1, 0], [0, 0, 0, 0])
+    np.testing.assert_allclose(rew, [-3.0, -0.5, -10.0, -20.0])
+    assert list(done) == [0, 0, 1, 1]
+    np.testing.assert_allclose(obs[6:10, 2], [1.0, 0, 0, 0])
+    np.testing.assert_allclose(obs[0:3, 0], [1.0, 2.0, 2.0])
+    np.testing.assert_allclose(obs[3:6, 1], [0.0, 3.0, 4.0])
+    # the goal is subtracted, not added
+    obs2, rew2, _ = O.reach_task(st, goals + np.array([[1.0], [2.0], [2.0]]), [0] * n, [0] * n)
+    np.testing.assert_allclose(obs2[0:3, 0], 0.0, atol=1e-15)
+    assert rew2[0] == 0.0
+    _, _, done = O.reach_task(st, goals, [0] * n, [499, 500, 0, 0])
+    assert list(done) == [0, 1, 0, 1]
