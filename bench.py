@@ -7,7 +7,7 @@ STEPS_PER_CALL simulated steps (all stages: controller, allocation, motor
 lag, RK4, renormalisation, sphere-vs-box test, Philox resets, compaction).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--envs N_ENVS] [--steps-per-call C] [--parts fused,plain,e2e,paper,mixed,depth,adjoint,serve]
+                    [--envs N_ENVS] [--steps-per-call C] [--parts fused,plain,e2e,paper,mixed,depth,task,adjoint,serve]
 
 --envs / --steps-per-call / --parts run a reduced case of the same workload
 (for profiler captures); the default is the full workload and every part.
@@ -273,6 +273,8 @@ def gpu_arm(args) -> dict | None:
         out["mixed"] = mixed_part(seed, world)
     if "depth" in parts:
         out["depth"] = depth_part(seed, world)
+    if "task" in parts:
+        out["task"] = task_part(seed, world)
     if "adjoint" in parts:
         out["adjoint"] = adjoint_part(seed, world)
     if "serve" in parts:
@@ -365,6 +367,35 @@ def depth_part(seed: int, world: int) -> dict:
             "ray_box_tests_per_s": frames * 270 * 480 * 16 / secs,
             "workload": "1,024 robots x 270 x 480 depth camera, 16 oriented boxes per environment, 87 deg hfov",
             "paper_value": 1800.0, "paper_hardware": "2x RTX 3090, Isaac Gym camera sensors (graphics renderer)"}
+
+
+# -------------------------------------------------------------------- task --
+def task_part(seed: int, world: int) -> dict:
+    """Reach-a-setpoint task steps (ag_reach_step: actions to attitude
+    commands, one fleet step, reward, termination, auto-reset, observations)
+    over 1,048,576 quads, semi-implicit Euler, 1 substep, no obstacles."""
+    import torch
+    from paper_2305_16510_gb300.task import ReachEnv
+    n = 1 << 20
+    rng = np.random.default_rng(seed)
+    goals = torch.from_numpy(rng.uniform(-1.0, 1.0, (3, n)).astype(np.float32))
+    env = ReachEnv(n, goals=goals, seed=seed)
+    env.reset()
+    actions = torch.from_numpy(rng.uniform(-0.3, 0.3, (n, 4)).astype(np.float32)).cuda()
+    from paper_2305_16510_gb300 import _abi
+
+    def step():
+        _abi.ag_reach_step(env.fleet.ctx, actions, env.obs, env.reward, env.done)
+
+    for _ in range(5):
+        step()
+    torch.cuda.synchronize()
+    k = 200
+    secs, per = time_calls(env.fleet, step, k, world)
+    env.close()
+    return {"value": n * k * world / secs, "unit": "task env-steps/s", "ms_per_step": float(np.mean(per)),
+            "workload": "reach-a-setpoint, 1,048,576 quads, attitude interface, SIE 1 substep, no obstacles, "
+                        "obs [n,13] + reward + done per step", "launches_per_step": 3}
 
 
 # ----------------------------------------------------------------- adjoint --
@@ -565,7 +596,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--envs", type=int, default=0, help="reduced fleet size (default: the full workload)")
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
-    ap.add_argument("--parts", default="fused,plain,e2e,paper,mixed,depth,adjoint,serve")
+    ap.add_argument("--parts", default="fused,plain,e2e,paper,mixed,depth,task,adjoint,serve")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -287,6 +287,58 @@ ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, fl
                       float* grad_gains_per_env);
 
 /* ------------------------------------------------------------------------
+ * Reach-a-setpoint task (Sec. I: policies learn to fly the vehicle to a goal
+ * setpoint through the attitude or velocity command interface).
+ *
+ * One task step maps the policy's actions to every environment's command,
+ * advances the fleet one step (ag_step with substeps_per_step substeps,
+ * collision resets included) and then, per environment i with goal g_i:
+ *   reward  = -crash                                  if it collided
+ *             -|p - g| - w_v |v| - w_omega |Omega|    otherwise
+ *   done    = collided or |p - g| > max_dist or steps >= max_steps
+ *             (steps counts the episode's steps, this one included)
+ * An episode that ended without a collision is reset in place exactly as
+ * ag_reset draws it (a collision already reset it inside the step), and the
+ * step counter of every ended episode returns to 0. The observation then
+ * describes the state the policy acts on next (after any reset):
+ *   obs[i] = (p - g (3), v (3), q (w, x, y, z) with w >= 0 (4), Omega (3))
+ * All of it runs in two kernels besides the fleet step; nothing synchronises.
+ * ------------------------------------------------------------------------ */
+typedef struct ag_reach_config {
+  uint32_t command_mode;   /* AG_MODE_ATT_THRUST or AG_MODE_BODY_VEL */
+  float action_scale[4];   /* command_k = action_offset[k] + action_scale[k] * clamp(a_k, -1, 1) */
+  float action_offset[4];  /* (targets as at ag_mode: attitude (phi, theta, psi_dot, f), velocity (v, psi_dot)) */
+  float w_v;               /* reward weight of the speed |v| [1/(m/s)] */
+  float w_omega;           /* reward weight of the body rate |Omega| [1/(rad/s)] */
+  float crash;             /* penalty of a collision */
+  float max_dist;          /* an episode ends beyond this distance to the goal [m] */
+  uint32_t max_steps;      /* an episode ends after this many steps (>= 1) */
+} ag_reach_config;
+
+/* Attitude interface for the default 0.75 kg quad: roll and pitch within
+ * +-pi/6, yaw rate within +-1 rad/s, thrust m g (1 +- 0.5); w_v 0.1,
+ * w_omega 0.01, crash 10, max_dist 8 m, max_steps 500. */
+void ag_reach_config_default(ag_reach_config* cfg);
+
+/* Starts the task: every environment's mode becomes cfg->command_mode, the
+ * goals float[3][n_envs] (host or device) are copied and every step counter
+ * is set to 0. States are left as they are (call ag_reset first for fresh
+ * episodes). AG_ERR_INVALID for another mode, max_steps 0, a negative weight
+ * or penalty, max_dist <= 0 or goals NULL. */
+ag_status ag_reach_begin(ag_ctx* ctx, const ag_reach_config* cfg, const float* goals);
+
+/* One task step. actions: device float[n_envs][4], 16-byte aligned. obs:
+ * device float[n_envs][13]; reward: device float[n_envs]; done: device
+ * uint8[n_envs]. The collision resets use the context's reset seed (that of
+ * the last ag_reset, else the config's). AG_ERR_STATE before ag_reach_begin;
+ * AG_ERR_INVALID for a NULL or misaligned pointer. */
+ag_status ag_reach_step(ag_ctx* ctx, const float* actions, float* obs, float* reward, uint8_t* done);
+
+/* Observations float[n_envs][13] (device) of the current states, as written
+ * by ag_reach_step; nothing else changes. AG_ERR_STATE before ag_reach_begin. */
+ag_status ag_reach_observe(ag_ctx* ctx, float* obs);
+
+/* ------------------------------------------------------------------------
  * Continuous-batching rollout server.
  *
  * A server owns one device slab of hbm_budget_bytes (allocated once at

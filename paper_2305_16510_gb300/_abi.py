@@ -47,6 +47,12 @@ class ag_box_randomization(ctypes.Structure):
                 ("lock", ctypes.c_uint32), ("fixed", ctypes.c_float * 6)]
 
 
+class ag_reach_config(ctypes.Structure):
+    _fields_ = [("command_mode", ctypes.c_uint32), ("action_scale", ctypes.c_float * 4),
+                ("action_offset", ctypes.c_float * 4), ("w_v", ctypes.c_float), ("w_omega", ctypes.c_float),
+                ("crash", ctypes.c_float), ("max_dist", ctypes.c_float), ("max_steps", ctypes.c_uint32)]
+
+
 class ag_server_config(ctypes.Structure):
     _fields_ = [("physics", ag_config), ("max_active", ctypes.c_uint32), ("chunk_steps", ctypes.c_uint32),
                 ("hbm_budget_bytes", ctypes.c_uint64)]
@@ -95,6 +101,10 @@ SIGNATURES = {
     "ag_set_gains": (ctypes.c_int, [_vp, _vp]),
     "ag_rollout_loss": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
     "ag_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ag_reach_config_default": (None, [ctypes.POINTER(ag_reach_config)]),
+    "ag_reach_begin": (ctypes.c_int, [_vp, ctypes.POINTER(ag_reach_config), _vp]),
+    "ag_reach_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ag_reach_observe": (ctypes.c_int, [_vp, _vp]),
     "ag_server_config_default": (None, [ctypes.POINTER(ag_server_config)]),
     "ag_server_create": (ctypes.c_int, [ctypes.POINTER(ag_server_config), ctypes.POINTER(_vp)]),
     "ag_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(ag_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -267,6 +277,24 @@ def ag_rollout_loss(ctx: int, n_steps: int, w_pos: float, w_omega: float, p_goal
 def ag_backward(ctx: int, loss_weights=None, grad_x0=None, grad_gains=None, grad_gains_per_env=None) -> None:
     _check(lib().ag_backward(ctx, ptr(loss_weights), ptr(grad_x0), ptr(grad_gains), ptr(grad_gains_per_env)),
            "ag_backward", ctx)
+
+
+def ag_reach_config_default() -> ag_reach_config:
+    c = ag_reach_config()
+    lib().ag_reach_config_default(ctypes.byref(c))
+    return c
+
+
+def ag_reach_begin(ctx: int, cfg: ag_reach_config, goals) -> None:
+    _check(lib().ag_reach_begin(ctx, ctypes.byref(cfg), ptr(goals)), "ag_reach_begin", ctx)
+
+
+def ag_reach_step(ctx: int, actions, obs, reward, done) -> None:
+    _check(lib().ag_reach_step(ctx, ptr(actions), ptr(obs), ptr(reward), ptr(done)), "ag_reach_step", ctx)
+
+
+def ag_reach_observe(ctx: int, obs) -> None:
+    _check(lib().ag_reach_observe(ctx, ptr(obs)), "ag_reach_observe", ctx)
 
 
 def ag_server_config_default() -> ag_server_config:

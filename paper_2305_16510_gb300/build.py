@@ -19,7 +19,7 @@ LIB_NAME = "libaerialgb.so"
 LIB_PATH = os.path.join(PKG, LIB_NAME)
 BUILD_DIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["ag_api.cu", "fleet_kernels.cu", "adjoint.cu", "serve.cu", "depth.cu"]
+CUDA_SOURCES = ["ag_api.cu", "fleet_kernels.cu", "adjoint.cu", "serve.cu", "depth.cu", "task.cu"]
 
 
 def _nvcc() -> str:

@@ -19,6 +19,7 @@
 #include "ag.h"
 #include "depth_internal.h"
 #include "fleet_internal.h"
+#include "task_internal.h"
 
 struct ag_ctx {
   ag_config cfg;
@@ -43,6 +44,11 @@ struct ag_ctx {
   uint32_t* cam_ids;         // [n_envs]
   float* depth_stage;        // device staging when the caller's buffer is on the host
   size_t depth_stage_cap;    // floats
+  // reach-a-setpoint task (allocated at the first ag_reach_begin)
+  ag_reach_config reach;
+  float* reach_goals;        // [3][n_envs]
+  uint32_t* reach_steps;     // [n_envs]
+  bool reach_active;
 };
 
 namespace {
@@ -206,6 +212,8 @@ void free_all(ag_ctx* ctx) {
   free_adjoint(ctx);
   if (ctx->cam_ids) cudaFree(ctx->cam_ids);
   if (ctx->depth_stage) cudaFree(ctx->depth_stage);
+  if (ctx->reach_goals) cudaFree(ctx->reach_goals);
+  if (ctx->reach_steps) cudaFree(ctx->reach_steps);
   agk::FleetBuffers& f = ctx->fb;
   void* ptrs[] = {f.state, f.motors, f.body, f.modes, f.targets, f.boxes, f.epoch, f.collided, f.reset_ids,
                   f.n_reset, f.cmd, f.wrench, f.resets, f.hits, f.order, f.boxes_slot, ctx->mask_dev,
@@ -276,6 +284,9 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   ctx->cam_ids = nullptr;
   ctx->depth_stage = nullptr;
   ctx->depth_stage_cap = 0;
+  ctx->reach_goals = nullptr;
+  ctx->reach_steps = nullptr;
+  ctx->reach_active = false;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     g_create_error = "no CUDA device";
     delete ctx;
@@ -528,6 +539,100 @@ ag_status ag_reset(ag_ctx* ctx, const uint8_t* mask, uint64_t seed) {
   ctx->seed = seed;
   return check_cuda(ctx, agk::launch_reset(ctx->fb, mask_dev, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32),
                                            ctx->stream), "reset launch");
+}
+
+void ag_reach_config_default(ag_reach_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->command_mode = AG_MODE_ATT_THRUST;
+  const float pi6 = 0.52359878f, mg = 0.75f * 9.81f;
+  const float scale[4] = {pi6, pi6, 1.0f, 0.5f * mg}, offset[4] = {0.f, 0.f, 0.f, mg};
+  for (int k = 0; k < 4; ++k) {
+    c->action_scale[k] = scale[k];
+    c->action_offset[k] = offset[k];
+  }
+  c->w_v = 0.1f;
+  c->w_omega = 0.01f;
+  c->crash = 10.f;
+  c->max_dist = 8.f;
+  c->max_steps = 500;
+}
+
+ag_status ag_reach_begin(ag_ctx* ctx, const ag_reach_config* cfg, const float* goals) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!cfg || !goals) return fail_invalid(ctx, "cfg and goals must be non-NULL");
+  if (cfg->command_mode != AG_MODE_ATT_THRUST && cfg->command_mode != AG_MODE_BODY_VEL)
+    return fail_invalid(ctx, "command_mode must be AG_MODE_ATT_THRUST or AG_MODE_BODY_VEL");
+  if (cfg->max_steps == 0) return fail_invalid(ctx, "max_steps must be >= 1");
+  if (!(cfg->w_v >= 0.f && cfg->w_omega >= 0.f && cfg->crash >= 0.f))
+    return fail_invalid(ctx, "weights and the crash penalty must be >= 0");
+  if (!(cfg->max_dist > 0.f)) return fail_invalid(ctx, "max_dist must be > 0");
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(cfg->action_scale[k]) || !std::isfinite(cfg->action_offset[k]))
+      return fail_invalid(ctx, "action scale and offset must be finite");
+  const size_t n = ctx->cfg.n_envs;
+  cudaStream_t st = ctx->stream;
+  if (!ctx->reach_goals && (s = check_cuda(ctx, alloc(ctx, &ctx->reach_goals, 3 * n), "allocate goals")) != AG_OK)
+    return s;
+  if (!ctx->reach_steps && (s = check_cuda(ctx, alloc(ctx, &ctx->reach_steps, n), "allocate step counters")) != AG_OK)
+    return s;
+  if ((s = check_cuda(ctx, cudaMemcpyAsync(ctx->reach_goals, goals, 3 * n * sizeof(float), cudaMemcpyDefault, st),
+                      "copy goals")) != AG_OK) return s;
+  if ((s = check_cuda(ctx, cudaMemsetAsync(ctx->reach_steps, 0, n * sizeof(uint32_t), st), "clear step counters")) !=
+      AG_OK) return s;
+  if ((s = check_cuda(ctx, cudaMemsetAsync(ctx->fb.modes, (int)cfg->command_mode, n, st), "set modes")) != AG_OK)
+    return s;
+  if ((s = check_cuda(ctx, agk::launch_build_order(ctx->fb, ctx->order_scratch, st), "build order")) != AG_OK)
+    return s;
+  ctx->reach = *cfg;
+  ctx->reach_active = true;
+  return AG_OK;
+}
+
+static agk::ReachArgs reach_args(ag_ctx* ctx, const float* actions, float* obs, float* reward, uint8_t* done) {
+  agk::ReachArgs a;
+  a.fb = ctx->fb;
+  a.actions = actions;
+  a.goals = ctx->reach_goals;
+  a.steps = ctx->reach_steps;
+  a.obs = obs;
+  a.reward = reward;
+  a.done = done;
+  const ag_reach_config& c = ctx->reach;
+  for (int k = 0; k < 4; ++k) {
+    a.scale[k] = c.action_scale[k];
+    a.offset[k] = c.action_offset[k];
+  }
+  a.w_v = c.w_v;
+  a.w_omega = c.w_omega;
+  a.crash = c.crash;
+  a.max_dist = c.max_dist;
+  a.max_steps = c.max_steps;
+  a.seed_lo = (uint32_t)(ctx->seed & 0xFFFFFFFFu);
+  a.seed_hi = (uint32_t)(ctx->seed >> 32);
+  return a;
+}
+
+ag_status ag_reach_step(ag_ctx* ctx, const float* actions, float* obs, float* reward, uint8_t* done) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!ctx->reach_active) return AG_ERR_STATE;
+  if (!actions || !obs || !reward || !done) return fail_invalid(ctx, "actions, obs, reward and done must be non-NULL");
+  if (reinterpret_cast<uintptr_t>(actions) % 16 != 0) return fail_invalid(ctx, "actions must be 16-byte aligned");
+  const agk::ReachArgs a = reach_args(ctx, actions, obs, reward, done);
+  if ((s = check_cuda(ctx, agk::launch_reach_actions(a, ctx->stream), "task action launch")) != AG_OK) return s;
+  if ((s = step_common(ctx, ctx->cfg.substeps_per_step, true)) != AG_OK) return s;
+  return check_cuda(ctx, agk::launch_reach_tail(a, false, ctx->stream), "task tail launch");
+}
+
+ag_status ag_reach_observe(ag_ctx* ctx, float* obs) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!ctx->reach_active) return AG_ERR_STATE;
+  if (!obs) return fail_invalid(ctx, "obs must be non-NULL");
+  return check_cuda(ctx, agk::launch_reach_tail(reach_args(ctx, nullptr, obs, nullptr, nullptr), true, ctx->stream),
+                    "task observe launch");
 }
 
 ag_status ag_get_state(ag_ctx* ctx, float* state, uint8_t* collided, uint32_t* reset_ids, uint32_t* n_reset) {

@@ -164,20 +164,7 @@ __global__ void __launch_bounds__(256) k_reset(FleetBuffers fb, const uint8_t* m
   const uint32_t n = fb.n;
   const bool active = env < n;
   const bool flag = active && (mask == nullptr || mask[env] != 0);
-  if (flag) {
-    const uint32_t epoch = fb.epoch[env] + 1u;
-    fb.epoch[env] = epoch;
-    ResetValues r = draw_reset(seed_lo, seed_hi, env, epoch);
-    float* st = fb.state;
-    st[0 * n + env] = r.p[0]; st[1 * n + env] = r.p[1]; st[2 * n + env] = r.p[2];
-    st[3 * n + env] = r.v[0]; st[4 * n + env] = r.v[1]; st[5 * n + env] = r.v[2];
-    st[6 * n + env] = r.q[0]; st[7 * n + env] = r.q[1]; st[8 * n + env] = r.q[2]; st[9 * n + env] = r.q[3];
-    st[10 * n + env] = 0.f; st[11 * n + env] = 0.f; st[12 * n + env] = 0.f;
-    const int nrot = rotor_count(fb, env);
-    const float hv = hover_per_motor(fb.body[env], nrot);
-    for (int k = 0; k < 8; ++k) fb.motors[k * n + env] = k < nrot ? hv : 0.f;
-    if (fb.box_rand) redraw_boxes(fb, env, fb.slot_of ? fb.slot_of[env] : env, epoch, seed_lo, seed_hi, NoBoxes{});
-  }
+  if (flag) reset_env(fb, env, seed_lo, seed_hi);
   if (active) fb.collided[env] = 0;
   append_compact(flag, env, fb.reset_ids, fb.n_reset);
 }

@@ -193,6 +193,25 @@ __device__ __noinline__ void redraw_boxes(const FleetBuffers& fb, uint32_t env, 
   }
 }
 
+// Resets environment env in device memory (the ag_reset draw): epoch + 1,
+// Philox state draw, every motor at hover, zero for the unused ones, and new
+// box poses when re-placement is on.
+__device__ __forceinline__ void reset_env(const FleetBuffers& fb, uint32_t env, uint32_t seed_lo, uint32_t seed_hi) {
+  const uint32_t n = fb.n;
+  const uint32_t epoch = fb.epoch[env] + 1u;
+  fb.epoch[env] = epoch;
+  ResetValues r = draw_reset(seed_lo, seed_hi, env, epoch);
+  float* st = fb.state;
+  st[0 * n + env] = r.p[0]; st[1 * n + env] = r.p[1]; st[2 * n + env] = r.p[2];
+  st[3 * n + env] = r.v[0]; st[4 * n + env] = r.v[1]; st[5 * n + env] = r.v[2];
+  st[6 * n + env] = r.q[0]; st[7 * n + env] = r.q[1]; st[8 * n + env] = r.q[2]; st[9 * n + env] = r.q[3];
+  st[10 * n + env] = 0.f; st[11 * n + env] = 0.f; st[12 * n + env] = 0.f;
+  const int nrot = rotor_count(fb, env);
+  const float hv = hover_per_motor(fb.body[env], nrot);
+  for (int k = 0; k < 8; ++k) fb.motors[k * n + env] = k < nrot ? hv : 0.f;
+  if (fb.box_rand) redraw_boxes(fb, env, fb.slot_of ? fb.slot_of[env] : env, epoch, seed_lo, seed_hi, NoBoxes{});
+}
+
 template <int NROT, int INTEG, bool DRAG, class Boxes>
 __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, uint32_t slot,
                                          int n_steps, int substeps, int n_obs, const Boxes& boxes, uint32_t seed_lo,

@@ -1,0 +1,32 @@
+// task_internal.h — launch interface of the reach-a-setpoint task kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fleet_internal.h"
+
+namespace agk {
+
+struct ReachArgs {
+  FleetBuffers fb;
+  const float* actions;  // [n][4], 16-byte aligned
+  const float* goals;    // [3][n]
+  uint32_t* steps;       // [n] steps taken in the current episode
+  float* obs;            // [n][13]
+  float* reward;         // [n]
+  uint8_t* done;         // [n]
+  float scale[4], offset[4];
+  float w_v, w_omega, crash, max_dist;
+  uint32_t max_steps;
+  uint32_t seed_lo, seed_hi;
+};
+
+// commands = offset + scale * clamp(actions, -1, 1), into fb.targets
+cudaError_t launch_reach_actions(const ReachArgs& a, cudaStream_t st);
+// reward and termination of the step just taken, in-place reset of the
+// episodes that ended without a collision, observations of the new state;
+// observe_only: observations alone
+cudaError_t launch_reach_tail(const ReachArgs& a, bool observe_only, cudaStream_t st);
+
+}  // namespace agk

@@ -1,0 +1,166 @@
+"""Reach-a-setpoint task (ag_reach_step) vs the oracle, one step at a time.
+
+Sec. I: policies fly the vehicle to a goal setpoint through the attitude or
+the velocity command interface. Each task step maps actions to commands,
+takes one fleet step, scores it, ends episodes (collision, distance, step
+limit), re-draws the episodes that ended without a collision and observes
+the new state. The oracle side composes the same definition from its own
+rollout, reset and task functions, starting every step from the GPU's
+float32 state (teacher forcing).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from harness import box_margin, oracle_fleet_from, oracle_world
+from paper_2305_16510_gb300 import _abi
+from paper_2305_16510_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2305_16510_gb300 import build
+    build.build()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _cfg(mode, max_steps, max_dist):
+    c = _abi.ag_reach_config_default()
+    c.command_mode = mode
+    if mode == _abi.AG_MODE_BODY_VEL:
+        c.action_scale[:] = [2.0, 2.0, 2.0, 1.0]
+        c.action_offset[:] = [0.0, 0.0, 0.0, 0.0]
+    c.max_steps, c.max_dist = max_steps, max_dist
+    return c
+
+
+def _params(c):
+    return dict(w_v=c.w_v, w_w=c.w_omega, crash=c.crash, max_dist=c.max_dist, max_steps=c.max_steps)
+
+
+CASES = [
+    # RK4, 4 substeps, boxes (collisions end episodes), attitude interface
+    (W.Workload("reach_att", 3000, 4, 1, 8, 3000, 0, 0), _abi.AG_MODE_ATT_THRUST),
+    # semi-implicit Euler, quad / hexa / octo, no boxes, velocity interface
+    (W.Workload("reach_vel", 2500, 1, 0, 0, 1000, 1000, 500, drag=0.1), _abi.AG_MODE_BODY_VEL),
+]
+
+
+@pytest.mark.parametrize("w,mode", CASES, ids=[c[0].name for c in CASES])
+def test_reach_step_matches_oracle(w, mode):
+    from harness import gpu_fleet
+    seed = 23
+    inp = W.make_inputs(w, seed)
+    fl = gpu_fleet(w, inp, seed)
+    world = oracle_world(w)
+    world_free = O.World(**{**world.__dict__, "n_obs": 0})
+    rng = np.random.default_rng(5)
+    goals = rng.uniform(-1.0, 1.0, (3, w.n_envs)).astype(np.float32)
+    cfg = _cfg(mode, max_steps=3, max_dist=3.0)
+    fl.reset(None, seed)
+    _abi.ag_reach_begin(fl.ctx, cfg, torch.from_numpy(goals).cuda())
+    dev = fl.device
+    obs = torch.empty((w.n_envs, 13), device=dev)
+    rew = torch.empty((w.n_envs,), device=dev)
+    done = torch.empty((w.n_envs,), dtype=torch.uint8, device=dev)
+    modes = np.full(w.n_envs, mode, np.uint8)
+    scale, offset = np.array(cfg.action_scale[:]), np.array(cfg.action_offset[:])
+    steps = np.zeros(w.n_envs, np.uint32)
+    seen = {"collided": 0, "far": 0, "timeout": 0}
+    for _ in range(7):
+        s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
+        act = rng.uniform(-1.3, 1.3, (w.n_envs, 4)).astype(np.float32)
+        _abi.ag_reach_step(fl.ctx, torch.from_numpy(act).to(dev), obs, rew, done)
+        g_obs, g_rew, g_done = _np(obs), _np(rew), _np(done)
+        g_col = _np(fl.events()[0])
+        g_epoch = _np(fl.epoch())
+        # oracle: commands, one step, score, end, re-draw, observe
+        tgt = (offset[:, None] + scale[:, None] * np.clip(act.T.astype(np.float64), -1.0, 1.0))
+        cur = W.Inputs(modes, tgt, inp.body, inp.boxes)
+        orc = oracle_fleet_from(w, cur, s0, m0, e0, seed)
+        ocol, _ = O.rollout(world, orc, 1)
+        nxt = steps + 1
+        _, o_rew, o_done = O.reach_task(orc.state, goals, ocol, nxt, **_params(cfg))
+        dist = np.linalg.norm(orc.state[0:3] - goals, axis=0)
+        O.reset(world, orc, (o_done == 1) & (ocol == 0), seed)
+        o_obs = O.reach_task(orc.state, goals, ocol, nxt, **_params(cfg))[0].T
+        # float32 / float64 near-ties of the two decisions are left out
+        ok = np.abs(dist - cfg.max_dist) >= 1e-4
+        if w.n_obstacles:
+            pre = oracle_fleet_from(w, W.Inputs(modes, tgt, inp.body, None), s0, m0, e0, seed)
+            O.rollout(world_free, pre, 1)
+            ok &= np.abs(box_margin(pre.state[0:3], inp.boxes.astype(np.float64))) >= 1e-5
+        assert ok.mean() > 0.99
+        np.testing.assert_array_equal(g_col[ok], ocol[ok])
+        np.testing.assert_array_equal(g_done[ok], o_done[ok])
+        np.testing.assert_array_equal(g_epoch[ok], orc.epoch[ok])
+        hit = ok & (ocol == 1)
+        assert np.all(g_rew[hit] == np.float32(-cfg.crash))
+        free = ok & (ocol == 0)
+        np.testing.assert_allclose(g_rew[free], o_rew[free], rtol=1e-4, atol=1e-4)
+        # observations; q and -q describe one attitude, so near w = 0 the sign may differ
+        d = np.abs(g_obs[ok].astype(np.float64) - o_obs[ok])
+        tol = 1e-4 * (1.0 + np.abs(o_obs[ok]))
+        flip = np.abs(o_obs[ok, 6]) < 1e-4
+        d[flip, 6:10] = np.abs(np.abs(g_obs[ok][flip, 6:10]) - np.abs(o_obs[ok][flip, 6:10]))
+        assert np.all(d <= tol), float((d - tol).max())
+        # episodes that ended restart from the reset draw: their observation is exact up to the goal subtraction
+        ended = ok & (o_done == 1)
+        np.testing.assert_allclose(g_obs[ended], o_obs[ended], atol=2e-6)
+        seen["collided"] += int(hit.sum())
+        seen["far"] += int((free & (dist > cfg.max_dist)).sum())
+        seen["timeout"] += int((free & (nxt >= cfg.max_steps) & (dist <= cfg.max_dist)).sum())
+        steps = np.where(g_done == 1, 0, steps + 1).astype(np.uint32)
+    assert seen["far"] > 0 and seen["timeout"] > 0
+    if w.n_obstacles:
+        assert seen["collided"] > 0
+    fl.close()
+
+
+def test_reach_env_reset_and_autoreset():
+    from paper_2305_16510_gb300.task import ReachEnv
+    n = 4096
+    env = ReachEnv(n, seed=9)
+    obs = env.reset()
+    st = _np(env.fleet.state())
+    o_obs = O.reach_task(st.astype(np.float64), np.zeros((3, n)), np.zeros(n, np.uint8), np.zeros(n, np.uint32))[0].T
+    np.testing.assert_allclose(_np(obs), o_obs, atol=1e-7)
+    assert np.all(_np(obs)[:, 6] >= 0.0)
+    ep0 = _np(env.fleet.epoch()).copy()
+    ended = np.zeros(n, np.int64)
+    hover = torch.zeros((n, 4), device=env.device)   # level attitude, hover thrust
+    for t in range(env.task.max_steps):
+        obs, rew, done, info = env.step(hover)
+        ended += _np(done)
+        assert torch.isfinite(rew).all()
+    # every episode hit the step limit at the latest, and restarted with a new draw
+    assert np.all(ended >= 1)
+    assert np.all(_np(env.fleet.epoch()) - ep0 == ended)
+    env.close()
+
+
+def test_reach_errors():
+    from paper_2305_16510_gb300.fleet import Fleet
+    fl = Fleet(256)
+    buf = torch.zeros((256 * 13 + 8,), device=fl.device)
+    with pytest.raises(_abi.AgError) as e:
+        _abi.ag_reach_step(fl.ctx, buf, buf, buf, buf)
+    assert e.value.status == _abi.AG_ERR_STATE
+    bad = _abi.ag_reach_config_default()
+    bad.command_mode = _abi.AG_MODE_POSITION
+    with pytest.raises(_abi.AgError) as e:
+        _abi.ag_reach_begin(fl.ctx, bad, torch.zeros((3, 256), device=fl.device))
+    assert e.value.status == _abi.AG_ERR_INVALID
+    _abi.ag_reach_begin(fl.ctx, _abi.ag_reach_config_default(), torch.zeros((3, 256), device=fl.device))
+    with pytest.raises(_abi.AgError) as e:   # rejected on the host before any launch
+        _abi.ag_reach_step(fl.ctx, buf.data_ptr() + 4, buf, buf, buf)
+    assert e.value.status == _abi.AG_ERR_INVALID
+    fl.close()
