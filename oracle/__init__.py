@@ -97,7 +97,7 @@ def _declare(L: ctypes.CDLL) -> None:
     L.orc_vehicle_loss.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.c_int, _dp,
                                    ctypes.c_double, ctypes.c_double]
     L.orc_vehicle_loss.restype = ctypes.c_double
-    L.orc_vehicle_loss_jvp.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+    L.orc_vehicle_loss_jvp.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                        ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, _dp]
     L.orc_vehicle_loss_jvp.restype = ctypes.c_double
 
@@ -426,7 +426,9 @@ def vehicle_loss(world: World, n_rot, mode, tgt4, body4, state13, motors, gains1
 
 
 def vehicle_loss_jvp(world: World, n_rot, mode, tgt4, body4, state13, motors, gains12, d_state13, d_gains12,
-                     horizon, p_goal, w_pos=1.0, w_omega=0.01):
+                     horizon, p_goal, w_pos=1.0, w_omega=0.01, d_tgt4=None):
+    """(loss, directional derivative along (d_state13, d_gains12, d_tgt4)); d_tgt4 None holds the targets."""
+    dt = None if d_tgt4 is None else _f64(d_tgt4)
     mot = np.zeros(8)
     mot[:len(motors)] = motors
     dl = ctypes.c_double()
@@ -434,6 +436,6 @@ def vehicle_loss_jvp(world: World, n_rot, mode, tgt4, body4, state13, motors, ga
     L = lib().orc_vehicle_loss_jvp(ctypes.byref(w), int(n_rot), int(mode), _ptr(_f64(tgt4), _dp),
                                    _ptr(_f64(body4), _dp), _ptr(_f64(state13), _dp), _ptr(mot, _dp),
                                    _ptr(_f64(gains12), _dp), _ptr(_f64(d_state13), _dp), _ptr(_f64(d_gains12), _dp),
-                                   int(horizon), _ptr(_f64(p_goal), _dp), float(w_pos), float(w_omega),
+                                   _ptr(dt, _dp), int(horizon), _ptr(_f64(p_goal), _dp), float(w_pos), float(w_omega),
                                    ctypes.byref(dl))
     return float(L), float(dl.value)

@@ -166,12 +166,12 @@ World world_of(const void* p) {
 //   L = sum_{t=1..H} ( w_pos |p_t - p_goal|^2 + w_omega |Omega_t|^2 ),
 // x_t the state after step t. Gains are inputs so their tangents can be set.
 template <class T>
-T vehicle_loss(const World& w, const Rotors& rot, int mode, const double tgt_d[4], const Body<T>& body,
+T vehicle_loss(const World& w, const Rotors& rot, int mode, const T tgt_in[4], const Body<T>& body,
                State<T> s, T u[8], const Gains<T>& g, int horizon, const double p_goal[3], double w_pos,
                double w_omega) {
   const double alpha = motor_alpha(w);
   const T h = T(w.dt / w.substeps_per_step);
-  T tgt[4] = {T(tgt_d[0]), T(tgt_d[1]), T(tgt_d[2]), T(tgt_d[3])};
+  T tgt[4] = {tgt_in[0], tgt_in[1], tgt_in[2], tgt_in[3]};
   Vec3<T> goal = {T(p_goal[0]), T(p_goal[1]), T(p_goal[2])};
   T loss = T(0);
   for (int t = 0; t < horizon; ++t) {
@@ -449,12 +449,13 @@ double orc_vehicle_loss(const void* world, int n_rot, int mode, const double tgt
   return vehicle_loss(w, rot, mode, tgt, b, s, u, g, horizon, p_goal, w_pos, w_omega);
 }
 
-// Directional derivative of orc_vehicle_loss along (d_state13, d_gains12),
-// by forward-mode dual numbers. Returns the loss; *dloss receives the JVP.
+// Directional derivative of orc_vehicle_loss along (d_state13, d_gains12,
+// d_tgt4), by forward-mode dual numbers; d_tgt4 may be NULL (targets held).
+// Returns the loss; *dloss receives the JVP.
 double orc_vehicle_loss_jvp(const void* world, int n_rot, int mode, const double tgt[4], const double body4[4],
                             const double state13[13], const double motors[8], const double gains12[12],
-                            const double d_state13[13], const double d_gains12[12], int horizon,
-                            const double p_goal[3], double w_pos, double w_omega, double* dloss) {
+                            const double d_state13[13], const double d_gains12[12], const double* d_tgt4,
+                            int horizon, const double p_goal[3], double w_pos, double w_omega, double* dloss) {
   World w = world_of(world);
   Rotors rot = make_rotors(n_rot, w.arm, w.k_yaw);
   Body<Dual> b = {Dual(body4[0]), {Dual(body4[1]), Dual(body4[2]), Dual(body4[3])}};
@@ -472,7 +473,9 @@ double orc_vehicle_loss_jvp(const void* world, int n_rot, int mode, const double
   g.kv = {Dual(gains12[3], d_gains12[3]), Dual(gains12[4], d_gains12[4]), Dual(gains12[5], d_gains12[5])};
   g.kR = {Dual(gains12[6], d_gains12[6]), Dual(gains12[7], d_gains12[7]), Dual(gains12[8], d_gains12[8])};
   g.kW = {Dual(gains12[9], d_gains12[9]), Dual(gains12[10], d_gains12[10]), Dual(gains12[11], d_gains12[11])};
-  Dual L = vehicle_loss(w, rot, mode, tgt, b, s, u, g, horizon, p_goal, w_pos, w_omega);
+  Dual tg[4];
+  for (int k = 0; k < 4; ++k) tg[k] = Dual(tgt[k], d_tgt4 ? d_tgt4[k] : 0.0);
+  Dual L = vehicle_loss(w, rot, mode, tg, b, s, u, g, horizon, p_goal, w_pos, w_omega);
   *dloss = L.d;
   return L.v;
 }

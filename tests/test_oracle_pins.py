@@ -548,6 +548,34 @@ def test_dual_jvp_matches_central_difference():
     assert abs(dL - (Lp - Lm) / (2 * eps)) < 1e-6 * max(1.0, abs(dL))
 
 
+@pytest.mark.parametrize("mode,tgt", [
+    (O.MODE_POSITION, [0.5, -0.4, 0.6, 0.2]),
+    (O.MODE_BODY_VEL, [0.4, -0.3, 0.2, 0.3]),
+    (O.MODE_ATT_THRUST, [0.1, -0.15, 0.2, 0.75 * G * 1.05]),
+    (O.MODE_WRENCH, [0.75 * G, 0.001, -0.002, 0.0005]),
+])
+def test_dual_jvp_target_tangent_matches_central_difference(mode, tgt):
+    # the tangent seeded on the four targets of every command mode
+    world = O.World(n_envs=1)
+    rng = np.random.default_rng(15 + mode)
+    s0 = state13(p=(0.2, -0.1, 0.3), v=(0.1, 0.2, -0.1), q=quat_wxyz(Rotation.from_euler("ZYX", [0.3, 0.1, -0.1])),
+                 w=(0.1, -0.1, 0.05))
+    motors = np.full(4, 0.75 * G / 4)
+    goal = np.array([0.5, -0.4, 0.6])
+    ds, dg, dt = rng.normal(size=13), rng.normal(size=12), rng.normal(size=4)
+    L, dL = O.vehicle_loss_jvp(world, 4, mode, tgt, BODY, s0, motors, GAINS, ds, dg, 50, goal, d_tgt4=dt)
+    _, dL_no_t = O.vehicle_loss_jvp(world, 4, mode, tgt, BODY, s0, motors, GAINS, ds, dg, 50, goal)
+    eps = 1e-6
+    t = np.asarray(tgt, dtype=np.float64)
+    Lp = O.vehicle_loss(world, 4, mode, t + eps * dt, BODY, s0 + eps * ds, motors, GAINS + eps * dg, 50, goal)
+    Lm = O.vehicle_loss(world, 4, mode, t - eps * dt, BODY, s0 - eps * ds, motors, GAINS - eps * dg, 50, goal)
+    assert abs(dL - (Lp - Lm) / (2 * eps)) < 1e-6 * max(1.0, abs(dL))
+    # the target tangent alone
+    Lp = O.vehicle_loss(world, 4, mode, t + eps * dt, BODY, s0, motors, GAINS, 50, goal)
+    Lm = O.vehicle_loss(world, 4, mode, t - eps * dt, BODY, s0, motors, GAINS, 50, goal)
+    assert abs((dL - dL_no_t) - (Lp - Lm) / (2 * eps)) < 1e-6 * max(1.0, abs(dL))
+
+
 def test_op_counts_are_plausible():
     sie = O.World(n_envs=1)
     rk4 = O.World(n_envs=1, integrator=O.INTEG_RK4, substeps_per_step=4)
