@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define AG_ABI_VERSION 1
+#define AG_ABI_VERSION 2
 #define AG_MAX_OBSTACLES 64
 #define AG_STATE_DIM 13  /* p.xyz, v.xyz, q.wxyz, Omega.xyz */
 #define AG_MAX_ROTORS 8
@@ -259,18 +259,19 @@ ag_status ag_step_plain_noalloc(const ag_config* cfg, void* cuda_stream, uint32_
 ag_status ag_set_gains(ag_ctx* ctx, const float* gains12);
 
 /* Differentiable rollout, forward half. Advances every environment n_steps
- * steps from its current state with the position-tracking controller (Sec. I,
- * after Lee et al. 2011; attitude law Sec. IV-A Eqs. 3-5), allocation with
- * clamp and lag, and semi-implicit Euler, without collision tests; records a
- * checkpoint (state + motors) every record_every steps; and writes
+ * steps from its current state with the controller of its command mode
+ * (position tracking, Sec. I after Lee et al. 2011; body velocity, Eqs. 6-9;
+ * attitude and thrust, Eqs. 1-2; each with the attitude law of Sec. IV-A
+ * Eqs. 3-5; or a direct wrench), allocation with clamp and lag, and
+ * semi-implicit Euler, without collision tests; records a checkpoint (state +
+ * motors) every record_every steps; and writes
  *   loss[i] = sum_{t=1..n_steps} w_pos |p_t - p_goal_i|^2 + w_omega |Omega_t|^2
  * (x_t = the state after step t; p_goal float[3][n_envs]). saturated (may be
  * NULL) flags environments in which some motor command was clamped during
  * the rollout; there the gradient uses the clamp's subgradient 0. Requires
- * every environment in AG_MODE_POSITION, semi-implicit Euler, one substep per
- * step and no obstacles (else AG_ERR_UNSUPPORTED). Synchronises once (mode
- * check). Commands, body parameters and gains must not change until
- * ag_backward has run. */
+ * semi-implicit Euler, one substep per step and no obstacles (else
+ * AG_ERR_UNSUPPORTED). Does not synchronise. Commands, body parameters and
+ * gains must not change until ag_backward has run. */
 ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos, float w_omega, const float* p_goal,
                           float* loss, uint8_t* saturated);
 
@@ -279,12 +280,17 @@ ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos, float w_om
  * the gradient of sum_i c_i loss[i] with respect to each environment's
  * initial state float[13][n_envs] (grad_x0), with respect to the 12 gains
  * float[12] (grad_gains, the fleet sum, reduced in a fixed order so repeated
- * calls give identical bits) and, optionally, each environment's share
- * float[12][n_envs] (grad_gains_per_env). Any output may be NULL. The
- * gradient with respect to the initial quaternion is that of the loss as a
- * function of q_0 / |q_0|. Returns AG_ERR_STATE if nothing was recorded. */
+ * calls give identical bits), optionally each environment's share
+ * float[12][n_envs] (grad_gains_per_env), and with respect to each
+ * environment's four command targets float[4][n_envs] (grad_targets, in the
+ * target order of ag_mode: angles in radians, yaw rate in rad/s). Any output
+ * may be NULL. The gradient with respect to the initial quaternion is that of
+ * the loss as a function of q_0 / |q_0|. Where the controller meets a
+ * degenerate direction (zero commanded acceleration, thrust along the
+ * heading, body x axis vertical) the gradient is that of the fallback
+ * branch. Returns AG_ERR_STATE if nothing was recorded. */
 ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, float* grad_gains,
-                      float* grad_gains_per_env);
+                      float* grad_gains_per_env, float* grad_targets);
 
 /* ------------------------------------------------------------------------
  * Reach-a-setpoint task (Sec. I: policies learn to fly the vehicle to a goal

@@ -100,7 +100,7 @@ SIGNATURES = {
     "ag_last_error": (ctypes.c_char_p, [_vp]),
     "ag_set_gains": (ctypes.c_int, [_vp, _vp]),
     "ag_rollout_loss": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
-    "ag_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ag_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "ag_reach_config_default": (None, [ctypes.POINTER(ag_reach_config)]),
     "ag_reach_begin": (ctypes.c_int, [_vp, ctypes.POINTER(ag_reach_config), _vp]),
     "ag_reach_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -116,6 +116,9 @@ SIGNATURES = {
                                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_char_p,
                                              ctypes.c_size_t]),
 }
+
+
+ABI_VERSION = 2  # AG_ABI_VERSION of include/ag.h these signatures describe
 
 
 def library_path() -> str:
@@ -136,6 +139,9 @@ def lib() -> ctypes.CDLL:
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
+            if L.ag_abi_version() != ABI_VERSION:
+                raise RuntimeError(f"{path} implements ABI {L.ag_abi_version()}, this binding ABI {ABI_VERSION}: "
+                                   "rebuild it")
             _lib = L
     return _lib
 
@@ -274,9 +280,10 @@ def ag_rollout_loss(ctx: int, n_steps: int, w_pos: float, w_omega: float, p_goal
                                  ptr(saturated)), "ag_rollout_loss", ctx)
 
 
-def ag_backward(ctx: int, loss_weights=None, grad_x0=None, grad_gains=None, grad_gains_per_env=None) -> None:
-    _check(lib().ag_backward(ctx, ptr(loss_weights), ptr(grad_x0), ptr(grad_gains), ptr(grad_gains_per_env)),
-           "ag_backward", ctx)
+def ag_backward(ctx: int, loss_weights=None, grad_x0=None, grad_gains=None, grad_gains_per_env=None,
+                grad_targets=None) -> None:
+    _check(lib().ag_backward(ctx, ptr(loss_weights), ptr(grad_x0), ptr(grad_gains), ptr(grad_gains_per_env),
+                             ptr(grad_targets)), "ag_backward", ctx)
 
 
 def ag_reach_config_default() -> ag_reach_config:

@@ -6,11 +6,14 @@
 // initial state x_0 (13 numbers per environment) and the 12 diagonal
 // controller gains (k_x, k_v, k_R, k_Omega), shared by the fleet.
 //
-// The differentiated step is the position-tracking controller (Sec. I, after
-// Lee et al. 2011) with the attitude law of Sec. IV-A (Eqs. 3-5), rotor
-// allocation with per-motor clamp (subgradient 0 on a clamped motor) and
-// first-order lag, and the semi-implicit Euler update with quaternion
-// renormalisation. Reverse mode is written out by hand, operation by
+// Gradients also go to each environment's four command targets.
+//
+// The differentiated step is the controller of the environment's command mode
+// (position tracking, Sec. I after Lee et al. 2011; body velocity, Eqs. 6-9;
+// attitude and thrust, Eqs. 1-2; or a direct wrench) with the attitude law
+// of Sec. IV-A (Eqs. 3-5), rotor allocation with per-motor clamp (subgradient
+// 0 on a clamped motor) and first-order lag, and the semi-implicit Euler
+// update with quaternion renormalisation. Reverse mode is written out by hand, operation by
 // operation in reverse order; the comments name the forward line each block
 // inverts.
 //
@@ -38,11 +41,32 @@ template <int NROT> struct Xs {  // differentiable state of one vehicle
   float u[NROT];
 };
 
+// Command of one environment over a recorded rollout: its mode, its four
+// targets and the sines and cosines of its angle targets, taken once.
+//   position: (c0, s0) = (cos, sin) psi_d
+//   attitude: (c0, s0) = (cos, sin) phi_d, (c1, s1) = (cos, sin) theta_d
+struct Cmd {
+  float t[4];
+  float c0, s0, c1, s1;
+};
+
 // Intermediates of one forward step, kept for its backward pass.
 template <int NROT> struct Step {
   float R[3][3];
-  V3 a, b3d, b1c, c, b2d, b1d, eR;
-  float an, cn, f;
+  V3 Rd[3];          // columns b1d, b2d, b3d of R_d
+  V3 eR, eW;
+  float f;           // commanded collective thrust
+  float rate;        // commanded yaw rate (velocity, attitude): R_d Omega_d = rate e_3
+  // position
+  V3 a, c, b1c;      // a is also the vehicle-frame acceleration of the velocity mode
+  float an, cn;
+  bool turned;       // heading fallback (b1c turned by 90 degrees) taken
+  // current yaw and tilt (velocity, attitude)
+  float cps, sps, ir;  // (cos, sin) psi = (R00, R10) * ir; ir = 0 when R00 = R10 = 0
+  V3 B[3];             // columns of R_y(theta_d) R_x(phi_d)
+  V3 vV;               // velocity in the yaw frame
+  float rxz, anv;      // |(a_x, a_z)|, |a|
+  // allocation and integration
   float pre[NROT];   // A^+ (f, M) before the clamp
   bool pass[NROT];   // 0 < pre < u_max: the clamp passes the gradient
   float uc[NROT];    // clamped command
@@ -60,38 +84,95 @@ __device__ __forceinline__ Gains gains_of(const StepParams& P) {
           {P.kW[0], P.kW[1], P.kW[2]}};
 }
 
-// One recorded step: position controller -> allocation/clamp/lag -> SIE.
-// x must hold a unit quaternion.
-template <int NROT>
-__device__ __forceinline__ void forward_step(const Xs<NROT>& x, V3 pd, float cpsi, float spsi, const Body& b,
-                                             const Gains& g, const StepParams& P, Step<NROT>& S, Xs<NROT>& xn) {
+// One recorded step: the controller of mode MODE -> allocation/clamp/lag ->
+// SIE. x must hold a unit quaternion.
+//   position (Sec. I, Lee 2011): a = -k_x (p - p_d) - k_v v + g e3, f = m a.b3,
+//     b3d = a/|a|, b2d = (b3d x b1c)/|.|, b1d = b2d x b3d, Omega_d = 0
+//   velocity (Eqs. 6-9): v^V = R_psi^T v, a = k_v (v_d - v^V) + g e3,
+//     f = m a.(R_psi^T b3), R_y(theta_d) R_x(phi_d) e3 = a/|a|
+//   attitude (Eqs. 1-2): phi_d, theta_d, psi_dot_d, f given
+//   velocity and attitude: R_d = R_psi R_y(theta_d) R_x(phi_d) with psi the
+//     current yaw, and R_d Omega_d (Eq. 2) = psi_dot_d e3
+//   Eqs. 3-5: e_R = 1/2 vee(R_d^T R - R^T R_d), e_W = W - R^T R_d Omega_d,
+//     M = -k_R e_R - k_W e_W + W x J W
+//   wrench: (f, M) = the targets
+template <int NROT, int MODE>
+__device__ __forceinline__ void forward_step(const Xs<NROT>& x, const Cmd& cm, const Body& b, const Gains& g,
+                                             const StepParams& P, Step<NROT>& S, Xs<NROT>& xn) {
   constexpr int T = NROT == 4 ? 0 : (NROT == 6 ? 1 : 2);
   rotation(x.q, S.R);
-  V3 b3 = {S.R[0][2], S.R[1][2], S.R[2][2]};
-  S.a = {-g.kx.x * (x.p.x - pd.x) - g.kv.x * x.v.x, -g.kx.y * (x.p.y - pd.y) - g.kv.y * x.v.y,
-         -g.kx.z * (x.p.z - pd.z) - g.kv.z * x.v.z + kGravity};
-  S.f = b.m * dot(S.a, b3);
-  S.an = sqrtf(dot(S.a, S.a));
-  S.b3d = S.an > 1e-9f ? (1.f / S.an) * S.a : V3{0.f, 0.f, 1.f};
-  S.b1c = {cpsi, spsi, 0.f};
-  S.c = cross(S.b3d, S.b1c);
-  S.cn = sqrtf(dot(S.c, S.c));
-  if (!(S.cn > 1e-9f)) {  // commanded thrust along the heading: use the heading turned by 90 degrees
-    S.b1c = {-spsi, cpsi, 0.f};
-    S.c = cross(S.b3d, S.b1c);
-    S.cn = sqrtf(dot(S.c, S.c));
+  const V3 b3 = {S.R[0][2], S.R[1][2], S.R[2][2]};
+  const V3 JW = {b.jx * x.w.x, b.jy * x.w.y, b.jz * x.w.z};
+  const V3 gyro = cross(x.w, JW);
+  if (MODE == kModeWrench) {
+    S.M = {cm.t[0], cm.t[1], cm.t[2], cm.t[3]};
+  } else {
+    if (MODE == kModePosition) {
+      S.a = {-g.kx.x * (x.p.x - cm.t[0]) - g.kv.x * x.v.x, -g.kx.y * (x.p.y - cm.t[1]) - g.kv.y * x.v.y,
+             -g.kx.z * (x.p.z - cm.t[2]) - g.kv.z * x.v.z + kGravity};
+      S.f = b.m * dot(S.a, b3);
+      S.an = sqrtf(dot(S.a, S.a));
+      const V3 b3d = S.an > 1e-9f ? (1.f / S.an) * S.a : V3{0.f, 0.f, 1.f};
+      S.b1c = {cm.c0, cm.s0, 0.f};
+      S.c = cross(b3d, S.b1c);
+      S.cn = sqrtf(dot(S.c, S.c));
+      S.turned = !(S.cn > 1e-9f);
+      if (S.turned) {  // commanded thrust along the heading: use the heading turned by 90 degrees
+        S.b1c = {-cm.s0, cm.c0, 0.f};
+        S.c = cross(b3d, S.b1c);
+        S.cn = sqrtf(dot(S.c, S.c));
+      }
+      const V3 b2d = (1.f / S.cn) * S.c;
+      S.Rd[0] = cross(b2d, b3d);
+      S.Rd[1] = b2d;
+      S.Rd[2] = b3d;
+      S.rate = 0.f;
+    } else {
+      const float rho2 = S.R[0][0] * S.R[0][0] + S.R[1][0] * S.R[1][0];
+      S.ir = rho2 > 0.f ? rsqrtf(rho2) : 0.f;
+      S.cps = rho2 > 0.f ? S.R[0][0] * S.ir : 1.f;
+      S.sps = rho2 > 0.f ? S.R[1][0] * S.ir : 0.f;
+      float cphi, sphi, cth, sth;
+      if (MODE == kModeBodyVel) {
+        S.vV = {S.cps * x.v.x + S.sps * x.v.y, -S.sps * x.v.x + S.cps * x.v.y, x.v.z};
+        S.a = {g.kv.x * (cm.t[0] - S.vV.x), g.kv.y * (cm.t[1] - S.vV.y), g.kv.z * (cm.t[2] - S.vV.z) + kGravity};
+        const V3 b3V = {S.cps * b3.x + S.sps * b3.y, -S.sps * b3.x + S.cps * b3.y, b3.z};
+        S.f = b.m * dot(S.a, b3V);
+        const float rxz2 = S.a.x * S.a.x + S.a.z * S.a.z;
+        S.rxz = sqrtf(rxz2);
+        S.anv = sqrtf(rxz2 + S.a.y * S.a.y);
+        cth = 1.f; sth = 0.f; cphi = 1.f; sphi = 0.f;
+        if (rxz2 > 0.f) {
+          cth = S.a.z / S.rxz;
+          sth = S.a.x / S.rxz;
+          cphi = S.rxz / S.anv;
+          sphi = -S.a.y / S.anv;
+        } else if (S.anv > 0.f) {  // a along +-y: phi_d = atan2(-a_y, 0), theta_d = atan2(0, 0) = 0
+          cphi = 0.f;
+          sphi = S.a.y > 0.f ? -1.f : 1.f;
+        }
+        S.rate = cm.t[3];
+      } else {
+        cphi = cm.c0; sphi = cm.s0; cth = cm.c1; sth = cm.s1;
+        S.rate = cm.t[2];
+        S.f = cm.t[3];
+      }
+      S.B[0] = {cth, 0.f, -sth};
+      S.B[1] = {sth * sphi, cphi, cth * sphi};
+      S.B[2] = {sth * cphi, -sphi, cth * cphi};
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        S.Rd[j] = {S.cps * S.B[j].x - S.sps * S.B[j].y, S.sps * S.B[j].x + S.cps * S.B[j].y, S.B[j].z};
+    }
+    // E = R_d^T R: E_ij = col_i(R_d) . col_j(R)
+    auto col = [&](int j) { return V3{S.R[0][j], S.R[1][j], S.R[2][j]}; };
+    S.eR = {0.5f * (dot(S.Rd[2], col(1)) - dot(S.Rd[1], col(2))),
+            0.5f * (dot(S.Rd[0], col(2)) - dot(S.Rd[2], col(0))),
+            0.5f * (dot(S.Rd[1], col(0)) - dot(S.Rd[0], col(1)))};
+    S.eW = {x.w.x - S.rate * S.R[2][0], x.w.y - S.rate * S.R[2][1], x.w.z - S.rate * S.R[2][2]};
+    S.M = {S.f, -g.kR.x * S.eR.x - g.kW.x * S.eW.x + gyro.x, -g.kR.y * S.eR.y - g.kW.y * S.eW.y + gyro.y,
+           -g.kR.z * S.eR.z - g.kW.z * S.eW.z + gyro.z};
   }
-  S.b2d = (1.f / S.cn) * S.c;
-  S.b1d = cross(S.b2d, S.b3d);
-  // E = R_d^T R with R_d = [b1d b2d b3d]: E_ij = col_i(R_d) . col_j(R)
-  V3 Rd[3] = {S.b1d, S.b2d, S.b3d};
-  auto col = [&](int j) { return V3{S.R[0][j], S.R[1][j], S.R[2][j]}; };
-  S.eR = {0.5f * (dot(Rd[2], col(1)) - dot(Rd[1], col(2))), 0.5f * (dot(Rd[0], col(2)) - dot(Rd[2], col(0))),
-          0.5f * (dot(Rd[1], col(0)) - dot(Rd[0], col(1)))};
-  V3 JW = {b.jx * x.w.x, b.jy * x.w.y, b.jz * x.w.z};
-  V3 gyro = cross(x.w, JW);
-  S.M = {S.f, -g.kR.x * S.eR.x - g.kW.x * x.w.x + gyro.x, -g.kR.y * S.eR.y - g.kW.y * x.w.y + gyro.y,
-         -g.kR.z * S.eR.z - g.kW.z * x.w.z + gyro.z};
   S.W = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < NROT; ++i) {
@@ -149,10 +230,11 @@ __device__ __forceinline__ V3 normalize_bwd(V3 y, float n, V3 ybar) {
 
 // Reverse of forward_step. On entry lam is the adjoint of (x_{t+1}, u_{t+1})
 // including this step's loss term; on exit it is the adjoint of (x_t, u_t).
-template <int NROT>
-__device__ __forceinline__ void backward_step(const Xs<NROT>& x, V3 pd, float cpsi, float spsi, const Body& b,
-                                              const Gains& g, const StepParams& P, const Step<NROT>& S,
-                                              Adj<NROT>& lam, GainAdj& gb) {
+// Gain adjoints accumulate into gb, target adjoints into tb.
+template <int NROT, int MODE>
+__device__ __forceinline__ void backward_step(const Xs<NROT>& x, const Cmd& cm, const Body& b, const Gains& g,
+                                              const StepParams& P, const Step<NROT>& S, Adj<NROT>& lam, GainAdj& gb,
+                                              float (&tb)[4]) {
   constexpr int T = NROT == 4 ? 0 : (NROT == 6 ? 1 : 2);
   const float h = P.h, hh = 0.5f * h;
   const Q4& q = x.q;
@@ -183,7 +265,7 @@ __device__ __forceinline__ void backward_step(const Xs<NROT>& x, V3 pd, float cp
   const V3 b3 = {S.R[0][2], S.R[1][2], S.R[2][2]};
   Wrench4 Wb;
   Wb.f = h * b.inv_m * dot(b3, vnb);
-  V3 b3b = (h * S.W.f * b.inv_m) * vnb;
+  V3 Rcb[3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, (h * S.W.f * b.inv_m) * vnb};  // adjoints of the columns of R
   // w_n = w + h J^-1 (W.M - gyro(w)), gyro(w) = w x (J w)
   const V3 JW = {b.jx * x.w.x, b.jy * x.w.y, b.jz * x.w.z};
   V3 wb = wnb;
@@ -210,49 +292,124 @@ __device__ __forceinline__ void backward_step(const Xs<NROT>& x, V3 pd, float cp
     Mb.my += P.Ap[T][i][2] * ucb[i];
     Mb.mz += P.Ap[T][i][3] * ucb[i];
   }
-  // M = -k_R e_R - k_W w + gyro(w)
-  const V3 Mmb = {Mb.mx, Mb.my, Mb.mz};
-  gyrob = gyrob + Mmb;
-  V3 eRb = {-g.kR.x * Mb.mx, -g.kR.y * Mb.my, -g.kR.z * Mb.mz};
-  wb = wb - V3{g.kW.x * Mb.mx, g.kW.y * Mb.my, g.kW.z * Mb.mz};
-  gb.kR = gb.kR - V3{S.eR.x * Mb.mx, S.eR.y * Mb.my, S.eR.z * Mb.mz};
-  gb.kW = gb.kW - V3{x.w.x * Mb.mx, x.w.y * Mb.my, x.w.z * Mb.mz};
+  if (MODE == kModeWrench) {
+    tb[0] += Mb.f; tb[1] += Mb.mx; tb[2] += Mb.my; tb[3] += Mb.mz;
+  } else {
+    // M = -k_R e_R - k_W e_W + gyro(w)
+    const V3 Mmb = {Mb.mx, Mb.my, Mb.mz};
+    gyrob = gyrob + Mmb;
+    const V3 eRb = {-g.kR.x * Mb.mx, -g.kR.y * Mb.my, -g.kR.z * Mb.mz};
+    const V3 eWb = {-g.kW.x * Mb.mx, -g.kW.y * Mb.my, -g.kW.z * Mb.mz};
+    gb.kR = gb.kR - V3{S.eR.x * Mb.mx, S.eR.y * Mb.my, S.eR.z * Mb.mz};
+    gb.kW = gb.kW - V3{S.eW.x * Mb.mx, S.eW.y * Mb.my, S.eW.z * Mb.mz};
+    // e_W = w - rate (R20, R21, R22)
+    wb = wb + eWb;
+    Rcb[0].z -= S.rate * eWb.x;
+    Rcb[1].z -= S.rate * eWb.y;
+    Rcb[2].z -= S.rate * eWb.z;
+    const float rateb = -(S.R[2][0] * eWb.x + S.R[2][1] * eWb.y + S.R[2][2] * eWb.z);
+    // e_R = 1/2 (E21 - E12, E02 - E20, E10 - E01), E_ij = Rd_i . R_j
+    V3 Rdb[3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    const V3 Rc[3] = {{S.R[0][0], S.R[1][0], S.R[2][0]}, {S.R[0][1], S.R[1][1], S.R[2][1]}, b3};
+    auto Eb = [&](int i, int j, float e) {  // E_ij gets adjoint e
+      Rdb[i] = Rdb[i] + e * Rc[j];
+      Rcb[j] = Rcb[j] + e * S.Rd[i];
+    };
+    Eb(2, 1, 0.5f * eRb.x); Eb(1, 2, -0.5f * eRb.x);
+    Eb(0, 2, 0.5f * eRb.y); Eb(2, 0, -0.5f * eRb.y);
+    Eb(1, 0, 0.5f * eRb.z); Eb(0, 1, -0.5f * eRb.z);
+    if (MODE == kModePosition) {
+      // f = m a . b3
+      V3 ab = (b.m * Mb.f) * b3;
+      Rcb[2] = Rcb[2] + (b.m * Mb.f) * S.a;
+      // b1d = b2d x b3d
+      V3 b2db = Rdb[1], b3db = Rdb[2];
+      cross_bwd(S.Rd[1], S.Rd[2], Rdb[0], b2db, b3db);
+      // b2d = c / |c|,  c = b3d x b1c
+      const V3 cb = normalize_bwd(S.Rd[1], S.cn, b2db);
+      V3 b1cb = {0.f, 0.f, 0.f};
+      cross_bwd(S.Rd[2], S.b1c, cb, b3db, b1cb);
+      // b3d = a / |a| (constant e3 in the degenerate case |a| = 0)
+      if (S.an > 1e-9f) ab = ab + normalize_bwd(S.Rd[2], S.an, b3db);
+      // a = -k_x (p - p_d) - k_v v + g e3
+      const V3 ex = {x.p.x - cm.t[0], x.p.y - cm.t[1], x.p.z - cm.t[2]};
+      pb = pb - V3{g.kx.x * ab.x, g.kx.y * ab.y, g.kx.z * ab.z};
+      vb = vb - V3{g.kv.x * ab.x, g.kv.y * ab.y, g.kv.z * ab.z};
+      gb.kx = gb.kx - V3{ex.x * ab.x, ex.y * ab.y, ex.z * ab.z};
+      gb.kv = gb.kv - V3{x.v.x * ab.x, x.v.y * ab.y, x.v.z * ab.z};
+      tb[0] += g.kx.x * ab.x;
+      tb[1] += g.kx.y * ab.y;
+      tb[2] += g.kx.z * ab.z;
+      // b1c = (cos psi_d, sin psi_d, 0), or (-sin psi_d, cos psi_d, 0) when turned
+      tb[3] += S.turned ? -cm.c0 * b1cb.x - cm.s0 * b1cb.y : -cm.s0 * b1cb.x + cm.c0 * b1cb.y;
+    } else {
+      // R_d = R_psi B: adjoints of B's columns and of (cos psi, sin psi)
+      V3 Bb[3];
+      float cpb = 0.f, spb = 0.f;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Bb[j] = {S.cps * Rdb[j].x + S.sps * Rdb[j].y, -S.sps * Rdb[j].x + S.cps * Rdb[j].y, Rdb[j].z};
+        cpb += Rdb[j].x * S.B[j].x + Rdb[j].y * S.B[j].y;
+        spb += -Rdb[j].x * S.B[j].y + Rdb[j].y * S.B[j].x;
+      }
+      if (MODE == kModeAttThrust) {
+        // B = R_y(theta_d) R_x(phi_d): columns (ct, 0, -st), (st sp, cp, ct sp), (st cp, -sp, ct cp)
+        const float cp = cm.c0, sp = cm.s0, ct = cm.c1, st = cm.s1;
+        const float thb = Bb[0].x * -st + Bb[0].z * -ct + Bb[1].x * (ct * sp) + Bb[1].z * (-st * sp) +
+                          Bb[2].x * (ct * cp) + Bb[2].z * (-st * cp);
+        const float phb = Bb[1].x * (st * cp) + Bb[1].y * -sp + Bb[1].z * (ct * cp) + Bb[2].x * (-st * sp) +
+                          Bb[2].y * -cp + Bb[2].z * (-ct * sp);
+        tb[0] += phb;
+        tb[1] += thb;
+        tb[2] += rateb;
+        tb[3] += Mb.f;
+      } else {
+        // f = m a . b3V, b3V = R_psi^T b3
+        const V3 b3V = {S.cps * b3.x + S.sps * b3.y, -S.sps * b3.x + S.cps * b3.y, b3.z};
+        V3 ab = (b.m * Mb.f) * b3V;
+        const V3 b3Vb = (b.m * Mb.f) * S.a;
+        Rcb[2].x += S.cps * b3Vb.x - S.sps * b3Vb.y;
+        Rcb[2].y += S.sps * b3Vb.x + S.cps * b3Vb.y;
+        Rcb[2].z += b3Vb.z;
+        cpb += b3.x * b3Vb.x + b3.y * b3Vb.y;
+        spb += b3.y * b3Vb.x - b3.x * b3Vb.y;
+        // B from a: B_2 = a/|a|, B_0 = (a_z, 0, -a_x)/|(a_x, a_z)|, B_1 = B_2 x B_0 (constant when a_x = a_z = 0)
+        if (S.rxz > 0.f) {
+          V3 B2b = Bb[2], B0b = Bb[0];
+          cross_bwd(S.B[2], S.B[0], Bb[1], B2b, B0b);
+          const V3 wbar = normalize_bwd(S.B[0], S.rxz, B0b);
+          ab.z += wbar.x;
+          ab.x -= wbar.z;
+          ab = ab + normalize_bwd(S.B[2], S.anv, B2b);
+        }
+        // a = k_v (v_d - v^V) + g e3
+        const V3 vVb = {-g.kv.x * ab.x, -g.kv.y * ab.y, -g.kv.z * ab.z};
+        tb[0] += g.kv.x * ab.x;
+        tb[1] += g.kv.y * ab.y;
+        tb[2] += g.kv.z * ab.z;
+        gb.kv = gb.kv + V3{(cm.t[0] - S.vV.x) * ab.x, (cm.t[1] - S.vV.y) * ab.y, (cm.t[2] - S.vV.z) * ab.z};
+        // v^V = R_psi^T v
+        vb.x += S.cps * vVb.x - S.sps * vVb.y;
+        vb.y += S.sps * vVb.x + S.cps * vVb.y;
+        vb.z += vVb.z;
+        cpb += x.v.x * vVb.x + x.v.y * vVb.y;
+        spb += x.v.y * vVb.x - x.v.x * vVb.y;
+        tb[3] += rateb;
+      }
+      // (cos psi, sin psi) = (R00, R10) / |(R00, R10)|
+      if (S.ir > 0.f) {
+        const float d = S.cps * cpb + S.sps * spb;
+        Rcb[0].x += S.ir * (cpb - d * S.cps);
+        Rcb[0].y += S.ir * (spb - d * S.sps);
+      }
+    }
+  }
   // gyro = w x (J w): w_bar += (J w) x g_bar + J (g_bar x w)
   {
     V3 jwb = {0.f, 0.f, 0.f};
     cross_bwd(x.w, JW, gyrob, wb, jwb);
     wb = wb + V3{b.jx * jwb.x, b.jy * jwb.y, b.jz * jwb.z};
   }
-  // e_R = 1/2 (E21 - E12, E02 - E20, E10 - E01), E_ij = Rd_i . R_j
-  V3 Rdb[3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  V3 Rcb[3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  const V3 Rd[3] = {S.b1d, S.b2d, S.b3d};
-  const V3 Rc[3] = {{S.R[0][0], S.R[1][0], S.R[2][0]}, {S.R[0][1], S.R[1][1], S.R[2][1]}, b3};
-  auto Eb = [&](int i, int j, float e) {  // E_ij gets adjoint e
-    Rdb[i] = Rdb[i] + e * Rc[j];
-    Rcb[j] = Rcb[j] + e * Rd[i];
-  };
-  Eb(2, 1, 0.5f * eRb.x); Eb(1, 2, -0.5f * eRb.x);
-  Eb(0, 2, 0.5f * eRb.y); Eb(2, 0, -0.5f * eRb.y);
-  Eb(1, 0, 0.5f * eRb.z); Eb(0, 1, -0.5f * eRb.z);
-  // f = m a . b3 (the commanded thrust's adjoint is Mb.f)
-  V3 ab = (b.m * Mb.f) * b3;
-  b3b = b3b + (b.m * Mb.f) * S.a;
-  Rcb[2] = Rcb[2] + b3b;
-  // b1d = b2d x b3d
-  V3 b2db = Rdb[1], b3db = Rdb[2];
-  cross_bwd(S.b2d, S.b3d, Rdb[0], b2db, b3db);
-  // b2d = c / |c|,  c = b3d x b1c
-  const V3 cb = normalize_bwd(S.b2d, S.cn, b2db);
-  b3db = b3db + cross(S.b1c, cb);
-  // b3d = a / |a| (constant e3 in the degenerate case |a| = 0)
-  if (S.an > 1e-9f) ab = ab + normalize_bwd(S.b3d, S.an, b3db);
-  // a = -k_x (p - p_d) - k_v v + g e3
-  const V3 ex = x.p - pd;
-  pb = pb - V3{g.kx.x * ab.x, g.kx.y * ab.y, g.kx.z * ab.z};
-  vb = vb - V3{g.kv.x * ab.x, g.kv.y * ab.y, g.kv.z * ab.z};
-  gb.kx = gb.kx - V3{ex.x * ab.x, ex.y * ab.y, ex.z * ab.z};
-  gb.kv = gb.kv - V3{x.v.x * ab.x, x.v.y * ab.y, x.v.z * ab.z};
   // R = R(q), unit-quaternion formula; Rcb[j] is the adjoint of column j
   {
     const float w0 = q.w, x0 = q.x, y0 = q.y, z0 = q.z;
@@ -306,10 +463,29 @@ __device__ __forceinline__ int rotors_of(const AdjointBuffers& ab, uint32_t i) {
   return i < ab.n_quad ? 4 : (i < ab.n_quad + ab.n_hexa ? 6 : 8);
 }
 
+__device__ __forceinline__ Cmd load_cmd(const AdjointBuffers& ab, uint32_t i, int mode) {
+  const uint32_t n = ab.n;
+  Cmd cm;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cm.t[k] = ab.targets[k * n + i];
+  cm.c0 = 1.f; cm.s0 = 0.f; cm.c1 = 1.f; cm.s1 = 0.f;
+  if (mode == kModePosition) sincosf(cm.t[3], &cm.s0, &cm.c0);
+  if (mode == kModeAttThrust) {
+    sincosf(cm.t[0], &cm.s0, &cm.c0);
+    sincosf(cm.t[1], &cm.s1, &cm.c1);
+  }
+  return cm;
+}
+
+__device__ __forceinline__ int mode_of(const AdjointBuffers& ab, uint32_t i) {
+  const int m = ab.modes[i];
+  return m > kModeWrench ? kModeWrench : m;
+}
+
 // Forward recording: n_steps steps from the fleet state, checkpoint (state,
 // motors) every K steps into ckpt[s][13 + 8][n], loss per env, final state
 // written back, saturation flag per env.
-template <int NROT>
+template <int NROT, int MODE>
 __device__ void record_one(const AdjointBuffers& ab, const StepParams& P, uint32_t i) {
   const uint32_t n = ab.n;
   Xs<NROT> x;
@@ -318,9 +494,7 @@ __device__ void record_one(const AdjointBuffers& ab, const StepParams& P, uint32
   normalize(x.q);
   const Body b = body_at(ab.body, n, i);
   const Gains g = gains_of(P);
-  const V3 pd = {ab.targets[i], ab.targets[n + i], ab.targets[2 * n + i]};
-  float spsi, cpsi;
-  sincosf(ab.targets[3 * n + i], &spsi, &cpsi);
+  const Cmd cm = load_cmd(ab, i, MODE);
   const V3 goal = {ab.p_goal[i], ab.p_goal[n + i], ab.p_goal[2 * n + i]};
   float loss = 0.f;
   bool saturated = false;
@@ -329,7 +503,7 @@ __device__ void record_one(const AdjointBuffers& ab, const StepParams& P, uint32
       store_x(ab.ckpt + (size_t)(t / ab.K) * 21 * n, ab.ckpt + (size_t)(t / ab.K) * 21 * n + 13 * n, n, i, x);
     Step<NROT> S;
     Xs<NROT> xn;
-    forward_step(x, pd, cpsi, spsi, b, g, P, S, xn);
+    forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
 #pragma unroll
     for (int k = 0; k < NROT; ++k) saturated |= !S.pass[k];
     x = xn;
@@ -341,23 +515,31 @@ __device__ void record_one(const AdjointBuffers& ab, const StepParams& P, uint32
   ab.saturated[i] = saturated ? 1 : 0;
 }
 
+template <int NROT>
+__device__ __forceinline__ void record_mode(const AdjointBuffers& ab, const StepParams& P, uint32_t i) {
+  switch (mode_of(ab, i)) {
+    case kModePosition: record_one<NROT, kModePosition>(ab, P, i); break;
+    case kModeBodyVel: record_one<NROT, kModeBodyVel>(ab, P, i); break;
+    case kModeAttThrust: record_one<NROT, kModeAttThrust>(ab, P, i); break;
+    default: record_one<NROT, kModeWrench>(ab, P, i); break;
+  }
+}
+
 __global__ void __launch_bounds__(128) k_record(AdjointBuffers ab, StepParams P) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ab.n) return;
   const int nr = rotors_of(ab, i);
-  if (nr == 4) record_one<4>(ab, P, i);
-  else if (nr == 6) record_one<6>(ab, P, i);
-  else record_one<8>(ab, P, i);
+  if (nr == 4) record_mode<4>(ab, P, i);
+  else if (nr == 6) record_mode<6>(ab, P, i);
+  else record_mode<8>(ab, P, i);
 }
 
-template <int NROT>
+template <int NROT, int MODE>
 __device__ void adjoint_one(const AdjointBuffers& ab, const StepParams& P, uint32_t i) {
   const uint32_t n = ab.n;
   const Body b = body_at(ab.body, n, i);
   const Gains g = gains_of(P);
-  const V3 pd = {ab.targets[i], ab.targets[n + i], ab.targets[2 * n + i]};
-  float spsi, cpsi;
-  sincosf(ab.targets[3 * n + i], &spsi, &cpsi);
+  const Cmd cm = load_cmd(ab, i, MODE);
   const V3 goal = {ab.p_goal[i], ab.p_goal[n + i], ab.p_goal[2 * n + i]};
   const float wgt = ab.loss_weights ? ab.loss_weights[i] : 1.f;
   Adj<NROT> lam;
@@ -367,6 +549,7 @@ __device__ void adjoint_one(const AdjointBuffers& ab, const StepParams& P, uint3
   for (int k = 0; k < NROT; ++k) lam.u[k] = 0.f;
   GainAdj gb;
   gb.kx = gb.kv = gb.kR = gb.kW = {0.f, 0.f, 0.f};
+  float tb[4] = {0.f, 0.f, 0.f, 0.f};
   const int H = ab.n_steps, K = ab.K;
   const int n_seg = (H + K - 1) / K;
   for (int seg = n_seg - 1; seg >= 0; --seg) {
@@ -380,7 +563,7 @@ __device__ void adjoint_one(const AdjointBuffers& ab, const StepParams& P, uint3
       store_x(ab.tape + (size_t)t * 21 * n, ab.tape + (size_t)t * 21 * n + 13 * n, n, i, x);
       Step<NROT> S;
       Xs<NROT> xn;
-      forward_step(x, pd, cpsi, spsi, b, g, P, S, xn);
+      forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
       x = xn;
     }
     // reverse sweep
@@ -388,12 +571,12 @@ __device__ void adjoint_one(const AdjointBuffers& ab, const StepParams& P, uint3
       load_x(ab.tape + (size_t)t * 21 * n, ab.tape + (size_t)t * 21 * n + 13 * n, n, i, x);
       Step<NROT> S;
       Xs<NROT> xn;
-      forward_step(x, pd, cpsi, spsi, b, g, P, S, xn);
+      forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
       // this step's loss term acts on x_{t+1}
       const V3 e = xn.p - goal;
       lam.p = lam.p + (2.f * ab.w_pos * wgt) * e;
       lam.w = lam.w + (2.f * ab.w_omega * wgt) * xn.w;
-      backward_step(x, pd, cpsi, spsi, b, g, P, S, lam, gb);
+      backward_step<NROT, MODE>(x, cm, b, g, P, S, lam, gb, tb);
     }
   }
   // the kernel normalised q_0 at load: q_hat = q0 / |q0|
@@ -415,15 +598,27 @@ __device__ void adjoint_one(const AdjointBuffers& ab, const StepParams& P, uint3
                          gb.kR.x, gb.kR.y, gb.kR.z, gb.kW.x, gb.kW.y, gb.kW.z};
 #pragma unroll
   for (int k = 0; k < 12; ++k) gg[k * n + i] = v12[k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ab.grad_targets[k * n + i] = tb[k];
+}
+
+template <int NROT>
+__device__ __forceinline__ void adjoint_mode(const AdjointBuffers& ab, const StepParams& P, uint32_t i) {
+  switch (mode_of(ab, i)) {
+    case kModePosition: adjoint_one<NROT, kModePosition>(ab, P, i); break;
+    case kModeBodyVel: adjoint_one<NROT, kModeBodyVel>(ab, P, i); break;
+    case kModeAttThrust: adjoint_one<NROT, kModeAttThrust>(ab, P, i); break;
+    default: adjoint_one<NROT, kModeWrench>(ab, P, i); break;
+  }
 }
 
 __global__ void __launch_bounds__(128) k_adjoint(AdjointBuffers ab, StepParams P) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ab.n) return;
   const int nr = rotors_of(ab, i);
-  if (nr == 4) adjoint_one<4>(ab, P, i);
-  else if (nr == 6) adjoint_one<6>(ab, P, i);
-  else adjoint_one<8>(ab, P, i);
+  if (nr == 4) adjoint_mode<4>(ab, P, i);
+  else if (nr == 6) adjoint_mode<6>(ab, P, i);
+  else adjoint_mode<8>(ab, P, i);
 }
 
 // Deterministic fleet sum of the 12 per-env gain gradients: each of the
@@ -464,21 +659,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const float* parti
   if (threadIdx.x == 0) out[k] = s;
 }
 
-__global__ void __launch_bounds__(256) k_count_non_position(const uint8_t* modes, uint32_t n, uint32_t* count) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool bad = i < n && modes[i] != kModePosition;
-  const unsigned m = __ballot_sync(0xFFFFFFFFu, bad);
-  if ((threadIdx.x & 31u) == 0 && m) atomicAdd(count, (uint32_t)__popc(m));
-}
-
 }  // namespace
-
-cudaError_t launch_count_non_position(const uint8_t* modes, uint32_t n, uint32_t* count, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
-  k_count_non_position<<<(n + 255) / 256, 256, 0, st>>>(modes, n, count);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_record(const AdjointBuffers& ab, const StepParams& P, cudaStream_t st) {
   k_record<<<(ab.n + 127) / 128, 128, 0, st>>>(ab, P);

@@ -17,7 +17,8 @@ struct AdjointBuffers {
   float* state;                // [13][n] fleet state (advanced by the record)
   float* motors;               // [8][n]
   const float* body;           // [4][n]
-  const float* targets;        // [4][n] position targets (p_d, psi_d)
+  const uint8_t* modes;        // [n] command mode per env (values above 3 act as a wrench)
+  const float* targets;        // [4][n] command targets
   const float* p_goal;         // [3][n]
   float* ckpt;                 // [S][21][n]
   float* tape;                 // [K][21][n]
@@ -26,6 +27,7 @@ struct AdjointBuffers {
   const float* loss_weights;   // [n] upstream gradient of each env's loss (NULL = 1)
   float* grad_x0;              // [13][n]
   float* grad_gains_env;       // [12][n]
+  float* grad_targets;         // [4][n]
   float* partial;              // [12][kReduceParts]
   float* grad_gains;           // [12]
   uint32_t n, n_quad, n_hexa, n_octo;
@@ -34,8 +36,6 @@ struct AdjointBuffers {
 };
 
 cudaError_t launch_record(const AdjointBuffers& ab, const StepParams& P, cudaStream_t st);
-// Counts environments whose mode is not position tracking into *count.
-cudaError_t launch_count_non_position(const uint8_t* modes, uint32_t n, uint32_t* count, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjointBuffers& ab, const StepParams& P, cudaStream_t st);
 
 }  // namespace agk

@@ -37,7 +37,6 @@ struct ag_ctx {
   agk::AdjointBuffers adj;
   size_t adj_ckpt_cap;       // checkpoints the ckpt buffer holds
   int adj_tape_cap;          // steps the tape holds
-  uint32_t* adj_count;       // [1] device scratch
   bool adj_recorded;
   agk::StepParams adj_P;     // parameters of the recorded rollout
   // depth rendering staging (allocated on first use, grown as needed)
@@ -203,7 +202,7 @@ ag_status enter(ag_ctx* ctx) {
 void free_adjoint(ag_ctx* ctx) {
   agk::AdjointBuffers& a = ctx->adj;
   void* ptrs[] = {(void*)a.p_goal, a.ckpt, a.tape, a.loss, a.saturated, (void*)a.loss_weights, a.grad_x0,
-                  a.grad_gains_env, a.partial, a.grad_gains, ctx->adj_count};
+                  a.grad_gains_env, a.grad_targets, a.partial, a.grad_gains};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -279,7 +278,6 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   std::memset(&ctx->adj, 0, sizeof(ctx->adj));
   ctx->adj_ckpt_cap = 0;
   ctx->adj_tape_cap = 0;
-  ctx->adj_count = nullptr;
   ctx->adj_recorded = false;
   ctx->cam_ids = nullptr;
   ctx->depth_stage = nullptr;
@@ -718,9 +716,9 @@ ag_status ensure_adjoint(ag_ctx* ctx, int n_steps, int K) {
     if (e == cudaSuccess) e = alloc(ctx, &lw, n);
     if (e == cudaSuccess) e = alloc(ctx, &a.grad_x0, 13 * n);
     if (e == cudaSuccess) e = alloc(ctx, &a.grad_gains_env, 12 * n);
+    if (e == cudaSuccess) e = alloc(ctx, &a.grad_targets, 4 * n);
     if (e == cudaSuccess) e = alloc(ctx, &a.partial, 12 * (size_t)agk::kReduceParts);
     if (e == cudaSuccess) e = alloc(ctx, &a.grad_gains, 12);
-    if (e == cudaSuccess) e = alloc(ctx, &ctx->adj_count, 1);
     a.p_goal = pg;
     a.loss_weights = lw;
     if (e != cudaSuccess) { cudaGetLastError(); ctx->err = "adjoint buffers do not fit"; return AG_ERR_OOM; }
@@ -769,21 +767,11 @@ extern "C" ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos,
   const size_t n = c.n_envs;
   const int K = c.record_every ? (int)c.record_every : 32;
   if ((s = ensure_adjoint(ctx, (int)n_steps, K)) != AG_OK) return s;
-  // every environment must be in position mode
-  uint32_t bad = 0;
-  if ((s = check_cuda(ctx, agk::launch_count_non_position(ctx->fb.modes, (uint32_t)n, ctx->adj_count, ctx->stream),
-                      "mode check")) != AG_OK) return s;
-  if ((s = check_cuda(ctx, cudaMemcpyAsync(&bad, ctx->adj_count, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream),
-                      "mode check copy")) != AG_OK) return s;
-  if ((s = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "synchronize")) != AG_OK) return s;
-  if (bad) {
-    ctx->err = "the differentiable rollout supports position mode only (" + std::to_string(bad) + " envs are not)";
-    return AG_ERR_UNSUPPORTED;
-  }
   agk::AdjointBuffers& a = ctx->adj;
   if ((s = check_cuda(ctx, cudaMemcpyAsync((void*)a.p_goal, p_goal, 3 * n * sizeof(float), cudaMemcpyDefault,
                                            ctx->stream), "copy goals")) != AG_OK) return s;
   a.state = ctx->fb.state; a.motors = ctx->fb.motors; a.body = ctx->fb.body; a.targets = ctx->fb.targets;
+  a.modes = ctx->fb.modes;
   a.n = c.n_envs; a.n_quad = c.n_quad; a.n_hexa = c.n_hexa; a.n_octo = c.n_octo;
   a.n_steps = (int)n_steps; a.K = K; a.w_pos = w_pos; a.w_omega = w_omega;
   ctx->adj_P = step_params(ctx);
@@ -798,14 +786,14 @@ extern "C" ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos,
 }
 
 extern "C" ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, float* grad_gains,
-                                 float* grad_gains_per_env) {
+                                 float* grad_gains_per_env, float* grad_targets) {
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   if (!ctx->adj_recorded) {
     ctx->err = "ag_backward needs a rollout recorded by ag_rollout_loss";
     return AG_ERR_STATE;
   }
-  if (!grad_x0 && !grad_gains && !grad_gains_per_env) return AG_OK;
+  if (!grad_x0 && !grad_gains && !grad_gains_per_env && !grad_targets) return AG_OK;
   agk::AdjointBuffers a = ctx->adj;
   const size_t n = ctx->cfg.n_envs;
   if (loss_weights) {
@@ -820,9 +808,12 @@ extern "C" ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* 
                                                       st), "copy grad x0")) != AG_OK) return s;
   if (grad_gains && (s = check_cuda(ctx, cudaMemcpyAsync(grad_gains, a.grad_gains, 12 * sizeof(float),
                                                          cudaMemcpyDefault, st), "copy grad gains")) != AG_OK) return s;
-  if (grad_gains_per_env)
-    s = check_cuda(ctx, cudaMemcpyAsync(grad_gains_per_env, a.grad_gains_env, 12 * n * sizeof(float),
-                                        cudaMemcpyDefault, st), "copy per-env grad gains");
+  if (grad_gains_per_env && (s = check_cuda(ctx, cudaMemcpyAsync(grad_gains_per_env, a.grad_gains_env,
+                                                                  12 * n * sizeof(float), cudaMemcpyDefault, st),
+                                             "copy per-env grad gains")) != AG_OK) return s;
+  if (grad_targets)
+    s = check_cuda(ctx, cudaMemcpyAsync(grad_targets, a.grad_targets, 4 * n * sizeof(float), cudaMemcpyDefault, st),
+                   "copy grad targets");
   return s;
 }
 

@@ -41,7 +41,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_defaults(lib):
-    assert _abi.ag_abi_version() == 1
+    header = open(os.path.join(ROOT, "include", "ag.h")).read()
+    assert f"#define AG_ABI_VERSION {_abi.ABI_VERSION}" in header
+    assert _abi.ag_abi_version() == _abi.ABI_VERSION
     c = _abi.ag_config_default()
     assert c.n_envs == 1024 and c.n_quad == 1024 and c.substeps_per_step == 1
     assert abs(c.dt - 0.01) < 1e-9 and abs(c.u_max - 5.0) < 1e-9 and abs(c.motor_tau - 0.03) < 1e-9

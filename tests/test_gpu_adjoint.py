@@ -1,6 +1,6 @@
 """The hand-written adjoint (ag_backward) against the FP64 oracle.
 
-Workload: 65,536 quads in position mode, semi-implicit Euler, 256 steps,
+Main workload: 65,536 quads in position mode, semi-implicit Euler, 256 steps,
 loss = sum_t |p_t - p_goal|^2 + 0.01 |Omega_t|^2, checkpoint every 32 steps.
 Gradients with respect to the initial state (13 per vehicle) and the 12
 gains are compared with FP64 central finite differences of the oracle's loss
@@ -10,6 +10,9 @@ switches inside the finite-difference step the loss has a kink there: a
 component whose one-sided differences keep the same gap when the step is
 halved is such a kink and is excluded (and counted); a second workload with
 small errors, where no motor ever saturates, must match on every component.
+The other command modes (body velocity, attitude and thrust, wrench) and
+hexa / octo rotors are checked the same way, including the gradient with
+respect to each environment's four command targets.
 """
 import numpy as np
 import pytest
@@ -195,9 +198,153 @@ def test_unsupported_configurations_are_refused():
         _abi.ag_backward(fl.ctx, None, torch.empty((13, 256), device="cuda"))
     assert e.value.status == _abi.AG_ERR_STATE
     fl.close()
-    w = W.Workload("vel", 256, 1, 0, 0, 256, 0, 0, mode_mix=(W.MODE_BODY_VEL,))
+    w = W.Workload("obs", 256, 1, 0, 2, 256, 0, 0)
     fl = gpu_fleet(w, W.make_inputs(w, 1), 1)
     with pytest.raises(_abi.AgError) as e:
         _abi.ag_rollout_loss(fl.ctx, 10, 1.0, 0.01, goal, loss)
     assert e.value.status == _abi.AG_ERR_UNSUPPORTED
+    fl.close()
+
+
+# --------------------------------------------------- every command mode --
+H_MODES = 96
+MODE_NAMES = {W.MODE_POSITION: "position", W.MODE_BODY_VEL: "velocity", W.MODE_ATT_THRUST: "attitude",
+              W.MODE_WRENCH: "wrench"}
+
+
+def _mode_inputs(w, seed, gentle):
+    """Inputs of every mode; gentle keeps each motor well inside [0, u_max]."""
+    inp = W.make_inputs(w, seed)
+    rng = np.random.default_rng(seed + 100)
+    m = inp.body[0].astype(np.float64)
+    t = inp.targets.astype(np.float64)
+    for i in range(w.n_envs):
+        md = inp.modes[i]
+        if md == W.MODE_WRENCH:
+            t[:, i] = [m[i] * 9.81 * rng.uniform(0.97, 1.03), *rng.uniform(-2e-3, 2e-3, 3)]
+        elif gentle and md == W.MODE_ATT_THRUST:
+            t[:, i] = [*rng.uniform(-0.15, 0.15, 2), rng.uniform(-0.5, 0.5), m[i] * 9.81 * rng.uniform(0.95, 1.05)]
+        elif gentle and md == W.MODE_BODY_VEL:
+            t[:, i] = [*rng.uniform(-0.5, 0.5, 3), rng.uniform(-0.3, 0.3)]
+        elif gentle and md == W.MODE_POSITION:
+            t[:, i] = [*rng.uniform(-0.5, 0.5, 3), rng.uniform(-np.pi, np.pi)]
+    return W.Inputs(inp.modes, t.astype(np.float32), inp.body, None)
+
+
+def _run_modes(w, inp, seed, gentle):
+    fl = gpu_fleet(w, inp, seed)
+    fl.reset(None, seed)
+    if gentle:   # level, at rest, yaw U[-pi, pi); position-mode vehicles within 0.3 m of their target
+        rng = np.random.default_rng(seed)
+        st = _np(fl.state())
+        pos = inp.modes == W.MODE_POSITION
+        st[0:3, pos] = inp.targets[0:3, pos] + rng.uniform(-0.3, 0.3, (3, int(pos.sum())))
+        st[3:6] = 0.0
+        st[10:13] = 0.0
+        yaw = rng.uniform(-np.pi, np.pi, w.n_envs)
+        # yaw authority is small (k_yaw = 0.016): a yaw error of 0.2 rad already drives a motor to 0
+        yaw[pos] = inp.targets[3, pos] + rng.uniform(-0.05, 0.05, int(pos.sum()))
+        half = yaw / 2
+        st[6], st[7], st[8], st[9] = np.cos(half), 0.0, 0.0, np.sin(half)
+        fl.set_state(st.astype(np.float32))
+    x0, m0 = _np(fl.state()), _np(fl.motors())
+    n = w.n_envs
+    goal = (x0[0:3] + 0.2 * np.random.default_rng(seed + 1).uniform(-1, 1, (3, n))).astype(np.float32)
+    loss = torch.empty(n, device="cuda")
+    sat = torch.empty(n, dtype=torch.uint8, device="cuda")
+    _abi.ag_rollout_loss(fl.ctx, H_MODES, W_POS, W_OMEGA, torch.from_numpy(goal).cuda(), loss, sat)
+    gx = torch.empty((13, n), device="cuda")
+    gge = torch.empty((12, n), device="cuda")
+    gt = torch.empty((4, n), device="cuda")
+    _abi.ag_backward(fl.ctx, None, gx, None, gge, gt)
+    torch.cuda.synchronize()
+    fl.close()
+    return x0, m0, goal, _np(loss), _np(sat), _np(gx), _np(gge), _np(gt)
+
+
+def _rotors(w, i):
+    return 4 if i < w.n_quad else (6 if i < w.n_quad + w.n_hexa else 8)
+
+
+def _loss29(world, w, inp, i, x0, m0, goal, v):
+    """Oracle loss at v = (x0 (13), gains (12), targets (4))."""
+    nr = _rotors(w, i)
+    return O.vehicle_loss(world, nr, int(inp.modes[i]), v[25:29], inp.body[:, i].astype(np.float64), v[:13],
+                          m0[0:nr, i].astype(np.float64), v[13:25], H_MODES, goal[:, i].astype(np.float64), W_POS,
+                          W_OMEGA)
+
+
+def _sample(w, inp, per_cell, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for md in MODE_NAMES:
+        for lo, hi in [(0, w.n_quad), (w.n_quad, w.n_quad + w.n_hexa), (w.n_quad + w.n_hexa, w.n_envs)]:
+            cand = np.nonzero(inp.modes[lo:hi] == md)[0] + lo
+            out += list(rng.choice(cand, min(per_cell, len(cand)), replace=False))
+    return sorted(out)
+
+
+MODES_W = W.Workload("modes", 3072, 1, 0, 0, 1024, 1024, 1024, drag=0.1, horizon=H_MODES,
+                     mode_mix=(W.MODE_POSITION, W.MODE_BODY_VEL, W.MODE_ATT_THRUST, W.MODE_WRENCH))
+
+
+def test_adjoint_every_mode_matches_oracle_jvp_with_target_tangents():
+    w = MODES_W
+    inp = _mode_inputs(w, 21, gentle=False)
+    x0, m0, goal, loss, sat, gx, gge, gt = _run_modes(w, inp, 21, gentle=False)
+    world = oracle_world(w)
+    rng = np.random.default_rng(22)
+    for i in _sample(w, inp, 3, 23):
+        nr = _rotors(w, i)
+        v = np.concatenate([x0[:, i], GAINS, inp.targets[:, i]]).astype(np.float64)
+        L = _loss29(world, w, inp, i, x0, m0, goal, v)
+        assert abs(loss[i] - L) <= 1e-4 * max(1.0, abs(L)), (i, loss[i], L)
+        ds, dg, dt = rng.normal(size=13), rng.normal(size=12), rng.normal(size=4)
+        _, jvp = O.vehicle_loss_jvp(world, nr, int(inp.modes[i]), v[25:29], inp.body[:, i].astype(np.float64),
+                                    v[:13], m0[0:nr, i].astype(np.float64), GAINS, ds, dg, H_MODES,
+                                    goal[:, i].astype(np.float64), W_POS, W_OMEGA, d_tgt4=dt)
+        dot = float(gx[:, i].astype(np.float64) @ ds + gge[:, i].astype(np.float64) @ dg +
+                    gt[:, i].astype(np.float64) @ dt)
+        assert abs(dot - jvp) <= 1e-3 * max(1.0, abs(jvp)), (MODE_NAMES[int(inp.modes[i])], nr, i, dot, jvp)
+
+
+def test_adjoint_every_mode_matches_fd_on_every_component():
+    w = MODES_W
+    inp = _mode_inputs(w, 31, gentle=True)
+    x0, m0, goal, loss, sat, gx, gge, gt = _run_modes(w, inp, 31, gentle=True)
+    # no clamp anywhere: every component is compared
+    assert sat.sum() == 0, {MODE_NAMES[m]: int(sat[inp.modes == m].sum()) for m in MODE_NAMES}
+    world = oracle_world(w)
+    for i in _sample(w, inp, 2, 32):
+        base = np.concatenate([x0[:, i], GAINS, inp.targets[:, i]]).astype(np.float64)
+        g_fd = np.zeros(29)
+        for k in range(29):
+            h = 1e-6 * max(1.0, abs(base[k]))
+            vp, vm = base.copy(), base.copy()
+            vp[k] += h
+            vm[k] -= h
+            g_fd[k] = (_loss29(world, w, inp, i, x0, m0, goal, vp) - _loss29(world, w, inp, i, x0, m0, goal, vm)) / (2 * h)
+        g_gpu = np.concatenate([gx[:, i], gge[:, i], gt[:, i]]).astype(np.float64)
+        err = np.linalg.norm(g_gpu - g_fd) / max(np.linalg.norm(g_fd), 1e-6)
+        assert err <= 1e-3, (MODE_NAMES[int(inp.modes[i])], _rotors(w, i), i, err, g_gpu, g_fd)
+        # the target part alone (it is small next to the state part in some modes)
+        et = np.linalg.norm(g_gpu[25:] - g_fd[25:]) / max(np.linalg.norm(g_fd[25:]), 1e-6)
+        assert et <= 2e-3, (MODE_NAMES[int(inp.modes[i])], i, et, g_gpu[25:], g_fd[25:])
+
+
+def test_autograd_target_gradient_matches_ag_backward():
+    from paper_2305_16510_gb300.autograd import rollout_loss
+    w = W.scaled(MODES_W, 512)
+    inp = _mode_inputs(w, 41, gentle=False)
+    x0, m0, goal, loss, sat, gx, gge, gt = _run_modes(w, inp, 41, gentle=False)
+    fl = gpu_fleet(w, inp, 41)
+    x0_t = torch.from_numpy(x0).cuda().requires_grad_(True)
+    tg_t = torch.from_numpy(inp.targets).cuda().requires_grad_(True)
+    gains_t = torch.tensor(GAINS, dtype=torch.float32, requires_grad=True)
+    out = rollout_loss(fl, x0_t, gains_t, torch.from_numpy(m0).cuda(), H_MODES, torch.from_numpy(goal).cuda(),
+                       W_POS, W_OMEGA, targets=tg_t)
+    np.testing.assert_allclose(_np(out), loss, rtol=1e-6)
+    out.sum().backward()
+    np.testing.assert_allclose(_np(tg_t.grad), gt, rtol=1e-6, atol=1e-6 * np.abs(gt).max())
+    np.testing.assert_allclose(_np(x0_t.grad), gx, rtol=1e-6, atol=1e-6 * np.abs(gx).max())
     fl.close()
