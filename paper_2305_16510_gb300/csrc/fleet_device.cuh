@@ -279,50 +279,64 @@ __device__ __forceinline__ void step_sie(VState& s, V3 b3, const Wrench4& W, con
 }
 
 // Classic RK4 on (p, v, q, Omega) with the wrench held over the stages;
-// renormalise q. The first stage uses the start attitude's b3 (unit q). The
-// factor 1/2 of the quaternion rate is folded into the stage weights.
+// renormalise q. The first stage uses the start attitude's b3 (unit q).
+//
+// The state travels as seven FP32 pairs, (vx vy) (vz wx) (wy wz) (qw qx)
+// (qy qz) (px py) (pz -), and each stage's rates in the same order as
+// (v' | Omega' | q' | p'), with q' = q (x) (0, Omega / 2). Every stage state
+// x + c k and every accumulation s + 2 k is then one packed FMA per pair
+// (__ffma2_rn); halving Omega and the step weights is exact, so each product
+// equals that of the scalar form.
+template <bool DRAG>
+__device__ __forceinline__ void rk4_rates(const float2 (&y)[7], V3 b3, float fm, float dm, V3 aw, const Body& b,
+                                          float2 (&k)[7]) {
+  const V3 v = {y[0].x, y[0].y, y[1].x}, w = {y[1].y, y[2].x, y[2].y};
+  const Q4 q = {y[3].x, y[3].y, y[4].x, y[4].y};
+  const V3 a = accel<DRAG>(b3, v, fm, dm);
+  const V3 al = ang_accel(w, aw, b);
+  const Q4 r = quat_rate2(q, {0.5f * w.x, 0.5f * w.y, 0.5f * w.z});
+  k[0] = make_float2(a.x, a.y);
+  k[1] = make_float2(a.z, al.x);
+  k[2] = make_float2(al.y, al.z);
+  k[3] = make_float2(r.w, r.x);
+  k[4] = make_float2(r.y, r.z);
+  k[5] = make_float2(v.x, v.y);
+  k[6] = make_float2(v.z, 0.f);
+}
+
 template <bool DRAG>
 __device__ __forceinline__ void step_rk4(VState& s, V3 b3, const Wrench4& W, const Body& b, float drag, float h) {
   const float fm = W.f * b.inv_m, dm = drag * b.inv_m;
   const V3 aw = {b.ijx * W.mx, b.ijy * W.my, b.ijz * W.mz};
-  const float h2 = 0.5f * h, h4 = 0.25f * h;
-  // stage 1; the accumulators collect k1 + 2 k2 + 2 k3 + k4
-  V3 a = accel<DRAG>(b3, s.v, fm, dm);
-  V3 al = ang_accel(s.w, aw, b);
-  Q4 r = quat_rate2(s.q, s.w);
-  V3 sp = s.v, sv = a, sw = al;
-  Q4 sq = r;
-  // stages 2 and 3 (t + h/2, each from the previous stage's rates)
+  const float2 x[7] = {make_float2(s.v.x, s.v.y), make_float2(s.v.z, s.w.x), make_float2(s.w.y, s.w.z),
+                       make_float2(s.q.w, s.q.x), make_float2(s.q.y, s.q.z), make_float2(s.p.x, s.p.y),
+                       make_float2(s.p.z, 0.f)};
+  float2 k[7], acc[7], y[7];
+  // stage 1; acc collects k1 + 2 k2 + 2 k3 + k4
+  rk4_rates<DRAG>(x, b3, fm, dm, aw, b, k);
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const V3 v = s.v + h2 * a, w = s.w + h2 * al;
-    const Q4 q = {s.q.w + h4 * r.w, s.q.x + h4 * r.x, s.q.y + h4 * r.y, s.q.z + h4 * r.z};
-    a = accel<DRAG>(body_z(q), v, fm, dm);
-    al = ang_accel(w, aw, b);
-    r = quat_rate2(q, w);
-    sp = sp + 2.f * v;
-    sv = sv + 2.f * a;
-    sw = sw + 2.f * al;
-    sq = {sq.w + 2.f * r.w, sq.x + 2.f * r.x, sq.y + 2.f * r.y, sq.z + 2.f * r.z};
+  for (int i = 0; i < 7; ++i) acc[i] = k[i];
+  // stages 2 and 3 at t + h/2, stage 4 at t + h, each from the previous stage's rates
+  const float2 c2 = make_float2(0.5f * h, 0.5f * h), c4 = make_float2(h, h), two = make_float2(2.f, 2.f);
+#pragma unroll
+  for (int st = 0; st < 3; ++st) {
+    const float2 c = st < 2 ? c2 : c4;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) y[i] = __ffma2_rn(c, k[i], x[i]);  // v, Omega, q (p is not needed)
+    rk4_rates<DRAG>(y, body_z({y[3].x, y[3].y, y[4].x, y[4].y}), fm, dm, aw, b, k);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) acc[i] = st < 2 ? __ffma2_rn(two, k[i], acc[i]) : __fadd2_rn(k[i], acc[i]);
   }
-  // stage 4 (t + h, from stage 3's rates)
-  {
-    const V3 v = s.v + h * a, w = s.w + h * al;
-    const Q4 q = {s.q.w + h2 * r.w, s.q.x + h2 * r.x, s.q.y + h2 * r.y, s.q.z + h2 * r.z};
-    a = accel<DRAG>(body_z(q), v, fm, dm);
-    al = ang_accel(w, aw, b);
-    r = quat_rate2(q, w);
-    sp = sp + v;
-    sv = sv + a;
-    sw = sw + al;
-    sq = {sq.w + r.w, sq.x + r.x, sq.y + r.y, sq.z + r.z};
-  }
-  // x + h/6 (k1 + 2 k2 + 2 k3 + k4); p' = v, q' = r / 2
-  const float h6 = h * (1.f / 6.f), h12 = h * (1.f / 12.f);
-  s.p = s.p + h6 * sp;
-  s.v = s.v + h6 * sv;
-  s.w = s.w + h6 * sw;
-  s.q = {s.q.w + h12 * sq.w, s.q.x + h12 * sq.x, s.q.y + h12 * sq.y, s.q.z + h12 * sq.z};
+  // x + h/6 (k1 + 2 k2 + 2 k3 + k4)
+  const float h6 = h * (1.f / 6.f);
+  const float2 c6 = make_float2(h6, h6);
+  float2 xn[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) xn[i] = __ffma2_rn(c6, acc[i], x[i]);
+  s.v = {xn[0].x, xn[0].y, xn[1].x};
+  s.w = {xn[1].y, xn[2].x, xn[2].y};
+  s.q = {xn[3].x, xn[3].y, xn[4].x, xn[4].y};
+  s.p = {xn[5].x, xn[5].y, xn[6].x};
   normalize(s.q);
 }
 

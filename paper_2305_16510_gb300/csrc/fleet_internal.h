@@ -59,14 +59,18 @@ inline size_t box_pair_elems(size_t n, size_t n_obs) { return (n_obs + 1) / 2 * 
 // An odd box count is padded with a box at 1e30 that no sphere can touch.
 cudaError_t launch_permute_boxes(const FleetBuffers& fb, cudaStream_t st);
 
-// Threads per block of the fused kernel for a given obstacle count (the
-// per-block shared-memory staging grows with it).
-int fused_block_size(int n_obs);
+// Dynamic shared memory of a fused-kernel block of B threads: box pairs 1..
+// of every thread (pair 0 stays in registers).
+inline size_t fused_smem_bytes(int n_obs, int B) {
+  const int pairs = (n_obs + 1) / 2;
+  return pairs > 1 ? (size_t)(pairs - 1) * 10 * B * 8 : 0;
+}
 
-// Launch choices of the fused kernel. Defaults: mode-grouped order and
-// fused_block_size(). Tuning overrides (read at each launch):
-// AG_FUSED_ORDER=identity runs env i in slot i (the ungrouped ablation),
-// AG_FUSED_BLOCK=32..128 (multiple of 32) sets the block size.
+// Launch choices of the fused kernel. Defaults: mode-grouped order and the
+// block size (from 64, 128, 96, 32) with the most resident warps per SM by
+// the occupancy calculator (block = 0 here). Tuning overrides (read at each
+// launch): AG_FUSED_ORDER=identity runs env i in slot i (the ungrouped
+// ablation), AG_FUSED_BLOCK=32..128 (multiple of 32) sets the block size.
 struct FusedTuning { bool sorted; int block; };
 FusedTuning fused_tuning_from_env(int n_obs);
 

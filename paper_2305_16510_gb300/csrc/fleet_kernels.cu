@@ -22,36 +22,47 @@
 namespace agk {
 namespace {
 
+// Dynamic shared memory cap of the fused kernel (box staging).
+constexpr size_t kFusedSmemCap = 200 * 1024;
+
 // Thread slot i of the launch simulates environment order[i] (a permutation
 // that groups environments of equal rotor count and command mode, so the
 // mode branches of the controller are warp-uniform), or environment i when
-// order is NULL. Each thread stages its environment's boxes once per launch
-// in shared memory as [box][thread][10 floats]: 40-byte records, so the
-// five 8-byte loads of a warp hit 32 distinct bank pairs per phase. A thread
-// reads only what it wrote, so no barrier is needed.
+// order is NULL. Each thread stages its environment's boxes once per launch:
+// boxes 0 and 1 in registers, the others in shared memory as float2
+// [pair][field][thread], so a warp's 8-byte loads of one field are
+// consecutive and conflict-free. A thread reads only what it wrote, so no
+// barrier is needed.
 template <int INTEG, bool QUAD_ONLY, bool DRAG>
-__global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
-  extern __shared__ float2 sm_pairs[];  // [ceil(n_obs / 2)][10][blockDim.x] box pairs
+__global__ void __launch_bounds__(128, 3) k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
+  extern __shared__ float2 sm_pairs[];  // [ceil(n_obs / 2) - 1][10][blockDim.x] box pairs 1..
   const int B = blockDim.x;
   const uint32_t slot = blockIdx.x * B + threadIdx.x;
   const bool active = slot < fb.n;
   const uint32_t env = active ? (fb.order ? fb.order[slot] : slot) : slot;
-  float2* my = sm_pairs + threadIdx.x;
-  if (active) {
-    const int n_obs = (int)fb.n_obs;
+  RegSmemBoxPairs bx;
+  bx.sm = sm_pairs + threadIdx.x;
+  bx.B = B;
+#pragma unroll
+  for (int f = 0; f < 10; ++f) bx.r[f] = make_float2(0.f, 0.f);
+  const int n_obs = (int)fb.n_obs;
+  if (active && n_obs > 0) {
     const int pairs = (n_obs + 1) / 2;
     if (fb.order) {
       // the slot-ordered pair copy: coalesced 8-byte rows
-      for (int r = 0; r < pairs * 10; ++r) my[r * B] = fb.boxes_slot[(size_t)r * fb.n + slot];
+#pragma unroll
+      for (int f = 0; f < 10; ++f) bx.r[f] = fb.boxes_slot[(size_t)f * fb.n + slot];
+      for (int r = 10; r < pairs * 10; ++r) bx.sm[(r - 10) * B] = fb.boxes_slot[(size_t)r * fb.n + slot];
     } else {
       // ungrouped (env == slot): pair up the env-ordered rows here
-      for (int j = 0; j < pairs; ++j) {
+      bx.reload(fb, slot);
+      for (int j = 1; j < pairs; ++j) {
         const int k0 = 2 * j, k1 = 2 * j + 1;
 #pragma unroll
         for (int f = 0; f < 10; ++f) {
           const float a = fb.boxes[((size_t)k0 * 10 + f) * fb.n + slot];
           const float b = k1 < n_obs ? fb.boxes[((size_t)k1 * 10 + f) * fb.n + slot] : box_pad_field(f);
-          my[(j * 10 + f) * B] = make_float2(a, b);
+          bx.sm[((j - 1) * 10 + f) * B] = make_float2(a, b);
         }
       }
     }
@@ -60,8 +71,6 @@ __global__ void __launch_bounds__(128) k_fused_step(FleetBuffers fb, StepParams 
   bool any_hit = false;
   if (active) {
     const int nrot = QUAD_ONLY ? 4 : rotor_count(fb, env);
-    const SmemBoxPairs bx{my, B};
-    const int n_obs = (int)fb.n_obs;
     if (nrot == 4)
       simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
     else if (nrot == 6)
@@ -259,16 +268,28 @@ __global__ void __launch_bounds__(256) k_plain_compact(FleetBuffers fb) {
 template <int INTEG, bool QUAD_ONLY, bool DRAG>
 cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
                            cudaStream_t st) {
-  const size_t smem = (size_t)((fb.n_obs + 1) / 2) * 10 * B * sizeof(float2);
+  const auto kernel = k_fused_step<INTEG, QUAD_ONLY, DRAG>;
   static bool attr_set = false;  // per instantiation; raise the dynamic shared-memory cap once
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_step<INTEG, QUAD_ONLY, DRAG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemCap);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  if (B == 0) {  // the block size with the most resident warps per SM (ties: the earlier candidate)
+    int best = -1;
+    for (int b : {64, 128, 96, 32}) {
+      const size_t sm = fused_smem_bytes((int)fb.n_obs, b);
+      if (sm > kFusedSmemCap) continue;
+      int blocks = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, b, sm);
+      if (e != cudaSuccess) return e;
+      if (blocks * b > best) { best = blocks * b; B = b; }
+    }
+    if (best <= 0) return cudaErrorInvalidConfiguration;
+  }
+  const size_t smem = fused_smem_bytes((int)fb.n_obs, B);
   const unsigned grid = (fb.n + B - 1) / B;
-  k_fused_step<INTEG, QUAD_ONLY, DRAG><<<grid, B, smem, st>>>(fb, P, n_steps, substeps);
+  kernel<<<grid, B, smem, st>>>(fb, P, n_steps, substeps);
   return cudaGetLastError();
 }
 
@@ -286,32 +307,14 @@ cudaError_t launch_fused_i(const FleetBuffers& fb, const StepParams& P, int n_st
 
 }  // namespace
 
-int fused_block_size(int n_obs) {
-  // Largest block in {128, 96, 64, 32} that maximises resident warps per SM
-  // under 228 KB of shared memory (1 KB reserved per block) and ~96
-  // registers per thread.
-  const int per_thread = ((n_obs + 1) / 2) * 10 * (int)sizeof(float2);
-  int best_b = 128, best_warps = -1;
-  for (int b = 128; b >= 32; b -= 32) {
-    const int smem_blocks = per_thread ? 233472 / (per_thread * b + 1024) : 32;
-    const int reg_blocks = 65536 / (96 * b);
-    int blocks = smem_blocks < reg_blocks ? smem_blocks : reg_blocks;
-    if (blocks > 32) blocks = 32;
-    if (per_thread * b > 200 * 1024) blocks = 0;
-    const int warps = blocks * b / 32;
-    if (warps > best_warps) { best_warps = warps; best_b = b; }
-  }
-  return best_b;
-}
-
 FusedTuning fused_tuning_from_env(int n_obs) {
   FusedTuning t;
   t.sorted = true;
-  t.block = fused_block_size(n_obs);
+  t.block = 0;
   if (const char* v = std::getenv("AG_FUSED_ORDER")) t.sorted = std::strcmp(v, "identity") != 0;
   if (const char* v = std::getenv("AG_FUSED_BLOCK")) {
     int b = std::atoi(v);
-    if (b >= 32 && b <= 128 && b % 32 == 0 && (size_t)((n_obs + 1) / 2) * 80 * b <= 200 * 1024) t.block = b;
+    if (b >= 32 && b <= 128 && b % 32 == 0 && fused_smem_bytes(n_obs, b) <= kFusedSmemCap) t.block = b;
   }
   return t;
 }

@@ -117,25 +117,45 @@ __device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float
   return !(r2 < e2.x) | !(r2 < e2.y);
 }
 
-struct SmemBoxPairs {
-  float2* sm;  // this thread's column: element (j * 10 + f) * B
+// RegSmemBoxPairs: the first pair (boxes 0 and 1) in registers, the others
+// in shared memory as float2 [pair - 1][field][thread]. Holding one pair in
+// registers shrinks each thread's shared-memory footprint by a tenth of the
+// 16-box case, which lets one more block reside per SM.
+struct RegSmemBoxPairs {
+  float2 r[10];  // pair 0, fields 0..9
+  float2* sm;    // this thread's column of pairs 1..: element ((j - 1) * 10 + f) * B
   int B;
-  // replace field f of box k (a re-drawn pose)
-  __device__ __forceinline__ void set(int k, int f, float v) const {
-    float2& e = sm[(size_t)((k >> 1) * 10 + f) * B];
-    if (k & 1) e.y = v; else e.x = v;
-  }
   __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
     const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
-    bool hit = false;
+    bool hit = pair_hits(px, py, pz, r2, r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7], r[8], r[9]);
     const int pairs = (n_obs + 1) >> 1;
 #pragma unroll 2
-    for (int j = 0; j < pairs; ++j) {
-      const float2* f = sm + (size_t)j * 10 * B;
+    for (int j = 1; j < pairs; ++j) {
+      const float2* f = sm + (size_t)(j - 1) * 10 * B;
       hit |= pair_hits(px, py, pz, r2, f[0], f[B], f[2 * B], f[3 * B], f[4 * B], f[5 * B], f[6 * B], f[7 * B],
                        f[8 * B], f[9 * B]);
     }
     return hit;
+  }
+  // The shared-memory part, as the target of a re-draw (boxes 2..).
+  struct Staged {
+    float2* sm;
+    int B;
+    __device__ __forceinline__ void set(int k, int f, float v) const {
+      if (k < 2) return;
+      float2& e = sm[(size_t)(((k >> 1) - 1) * 10 + f) * B];
+      if (k & 1) e.y = v; else e.x = v;
+    }
+  };
+  __device__ __forceinline__ Staged staged() const { return {sm, B}; }
+  // pair 0 from the env-ordered boxes (after a re-draw)
+  __device__ __forceinline__ void reload(const FleetBuffers& fb, uint32_t env) {
+    const uint32_t n = fb.n;
+#pragma unroll
+    for (int f = 0; f < 10; ++f) {
+      r[f].x = fb.boxes[(size_t)f * n + env];
+      r[f].y = fb.n_obs > 1 ? fb.boxes[(size_t)(10 + f) * n + env] : box_pad_field(f);
+    }
   }
 };
 
@@ -149,8 +169,10 @@ struct NoBoxes {
 struct GlobalBoxPairs {
   const float2* __restrict__ rows;
   uint32_t n, idx;
-  // the global copy is refreshed by the caller of a re-draw; nothing cached here
+  // a re-draw refreshes the global copy itself; nothing is cached here
   __device__ __forceinline__ void set(int, int, float) const {}
+  __device__ __forceinline__ NoBoxes staged() const { return {}; }
+  __device__ __forceinline__ void reload(const FleetBuffers&, uint32_t) {}
   __device__ __forceinline__ float2 at(int r) const { return __ldg(rows + (size_t)r * n + idx); }
   __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
     const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
@@ -214,7 +236,7 @@ __device__ __forceinline__ void reset_env(const FleetBuffers& fb, uint32_t env, 
 
 template <int NROT, int INTEG, bool DRAG, class Boxes>
 __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, uint32_t slot,
-                                         int n_steps, int substeps, int n_obs, const Boxes& boxes, uint32_t seed_lo,
+                                         int n_steps, int substeps, int n_obs, Boxes& boxes, uint32_t seed_lo,
                                          uint32_t seed_hi, uint32_t& resets, bool& any_hit) {
   const uint32_t n = fb.n;
   VState s = load_state(fb.state, n, env);
@@ -238,7 +260,10 @@ __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParam
         resets += 1;
         epoch += 1;
         reset_in_registers<NROT>(s, u, b.m, env, epoch, seed_lo, seed_hi);
-        if (fb.box_rand) redraw_boxes(fb, env, slot, epoch, seed_lo, seed_hi, boxes);
+        if (fb.box_rand) {
+          redraw_boxes(fb, env, slot, epoch, seed_lo, seed_hi, boxes.staged());
+          boxes.reload(fb, env);
+        }
       }
     }
   }

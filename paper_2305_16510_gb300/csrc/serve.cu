@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kServeBlock) k_serve_step(const ServeDesc* __r
   const uint32_t slot = (blockIdx.x - d.block_begin) * blockDim.x + threadIdx.x;
   if (slot >= d.fb.n || d.steps <= 0) return;
   const uint32_t env = d.fb.order[slot];
-  const GlobalBoxPairs bx{d.fb.boxes_slot, d.fb.n, slot};
+  GlobalBoxPairs bx{d.fb.boxes_slot, d.fb.n, slot};
   uint32_t resets = 0;
   bool hit = false;
   simulate<4, INTEG, DRAG>(d.fb, P, env, slot, d.steps, substeps, (int)d.fb.n_obs, bx, d.seed_lo, d.seed_hi, resets,
