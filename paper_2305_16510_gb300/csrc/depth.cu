@@ -2,98 +2,187 @@
 //
 // The paper renders depth images through Isaac Gym's camera sensors (Sec. III,
 // a graphics-API renderer) and names kernel-based ray casting as the way to
-// render for many more robots (Sec. I, Sec. VII). Here every pixel is one
-// thread: a pinhole camera mounted on the vehicle (offset o_b in the body
-// frame, looking along body +x with body +z up) casts the ray
+// render for many more robots (Sec. I, Sec. VII). Here every pixel's ray is
+// traced on its own: a pinhole camera mounted on the vehicle (at a fixed
+// offset in the body frame, looking along body +x with body +z up) casts the
+// ray
 //   d = R (1, -(c + 0.5 - W/2) / f, -(r + 0.5 - H/2) / f),  f = (W/2) / tan(hfov/2)
 // through pixel (r, c); the depth is the smallest t >= 0 at which the ray is
 // inside a box (slab method in the box frame), which is the distance along
 // the optical axis because d has a unit forward component; max_range when
 // nothing is closer.
 //
-// One block renders 256 consecutive pixels of one camera. Its prologue turns
-// each box into (R_b^T, camera origin in the box frame, half-extents) once in
-// shared memory, so the per-pixel work is R_b^T d and three slabs per box.
+// A block of 256 threads renders one 32 x 32 tile of one camera's image, four
+// pixels per thread (column tx, rows ty, ty + 8, ty + 16, ty + 24: each warp
+// stores 32 consecutive pixels of a row). Its prologue turns each box into one
+// 16-float record in shared memory: M = R_b^T R (the camera's axes in the box
+// frame) and the slab bounds lo = -h - o_b, hi = h - o_b (o_b the camera
+// origin in the box frame). Per pixel and box the ray's box-frame direction
+// is then M (1, dy, dz) (six FMAs), followed by three reciprocals and the
+// slab intervals; records are read as four broadcast 16-byte loads and
+// reused for the thread's four pixels.
+//
+// The prologue also culls, conservatively, the boxes no ray of the tile can
+// reach closer than max_range: the box's bounding sphere (centre s in the
+// camera frame, radius |h| with a rounding margin) lies beyond max_range
+// along the axis, behind the camera, or outside one of the four planes
+// through the camera origin that bound the tile's rays (y = dy x and
+// z = dz x at the tile's extreme pixel centres). A culled box can change no
+// pixel of the tile, so the image is the same as without culling.
 #include <cmath>
 #include <cstdint>
 
 #include <cuda_runtime.h>
 
+#include "ag.h"
 #include "depth_internal.h"
 
 namespace agk {
 namespace {
 
-constexpr int kDepthBlock = 256;
-constexpr int kBoxRec = 15;  // R_b^T (9), camera origin in the box frame (3), half-extents (3)
+constexpr int kDepthTile = 32;                           // tile edge in pixels
+constexpr int kDepthThreads = 256;
+constexpr int kDepthPix = kDepthTile * kDepthTile / kDepthThreads;  // pixels per thread: 4
+constexpr int kDepthRows = kDepthThreads / kDepthTile;             // rows between a thread's pixels: 8
 
-__global__ void __launch_bounds__(kDepthBlock) k_render_depth(DepthArgs a) {
-  extern __shared__ float sm[];  // [n_obs][kBoxRec]
-  __shared__ float cam[12];      // R (9, row-major), origin (3)
-  const uint32_t j = blockIdx.y;
-  const uint32_t env = a.env_ids ? a.env_ids[j] : j;
+struct CamPose {
+  float R[3][3];
+  float o[3];
+};
+
+__device__ __forceinline__ CamPose camera_pose(const DepthArgs& a, uint32_t env) {
+  const float* st = a.state;
   const uint32_t n = a.n;
-  if (threadIdx.x == 0) {
-    const float* st = a.state;
-    Q4 q = {st[6 * n + env], st[7 * n + env], st[8 * n + env], st[9 * n + env]};
-    normalize(q);
-    float R[3][3];
-    rotation(q, R);
-    for (int i = 0; i < 3; ++i)
-      for (int k = 0; k < 3; ++k) cam[i * 3 + k] = R[i][k];
-    for (int i = 0; i < 3; ++i)
-      cam[9 + i] = st[i * n + env] + R[i][0] * a.offset[0] + R[i][1] * a.offset[1] + R[i][2] * a.offset[2];
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < (int)a.n_obs; k += blockDim.x) {
-    const float* bx = a.boxes + (size_t)k * 10 * n + env;
-    float R[3][3];
-    rotation(Q4{bx[6 * n], bx[7 * n], bx[8 * n], bx[9 * n]}, R);
-    const V3 v = {cam[9] - bx[0], cam[10] - bx[n], cam[11] - bx[2 * n]};
-    float* rec = sm + k * kBoxRec;
-    for (int i = 0; i < 3; ++i)
-      for (int m = 0; m < 3; ++m) rec[i * 3 + m] = R[m][i];  // R_b^T
-    rec[9] = R[0][0] * v.x + R[1][0] * v.y + R[2][0] * v.z;
-    rec[10] = R[0][1] * v.x + R[1][1] * v.y + R[2][1] * v.z;
-    rec[11] = R[0][2] * v.x + R[1][2] * v.y + R[2][2] * v.z;
-    rec[12] = bx[3 * n];
-    rec[13] = bx[4 * n];
-    rec[14] = bx[5 * n];
-  }
-  __syncthreads();
-  const uint32_t pix = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t n_pix = a.width * a.height;
-  if (pix >= n_pix) return;
-  const uint32_t r = pix / a.width, c = pix - r * a.width;
-  const float dy = -((float)c + 0.5f - 0.5f * (float)a.width) * a.inv_f;
-  const float dz = -((float)r + 0.5f - 0.5f * (float)a.height) * a.inv_f;
-  const V3 d = {cam[0] + cam[1] * dy + cam[2] * dz, cam[3] + cam[4] * dy + cam[5] * dz,
-                cam[6] + cam[7] * dy + cam[8] * dz};
-  float best = a.max_range;
-  for (int k = 0; k < (int)a.n_obs; ++k) {
-    const float* rec = sm + k * kBoxRec;
-    float t_in = 0.f, t_out = best;  // only hits in [0, best) matter
+  Q4 q = {st[6 * n + env], st[7 * n + env], st[8 * n + env], st[9 * n + env]};
+  normalize(q);
+  CamPose c;
+  rotation(q, c.R);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float di = rec[3 * i] * d.x + rec[3 * i + 1] * d.y + rec[3 * i + 2] * d.z;
-      const float inv = __frcp_rn(di);
-      const float t1 = (-rec[12 + i] - rec[9 + i]) * inv, t2 = (rec[12 + i] - rec[9 + i]) * inv;
-      t_in = fmaxf(t_in, fminf(t1, t2));
-      t_out = fminf(t_out, fmaxf(t1, t2));
-    }
-    if (t_in <= t_out) best = t_in;
+  for (int i = 0; i < 3; ++i)
+    c.o[i] = st[i * n + env] + c.R[i][0] * a.offset[0] + c.R[i][1] * a.offset[1] + c.R[i][2] * a.offset[2];
+  return c;
+}
+
+// record of box k: (M00 M01 M02 M10) (M11 M12 M20 M21) (M22 lo.x lo.y lo.z) (hi.x hi.y hi.z 0)
+__device__ __forceinline__ void box_record(const DepthArgs& a, uint32_t env, const CamPose& c, int k, float4* rec) {
+  const uint32_t n = a.n;
+  const float* bx = a.boxes + (size_t)k * 10 * n + env;
+  float Rb[3][3];
+  rotation(Q4{bx[6 * n], bx[7 * n], bx[8 * n], bx[9 * n]}, Rb);
+  const float v[3] = {c.o[0] - bx[0], c.o[1] - bx[n], c.o[2] - bx[2 * n]};
+  float M[3][3], ob[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    ob[i] = Rb[0][i] * v[0] + Rb[1][i] * v[1] + Rb[2][i] * v[2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[i][j] = Rb[0][i] * c.R[0][j] + Rb[1][i] * c.R[1][j] + Rb[2][i] * c.R[2][j];
   }
-  a.out[(size_t)j * n_pix + pix] = best;
+  const float h[3] = {bx[3 * n], bx[4 * n], bx[5 * n]};
+  rec[0] = make_float4(M[0][0], M[0][1], M[0][2], M[1][0]);
+  rec[1] = make_float4(M[1][1], M[1][2], M[2][0], M[2][1]);
+  rec[2] = make_float4(M[2][2], -h[0] - ob[0], -h[1] - ob[1], -h[2] - ob[2]);
+  rec[3] = make_float4(h[0] - ob[0], h[1] - ob[1], h[2] - ob[2], 0.f);
+}
+
+// The box's bounding sphere cannot meet any ray of the tile at depth below
+// max_range. Rays are (1, y, z) in the camera frame, y in [ylo, yhi], z in
+// [zlo, zhi].
+__device__ __forceinline__ bool box_culled(const DepthArgs& a, uint32_t env, const CamPose& c, int k, float ylo,
+                                           float yhi, float zlo, float zhi) {
+  const uint32_t n = a.n;
+  const float* bx = a.boxes + (size_t)k * 10 * n + env;
+  const float v[3] = {bx[0] - c.o[0], bx[n] - c.o[1], bx[2 * n] - c.o[2]};
+  const float sx = c.R[0][0] * v[0] + c.R[1][0] * v[1] + c.R[2][0] * v[2];
+  const float sy = c.R[0][1] * v[0] + c.R[1][1] * v[1] + c.R[2][1] * v[2];
+  const float sz = c.R[0][2] * v[0] + c.R[1][2] * v[1] + c.R[2][2] * v[2];
+  const float h0 = bx[3 * n], h1 = bx[4 * n], h2 = bx[5 * n];
+  const float rho = 1.001f * sqrtf(h0 * h0 + h1 * h1 + h2 * h2) + 1e-4f * (fabsf(sx) + fabsf(sy) + fabsf(sz)) + 1e-6f;
+  if (sx - rho > a.max_range || sx + rho < 0.f) return true;
+  // signed distances to the four planes (positive inside the tile's pyramid)
+  if (yhi * sx - sy < -rho * sqrtf(1.f + yhi * yhi)) return true;
+  if (sy - ylo * sx < -rho * sqrtf(1.f + ylo * ylo)) return true;
+  if (zhi * sx - sz < -rho * sqrtf(1.f + zhi * zhi)) return true;
+  if (sz - zlo * sx < -rho * sqrtf(1.f + zlo * zlo)) return true;
+  return false;
+}
+
+__global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
+  __shared__ float4 recs[AG_MAX_OBSTACLES * 4];
+  __shared__ uint8_t live[AG_MAX_OBSTACLES];
+  // block -> (camera, tile row, tile column); cameras cam0, cam0 + 1, ...
+  const uint32_t tiles_x = (a.width + kDepthTile - 1) / kDepthTile;
+  const uint32_t tiles = tiles_x * ((a.height + kDepthTile - 1) / kDepthTile);
+  const uint32_t j = a.cam0 + blockIdx.x / tiles;
+  const uint32_t t = blockIdx.x % tiles;
+  const uint32_t env = a.env_ids ? a.env_ids[j] : j;
+  const uint32_t n_pix = a.width * a.height;
+  const uint32_t tx = threadIdx.x & (kDepthTile - 1), ty = threadIdx.x / kDepthTile;
+  const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
+  const uint32_t col = x0 + tx;
+  const float half_w = 0.5f * (float)a.width, half_h = 0.5f * (float)a.height;
+  const float dy = -((float)col + 0.5f - half_w) * a.inv_f;
+  float dz[kDepthPix], best[kDepthPix];
+#pragma unroll
+  for (int k = 0; k < kDepthPix; ++k) {
+    dz[k] = -((float)(y0 + ty + k * kDepthRows) + 0.5f - half_h) * a.inv_f;
+    best[k] = a.max_range;
+  }
+  const int n_obs = (int)a.n_obs;  // at most AG_MAX_OBSTACLES (checked when the context is created)
+  if (n_obs > 0) {
+    // the tile's extreme pixel centres (clipped to the image)
+    const uint32_t x1 = min(x0 + kDepthTile, a.width) - 1, y1 = min(y0 + kDepthTile, a.height) - 1;
+    const float yhi = -((float)x0 + 0.5f - half_w) * a.inv_f, ylo = -((float)x1 + 0.5f - half_w) * a.inv_f;
+    const float zhi = -((float)y0 + 0.5f - half_h) * a.inv_f, zlo = -((float)y1 + 0.5f - half_h) * a.inv_f;
+    const CamPose cam = camera_pose(a, env);
+    for (int k = threadIdx.x; k < n_obs; k += kDepthThreads) {
+      const bool culled = box_culled(a, env, cam, k, ylo, yhi, zlo, zhi);
+      live[k] = culled ? 0 : 1;
+      if (!culled) box_record(a, env, cam, k, recs + 4 * k);
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < n_obs; ++k) {
+    if (!live[k]) continue;  // the same for the whole block
+    const float4 r0 = recs[4 * k], r1 = recs[4 * k + 1], r2 = recs[4 * k + 2], r3 = recs[4 * k + 3];
+    // the column's part of M (1, dy, dz), shared by the thread's four pixels
+    const float cx = fmaf(dy, r0.y, r0.x), cy = fmaf(dy, r1.x, r0.w), cz = fmaf(dy, r1.w, r1.z);
+#pragma unroll
+    for (int p = 0; p < kDepthPix; ++p) {
+      const float ix = __fdividef(1.f, fmaf(dz[p], r0.z, cx));
+      const float iy = __fdividef(1.f, fmaf(dz[p], r1.y, cy));
+      const float iz = __fdividef(1.f, fmaf(dz[p], r2.x, cz));
+      const float ax = r2.y * ix, bx = r3.x * ix, ay = r2.z * iy, by = r3.y * iy, az = r2.w * iz, bz = r3.z * iz;
+      // only hits in [0, best) matter
+      const float t_in = fmaxf(fmaxf(0.f, fminf(ax, bx)), fmaxf(fminf(ay, by), fminf(az, bz)));
+      const float t_out = fminf(fminf(best[p], fmaxf(ax, bx)), fminf(fmaxf(ay, by), fmaxf(az, bz)));
+      if (t_in <= t_out) best[p] = t_in;
+    }
+  }
+  if (col < a.width) {
+#pragma unroll
+    for (int k = 0; k < kDepthPix; ++k) {
+      const uint32_t row = y0 + ty + k * kDepthRows;
+      if (row < a.height) a.out[(size_t)j * n_pix + (size_t)row * a.width + col] = best[k];
+    }
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_render_depth(const DepthArgs& a, cudaStream_t st) {
-  const uint32_t n_pix = a.width * a.height;
-  dim3 grid((n_pix + kDepthBlock - 1) / kDepthBlock, a.n_cams);
-  const size_t smem = (size_t)a.n_obs * kBoxRec * sizeof(float);
-  k_render_depth<<<grid, kDepthBlock, smem, st>>>(a);
-  return cudaGetLastError();
+cudaError_t launch_render_depth(const DepthArgs& a_in, cudaStream_t st) {
+  const uint64_t tiles = (uint64_t)((a_in.width + kDepthTile - 1) / kDepthTile) *
+                         ((a_in.height + kDepthTile - 1) / kDepthTile);
+  // at most 2^31 - 1 blocks per launch
+  const uint64_t cams_per_launch = ((1ull << 31) - 1) / tiles;
+  DepthArgs a = a_in;
+  for (uint64_t c0 = 0; c0 < a_in.n_cams; c0 += cams_per_launch) {
+    const uint64_t nc = a_in.n_cams - c0 < cams_per_launch ? a_in.n_cams - c0 : cams_per_launch;
+    a.cam0 = (uint32_t)c0;
+    k_render_depth<<<(unsigned)(nc * tiles), kDepthThreads, 0, st>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace agk

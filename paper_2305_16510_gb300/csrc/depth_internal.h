@@ -14,6 +14,7 @@ struct DepthArgs {
   const uint32_t* env_ids; // [n_cams] or NULL (camera j = env j)
   float* out;              // [n_cams][height][width]
   uint32_t n, n_obs, n_cams, width, height;
+  uint32_t cam0;           // first camera of a launch (set by the launcher)
   float inv_f;             // tan(hfov / 2) / (width / 2)
   float max_range;
   float offset[3];         // camera position in the body frame

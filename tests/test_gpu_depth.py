@@ -77,3 +77,39 @@ def test_depth_paper_resolution_1024_robots_sampled():
         ref = O.render_depth(st, bx, [j], 480, 270, math.radians(87), 10.0)
         _compare(_np(img[j:j + 1]), ref, 0.002)
     fl.close()
+
+
+def test_depth_with_the_maximum_box_count():
+    # AG_MAX_OBSTACLES boxes per environment, the nearest surface taken over all of them
+    n_obs = _abi.AG_MAX_OBSTACLES
+    w = W.Workload("cams_many", 4, 1, 0, n_obs, 4, 0, 0)
+    inp = W.make_inputs(w, 14)
+    fl = gpu_fleet(w, inp, 14)
+    fl.reset(None, 14)
+    hfov, rng_max = math.radians(70), 20.0
+    img = _np(fl.render_depth(40, 24, hfov, rng_max))
+    ref = O.render_depth(_np(fl.state()), _np(fl.obstacles()), np.arange(4), 40, 24, hfov, rng_max)
+    _compare(img, ref, 0.01)
+    assert (ref < rng_max).mean() > 0.3
+    # the last box alone decides some pixels: moving it away changes them
+    boxes = _np(fl.obstacles()).copy()
+    boxes[n_obs - 1, 0:3] = 1e6
+    fl.set_obstacles(boxes)
+    img2 = _np(fl.render_depth(40, 24, hfov, rng_max))
+    ref2 = O.render_depth(_np(fl.state()), boxes, np.arange(4), 40, 24, hfov, rng_max)
+    _compare(img2, ref2, 0.01)
+    fl.close()
+
+
+def test_depth_more_cameras_than_a_grid_dimension():
+    # 70,000 cameras (above the 65,535 limit of a grid's y and z dimensions)
+    w = W.Workload("cams_wide", 70000, 1, 0, 2, 70000, 0, 0)
+    inp = W.make_inputs(w, 15)
+    fl = gpu_fleet(w, inp, 15)
+    fl.reset(None, 15)
+    hfov, rng_max = math.radians(90), 12.0
+    img = _np(fl.render_depth(8, 6, hfov, rng_max))
+    ref = O.render_depth(_np(fl.state()), _np(fl.obstacles()), np.arange(w.n_envs), 8, 6, hfov, rng_max)
+    _compare(img, ref, 0.002)
+    assert (ref[-100:] < rng_max).any()       # the last cameras were rendered too
+    fl.close()
