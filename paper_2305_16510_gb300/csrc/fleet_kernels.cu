@@ -33,8 +33,11 @@ constexpr size_t kFusedSmemCap = 200 * 1024;
 // [pair][field][thread], so a warp's 8-byte loads of one field are
 // consecutive and conflict-free. A thread reads only what it wrote, so no
 // barrier is needed.
-template <int INTEG, bool QUAD_ONLY, bool DRAG>
-__global__ void __launch_bounds__(128, 3) k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
+// BOXES = false (no obstacles) keeps the kernel within 128 registers, so
+// more warps are resident when there is no staging to pay for.
+template <int INTEG, bool QUAD_ONLY, bool DRAG, bool BOXES>
+__global__ void __launch_bounds__(128, BOXES ? 3 : 4) k_fused_step(FleetBuffers fb, StepParams P, int n_steps,
+                                                                  int substeps) {
   extern __shared__ float2 sm_pairs[];  // [ceil(n_obs / 2) - 1][10][blockDim.x] box pairs 1..
   const int B = blockDim.x;
   const uint32_t slot = blockIdx.x * B + threadIdx.x;
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(128, 3) k_fused_step(FleetBuffers fb, StepPara
 #pragma unroll
   for (int f = 0; f < 10; ++f) bx.r[f] = make_float2(0.f, 0.f);
   const int n_obs = (int)fb.n_obs;
-  if (active && n_obs > 0) {
+  if (BOXES && active && n_obs > 0) {
     const int pairs = (n_obs + 1) / 2;
     if (fb.order) {
       // the slot-ordered pair copy: coalesced 8-byte rows
@@ -71,12 +74,22 @@ __global__ void __launch_bounds__(128, 3) k_fused_step(FleetBuffers fb, StepPara
   bool any_hit = false;
   if (active) {
     const int nrot = QUAD_ONLY ? 4 : rotor_count(fb, env);
-    if (nrot == 4)
-      simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
-    else if (nrot == 6)
-      simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
-    else
-      simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+    if (BOXES) {
+      if (nrot == 4)
+        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+      else if (nrot == 6)
+        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+      else
+        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+    } else {
+      NoBoxSource none;
+      if (nrot == 4)
+        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit);
+      else if (nrot == 6)
+        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit);
+      else
+        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit);
+    }
     fb.collided[env] = any_hit ? 1 : 0;
   }
   append_compact(resets > 0u, env, fb.reset_ids, fb.n_reset);
@@ -265,10 +278,10 @@ __global__ void __launch_bounds__(256) k_plain_compact(FleetBuffers fb) {
   append_compact(pred, i, fb.reset_ids, fb.n_reset);
 }
 
-template <int INTEG, bool QUAD_ONLY, bool DRAG>
-cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
+template <int INTEG, bool QUAD_ONLY, bool DRAG, bool BOXES>
+cudaError_t launch_fused_b(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
                            cudaStream_t st) {
-  const auto kernel = k_fused_step<INTEG, QUAD_ONLY, DRAG>;
+  const auto kernel = k_fused_step<INTEG, QUAD_ONLY, DRAG, BOXES>;
   static bool attr_set = false;  // per instantiation; raise the dynamic shared-memory cap once
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemCap);
@@ -291,6 +304,13 @@ cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_st
   const unsigned grid = (fb.n + B - 1) / B;
   kernel<<<grid, B, smem, st>>>(fb, P, n_steps, substeps);
   return cudaGetLastError();
+}
+
+template <int INTEG, bool QUAD_ONLY, bool DRAG>
+cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
+                           cudaStream_t st) {
+  return fb.n_obs > 0 ? launch_fused_b<INTEG, QUAD_ONLY, DRAG, true>(fb, P, n_steps, substeps, B, st)
+                      : launch_fused_b<INTEG, QUAD_ONLY, DRAG, false>(fb, P, n_steps, substeps, B, st);
 }
 
 template <int INTEG>

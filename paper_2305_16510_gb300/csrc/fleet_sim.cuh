@@ -164,6 +164,13 @@ struct NoBoxes {
   __device__ __forceinline__ void set(int, int, float) const {}
 };
 
+// No boxes at all (a fleet without obstacles): nothing to test or re-load.
+struct NoBoxSource {
+  __device__ __forceinline__ bool any_hit(V3, float, int) const { return false; }
+  __device__ __forceinline__ NoBoxes staged() const { return {}; }
+  __device__ __forceinline__ void reload(const FleetBuffers&, uint32_t) {}
+};
+
 // GlobalBoxPairs: the slot-ordered pair copy in global memory, element
 // (j * 10 + f) * n + idx, read through the read-only cache.
 struct GlobalBoxPairs {
