@@ -12,21 +12,21 @@
 // the optical axis because d has a unit forward component; max_range when
 // nothing is closer.
 //
-// A block of 256 threads renders one 32 x 32 tile of one camera's image, four
-// pixels per thread (column tx, rows ty, ty + 8, ty + 16, ty + 24: each warp
-// stores 32 consecutive pixels of a row). Its prologue turns each box into one
-// 16-float record in shared memory: M = R_b^T R (the camera's axes in the box
-// frame) and the slab bounds lo = -h - o_b, hi = h - o_b (o_b the camera
-// origin in the box frame). Per pixel and box the ray's box-frame direction
-// is then M (1, dy, dz) (six FMAs), followed by three reciprocals and the
-// slab intervals; records are read as four broadcast 16-byte loads and
-// reused for the thread's four pixels.
+// A block of 256 threads renders up to eight 32 x 32 tiles of one camera's
+// image in turn, four pixels per thread (column tx, rows ty, ty + 8, ty + 16,
+// ty + 24: each warp stores 32 consecutive pixels of a row). Once per block it
+// turns each box into one 16-float record in shared memory: M = R_b^T R (the
+// camera's axes in the box frame) and the slab bounds lo = -h - o_b,
+// hi = h - o_b (o_b the camera origin in the box frame). Per pixel and box
+// the ray's box-frame direction is then M (1, dy, dz) (six FMAs), followed by
+// three reciprocals and the slab intervals; records are read as four
+// broadcast 16-byte loads and reused for the thread's four pixels.
 //
-// The prologue also culls, conservatively, the boxes no ray of the tile can
-// reach closer than max_range: the box's bounding sphere (centre s in the
-// camera frame, radius |h| with a rounding margin) lies beyond max_range
-// along the axis, behind the camera, or outside one of the four planes
-// through the camera origin that bound the tile's rays (y = dy x and
+// Before each tile the block culls, conservatively, the boxes that no ray of
+// the tile can reach closer than max_range: the box's bounding sphere (centre
+// s in the camera frame, radius |h| with a rounding margin) lies beyond
+// max_range along the axis, behind the camera, or outside one of the four
+// planes through the camera origin that bound the tile's rays (y = dy x and
 // z = dz x at the tile's extreme pixel centres). A culled box can change no
 // pixel of the tile, so the image is the same as without culling.
 #include <cmath>
@@ -44,6 +44,7 @@ constexpr int kDepthTile = 32;                           // tile edge in pixels
 constexpr int kDepthThreads = 256;
 constexpr int kDepthPix = kDepthTile * kDepthTile / kDepthThreads;  // pixels per thread: 4
 constexpr int kDepthRows = kDepthThreads / kDepthTile;             // rows between a thread's pixels: 8
+constexpr int kDepthTilesPerBlock = 8;                             // tiles of one camera per block
 
 struct CamPose {
   float R[3][3];
@@ -84,11 +85,9 @@ __device__ __forceinline__ void box_record(const DepthArgs& a, uint32_t env, con
   rec[3] = make_float4(h[0] - ob[0], h[1] - ob[1], h[2] - ob[2], 0.f);
 }
 
-// The box's bounding sphere cannot meet any ray of the tile at depth below
-// max_range. Rays are (1, y, z) in the camera frame, y in [ylo, yhi], z in
-// [zlo, zhi].
-__device__ __forceinline__ bool box_culled(const DepthArgs& a, uint32_t env, const CamPose& c, int k, float ylo,
-                                           float yhi, float zlo, float zhi) {
+// Bounding sphere of box k in the camera frame: centre s, radius |h| with a
+// rounding margin.
+__device__ __forceinline__ float4 box_sphere(const DepthArgs& a, uint32_t env, const CamPose& c, int k) {
   const uint32_t n = a.n;
   const float* bx = a.boxes + (size_t)k * 10 * n + env;
   const float v[3] = {bx[0] - c.o[0], bx[n] - c.o[1], bx[2 * n] - c.o[2]};
@@ -97,72 +96,100 @@ __device__ __forceinline__ bool box_culled(const DepthArgs& a, uint32_t env, con
   const float sz = c.R[0][2] * v[0] + c.R[1][2] * v[1] + c.R[2][2] * v[2];
   const float h0 = bx[3 * n], h1 = bx[4 * n], h2 = bx[5 * n];
   const float rho = 1.001f * sqrtf(h0 * h0 + h1 * h1 + h2 * h2) + 1e-4f * (fabsf(sx) + fabsf(sy) + fabsf(sz)) + 1e-6f;
-  if (sx - rho > a.max_range || sx + rho < 0.f) return true;
+  return make_float4(sx, sy, sz, rho);
+}
+
+// Rays of a tile: (1, y, z) in the camera frame with y in [ylo, yhi] and z in
+// [zlo, zhi] (the tile's extreme pixel centres); ny_* = sqrt(1 + y^2) etc.
+struct TileRays {
+  float ylo, yhi, zlo, zhi, nylo, nyhi, nzlo, nzhi;
+};
+
+// The sphere cannot meet any ray of the tile at depth below max_range.
+__device__ __forceinline__ bool sphere_culled(float4 s, const TileRays& t, float max_range) {
+  const float rho = s.w;
+  if (s.x - rho > max_range || s.x + rho < 0.f) return true;
   // signed distances to the four planes (positive inside the tile's pyramid)
-  if (yhi * sx - sy < -rho * sqrtf(1.f + yhi * yhi)) return true;
-  if (sy - ylo * sx < -rho * sqrtf(1.f + ylo * ylo)) return true;
-  if (zhi * sx - sz < -rho * sqrtf(1.f + zhi * zhi)) return true;
-  if (sz - zlo * sx < -rho * sqrtf(1.f + zlo * zlo)) return true;
+  if (t.yhi * s.x - s.y < -rho * t.nyhi) return true;
+  if (s.y - t.ylo * s.x < -rho * t.nylo) return true;
+  if (t.zhi * s.x - s.z < -rho * t.nzhi) return true;
+  if (s.z - t.zlo * s.x < -rho * t.nzlo) return true;
   return false;
 }
 
 __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
   __shared__ float4 recs[AG_MAX_OBSTACLES * 4];
-  __shared__ uint8_t live[AG_MAX_OBSTACLES];
-  // block -> (camera, tile row, tile column); cameras cam0, cam0 + 1, ...
+  __shared__ float4 spheres[AG_MAX_OBSTACLES];
+  __shared__ uint8_t live[2][AG_MAX_OBSTACLES];  // per tile, alternating buffers
+  // block -> (camera, group of kDepthTilesPerBlock consecutive tiles); cameras cam0, cam0 + 1, ...
   const uint32_t tiles_x = (a.width + kDepthTile - 1) / kDepthTile;
   const uint32_t tiles = tiles_x * ((a.height + kDepthTile - 1) / kDepthTile);
-  const uint32_t j = a.cam0 + blockIdx.x / tiles;
-  const uint32_t t = blockIdx.x % tiles;
+  const uint32_t groups = (tiles + kDepthTilesPerBlock - 1) / kDepthTilesPerBlock;
+  const uint32_t j = a.cam0 + blockIdx.x / groups;
+  const uint32_t t_begin = (blockIdx.x % groups) * kDepthTilesPerBlock;
+  const uint32_t t_end = min(t_begin + kDepthTilesPerBlock, tiles);
   const uint32_t env = a.env_ids ? a.env_ids[j] : j;
   const uint32_t n_pix = a.width * a.height;
   const uint32_t tx = threadIdx.x & (kDepthTile - 1), ty = threadIdx.x / kDepthTile;
-  const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
-  const uint32_t col = x0 + tx;
   const float half_w = 0.5f * (float)a.width, half_h = 0.5f * (float)a.height;
-  const float dy = -((float)col + 0.5f - half_w) * a.inv_f;
-  float dz[kDepthPix], best[kDepthPix];
-#pragma unroll
-  for (int k = 0; k < kDepthPix; ++k) {
-    dz[k] = -((float)(y0 + ty + k * kDepthRows) + 0.5f - half_h) * a.inv_f;
-    best[k] = a.max_range;
-  }
   const int n_obs = (int)a.n_obs;  // at most AG_MAX_OBSTACLES (checked when the context is created)
-  if (n_obs > 0) {
-    // the tile's extreme pixel centres (clipped to the image)
-    const uint32_t x1 = min(x0 + kDepthTile, a.width) - 1, y1 = min(y0 + kDepthTile, a.height) - 1;
-    const float yhi = -((float)x0 + 0.5f - half_w) * a.inv_f, ylo = -((float)x1 + 0.5f - half_w) * a.inv_f;
-    const float zhi = -((float)y0 + 0.5f - half_h) * a.inv_f, zlo = -((float)y1 + 0.5f - half_h) * a.inv_f;
+  // once per block: each box's record and its bounding sphere in the camera frame
+  if ((int)threadIdx.x < n_obs) {
     const CamPose cam = camera_pose(a, env);
     for (int k = threadIdx.x; k < n_obs; k += kDepthThreads) {
-      const bool culled = box_culled(a, env, cam, k, ylo, yhi, zlo, zhi);
-      live[k] = culled ? 0 : 1;
-      if (!culled) box_record(a, env, cam, k, recs + 4 * k);
+      box_record(a, env, cam, k, recs + 4 * k);
+      spheres[k] = box_sphere(a, env, cam, k);
     }
   }
-  __syncthreads();
-  for (int k = 0; k < n_obs; ++k) {
-    if (!live[k]) continue;  // the same for the whole block
-    const float4 r0 = recs[4 * k], r1 = recs[4 * k + 1], r2 = recs[4 * k + 2], r3 = recs[4 * k + 3];
-    // the column's part of M (1, dy, dz), shared by the thread's four pixels
-    const float cx = fmaf(dy, r0.y, r0.x), cy = fmaf(dy, r1.x, r0.w), cz = fmaf(dy, r1.w, r1.z);
+  for (uint32_t t = t_begin; t < t_end; ++t) {
+    const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
+    uint8_t* lv = live[t & 1u];
+    if ((int)threadIdx.x < n_obs) {
+      const uint32_t x1 = min(x0 + kDepthTile, a.width) - 1, y1 = min(y0 + kDepthTile, a.height) - 1;
+      TileRays r;
+      r.yhi = -((float)x0 + 0.5f - half_w) * a.inv_f;
+      r.ylo = -((float)x1 + 0.5f - half_w) * a.inv_f;
+      r.zhi = -((float)y0 + 0.5f - half_h) * a.inv_f;
+      r.zlo = -((float)y1 + 0.5f - half_h) * a.inv_f;
+      r.nyhi = sqrtf(1.f + r.yhi * r.yhi);
+      r.nylo = sqrtf(1.f + r.ylo * r.ylo);
+      r.nzhi = sqrtf(1.f + r.zhi * r.zhi);
+      r.nzlo = sqrtf(1.f + r.zlo * r.zlo);
+      // (with the records, written before the first barrier of the block)
+      for (int k = threadIdx.x; k < n_obs; k += kDepthThreads) lv[k] = sphere_culled(spheres[k], r, a.max_range) ? 0 : 1;
+    }
+    __syncthreads();  // flags of this tile ready; every thread is done with the tile two back
+    const uint32_t col = x0 + tx;
+    const float dy = -((float)col + 0.5f - half_w) * a.inv_f;
+    float dz[kDepthPix], best[kDepthPix];
 #pragma unroll
     for (int p = 0; p < kDepthPix; ++p) {
-      const float ix = __fdividef(1.f, fmaf(dz[p], r0.z, cx));
-      const float iy = __fdividef(1.f, fmaf(dz[p], r1.y, cy));
-      const float iz = __fdividef(1.f, fmaf(dz[p], r2.x, cz));
-      const float ax = r2.y * ix, bx = r3.x * ix, ay = r2.z * iy, by = r3.y * iy, az = r2.w * iz, bz = r3.z * iz;
-      // only hits in [0, best) matter
-      const float t_in = fmaxf(fmaxf(0.f, fminf(ax, bx)), fmaxf(fminf(ay, by), fminf(az, bz)));
-      const float t_out = fminf(fminf(best[p], fmaxf(ax, bx)), fminf(fmaxf(ay, by), fmaxf(az, bz)));
-      if (t_in <= t_out) best[p] = t_in;
+      dz[p] = -((float)(y0 + ty + p * kDepthRows) + 0.5f - half_h) * a.inv_f;
+      best[p] = a.max_range;
     }
-  }
-  if (col < a.width) {
+    for (int k = 0; k < n_obs; ++k) {
+      if (!lv[k]) continue;  // the same for the whole block
+      const float4 r0 = recs[4 * k], r1 = recs[4 * k + 1], r2 = recs[4 * k + 2], r3 = recs[4 * k + 3];
+      // the column's part of M (1, dy, dz), shared by the thread's four pixels
+      const float cx = fmaf(dy, r0.y, r0.x), cy = fmaf(dy, r1.x, r0.w), cz = fmaf(dy, r1.w, r1.z);
 #pragma unroll
-    for (int k = 0; k < kDepthPix; ++k) {
-      const uint32_t row = y0 + ty + k * kDepthRows;
-      if (row < a.height) a.out[(size_t)j * n_pix + (size_t)row * a.width + col] = best[k];
+      for (int p = 0; p < kDepthPix; ++p) {
+        const float ix = __fdividef(1.f, fmaf(dz[p], r0.z, cx));
+        const float iy = __fdividef(1.f, fmaf(dz[p], r1.y, cy));
+        const float iz = __fdividef(1.f, fmaf(dz[p], r2.x, cz));
+        const float ax = r2.y * ix, bx = r3.x * ix, ay = r2.z * iy, by = r3.y * iy, az = r2.w * iz, bz = r3.z * iz;
+        // only hits in [0, best) matter
+        const float t_in = fmaxf(fmaxf(0.f, fminf(ax, bx)), fmaxf(fminf(ay, by), fminf(az, bz)));
+        const float t_out = fminf(fminf(best[p], fmaxf(ax, bx)), fminf(fmaxf(ay, by), fmaxf(az, bz)));
+        if (t_in <= t_out) best[p] = t_in;
+      }
+    }
+    if (col < a.width) {
+#pragma unroll
+      for (int p = 0; p < kDepthPix; ++p) {
+        const uint32_t row = y0 + ty + p * kDepthRows;
+        if (row < a.height) a.out[(size_t)j * n_pix + (size_t)row * a.width + col] = best[p];
+      }
     }
   }
 }
@@ -172,13 +199,14 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
 cudaError_t launch_render_depth(const DepthArgs& a_in, cudaStream_t st) {
   const uint64_t tiles = (uint64_t)((a_in.width + kDepthTile - 1) / kDepthTile) *
                          ((a_in.height + kDepthTile - 1) / kDepthTile);
+  const uint64_t groups = (tiles + kDepthTilesPerBlock - 1) / kDepthTilesPerBlock;
   // at most 2^31 - 1 blocks per launch
-  const uint64_t cams_per_launch = ((1ull << 31) - 1) / tiles;
+  const uint64_t cams_per_launch = ((1ull << 31) - 1) / groups;
   DepthArgs a = a_in;
   for (uint64_t c0 = 0; c0 < a_in.n_cams; c0 += cams_per_launch) {
     const uint64_t nc = a_in.n_cams - c0 < cams_per_launch ? a_in.n_cams - c0 : cams_per_launch;
     a.cam0 = (uint32_t)c0;
-    k_render_depth<<<(unsigned)(nc * tiles), kDepthThreads, 0, st>>>(a);
+    k_render_depth<<<(unsigned)(nc * groups), kDepthThreads, 0, st>>>(a);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
