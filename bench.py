@@ -395,7 +395,7 @@ def task_part(seed: int, world: int) -> dict:
     env.close()
     return {"value": n * k * world / secs, "unit": "task env-steps/s", "ms_per_step": float(np.mean(per)),
             "workload": "reach-a-setpoint, 1,048,576 quads, attitude interface, SIE 1 substep, no obstacles, "
-                        "obs [n,13] + reward + done per step", "launches_per_step": 3}
+                        "obs [n,13] + reward + done per step", "launches_per_step": 1}
 
 
 # ----------------------------------------------------------------- adjoint --

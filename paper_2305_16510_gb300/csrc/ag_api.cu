@@ -619,9 +619,8 @@ ag_status ag_reach_step(ag_ctx* ctx, const float* actions, float* obs, float* re
   if (!actions || !obs || !reward || !done) return fail_invalid(ctx, "actions, obs, reward and done must be non-NULL");
   if (reinterpret_cast<uintptr_t>(actions) % 16 != 0) return fail_invalid(ctx, "actions must be 16-byte aligned");
   const agk::ReachArgs a = reach_args(ctx, actions, obs, reward, done);
-  if ((s = check_cuda(ctx, agk::launch_reach_actions(a, ctx->stream), "task action launch")) != AG_OK) return s;
-  if ((s = step_common(ctx, ctx->cfg.substeps_per_step, true)) != AG_OK) return s;
-  return check_cuda(ctx, agk::launch_reach_tail(a, false, ctx->stream), "task tail launch");
+  return check_cuda(ctx, agk::launch_reach_step(a, step_params(ctx), (int)ctx->cfg.integrator,
+                                                (int)ctx->cfg.substeps_per_step, ctx->stream), "task step launch");
 }
 
 ag_status ag_reach_observe(ag_ctx* ctx, float* obs) {
@@ -629,7 +628,7 @@ ag_status ag_reach_observe(ag_ctx* ctx, float* obs) {
   if (s != AG_OK) return s;
   if (!ctx->reach_active) return AG_ERR_STATE;
   if (!obs) return fail_invalid(ctx, "obs must be non-NULL");
-  return check_cuda(ctx, agk::launch_reach_tail(reach_args(ctx, nullptr, obs, nullptr, nullptr), true, ctx->stream),
+  return check_cuda(ctx, agk::launch_reach_observe(reach_args(ctx, nullptr, obs, nullptr, nullptr), ctx->stream),
                     "task observe launch");
 }
 

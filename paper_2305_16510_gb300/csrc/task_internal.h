@@ -22,11 +22,13 @@ struct ReachArgs {
   uint32_t seed_lo, seed_hi;
 };
 
-// commands = offset + scale * clamp(actions, -1, 1), into fb.targets
-cudaError_t launch_reach_actions(const ReachArgs& a, cudaStream_t st);
-// reward and termination of the step just taken, in-place reset of the
-// episodes that ended without a collision, observations of the new state;
-// observe_only: observations alone
-cudaError_t launch_reach_tail(const ReachArgs& a, bool observe_only, cudaStream_t st);
+// One task step in one launch: commands = offset + scale * clamp(actions,
+// -1, 1) into fb.targets, one fleet step of `substeps` substeps (collision
+// resets listed in fb.reset_ids as ag_step lists them), reward and
+// termination, in-place reset of the episodes that ended without a
+// collision, observations of the new state.
+cudaError_t launch_reach_step(const ReachArgs& a, const StepParams& P, int integrator, int substeps, cudaStream_t st);
+// Observations of the current states alone.
+cudaError_t launch_reach_observe(const ReachArgs& a, cudaStream_t st);
 
 }  // namespace agk
