@@ -22,8 +22,9 @@
 // three reciprocals and the slab intervals; records are read as four
 // broadcast 16-byte loads and reused for the thread's four pixels.
 //
-// Before each tile the block culls, conservatively, the boxes that no ray of
-// the tile can reach closer than max_range: the box's bounding sphere (centre
+// Once per block, for each of its tiles, the block culls, conservatively, the
+// boxes that no ray of the tile can reach closer than max_range: the box's
+// bounding sphere (centre
 // s in the camera frame, radius |h| with a rounding margin) lies beyond
 // max_range along the axis, behind the camera, or outside one of the four
 // planes through the camera origin that bound the tile's rays (y = dy x and
@@ -120,7 +121,7 @@ __device__ __forceinline__ bool sphere_culled(float4 s, const TileRays& t, float
 __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
   __shared__ float4 recs[AG_MAX_OBSTACLES * 4];
   __shared__ float4 spheres[AG_MAX_OBSTACLES];
-  __shared__ uint8_t live[2][AG_MAX_OBSTACLES];  // per tile, alternating buffers
+  __shared__ uint8_t live[kDepthTilesPerBlock][AG_MAX_OBSTACLES];  // per tile of the block
   // block -> (camera, group of kDepthTilesPerBlock consecutive tiles); cameras cam0, cam0 + 1, ...
   const uint32_t tiles_x = (a.width + kDepthTile - 1) / kDepthTile;
   const uint32_t tiles = tiles_x * ((a.height + kDepthTile - 1) / kDepthTile);
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
   const uint32_t tx = threadIdx.x & (kDepthTile - 1), ty = threadIdx.x / kDepthTile;
   const float half_w = 0.5f * (float)a.width, half_h = 0.5f * (float)a.height;
   const int n_obs = (int)a.n_obs;  // at most AG_MAX_OBSTACLES (checked when the context is created)
-  // once per block: each box's record and its bounding sphere in the camera frame
+  // once per block: each box's record and its bounding sphere in the camera frame ...
   if ((int)threadIdx.x < n_obs) {
     const CamPose cam = camera_pose(a, env);
     for (int k = threadIdx.x; k < n_obs; k += kDepthThreads) {
@@ -141,24 +142,28 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
       spheres[k] = box_sphere(a, env, cam, k);
     }
   }
+  __syncthreads();
+  // ... then the cull flags of every (tile, box) pair of the block
+  const int pairs = (int)(t_end - t_begin) * n_obs;
+  for (int q = threadIdx.x; q < pairs; q += kDepthThreads) {
+    const uint32_t tl = (uint32_t)(q / n_obs), k = (uint32_t)(q % n_obs), t = t_begin + tl;
+    const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
+    const uint32_t x1 = min(x0 + kDepthTile, a.width) - 1, y1 = min(y0 + kDepthTile, a.height) - 1;
+    TileRays r;
+    r.yhi = -((float)x0 + 0.5f - half_w) * a.inv_f;
+    r.ylo = -((float)x1 + 0.5f - half_w) * a.inv_f;
+    r.zhi = -((float)y0 + 0.5f - half_h) * a.inv_f;
+    r.zlo = -((float)y1 + 0.5f - half_h) * a.inv_f;
+    r.nyhi = sqrtf(1.f + r.yhi * r.yhi);
+    r.nylo = sqrtf(1.f + r.ylo * r.ylo);
+    r.nzhi = sqrtf(1.f + r.zhi * r.zhi);
+    r.nzlo = sqrtf(1.f + r.zlo * r.zlo);
+    live[tl][k] = sphere_culled(spheres[k], r, a.max_range) ? 0 : 1;
+  }
+  __syncthreads();
   for (uint32_t t = t_begin; t < t_end; ++t) {
     const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
-    uint8_t* lv = live[t & 1u];
-    if ((int)threadIdx.x < n_obs) {
-      const uint32_t x1 = min(x0 + kDepthTile, a.width) - 1, y1 = min(y0 + kDepthTile, a.height) - 1;
-      TileRays r;
-      r.yhi = -((float)x0 + 0.5f - half_w) * a.inv_f;
-      r.ylo = -((float)x1 + 0.5f - half_w) * a.inv_f;
-      r.zhi = -((float)y0 + 0.5f - half_h) * a.inv_f;
-      r.zlo = -((float)y1 + 0.5f - half_h) * a.inv_f;
-      r.nyhi = sqrtf(1.f + r.yhi * r.yhi);
-      r.nylo = sqrtf(1.f + r.ylo * r.ylo);
-      r.nzhi = sqrtf(1.f + r.zhi * r.zhi);
-      r.nzlo = sqrtf(1.f + r.zlo * r.zlo);
-      // (with the records, written before the first barrier of the block)
-      for (int k = threadIdx.x; k < n_obs; k += kDepthThreads) lv[k] = sphere_culled(spheres[k], r, a.max_range) ? 0 : 1;
-    }
-    __syncthreads();  // flags of this tile ready; every thread is done with the tile two back
+    const uint8_t* lv = live[t - t_begin];
     const uint32_t col = x0 + tx;
     const float dy = -((float)col + 0.5f - half_w) * a.inv_f;
     float dz[kDepthPix], best[kDepthPix];

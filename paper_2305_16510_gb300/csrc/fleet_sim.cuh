@@ -241,10 +241,13 @@ __device__ __forceinline__ void reset_env(const FleetBuffers& fb, uint32_t env, 
   if (fb.box_rand) redraw_boxes(fb, env, fb.slot_of ? fb.slot_of[env] : env, epoch, seed_lo, seed_hi, NoBoxes{});
 }
 
+// simulate() with the command given (cm) instead of read from fb; returns
+// the final state, which it also stores.
 template <int NROT, int INTEG, bool DRAG, class Boxes>
-__device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, uint32_t slot,
-                                         int n_steps, int substeps, int n_obs, Boxes& boxes, uint32_t seed_lo,
-                                         uint32_t seed_hi, uint32_t& resets, bool& any_hit) {
+__device__ __forceinline__ VState simulate_cmd(const FleetBuffers& fb, const StepParams& P, uint32_t env,
+                                               uint32_t slot, const Command& cm, int n_steps, int substeps, int n_obs,
+                                               Boxes& boxes, uint32_t seed_lo, uint32_t seed_hi, uint32_t& resets,
+                                               bool& any_hit) {
   const uint32_t n = fb.n;
   VState s = load_state(fb.state, n, env);
   normalize(s.q);
@@ -252,7 +255,6 @@ __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParam
 #pragma unroll
   for (int k = 0; k < NROT; ++k) u[k] = fb.motors[k * n + env];
   const Body b = load_body(fb.body, n, env);
-  const Command cm = load_command(fb, env);
   uint32_t epoch = fb.epoch[env];
   for (int step = 0; step < n_steps; ++step) {
     for (int ss = 0; ss < substeps; ++ss) {
@@ -278,6 +280,15 @@ __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParam
 #pragma unroll
   for (int k = 0; k < NROT; ++k) fb.motors[k * n + env] = u[k];
   fb.epoch[env] = epoch;
+  return s;
+}
+
+template <int NROT, int INTEG, bool DRAG, class Boxes>
+__device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, uint32_t slot,
+                                         int n_steps, int substeps, int n_obs, Boxes& boxes, uint32_t seed_lo,
+                                         uint32_t seed_hi, uint32_t& resets, bool& any_hit) {
+  simulate_cmd<NROT, INTEG, DRAG>(fb, P, env, slot, load_command(fb, env), n_steps, substeps, n_obs, boxes, seed_lo,
+                                  seed_hi, resets, any_hit);
 }
 
 }  // namespace agk

@@ -26,6 +26,20 @@ constexpr int kObs = 13;
 
 __device__ __forceinline__ float norm3(float x, float y, float z) { return sqrtf(x * x + y * y + z * z); }
 
+__device__ __forceinline__ V3 load_goal(const ReachArgs& a, uint32_t i) {
+  const uint32_t n = a.fb.n;
+  return {a.goals[i], a.goals[n + i], a.goals[2 * n + i]};
+}
+
+// obs = (p - g, v, q with w >= 0, Omega)
+__device__ __forceinline__ void observe(const VState& s, V3 g, float* o) {
+  const float sgn = s.q.w < 0.f ? -1.f : 1.f;
+  o[0] = s.p.x - g.x; o[1] = s.p.y - g.y; o[2] = s.p.z - g.z;
+  o[3] = s.v.x; o[4] = s.v.y; o[5] = s.v.z;
+  o[6] = sgn * s.q.w; o[7] = sgn * s.q.x; o[8] = sgn * s.q.y; o[9] = sgn * s.q.z;
+  o[10] = s.w.x; o[11] = s.w.y; o[12] = s.w.z;
+}
+
 // Boxes of environment env read two at a time from the env-ordered array
 // (plain loads: a re-draw in the same launch rewrites them).
 struct EnvBoxPairs {
@@ -50,33 +64,23 @@ struct EnvBoxPairs {
 };
 
 // Reward, termination and in-place reset of environment i after its step
-// (hit: it collided, and the step already re-drew it), then its observation
-// into o[0..12].
-__device__ __forceinline__ void reach_tail(const ReachArgs& a, uint32_t i, bool hit, bool observe_only, float* o) {
-  const uint32_t n = a.fb.n;
-  const float* st = a.fb.state;
-  if (!observe_only) {
-    const uint32_t steps = a.steps[i] + 1u;
-    const float dist = norm3(st[0 * n + i] - a.goals[0 * n + i], st[1 * n + i] - a.goals[1 * n + i],
-                             st[2 * n + i] - a.goals[2 * n + i]);
-    const float speed = norm3(st[3 * n + i], st[4 * n + i], st[5 * n + i]);
-    const float rate = norm3(st[10 * n + i], st[11 * n + i], st[12 * n + i]);
-    const bool end = hit || dist > a.max_dist || steps >= a.max_steps;
-    a.reward[i] = hit ? -a.crash : -(dist + a.w_v * speed + a.w_omega * rate);
-    a.done[i] = end ? 1 : 0;
-    a.steps[i] = end ? 0u : steps;
-    if (end && !hit) reset_env(a.fb, i, a.seed_lo, a.seed_hi);
+// (s: its state after the step; hit: it collided, and the step already
+// re-drew it), then its observation into o[0..12].
+__device__ __forceinline__ void reach_tail(const ReachArgs& a, uint32_t i, VState s, bool hit, uint32_t steps_before,
+                                           V3 g, float* o) {
+  const uint32_t steps = steps_before + 1u;
+  const float dist = norm3(s.p.x - g.x, s.p.y - g.y, s.p.z - g.z);
+  const float speed = norm3(s.v.x, s.v.y, s.v.z);
+  const float rate = norm3(s.w.x, s.w.y, s.w.z);
+  const bool end = hit || dist > a.max_dist || steps >= a.max_steps;
+  a.reward[i] = hit ? -a.crash : -(dist + a.w_v * speed + a.w_omega * rate);
+  a.done[i] = end ? 1 : 0;
+  a.steps[i] = end ? 0u : steps;
+  if (end && !hit) {
+    reset_env(a.fb, i, a.seed_lo, a.seed_hi);
+    s = load_state(a.fb.state, a.fb.n, i);
   }
-  const float sgn = st[6 * n + i] < 0.f ? -1.f : 1.f;
-  o[0] = st[0 * n + i] - a.goals[0 * n + i];
-  o[1] = st[1 * n + i] - a.goals[1 * n + i];
-  o[2] = st[2 * n + i] - a.goals[2 * n + i];
-#pragma unroll
-  for (int r = 3; r < 6; ++r) o[r] = st[r * n + i];
-#pragma unroll
-  for (int r = 6; r < 10; ++r) o[r] = sgn * st[r * n + i];
-#pragma unroll
-  for (int r = 10; r < 13; ++r) o[r] = st[r * n + i];
+  observe(s, g, o);
 }
 
 // Coalesced write of the block's staged [kTaskBlock][13] observation rows.
@@ -100,26 +104,40 @@ __global__ void __launch_bounds__(kTaskBlock, BOXES ? 3 : 4) k_reach_step(ReachA
   const uint32_t n = fb.n;
   uint32_t resets = 0;
   if (i < n) {
+    // everything the step reads from memory, requested up front
     const float4 act = reinterpret_cast<const float4*>(a.actions)[i];
+    const V3 g = load_goal(a, i);
+    const uint32_t steps_before = a.steps[i];
     const float v[4] = {act.x, act.y, act.z, act.w};
+    float t[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) fb.targets[k * n + i] = fmaf(a.scale[k], fminf(fmaxf(v[k], -1.f), 1.f), a.offset[k]);
+    for (int k = 0; k < 4; ++k) t[k] = fmaf(a.scale[k], fminf(fmaxf(v[k], -1.f), 1.f), a.offset[k]);
+    const Command cm = prepare_command(fb.modes[i], t[0], t[1], t[2], t[3]);
     const int nrot = rotor_count(fb, i);
     const int n_obs = (int)fb.n_obs;
     bool hit = false;
+    VState s;
     if (BOXES) {
       EnvBoxPairs bx{fb.boxes, n, i};
-      if (nrot == 4) simulate<4, INTEG, DRAG>(fb, P, i, i, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
-      else if (nrot == 6) simulate<6, INTEG, DRAG>(fb, P, i, i, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
-      else simulate<8, INTEG, DRAG>(fb, P, i, i, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
+      if (nrot == 4)
+        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
+      else if (nrot == 6)
+        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
+      else
+        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
     } else {
       NoBoxSource none;
-      if (nrot == 4) simulate<4, INTEG, DRAG>(fb, P, i, i, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
-      else if (nrot == 6) simulate<6, INTEG, DRAG>(fb, P, i, i, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
-      else simulate<8, INTEG, DRAG>(fb, P, i, i, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
+      if (nrot == 4)
+        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
+      else if (nrot == 6)
+        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
+      else
+        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
     }
     fb.collided[i] = hit ? 1 : 0;
-    reach_tail(a, i, hit, false, stage + threadIdx.x * kObs);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fb.targets[k * n + i] = t[k];  // the commands, as ag_set_commands keeps them
+    reach_tail(a, i, s, hit, steps_before, g, stage + threadIdx.x * kObs);
   }
   append_compact(resets > 0u, i, fb.reset_ids, fb.n_reset);
   write_obs(a, stage);
@@ -128,7 +146,7 @@ __global__ void __launch_bounds__(kTaskBlock, BOXES ? 3 : 4) k_reach_step(ReachA
 __global__ void __launch_bounds__(kTaskBlock) k_reach_observe(ReachArgs a) {
   __shared__ float stage[kTaskBlock * kObs];
   const uint32_t i = blockIdx.x * kTaskBlock + threadIdx.x;
-  if (i < a.fb.n) reach_tail(a, i, false, true, stage + threadIdx.x * kObs);
+  if (i < a.fb.n) observe(load_state(a.fb.state, a.fb.n, i), load_goal(a, i), stage + threadIdx.x * kObs);
   write_obs(a, stage);
 }
 
