@@ -146,13 +146,21 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The largest x of all ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, slowest_secs: float) -> float:
+    """Weak scaling: every rank processes units_per_rank in its own fleet; the
+    job's rate is all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / slowest_secs
 
 
 def time_calls(fl, call, k: int, world: int):
@@ -206,8 +214,7 @@ def gpu_arm(args) -> dict | None:
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
         secs, per = time_calls(fl, lambda: fl.step(C), args.steps, world)
-    units = w.n_envs * C * args.steps * world
-    value = units / secs
+    value = whole_job_rate(w.n_envs * C * args.steps, world, secs)
     ms_per_step = secs * 1e3 / args.steps
     launch_ms = float(np.mean(per))
     achieved_tflops = w.n_envs * C * FLOP_PER_VEHICLE_STEP / (launch_ms * 1e-3) / 1e12
