@@ -10,6 +10,7 @@
 // the end of the launch (coalesced structure-of-arrays rows). Collision
 // resets happen in registers; the reset list is built with one
 // __ballot_sync + __popc prefix and one atomicAdd per warp.
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -282,11 +283,16 @@ template <int INTEG, bool QUAD_ONLY, bool DRAG, bool BOXES>
 cudaError_t launch_fused_b(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
                            cudaStream_t st) {
   const auto kernel = k_fused_step<INTEG, QUAD_ONLY, DRAG, BOXES>;
-  static bool attr_set = false;  // per instantiation; raise the dynamic shared-memory cap once
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemCap);
+  // raise the dynamic shared-memory cap once per instantiation and device (the attribute is per device)
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0;
+  if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemCap);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.fetch_or(bit, std::memory_order_release);
   }
   if (B == 0) {  // the block size with the most resident warps per SM (ties: the earlier candidate)
     int best = -1;
@@ -294,7 +300,7 @@ cudaError_t launch_fused_b(const FleetBuffers& fb, const StepParams& P, int n_st
       const size_t sm = fused_smem_bytes((int)fb.n_obs, b);
       if (sm > kFusedSmemCap) continue;
       int blocks = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, b, sm);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, b, sm);
       if (e != cudaSuccess) return e;
       if (blocks * b > best) { best = blocks * b; B = b; }
     }
