@@ -566,9 +566,12 @@ __device__ void adjoint_one(const AdjointBuffers& ab, const StepParams& P, uint3
       forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
       x = xn;
     }
-    // reverse sweep
+    // reverse sweep; the next (earlier) tape entry is requested one step ahead
+    Xs<NROT> x_prev;
+    load_x(ab.tape + (size_t)(len - 1) * 21 * n, ab.tape + (size_t)(len - 1) * 21 * n + 13 * n, n, i, x_prev);
     for (int t = len - 1; t >= 0; --t) {
-      load_x(ab.tape + (size_t)t * 21 * n, ab.tape + (size_t)t * 21 * n + 13 * n, n, i, x);
+      x = x_prev;
+      if (t > 0) load_x(ab.tape + (size_t)(t - 1) * 21 * n, ab.tape + (size_t)(t - 1) * 21 * n + 13 * n, n, i, x_prev);
       Step<NROT> S;
       Xs<NROT> xn;
       forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
@@ -612,7 +615,8 @@ __device__ __forceinline__ void adjoint_mode(const AdjointBuffers& ab, const Ste
   }
 }
 
-__global__ void __launch_bounds__(128) k_adjoint(AdjointBuffers ab, StepParams P) {
+constexpr int kAdjointBlock = 128;
+__global__ void __launch_bounds__(kAdjointBlock, 3) k_adjoint(AdjointBuffers ab, StepParams P) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ab.n) return;
   const int nr = rotors_of(ab, i);
@@ -667,7 +671,7 @@ cudaError_t launch_record(const AdjointBuffers& ab, const StepParams& P, cudaStr
 }
 
 cudaError_t launch_adjoint(const AdjointBuffers& ab, const StepParams& P, cudaStream_t st) {
-  k_adjoint<<<(ab.n + 127) / 128, 128, 0, st>>>(ab, P);
+  k_adjoint<<<(ab.n + kAdjointBlock - 1) / kAdjointBlock, kAdjointBlock, 0, st>>>(ab, P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 g1(kReduceParts, 12);
