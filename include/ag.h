@@ -336,8 +336,10 @@ ag_status ag_reach_begin(ag_ctx* ctx, const ag_reach_config* cfg, const float* g
 /* One task step. actions: device float[n_envs][4], 16-byte aligned. obs:
  * device float[n_envs][13]; reward: device float[n_envs]; done: device
  * uint8[n_envs]. The collision resets use the context's reset seed (that of
- * the last ag_reset, else the config's). AG_ERR_STATE before ag_reach_begin;
- * AG_ERR_INVALID for a NULL or misaligned pointer. */
+ * the last ag_reset, else the config's). The collided flags (ag_get_state)
+ * describe this step; the reset list is not updated (done marks every
+ * episode that ended). AG_ERR_STATE before ag_reach_begin; AG_ERR_INVALID
+ * for a NULL or misaligned pointer. */
 ag_status ag_reach_step(ag_ctx* ctx, const float* actions, float* obs, float* reward, uint8_t* done);
 
 /* Observations float[n_envs][13] (device) of the current states, as written

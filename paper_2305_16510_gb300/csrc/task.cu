@@ -139,7 +139,6 @@ __global__ void __launch_bounds__(kTaskBlock, BOXES ? 3 : 4) k_reach_step(ReachA
     for (int k = 0; k < 4; ++k) fb.targets[k * n + i] = t[k];  // the commands, as ag_set_commands keeps them
     reach_tail(a, i, s, hit, steps_before, g, stage + threadIdx.x * kObs);
   }
-  append_compact(resets > 0u, i, fb.reset_ids, fb.n_reset);
   write_obs(a, stage);
 }
 
@@ -163,8 +162,6 @@ cudaError_t launch_step_t(const ReachArgs& a, const StepParams& P, int substeps,
 }  // namespace
 
 cudaError_t launch_reach_step(const ReachArgs& a, const StepParams& P, int integrator, int substeps, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(a.fb.n_reset, 0, sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
   const bool drag = P.drag != 0.f;
   if (integrator == kIntegRK4)
     return drag ? launch_step_t<kIntegRK4, true>(a, P, substeps, st) : launch_step_t<kIntegRK4, false>(a, P, substeps, st);

@@ -23,10 +23,10 @@ struct ReachArgs {
 };
 
 // One task step in one launch: commands = offset + scale * clamp(actions,
-// -1, 1) into fb.targets, one fleet step of `substeps` substeps (collision
-// resets listed in fb.reset_ids as ag_step lists them), reward and
-// termination, in-place reset of the episodes that ended without a
-// collision, observations of the new state.
+// -1, 1) into fb.targets, one fleet step of `substeps` substeps (collided
+// flags set; the reset list is left alone, the done flags carry the episode
+// ends), reward and termination, in-place reset of the episodes that ended
+// without a collision, observations of the new state.
 cudaError_t launch_reach_step(const ReachArgs& a, const StepParams& P, int integrator, int substeps, cudaStream_t st);
 // Observations of the current states alone.
 cudaError_t launch_reach_observe(const ReachArgs& a, cudaStream_t st);
