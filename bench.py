@@ -564,8 +564,15 @@ def cpu_baseline(target_s: float = 12.0) -> dict:
     rate, _ = oracle_rate(n_envs, 20, threads)
     n_steps = max(2, int(target_s * rate / n_envs))
     rate, secs = oracle_rate(n_envs, n_steps, threads)
+    # one host thread, on a sample of about 3 s
+    n1 = 512
+    r1, _ = oracle_rate(n1, 5, 1)
+    steps1 = max(2, int(3.0 * r1 / n1))
+    r1, s1 = oracle_rate(n1, steps1, 1)
     return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n_envs} envs x {n_steps} steps of the same workload ({secs:.1f} s, FP64, {threads} threads)"}
+            "sample": f"{n_envs} envs x {n_steps} steps of the same workload ({secs:.1f} s, FP64, {threads} threads)",
+            "single_thread": {"value": r1, "unit": UNIT,
+                              "sample": f"{n1} envs x {steps1} steps ({s1:.1f} s, FP64, 1 thread)"}}
 
 
 def reference_arm(args) -> dict | None:
