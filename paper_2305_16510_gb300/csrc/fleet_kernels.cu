@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128, BOXES ? 3 : 4) k_fused_step(FleetBuffers 
         for (int f = 0; f < 10; ++f) {
           const float a = fb.boxes[((size_t)k0 * 10 + f) * fb.n + slot];
           const float b = k1 < n_obs ? fb.boxes[((size_t)k1 * 10 + f) * fb.n + slot] : box_pad_field(f);
-          bx.sm[((j - 1) * 10 + f) * B] = make_float2(a, b);
+          bx.sm[((j - 1) * 10 + f) * B] = make_float2(staged_field(f, a), staged_field(f, b));
         }
       }
     }
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) k_permute_boxes(FleetBuffers fb) {
     for (int f = 0; f < 10; ++f) {
       const float a = fb.boxes[((size_t)k0 * 10 + f) * fb.n + env];
       const float b = k1 < n_obs ? fb.boxes[((size_t)k1 * 10 + f) * fb.n + env] : box_pad_field(f);
-      fb.boxes_slot[(size_t)(j * 10 + f) * fb.n + slot] = make_float2(a, b);
+      fb.boxes_slot[(size_t)(j * 10 + f) * fb.n + slot] = make_float2(staged_field(f, a), staged_field(f, b));
     }
   }
 }

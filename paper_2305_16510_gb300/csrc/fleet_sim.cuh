@@ -93,19 +93,28 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // 1e30, zero extents, identity orientation (no sphere can touch it).
 __device__ __forceinline__ float box_pad_field(int f) { return f < 3 ? 1e30f : (f == 6 ? 1.f : 0.f); }
 
+// Staged form of box field f in the pair copies (the slot-ordered copy and
+// each thread's staged copy): the orientation's vector part u (fields 7-9)
+// is held doubled, which is exact, so that pair_hits needs no factor 2.
+__device__ __forceinline__ float staged_field(int f, float v) { return f >= 7 ? 2.f * v : v; }
+
 // Sphere (squared radius r2, centre p) against two boxes at once; the ten
-// float2 hold (box a, box b) of: centre x y z, half-extents x y z, q w x y z.
+// float2 hold (box a, box b) of: centre x y z, half-extents x y z, and the
+// orientation q = (w, u) staged as (w, 2u). With v = p - c and t = 2 u x v,
+// the box-frame point d = R_b^T v = v - w t + u x t is computed as
+// (v - w t) + 1/2 ((2u) x t); doubling and halving are exact, so d rounds as
+// the plain form would.
 __device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float r2, float2 cx, float2 cy, float2 cz,
-                                          float2 hx, float2 hy, float2 hz, float2 qw, float2 ux, float2 uy,
-                                          float2 uz) {
-  // v = p - c;  t = 2 u x v;  d = v - w t + u x t  (R_b^T (p - c))
+                                          float2 hx, float2 hy, float2 hz, float2 qw, float2 ux2, float2 uy2,
+                                          float2 uz2) {
   const float2 vx = add2(px, neg2(cx)), vy = add2(py, neg2(cy)), vz = add2(pz, neg2(cz));
-  const float2 tx = mul2(dup2(2.f), fma2(uy, vz, neg2(mul2(uz, vy))));
-  const float2 ty = mul2(dup2(2.f), fma2(uz, vx, neg2(mul2(ux, vz))));
-  const float2 tz = mul2(dup2(2.f), fma2(ux, vy, neg2(mul2(uy, vx))));
-  const float2 dx = add2(fma2(neg2(qw), tx, vx), fma2(uy, tz, neg2(mul2(uz, ty))));
-  const float2 dy = add2(fma2(neg2(qw), ty, vy), fma2(uz, tx, neg2(mul2(ux, tz))));
-  const float2 dz = add2(fma2(neg2(qw), tz, vz), fma2(ux, ty, neg2(mul2(uy, tx))));
+  const float2 tx = fma2(uy2, vz, neg2(mul2(uz2, vy)));
+  const float2 ty = fma2(uz2, vx, neg2(mul2(ux2, vz)));
+  const float2 tz = fma2(ux2, vy, neg2(mul2(uy2, vx)));
+  const float2 half = dup2(0.5f);
+  const float2 dx = fma2(half, fma2(uy2, tz, neg2(mul2(uz2, ty))), fma2(neg2(qw), tx, vx));
+  const float2 dy = fma2(half, fma2(uz2, tx, neg2(mul2(ux2, tz))), fma2(neg2(qw), ty, vy));
+  const float2 dz = fma2(half, fma2(ux2, ty, neg2(mul2(uy2, tx))), fma2(neg2(qw), tz, vz));
   // excess over the half-extents, clamped at 0
   const float2 ex = add2(make_float2(fabsf(dx.x), fabsf(dx.y)), neg2(hx));
   const float2 ey = add2(make_float2(fabsf(dy.x), fabsf(dy.y)), neg2(hy));
@@ -153,8 +162,8 @@ struct RegSmemBoxPairs {
     const uint32_t n = fb.n;
 #pragma unroll
     for (int f = 0; f < 10; ++f) {
-      r[f].x = fb.boxes[(size_t)f * n + env];
-      r[f].y = fb.n_obs > 1 ? fb.boxes[(size_t)(10 + f) * n + env] : box_pad_field(f);
+      r[f].x = staged_field(f, fb.boxes[(size_t)f * n + env]);
+      r[f].y = staged_field(f, fb.n_obs > 1 ? fb.boxes[(size_t)(10 + f) * n + env] : box_pad_field(f));
     }
   }
 };
@@ -213,11 +222,12 @@ __device__ __noinline__ void redraw_boxes(const FleetBuffers& fb, uint32_t env, 
     for (int m = 0; m < 7; ++m) {
       const int f = field[m];
       fb.boxes[((size_t)k * 10 + f) * n + env] = v[m];
+      const float sv = staged_field(f, v[m]);
       if (fb.boxes_slot) {
         float2& e = fb.boxes_slot[(size_t)((k >> 1) * 10 + f) * n + slot];
-        if (k & 1) e.y = v[m]; else e.x = v[m];
+        if (k & 1) e.y = sv; else e.x = sv;
       }
-      boxes.set(k, f, v[m]);
+      boxes.set(k, f, sv);
     }
   }
 }

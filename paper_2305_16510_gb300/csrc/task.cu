@@ -47,8 +47,8 @@ struct EnvBoxPairs {
   uint32_t n, env;
   __device__ __forceinline__ float2 at(int j, int f, int n_obs) const {
     const int k0 = 2 * j, k1 = 2 * j + 1;
-    return make_float2(boxes[((size_t)k0 * 10 + f) * n + env],
-                       k1 < n_obs ? boxes[((size_t)k1 * 10 + f) * n + env] : box_pad_field(f));
+    return make_float2(staged_field(f, boxes[((size_t)k0 * 10 + f) * n + env]),
+                       staged_field(f, k1 < n_obs ? boxes[((size_t)k1 * 10 + f) * n + env] : box_pad_field(f)));
   }
   __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
     const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
