@@ -113,3 +113,24 @@ def test_depth_more_cameras_than_a_grid_dimension():
     _compare(img, ref, 0.002)
     assert (ref[-100:] < rng_max).any()       # the last cameras were rendered too
     fl.close()
+
+
+def test_depth_full_size_sampled_cameras():
+    """The bench's depth workload (2^10 robots of the obstacle recipe, 16 boxes
+    each, after 10 steps, 270 x 480 at 87 deg): 12 sampled cameras are
+    rendered again by the oracle, whole."""
+    w = W.scaled(W.WORKLOADS["obstacles"], 1024)
+    seed = 1
+    inp = W.make_inputs(w, seed)
+    fl = gpu_fleet(w, inp, seed)
+    fl.reset(None, seed)
+    fl.step(10)
+    hfov, rng_max = math.radians(87), 10.0
+    img = fl.render_depth(480, 270, hfov, rng_max)
+    state, boxes = _np(fl.state()), _np(fl.obstacles())
+    cams = np.sort(np.random.default_rng(3).choice(w.n_envs, 12, replace=False))
+    got = _np(img[torch.from_numpy(cams).cuda()])
+    fl.close()
+    ref = O.render_depth(state, boxes, cams, 480, 270, hfov, rng_max)
+    _compare(got, ref, 0.002)
+    assert (ref < rng_max).mean() > 0.05

@@ -164,3 +164,46 @@ def test_reach_errors():
         _abi.ag_reach_step(fl.ctx, buf.data_ptr() + 4, buf, buf, buf)
     assert e.value.status == _abi.AG_ERR_INVALID
     fl.close()
+
+
+def test_reach_full_size_sampled_against_oracle():
+    """The bench's task workload (1,048,576 quads, attitude interface, SIE, no
+    obstacles) for three task steps with a step limit of 2, so every episode
+    ends by time at the second step and restarts from its Philox draw; 2,048
+    sampled environments are composed again by the oracle."""
+    from paper_2305_16510_gb300.task import ReachEnv
+    n, seed = 1 << 20, 1
+    rng = np.random.default_rng(seed)
+    goals = rng.uniform(-1.0, 1.0, (3, n)).astype(np.float32)
+    cfg = _abi.ag_reach_config_default()
+    cfg.max_steps = 2
+    env = ReachEnv(n, goals=goals, task=cfg, seed=seed)
+    env.reset()
+    fl = env.fleet
+    idx = np.sort(np.random.default_rng(7).choice(n, 2048, replace=False))
+    w = W.Workload("reach_full", len(idx), 1, 0, 0, len(idx), 0, 0)
+    world = oracle_world(w)
+    scale, offset = np.array(cfg.action_scale[:]), np.array(cfg.action_offset[:])
+    body = np.tile(np.array([[0.75], [0.007], [0.007], [0.012]], np.float32), (1, len(idx)))
+    steps = np.zeros(len(idx), np.uint32)
+    ended = 0
+    for _ in range(3):
+        s0, m0, e0 = _np(fl.state())[:, idx], _np(fl.motors())[:, idx], _np(fl.epoch()).astype(np.uint32)[idx]
+        act = rng.uniform(-1.2, 1.2, (n, 4)).astype(np.float32)
+        obs, rew, done, _ = env.step(torch.from_numpy(act).cuda())
+        g_obs, g_rew, g_done = _np(obs)[idx], _np(rew)[idx], _np(done)[idx]
+        tgt = offset[:, None] + scale[:, None] * np.clip(act[idx].T.astype(np.float64), -1.0, 1.0)
+        orc = oracle_fleet_from(w, W.Inputs(np.full(len(idx), _abi.AG_MODE_ATT_THRUST, np.uint8), tgt, body, None),
+                                s0, m0, e0, seed)
+        col, _ = O.rollout(world, orc, 1, env_ids=idx)
+        _, o_rew, o_done = O.reach_task(orc.state, goals[:, idx], col, steps + 1, **_params(cfg))
+        O.reset(world, orc, (o_done == 1) & (col == 0), seed, env_ids=idx)
+        o_obs = O.reach_task(orc.state, goals[:, idx], col, steps + 1, **_params(cfg))[0].T
+        np.testing.assert_array_equal(g_done, o_done)
+        np.testing.assert_allclose(g_rew, o_rew, rtol=1e-4, atol=1e-4)
+        np.testing.assert_allclose(g_obs, o_obs, rtol=1e-4, atol=1e-4)
+        np.testing.assert_array_equal(_np(fl.epoch()).astype(np.uint32)[idx], orc.epoch)
+        ended += int(g_done.sum())
+        steps = np.where(g_done == 1, 0, steps + 1).astype(np.uint32)
+    assert ended == len(idx)          # every sampled episode ended at its second step
+    env.close()
