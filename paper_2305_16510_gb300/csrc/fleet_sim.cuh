@@ -76,13 +76,13 @@ __device__ __forceinline__ void append_compact(bool pred, uint32_t env, uint32_t
 }
 
 // Box sources of the per-vehicle loop; any_hit(p, r2, n_obs) runs the
-// sphere-vs-box test against all boxes of the environment.
+// sphere-vs-box test against all boxes of the environment, staged() is the
+// copy a re-draw updates and reload() re-reads what a re-draw changed.
 //
-// SmemBoxPairs: the thread's boxes staged in shared memory in pairs, laid out
-// as float2 [pair][field][thread] (field f of boxes 2j and 2j+1 side by side),
-// so one conflict-free 8-byte load fetches a field of two boxes and the test
-// runs on both at once with Blackwell's packed FP32x2 arithmetic. An odd box
-// count is padded with a box at 1e30 that cannot be touched.
+// Boxes are handled in pairs (field f of boxes 2j and 2j+1 side by side), so
+// one 8-byte load fetches a field of two boxes and the test runs on both at
+// once with Blackwell's packed FP32x2 arithmetic. An odd box count is padded
+// with a box at 1e30 that cannot be touched.
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
