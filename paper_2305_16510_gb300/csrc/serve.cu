@@ -14,7 +14,9 @@
 //     device between launches;
 //   * a finished request's final state and reset epochs are copied to the
 //     host, its slab region is freed, and its latency (completion - submit)
-//     is recorded.
+//     is recorded;
+//   * the next chunk is enqueued before the host waits for the current one,
+//     so the device does not idle while the host retires and admits.
 // A request's chunk boundaries are counted from its own first launch, so the
 // same request gives bit-identical results alone or in any mix.
 // With max_active = 1 the same loop is the one-request-per-launch baseline.
@@ -158,11 +160,12 @@ struct ag_server {
   ag_server_config cfg;
   int device = 0;
   cudaStream_t stream = nullptr;
-  cudaEvent_t chunk_start = nullptr, chunk_done = nullptr;
+  // two chunks can be in flight: chunk k uses buffer k % 2
+  cudaEvent_t chunk_start[2] = {nullptr, nullptr}, chunk_done[2] = {nullptr, nullptr};
   unsigned char* slab = nullptr;
   agk::SlabAllocator* alloc = nullptr;
-  agk::ServeDesc* table_host = nullptr;  // pinned
-  agk::ServeDesc* table_dev = nullptr;
+  agk::ServeDesc* table_host[2] = {nullptr, nullptr};  // pinned
+  agk::ServeDesc* table_dev[2] = {nullptr, nullptr};
   agk::StepParams P{};
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -257,13 +260,27 @@ void fail_server(ag_server* s, cudaError_t e, const char* what) {
   s->cv_done.notify_all();
 }
 
+// A chunk handed to the device and not yet retired.
+struct InFlight {
+  bool valid = false;
+  std::vector<ServeRequest*> finishing;  // requests whose last steps (and result copies) it holds
+  double vehicle_steps = 0.0;
+};
+
+// The loop keeps the device fed: it enqueues chunk k (after any uploads of
+// newly admitted requests) and only then waits for chunk k - 1 and retires
+// the requests that finished in it, so the next chunk is already queued
+// while the host does its bookkeeping.
 void serve_loop(ag_server* s) {
   cudaSetDevice(s->device);
   const int substeps = (int)s->cfg.physics.substeps_per_step;
   const bool rk4 = s->cfg.physics.integrator == AG_INTEG_RK4;
   const bool drag = s->cfg.physics.drag != 0.f;
-  while (true) {
-    std::vector<ServeRequest*> admitted;
+  const uint32_t chunk = s->cfg.chunk_steps;
+  InFlight flight[2];
+  for (uint64_t k = 0;; ++k) {
+    const int b = (int)(k & 1);
+    std::vector<ServeRequest*> admitted, sched;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       while (!s->pending.empty() && s->active.size() < s->cfg.max_active) {
@@ -275,7 +292,9 @@ void serve_loop(ag_server* s) {
         s->active.push_back(r);
         admitted.push_back(r);
       }
-      if (s->active.empty()) {
+      for (ServeRequest* r : s->active)
+        if (r->remaining > 0) sched.push_back(r);
+      if (sched.empty() && !flight[b ^ 1].valid) {  // nothing to launch and nothing in flight
         if (s->stop) return;
         s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
         continue;
@@ -286,64 +305,69 @@ void serve_loop(ag_server* s) {
       if (e != cudaSuccess) { fail_server(s, e, "admit"); return; }
       r->started = true;
     }
-    // one launch for every active request
-    const uint32_t chunk = s->cfg.chunk_steps;
-    uint32_t blocks = 0;
-    std::vector<uint32_t> steps_now(s->active.size());
-    for (size_t k = 0; k < s->active.size(); ++k) {
-      ServeRequest* r = s->active[k];
-      agk::ServeDesc& d = s->table_host[k];
-      d.fb = r->fb;
-      d.seed_lo = (uint32_t)(r->in.seed & 0xFFFFFFFFu);
-      d.seed_hi = (uint32_t)(r->in.seed >> 32);
-      steps_now[k] = std::min(chunk, r->remaining);
-      d.steps = (int)steps_now[k];
-      d.block_begin = blocks;
-      blocks += (r->in.n_envs + agk::kServeBlock - 1) / agk::kServeBlock;
-    }
-    const int n_req = (int)s->active.size();
-    cudaError_t e = cudaMemcpyAsync(s->table_dev, s->table_host, sizeof(agk::ServeDesc) * n_req,
-                                    cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(s->chunk_start, s->stream);
-    if (e == cudaSuccess) {
-      if (rk4) {
-        if (drag) agk::k_serve_step<agk::kIntegRK4, true><<<blocks, agk::kServeBlock, 0, s->stream>>>(s->table_dev, n_req, s->P, substeps);
-        else agk::k_serve_step<agk::kIntegRK4, false><<<blocks, agk::kServeBlock, 0, s->stream>>>(s->table_dev, n_req, s->P, substeps);
-      } else {
-        if (drag) agk::k_serve_step<agk::kIntegSIE, true><<<blocks, agk::kServeBlock, 0, s->stream>>>(s->table_dev, n_req, s->P, substeps);
-        else agk::k_serve_step<agk::kIntegSIE, false><<<blocks, agk::kServeBlock, 0, s->stream>>>(s->table_dev, n_req, s->P, substeps);
+    // chunk k: one launch for every request with steps left (buffer b was
+    // last used by chunk k - 2, retired in the previous iteration)
+    cudaError_t e = cudaSuccess;
+    if (!sched.empty()) {
+      InFlight& f = flight[b];
+      uint32_t blocks = 0;
+      for (size_t j = 0; j < sched.size(); ++j) {
+        ServeRequest* r = sched[j];
+        agk::ServeDesc& d = s->table_host[b][j];
+        const uint32_t steps = std::min(chunk, r->remaining);
+        r->remaining -= steps;
+        if (r->remaining == 0) f.finishing.push_back(r);
+        f.vehicle_steps += (double)r->in.n_envs * steps;
+        d.fb = r->fb;
+        d.seed_lo = (uint32_t)(r->in.seed & 0xFFFFFFFFu);
+        d.seed_hi = (uint32_t)(r->in.seed >> 32);
+        d.steps = (int)steps;
+        d.block_begin = blocks;
+        blocks += (r->in.n_envs + agk::kServeBlock - 1) / agk::kServeBlock;
       }
-      e = cudaGetLastError();
+      const int n_req = (int)sched.size();
+      e = cudaMemcpyAsync(s->table_dev[b], s->table_host[b], sizeof(agk::ServeDesc) * n_req, cudaMemcpyHostToDevice,
+                          s->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(s->chunk_start[b], s->stream);
+      if (e == cudaSuccess) {
+        agk::ServeDesc* t = s->table_dev[b];
+        if (rk4) {
+          if (drag) agk::k_serve_step<agk::kIntegRK4, true><<<blocks, agk::kServeBlock, 0, s->stream>>>(t, n_req, s->P, substeps);
+          else agk::k_serve_step<agk::kIntegRK4, false><<<blocks, agk::kServeBlock, 0, s->stream>>>(t, n_req, s->P, substeps);
+        } else {
+          if (drag) agk::k_serve_step<agk::kIntegSIE, true><<<blocks, agk::kServeBlock, 0, s->stream>>>(t, n_req, s->P, substeps);
+          else agk::k_serve_step<agk::kIntegSIE, false><<<blocks, agk::kServeBlock, 0, s->stream>>>(t, n_req, s->P, substeps);
+        }
+        e = cudaGetLastError();
+      }
+      // results of the requests that finish in this chunk
+      for (ServeRequest* r : f.finishing) {
+        if (e != cudaSuccess) break;
+        const size_t n = r->in.n_envs;
+        r->final_state.resize(13 * n);
+        r->final_epoch.resize(n);
+        e = cudaMemcpyAsync(r->final_state.data(), r->fb.state, 13 * n * 4, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(r->final_epoch.data(), r->fb.epoch, n * 4, cudaMemcpyDeviceToHost, s->stream);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(s->chunk_done[b], s->stream);
+      if (e != cudaSuccess) { fail_server(s, e, "serve launch"); return; }
+      f.valid = true;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(s->chunk_done, s->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(s->chunk_done);
+    // retire chunk k - 1
+    InFlight& prev = flight[b ^ 1];
+    if (!prev.valid) continue;
     float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->chunk_start, s->chunk_done);
-    if (e != cudaSuccess) { fail_server(s, e, "serve launch"); return; }
-    // retire finished requests
-    std::vector<ServeRequest*> finished;
-    for (size_t k = 0; k < s->active.size(); ++k) {
-      ServeRequest* r = s->active[k];
-      r->remaining -= steps_now[k];
-      if (r->remaining == 0) finished.push_back(r);
-    }
-    for (ServeRequest* r : finished) {
-      const size_t n = r->in.n_envs;
-      r->final_state.resize(13 * n);
-      r->final_epoch.resize(n);
-      e = cudaMemcpyAsync(r->final_state.data(), r->fb.state, 13 * n * 4, cudaMemcpyDeviceToHost, s->stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(r->final_epoch.data(), r->fb.epoch, n * 4, cudaMemcpyDeviceToHost, s->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-      if (e != cudaSuccess) { fail_server(s, e, "retire"); return; }
-    }
+    e = cudaEventSynchronize(s->chunk_done[b ^ 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->chunk_start[b ^ 1], s->chunk_done[b ^ 1]);
+    if (e != cudaSuccess) { fail_server(s, e, "serve retire"); return; }
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->launches += 1;
       s->gpu_ms += ms;
-      for (size_t k = 0; k < s->active.size(); ++k) s->vehicle_steps += (double)s->active[k]->in.n_envs * steps_now[k];
+      s->vehicle_steps += prev.vehicle_steps;
       const auto now = Clock::now();
-      for (ServeRequest* r : finished) {
+      for (ServeRequest* r : prev.finishing) {
         r->t_done = now;
         r->done = true;
         s->alloc->release(r->offset);
@@ -351,7 +375,8 @@ void serve_loop(ag_server* s) {
         s->active.erase(std::find(s->active.begin(), s->active.end(), r));
       }
     }
-    if (!finished.empty()) s->cv_done.notify_all();
+    if (!prev.finishing.empty()) s->cv_done.notify_all();
+    prev = InFlight{};
   }
 }
 
@@ -382,18 +407,22 @@ ag_status ag_server_create(const ag_server_config* cfg, ag_server** out) {
   s->cfg = *cfg;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreate(&s->chunk_done);
-  if (e == cudaSuccess) e = cudaEventCreate(&s->chunk_start);
+  for (int b = 0; b < 2; ++b) {
+    if (e == cudaSuccess) e = cudaEventCreate(&s->chunk_done[b]);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->chunk_start[b]);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s->table_host[b], sizeof(agk::ServeDesc) * cfg->max_active);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->table_dev[b], sizeof(agk::ServeDesc) * cfg->max_active);
+  }
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->slab, cfg->hbm_budget_bytes);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&s->table_host, sizeof(agk::ServeDesc) * cfg->max_active);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&s->table_dev, sizeof(agk::ServeDesc) * cfg->max_active);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (s->slab) cudaFree(s->slab);
-    if (s->table_host) cudaFreeHost(s->table_host);
-    if (s->table_dev) cudaFree(s->table_dev);
-    if (s->chunk_done) cudaEventDestroy(s->chunk_done);
-    if (s->chunk_start) cudaEventDestroy(s->chunk_start);
+    for (int b = 0; b < 2; ++b) {
+      if (s->table_host[b]) cudaFreeHost(s->table_host[b]);
+      if (s->table_dev[b]) cudaFree(s->table_dev[b]);
+      if (s->chunk_done[b]) cudaEventDestroy(s->chunk_done[b]);
+      if (s->chunk_start[b]) cudaEventDestroy(s->chunk_start[b]);
+    }
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return e == cudaErrorMemoryAllocation ? AG_ERR_OOM : AG_ERR_CUDA;
@@ -481,10 +510,12 @@ ag_status ag_server_destroy(ag_server* s) {
   for (auto& kv : s->all) delete kv.second;
   delete s->alloc;
   cudaFree(s->slab);
-  cudaFreeHost(s->table_host);
-  cudaFree(s->table_dev);
-  cudaEventDestroy(s->chunk_done);
-  cudaEventDestroy(s->chunk_start);
+  for (int b = 0; b < 2; ++b) {
+    cudaFreeHost(s->table_host[b]);
+    cudaFree(s->table_dev[b]);
+    cudaEventDestroy(s->chunk_done[b]);
+    cudaEventDestroy(s->chunk_start[b]);
+  }
   cudaStreamDestroy(s->stream);
   delete s;
   return AG_OK;
