@@ -7,6 +7,7 @@ machinery: the library is plain C-ABI code that the ctypes binding loads.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -45,11 +46,25 @@ def is_stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles (if stale) and returns the path of libaerialgb.so."""
+    """Compiles (if stale) and returns the path of libaerialgb.so.
+
+    Processes that build at the same time (one per rank) take turns on a
+    lock file: the first compiles, the others then find the library fresh."""
     if not force and not is_stale():
         return LIB_PATH
-    nvcc = _nvcc()
     os.makedirs(BUILD_DIR, exist_ok=True)
+    with open(os.path.join(BUILD_DIR, "build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not is_stale():
+                return LIB_PATH
+            return _compile(verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _compile(verbose: bool) -> str:
+    nvcc = _nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
     if verbose:
         common += ["-Xptxas", "-v"]
