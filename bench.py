@@ -55,9 +55,9 @@ ALU_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 BYTES_PER_VEHICLE_LAUNCH = 4 * (26 + 8 + 4 + 4) + 1 + 8 + 4 * 160 + 1 + 4
 # DRAM traffic of one full-size fused launch (1,048,576 envs, 1,000 steps):
 # dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu capture of
-# exactly this launch (794.82 MB + 69.11 MB). It scales with the fleet size
+# exactly this launch (795.15 MB + 69.06 MB). It scales with the fleet size
 # (each env is loaded and stored once per launch), not with the step count.
-TRAFFIC_BYTES_FULL_LAUNCH = 794.82e6 + 69.11e6
+TRAFFIC_BYTES_FULL_LAUNCH = 795.15e6 + 69.06e6
 
 
 def dist_env():
