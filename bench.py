@@ -46,6 +46,11 @@ WORKLOAD_TEXT = ("1,048,576 quadrotors; command mode uniform over position / bod
 # command modes, RK4 x 4 substeps + 16 boxes. tests/test_bench_constants.py
 # re-derives it.
 FLOP_PER_VEHICLE_STEP = 4588.0
+# The same count for the other lines: the mixed fleet (body velocity, SIE,
+# drag, 40 % quad / 40 % hexa / 20 % octo) and the paper shape (attitude and
+# body velocity, SIE, quads, no boxes).
+FLOP_PER_VEHICLE_STEP_MIXED = 584.4
+FLOP_PER_VEHICLE_STEP_PAPER_SHAPE = 528.5
 # GB300 FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2,070 MHz
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 ALU_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
@@ -269,7 +274,9 @@ def gpu_arm(args) -> dict | None:
         fs.step(100)
         torch.cuda.synchronize()
         secs_s, _ = time_calls(fs, lambda: fs.step(1000), 3, world)
-        out["paper_shape"] = {"value": ws.n_envs * 1000 * 3 * world / secs_s, "unit": UNIT,
+        v_s = ws.n_envs * 1000 * 3 * world / secs_s
+        out["paper_shape"] = {"value": v_s, "unit": UNIT,
+                              "alu_frac": v_s / world * FLOP_PER_VEHICLE_STEP_PAPER_SHAPE / 1e12 / ALU_PEAK_TFLOPS,
                               "workload": "131,072 quads, attitude/body-velocity commands, no obstacles, SIE, "
                                           "1 substep",
                               "paper_value": 3.8e6,
@@ -341,7 +348,9 @@ def mixed_part(seed: int, world: int) -> dict:
     torch.cuda.synchronize()
     secs, _ = time_calls(fl, rollout, 3, world)
     fl.close()
-    return {"value": w.n_envs * 500 * 3 * world / secs, "unit": UNIT, "ms_per_rollout": secs * 1e3 / 3,
+    v = w.n_envs * 500 * 3 * world / secs
+    return {"value": v, "unit": UNIT, "ms_per_rollout": secs * 1e3 / 3,
+            "alu_frac": v / world * FLOP_PER_VEHICLE_STEP_MIXED / 1e12 / ALU_PEAK_TFLOPS,
             "workload": "4,194,304 vehicles (1,677,722 quad / 1,677,722 hexa / 838,860 octo), mass and inertia "
                         "x U[0.8, 1.2], tau 0.03, drag 0.1, body-velocity targets U[-2, 2]^3, SIE, 500 steps "
                         "as 10 x (50-step ag_step + 1 % ag_reset mask)"}

@@ -93,7 +93,7 @@ def _declare(L: ctypes.CDLL) -> None:
     L.orc_sincos_turn.argtypes = [ctypes.c_uint32, _fp, _fp]
     L.orc_log_u01.argtypes = [ctypes.c_uint32]
     L.orc_log_u01.restype = ctypes.c_float
-    L.orc_count_ops.argtypes = [vp, ctypes.c_int, ctypes.c_int, _i64p]
+    L.orc_count_ops.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p]
     L.orc_vehicle_loss.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.c_int, _dp,
                                    ctypes.c_double, ctypes.c_double]
     L.orc_vehicle_loss.restype = ctypes.c_double
@@ -407,10 +407,11 @@ def log_u01(w) -> np.float32:
     return np.float32(lib().orc_log_u01(int(w)))
 
 
-def count_ops(world: World, mode: int, n_obs: int) -> dict:
+def count_ops(world: World, mode: int, n_obs: int, n_rot: int = 4) -> dict:
+    """Operations of one step of one vehicle (substeps_per_step substeps, then n_obs box tests)."""
     out = np.zeros(6, dtype=np.int64)
     w = world.c()
-    lib().orc_count_ops(ctypes.byref(w), int(mode), int(n_obs), _ptr(out, _i64p))
+    lib().orc_count_ops(ctypes.byref(w), int(mode), int(n_obs), int(n_rot), _ptr(out, _i64p))
     return dict(zip(["add", "mul", "div", "sqrt", "trans", "cmp"], (int(x) for x in out)))
 
 

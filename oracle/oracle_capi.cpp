@@ -400,9 +400,9 @@ float orc_log_u01(uint32_t w) { return log_u01_f32(w); }
 // Algorithmic operation counts of ONE vehicle-step (substeps_per_step
 // substeps of the given mode plus one sphere-vs-box test per box of n_obs)
 // for a quadrotor near hover: counts = {add, mul, div, sqrt, trans, cmp}.
-void orc_count_ops(const void* world, int mode, int n_obs, long long counts[6]) {
+void orc_count_ops(const void* world, int mode, int n_obs, int n_rot, long long counts[6]) {
   World w = world_of(world);
-  Rotors rot = make_rotors(4, w.arm, w.k_yaw);
+  Rotors rot = make_rotors(n_rot, w.arm, w.k_yaw);
   Gains<Cnt> g = gains_of<Cnt>(w.kx, w.kv, w.kR, w.kW);
   Body<Cnt> b = {Cnt(0.75), {Cnt(0.007), Cnt(0.007), Cnt(0.012)}};
   State<Cnt> s;
