@@ -194,6 +194,14 @@ ag_status ag_step(ag_ctx* ctx, uint32_t n_substeps);
  * float32 rounding. */
 ag_status ag_step_plain(ag_ctx* ctx, uint32_t n_substeps);
 
+/* The controller stage alone (Sec. IV): for every environment, its command
+ * mode and targets, body parameters and the context's gains, writes the
+ * commanded collective thrust and moments float[4][n_envs] (f, M_x, M_y,
+ * M_z) at the states float[13][n_envs] (NULL = the current states; q need
+ * not be unit). Host or device pointers; nothing else changes. For
+ * inspecting what the controller asks for, and for testing it on its own. */
+ag_status ag_eval_controller(ag_ctx* ctx, const float* state, float* wrench);
+
 /* Resets the environments whose mask byte is non-zero (mask NULL = all):
  * epoch + 1, then position U[-2, 2)^3 m, attitude a rotation by U[0, pi/6)
  * about a uniformly random axis, velocity N(0, 0.5^2) m/s per axis, zero body

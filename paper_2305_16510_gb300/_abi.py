@@ -92,6 +92,7 @@ SIGNATURES = {
     "ag_step": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "ag_step_plain": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "ag_reset": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
+    "ag_eval_controller": (ctypes.c_int, [_vp, _vp, _vp]),
     "ag_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),
     "ag_get_motors": (ctypes.c_int, [_vp, _vp, _vp]),
     "ag_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -240,6 +241,10 @@ def ag_step(ctx: int, n_substeps: int) -> None:
 
 def ag_step_plain(ctx: int, n_substeps: int) -> None:
     _check(lib().ag_step_plain(ctx, int(n_substeps)), "ag_step_plain", ctx)
+
+
+def ag_eval_controller(ctx: int, state, wrench) -> None:
+    _check(lib().ag_eval_controller(ctx, ptr(state), ptr(wrench)), "ag_eval_controller", ctx)
 
 
 def ag_reset(ctx: int, mask, seed: int) -> None:

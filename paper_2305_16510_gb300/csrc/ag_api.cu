@@ -43,6 +43,7 @@ struct ag_ctx {
   uint32_t* cam_ids;         // [n_envs]
   float* depth_stage;        // device staging when the caller's buffer is on the host
   size_t depth_stage_cap;    // floats
+  float* eval_state;         // [13][n_envs] states of ag_eval_controller (allocated on first use)
   // reach-a-setpoint task (allocated at the first ag_reach_begin)
   ag_reach_config reach;
   float* reach_goals;        // [3][n_envs]
@@ -211,6 +212,7 @@ void free_all(ag_ctx* ctx) {
   free_adjoint(ctx);
   if (ctx->cam_ids) cudaFree(ctx->cam_ids);
   if (ctx->depth_stage) cudaFree(ctx->depth_stage);
+  if (ctx->eval_state) cudaFree(ctx->eval_state);
   if (ctx->reach_goals) cudaFree(ctx->reach_goals);
   if (ctx->reach_steps) cudaFree(ctx->reach_steps);
   agk::FleetBuffers& f = ctx->fb;
@@ -282,6 +284,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   ctx->cam_ids = nullptr;
   ctx->depth_stage = nullptr;
   ctx->depth_stage_cap = 0;
+  ctx->eval_state = nullptr;
   ctx->reach_goals = nullptr;
   ctx->reach_steps = nullptr;
   ctx->reach_active = false;
@@ -523,6 +526,26 @@ static ag_status step_common(ag_ctx* ctx, uint32_t n_substeps, bool fused) {
 
 ag_status ag_step(ag_ctx* ctx, uint32_t n_substeps) { return step_common(ctx, n_substeps, true); }
 ag_status ag_step_plain(ag_ctx* ctx, uint32_t n_substeps) { return step_common(ctx, n_substeps, false); }
+
+ag_status ag_eval_controller(ag_ctx* ctx, const float* state, float* wrench) {
+  ag_status s = enter(ctx);
+  if (s != AG_OK) return s;
+  if (!wrench) return fail_invalid(ctx, "wrench must be non-NULL");
+  const size_t n = ctx->cfg.n_envs;
+  cudaStream_t st = ctx->stream;
+  agk::FleetBuffers fb = ctx->fb;
+  if (state) {
+    if (!ctx->eval_state &&
+        (s = check_cuda(ctx, alloc(ctx, &ctx->eval_state, 13 * n), "allocate controller states")) != AG_OK) return s;
+    if ((s = check_cuda(ctx, cudaMemcpyAsync(ctx->eval_state, state, 13 * n * sizeof(float), cudaMemcpyDefault, st),
+                        "copy controller states")) != AG_OK) return s;
+    fb.state = ctx->eval_state;
+  }
+  // the unfused path's command scratch receives the result
+  if ((s = check_cuda(ctx, agk::launch_controller(fb, step_params(ctx), st), "controller launch")) != AG_OK) return s;
+  return check_cuda(ctx, cudaMemcpyAsync(wrench, fb.cmd, 4 * n * sizeof(float), cudaMemcpyDefault, st),
+                    "copy wrench out");
+}
 
 ag_status ag_reset(ag_ctx* ctx, const uint8_t* mask, uint64_t seed) {
   ag_status s = enter(ctx);

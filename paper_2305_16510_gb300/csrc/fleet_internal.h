@@ -46,6 +46,9 @@ cudaError_t launch_fused_step(const FleetBuffers& fb, const StepParams& P, int i
                               int substeps, cudaStream_t st);
 cudaError_t launch_reset(const FleetBuffers& fb, const uint8_t* mask, uint32_t seed_lo, uint32_t seed_hi,
                          cudaStream_t st);
+// The controller alone: fb.cmd[4][n] = commanded (f, M) of every environment
+// at fb.state (the unfused path's controller stage).
+cudaError_t launch_controller(const FleetBuffers& fb, const StepParams& P, cudaStream_t st);
 cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,
                               int substeps, cudaStream_t st);
 

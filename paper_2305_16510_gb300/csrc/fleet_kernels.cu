@@ -384,6 +384,11 @@ cudaError_t launch_reset(const FleetBuffers& fb, const uint8_t* mask, uint32_t s
   return cudaGetLastError();
 }
 
+cudaError_t launch_controller(const FleetBuffers& fb, const StepParams& P, cudaStream_t st) {
+  k_plain_controller<<<(fb.n + 255) / 256, 256, 0, st>>>(fb, P);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_plain_step(const FleetBuffers& fb, const StepParams& P, int integrator, int n_steps,
                               int substeps, cudaStream_t st) {
   const unsigned grid = (fb.n + 255) / 256;
