@@ -444,6 +444,12 @@ ag_status ag_synchronize(ag_ctx* ctx);
 /* Number of environments / the configuration the context was created with. */
 ag_status ag_get_config(const ag_ctx* ctx, ag_config* out);
 
+/* Fault injection for testing a caller's error handling: marks the context
+ * failed exactly as a CUDA error would (message: why, or "injected failure"),
+ * without touching the device. Later calls return AG_ERR_STATE as described
+ * above. AG_ERR_INVALID for a NULL ctx. */
+ag_status ag_inject_failure(ag_ctx* ctx, const char* why);
+
 /* Message of the last error of this context ("" if none); valid until the
  * next call on the context. NULL ctx gives the last ag_create failure. */
 const char* ag_last_error(const ag_ctx* ctx);

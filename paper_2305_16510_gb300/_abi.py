@@ -93,6 +93,7 @@ SIGNATURES = {
     "ag_step_plain": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "ag_reset": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
     "ag_eval_controller": (ctypes.c_int, [_vp, _vp, _vp]),
+    "ag_inject_failure": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "ag_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),
     "ag_get_motors": (ctypes.c_int, [_vp, _vp, _vp]),
     "ag_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -241,6 +242,10 @@ def ag_step(ctx: int, n_substeps: int) -> None:
 
 def ag_step_plain(ctx: int, n_substeps: int) -> None:
     _check(lib().ag_step_plain(ctx, int(n_substeps)), "ag_step_plain", ctx)
+
+
+def ag_inject_failure(ctx: int, why: str | None = None) -> None:
+    _check(lib().ag_inject_failure(ctx, why.encode() if why else None), "ag_inject_failure", ctx)
 
 
 def ag_eval_controller(ctx: int, state, wrench) -> None:

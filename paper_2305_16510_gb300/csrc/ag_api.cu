@@ -55,6 +55,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
+
 ag_status fail_invalid(ag_ctx* ctx, const std::string& msg) {
   if (ctx) ctx->err = msg;
   else g_create_error = msg;
@@ -364,6 +365,7 @@ ag_status ag_destroy(ag_ctx* ctx) {
 }
 
 ag_status ag_set_commands(ag_ctx* ctx, const uint8_t* modes, const float* targets) {
+  agk::NvtxRange range("ag_set_commands");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   const size_t n = ctx->cfg.n_envs;
@@ -380,6 +382,7 @@ ag_status ag_set_commands(ag_ctx* ctx, const uint8_t* modes, const float* target
 }
 
 ag_status ag_set_obstacles(ag_ctx* ctx, const float* boxes) {
+  agk::NvtxRange range("ag_set_obstacles");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   if (!boxes) return fail_invalid(ctx, "boxes is NULL");
@@ -403,6 +406,7 @@ ag_status ag_get_obstacles(ag_ctx* ctx, float* boxes) {
 
 ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
                           const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth) {
+  agk::NvtxRange range("ag_render_depth");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   const uint32_t n = ctx->cfg.n_envs;
@@ -512,6 +516,7 @@ ag_status ag_set_body(ag_ctx* ctx, const float* body) {
 }
 
 static ag_status step_common(ag_ctx* ctx, uint32_t n_substeps, bool fused) {
+  agk::NvtxRange range(fused ? "ag_step" : "ag_step_plain");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   const uint32_t sps = ctx->cfg.substeps_per_step;
@@ -527,7 +532,15 @@ static ag_status step_common(ag_ctx* ctx, uint32_t n_substeps, bool fused) {
 ag_status ag_step(ag_ctx* ctx, uint32_t n_substeps) { return step_common(ctx, n_substeps, true); }
 ag_status ag_step_plain(ag_ctx* ctx, uint32_t n_substeps) { return step_common(ctx, n_substeps, false); }
 
+ag_status ag_inject_failure(ag_ctx* ctx, const char* why) {
+  if (!ctx) return AG_ERR_INVALID;
+  ctx->failed = true;
+  ctx->err = why ? why : "injected failure";
+  return AG_OK;
+}
+
 ag_status ag_eval_controller(ag_ctx* ctx, const float* state, float* wrench) {
+  agk::NvtxRange range("ag_eval_controller");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   if (!wrench) return fail_invalid(ctx, "wrench must be non-NULL");
@@ -548,6 +561,7 @@ ag_status ag_eval_controller(ag_ctx* ctx, const float* state, float* wrench) {
 }
 
 ag_status ag_reset(ag_ctx* ctx, const uint8_t* mask, uint64_t seed) {
+  agk::NvtxRange range("ag_reset");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   const uint8_t* mask_dev = nullptr;
@@ -580,6 +594,7 @@ void ag_reach_config_default(ag_reach_config* c) {
 }
 
 ag_status ag_reach_begin(ag_ctx* ctx, const ag_reach_config* cfg, const float* goals) {
+  agk::NvtxRange range("ag_reach_begin");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   if (!cfg || !goals) return fail_invalid(ctx, "cfg and goals must be non-NULL");
@@ -636,6 +651,7 @@ static agk::ReachArgs reach_args(ag_ctx* ctx, const float* actions, float* obs, 
 }
 
 ag_status ag_reach_step(ag_ctx* ctx, const float* actions, float* obs, float* reward, uint8_t* done) {
+  agk::NvtxRange range("ag_reach_step");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   if (!ctx->reach_active) return AG_ERR_STATE;
@@ -647,6 +663,7 @@ ag_status ag_reach_step(ag_ctx* ctx, const float* actions, float* obs, float* re
 }
 
 ag_status ag_reach_observe(ag_ctx* ctx, float* obs) {
+  agk::NvtxRange range("ag_reach_observe");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   if (!ctx->reach_active) return AG_ERR_STATE;
@@ -688,6 +705,7 @@ ag_status ag_get_motors(ag_ctx* ctx, float* motors, uint32_t* epoch) {
 }
 
 ag_status ag_set_state(ag_ctx* ctx, const float* state, const float* motors, const uint32_t* epoch) {
+  agk::NvtxRange range("ag_set_state");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   if (!state) return fail_invalid(ctx, "state is NULL");
@@ -778,6 +796,7 @@ extern "C" ag_status ag_set_gains(ag_ctx* ctx, const float* gains12) {
 
 extern "C" ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos, float w_omega, const float* p_goal,
                                      float* loss, uint8_t* saturated) {
+  agk::NvtxRange range("ag_rollout_loss");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   const ag_config& c = ctx->cfg;
@@ -809,6 +828,7 @@ extern "C" ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos,
 
 extern "C" ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, float* grad_gains,
                                  float* grad_gains_per_env, float* grad_targets) {
+  agk::NvtxRange range("ag_backward");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   if (!ctx->adj_recorded) {

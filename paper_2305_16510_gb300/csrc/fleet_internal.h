@@ -3,12 +3,22 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "ag.h"
 #include "fleet_device.cuh"
 #include "reset_sampler.cuh"
 
 namespace agk {
+
+// NVTX range over a host-side span (a C-ABI call's checks and enqueueing, a
+// serving chunk), so a profiler's timeline names what issued each kernel.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device buffers of one fleet (all structure-of-arrays over n environments).
 struct FleetBuffers {

@@ -309,6 +309,7 @@ void serve_loop(ag_server* s) {
     // last used by chunk k - 2, retired in the previous iteration)
     cudaError_t e = cudaSuccess;
     if (!sched.empty()) {
+      agk::NvtxRange range("serve chunk");
       InFlight& f = flight[b];
       uint32_t blocks = 0;
       for (size_t j = 0; j < sched.size(); ++j) {

@@ -386,3 +386,26 @@ def test_full_size_mixed_fleet_with_reset_masks_sampled_against_oracle():
     assert dp.max() <= 1e-4, dp.max()
     assert dang.max() <= 1e-4, dang.max()
     np.testing.assert_allclose(mot[:, idx], orc.motors, atol=2e-4)
+
+
+def test_injected_failure_is_sticky_and_the_context_still_destroys():
+    """A failure injected on the host behaves as a CUDA error does: every later
+    call but ag_last_error and ag_destroy returns AG_ERR_STATE, the message is
+    kept, and the device is never touched by the failure itself."""
+    from paper_2305_16510_gb300.fleet import Fleet
+    fl = Fleet(256)
+    fl.reset(None, 1)
+    _abi.ag_inject_failure(fl.ctx, "link to the flight computer lost")
+    for call in (lambda: fl.step(1), lambda: fl.state(), lambda: fl.reset(None, 2),
+                 lambda: _abi.ag_set_commands(fl.ctx, None, None)):
+        with pytest.raises(_abi.AgError) as e:
+            call()
+        assert e.value.status == _abi.AG_ERR_STATE
+    assert _abi.ag_last_error(fl.ctx) == "link to the flight computer lost"
+    fl.close()
+    # a fresh context on the same device works
+    fl2 = Fleet(256)
+    fl2.reset(None, 1)
+    fl2.step(2)
+    assert np.isfinite(_np(fl2.state())).all()
+    fl2.close()
