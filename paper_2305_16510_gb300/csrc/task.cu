@@ -96,8 +96,10 @@ __device__ __forceinline__ void write_obs(const ReachArgs& a, const float* stage
 // step (controller, allocation, integration, collision test and reset, as in
 // the fused fleet step), then reach_tail. Every environment shares the task's
 // command mode, so warps are mode-uniform without a grouping permutation.
+// Without boxes the step is memory-latency bound: eight blocks (32 warps) per
+// SM at 64 registers, with a few bytes of spills, beat fewer warps without.
 template <int INTEG, bool DRAG, bool BOXES>
-__global__ void __launch_bounds__(kTaskBlock, BOXES ? 3 : 4) k_reach_step(ReachArgs a, StepParams P, int substeps) {
+__global__ void __launch_bounds__(kTaskBlock, BOXES ? 3 : 8) k_reach_step(ReachArgs a, StepParams P, int substeps) {
   __shared__ float stage[kTaskBlock * kObs];  // odd row length: conflict-free
   const FleetBuffers& fb = a.fb;
   const uint32_t i = blockIdx.x * kTaskBlock + threadIdx.x;
