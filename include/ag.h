@@ -123,7 +123,10 @@ ag_status ag_set_commands(ag_ctx* ctx, const uint8_t* modes, const float* target
 
 /* Copies the static obstacles: float[n_obstacles][10][n_envs], per box the
  * centre (3), half-extents (3, > 0) and a UNIT quaternion (4) of its
- * orientation (Sec. V: the obstacle state is privileged information). */
+ * orientation (Sec. V: the obstacle state is privileged information).
+ * AG_ERR_INVALID (context unchanged) for a non-finite centre, a half-extent
+ * <= 0 or a quaternion whose squared norm is more than 1e-4 from 1; a device
+ * array is checked by a kernel, and the call synchronises once. */
 ag_status ag_set_obstacles(ag_ctx* ctx, const float* boxes);
 
 /* Copies out the current obstacles float[n_obstacles][10][n_envs] (layout of
@@ -172,7 +175,9 @@ ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hf
                           const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth);
 
 /* Copies per-environment rigid-body parameters float[4][n_envs]: mass and
- * the diagonal inertia J_xx, J_yy, J_zz (all > 0). */
+ * the diagonal inertia J_xx, J_yy, J_zz. AG_ERR_INVALID (context unchanged)
+ * unless all are finite and > 0; a device array is checked by a kernel, and
+ * the call synchronises once. */
 ag_status ag_set_body(ag_ctx* ctx, const float* body);
 
 /* Advances every environment by n_substeps substeps (a positive multiple of

@@ -44,6 +44,7 @@ struct ag_ctx {
   float* depth_stage;        // device staging when the caller's buffer is on the host
   size_t depth_stage_cap;    // floats
   float* eval_state;         // [13][n_envs] states of ag_eval_controller (allocated on first use)
+  uint32_t* check_dev;       // [1] count of the setters' precondition checks
   // reach-a-setpoint task (allocated at the first ag_reach_begin)
   ag_reach_config reach;
   float* reach_goals;        // [3][n_envs]
@@ -121,6 +122,30 @@ __global__ void k_fill_rows(float* dst, uint32_t n, float v0, float v1, float v2
   if (i >= n) return;
   float v[4] = {v0, v1, v2, v3};
   for (int r = 0; r < rows; ++r) dst[(size_t)r * n + i] = v[r];
+}
+
+// Precondition checks of ag_set_body and ag_set_obstacles: each counts the
+// entries that break them into *bad (one atomic per offending entry).
+__device__ __host__ inline bool body_ok(float v) { return v > 0.f && v < 3.0e38f; }
+__device__ __host__ inline bool box_ok(const float f[10]) {
+  for (int k = 0; k < 3; ++k)
+    if (!(f[k] > -3.0e38f && f[k] < 3.0e38f) || !body_ok(f[3 + k])) return false;
+  const float q2 = f[6] * f[6] + f[7] * f[7] + f[8] * f[8] + f[9] * f[9];
+  return q2 > 1.f - 1e-4f && q2 < 1.f + 1e-4f;  // a unit quaternion (also rejects NaN)
+}
+
+__global__ void k_count_bad_body(const float* body, size_t count, uint32_t* bad) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count && !body_ok(body[i])) atomicAdd(bad, 1u);
+}
+
+__global__ void k_count_bad_boxes(const float* boxes, uint32_t n, uint32_t n_obs, uint32_t* bad) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)n * n_obs) return;
+  const size_t k = i / n, e = i % n;
+  float f[10];
+  for (int r = 0; r < 10; ++r) f[r] = boxes[(k * 10 + r) * n + e];
+  if (!box_ok(f)) atomicAdd(bad, 1u);
 }
 
 // Returns "" for a valid config, else a static message (no allocation).
@@ -214,6 +239,7 @@ void free_all(ag_ctx* ctx) {
   if (ctx->cam_ids) cudaFree(ctx->cam_ids);
   if (ctx->depth_stage) cudaFree(ctx->depth_stage);
   if (ctx->eval_state) cudaFree(ctx->eval_state);
+  if (ctx->check_dev) cudaFree(ctx->check_dev);
   if (ctx->reach_goals) cudaFree(ctx->reach_goals);
   if (ctx->reach_steps) cudaFree(ctx->reach_steps);
   agk::FleetBuffers& f = ctx->fb;
@@ -229,6 +255,28 @@ template <class T> cudaError_t alloc(ag_ctx* ctx, T** p, size_t count) {
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e == cudaSuccess) ctx->bytes += count * sizeof(T);
   return e;
+}
+
+// true for device or managed memory (a kernel can read it), false for host memory
+bool on_device(const void* p) {
+  cudaPointerAttributes pa;
+  const bool dev = cudaPointerGetAttributes(&pa, p) == cudaSuccess &&
+                   (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  return dev;
+}
+
+// Number of entries of a device array that break a setter's precondition
+// (counted by `launch` into ctx->check_dev; synchronises).
+template <class Launch>
+ag_status count_bad_on_device(ag_ctx* ctx, Launch launch, uint32_t* bad) {
+  cudaStream_t st = ctx->stream;
+  ag_status s = check_cuda(ctx, cudaMemsetAsync(ctx->check_dev, 0, sizeof(uint32_t), st), "clear check");
+  if (s == AG_OK) s = check_cuda(ctx, launch(st), "check launch");
+  if (s == AG_OK)
+    s = check_cuda(ctx, cudaMemcpyAsync(bad, ctx->check_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "copy check");
+  if (s == AG_OK) s = check_cuda(ctx, cudaStreamSynchronize(st), "synchronize");
+  return s;
 }
 
 }  // namespace
@@ -286,6 +334,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   ctx->depth_stage = nullptr;
   ctx->depth_stage_cap = 0;
   ctx->eval_state = nullptr;
+  ctx->check_dev = nullptr;
   ctx->reach_goals = nullptr;
   ctx->reach_steps = nullptr;
   ctx->reach_active = false;
@@ -316,6 +365,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = alloc(ctx, &f.resets, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.hits, n);
   if (e == cudaSuccess) e = alloc(ctx, &ctx->mask_dev, n);
+  if (e == cudaSuccess) e = alloc(ctx, &ctx->check_dev, 1);
   if (e == cudaSuccess) e = alloc(ctx, &f.order, n);
   if (e == cudaSuccess && cfg->n_obstacles) e = alloc(ctx, &f.slot_of, n);
   if (e == cudaSuccess) e = alloc(ctx, &ctx->order_scratch, agk::order_scratch_words(cfg->n_envs));
@@ -387,7 +437,25 @@ ag_status ag_set_obstacles(ag_ctx* ctx, const float* boxes) {
   if (s != AG_OK) return s;
   if (!boxes) return fail_invalid(ctx, "boxes is NULL");
   if (ctx->cfg.n_obstacles == 0) return AG_OK;
-  const size_t count = (size_t)ctx->cfg.n_obstacles * 10 * ctx->cfg.n_envs;
+  const uint32_t n = ctx->cfg.n_envs, n_obs = ctx->cfg.n_obstacles;
+  const size_t count = (size_t)n_obs * 10 * n;
+  uint32_t bad = 0;
+  if (on_device(boxes)) {
+    s = count_bad_on_device(ctx, [&](cudaStream_t st) {
+      const size_t items = (size_t)n * n_obs;
+      k_count_bad_boxes<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(boxes, n, n_obs, ctx->check_dev);
+      return cudaGetLastError();
+    }, &bad);
+    if (s != AG_OK) return s;
+  } else {
+    for (size_t k = 0; k < n_obs; ++k)
+      for (size_t e = 0; e < n; ++e) {
+        float f[10];
+        for (int r = 0; r < 10; ++r) f[r] = boxes[(k * 10 + r) * n + e];
+        bad += box_ok(f) ? 0u : 1u;
+      }
+  }
+  if (bad) return fail_invalid(ctx, "boxes: finite centres, half-extents > 0 and unit quaternions required");
   s = check_cuda(ctx, cudaMemcpyAsync(ctx->fb.boxes, boxes, count * sizeof(float), cudaMemcpyDefault, ctx->stream),
                  "copy boxes");
   if (s != AG_OK) return s;
@@ -420,11 +488,7 @@ ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hf
   cudaStream_t st = ctx->stream;
   const uint32_t* ids_dev = nullptr;
   if (env_ids) {
-    cudaPointerAttributes pa;
-    const bool on_device = cudaPointerGetAttributes(&pa, env_ids) == cudaSuccess &&
-                           (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
-    cudaGetLastError();
-    if (!on_device)
+    if (!on_device(env_ids))
       for (uint32_t j = 0; j < n_cams; ++j)
         if (env_ids[j] >= n) return fail_invalid(ctx, "environment id out of range");
     if (!ctx->cam_ids && (s = check_cuda(ctx, alloc(ctx, &ctx->cam_ids, n), "allocate camera ids")) != AG_OK) return s;
@@ -433,10 +497,7 @@ ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hf
     ids_dev = ctx->cam_ids;
   }
   const size_t count = (size_t)n_cams * width * height;
-  cudaPointerAttributes pa;
-  const bool out_on_device = cudaPointerGetAttributes(&pa, depth) == cudaSuccess &&
-                             (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
-  cudaGetLastError();
+  const bool out_on_device = on_device(depth);
   float* out = depth;
   if (!out_on_device) {
     if (count > ctx->depth_stage_cap) {
@@ -508,11 +569,24 @@ ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], con
 }
 
 ag_status ag_set_body(ag_ctx* ctx, const float* body) {
+  agk::NvtxRange range("ag_set_body");
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   if (!body) return fail_invalid(ctx, "body is NULL");
-  return check_cuda(ctx, cudaMemcpyAsync(ctx->fb.body, body, 4 * ctx->cfg.n_envs * sizeof(float), cudaMemcpyDefault,
-                                         ctx->stream), "copy body");
+  const size_t count = 4 * (size_t)ctx->cfg.n_envs;
+  uint32_t bad = 0;
+  if (on_device(body)) {
+    s = count_bad_on_device(ctx, [&](cudaStream_t st) {
+      k_count_bad_body<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(body, count, ctx->check_dev);
+      return cudaGetLastError();
+    }, &bad);
+    if (s != AG_OK) return s;
+  } else {
+    for (size_t i = 0; i < count; ++i) bad += body_ok(body[i]) ? 0u : 1u;
+  }
+  if (bad) return fail_invalid(ctx, "body: masses and inertias must be finite and > 0");
+  return check_cuda(ctx, cudaMemcpyAsync(ctx->fb.body, body, count * sizeof(float), cudaMemcpyDefault, ctx->stream),
+                    "copy body");
 }
 
 static ag_status step_common(ag_ctx* ctx, uint32_t n_substeps, bool fused) {

@@ -409,3 +409,45 @@ def test_injected_failure_is_sticky_and_the_context_still_destroys():
     fl2.step(2)
     assert np.isfinite(_np(fl2.state())).all()
     fl2.close()
+
+
+def test_setters_reject_broken_bodies_and_boxes_and_keep_the_context():
+    """ag_set_body and ag_set_obstacles check their documented preconditions
+    (finite positive masses and inertias; finite centres, positive
+    half-extents, unit quaternions) on host and device arrays before anything
+    is copied, so a rejected call leaves the context as it was."""
+    w = W.Workload("checks", 300, 1, 0, 4, 300, 0, 0)
+    inp = W.make_inputs(w, 2)
+    fl = gpu_fleet(w, inp, 2)
+    fl.reset(None, 2)
+    boxes0 = _np(fl.obstacles()).copy()
+    bodies = []
+    for r, v in ((0, 0.0), (2, -0.01), (3, np.nan), (1, np.inf)):
+        b = inp.body.copy()
+        b[r, 17] = v
+        bodies.append(b)
+    boxes = []
+    for k, f, v in ((0, 4, 0.0), (1, 0, np.nan), (2, 3, -0.5)):
+        b = boxes0.copy()
+        b[k, f, 5] = v
+        boxes.append(b)
+    b = boxes0.copy()
+    b[3, 6:10, 9] *= 1.01               # not a unit quaternion
+    boxes.append(b)
+    for arr, setter in [(x, _abi.ag_set_body) for x in bodies] + [(x, _abi.ag_set_obstacles) for x in boxes]:
+        for where in ("host", "device"):
+            src = np.ascontiguousarray(arr) if where == "host" else torch.from_numpy(np.ascontiguousarray(arr)).cuda()
+            with pytest.raises(_abi.AgError) as e:
+                setter(fl.ctx, src)
+            assert e.value.status == _abi.AG_ERR_INVALID, (setter.__name__, where)
+    np.testing.assert_array_equal(_np(fl.obstacles()), boxes0)
+    # still usable, and the body is the one set before
+    fl.step(5)
+    st = _np(fl.state())
+    assert np.isfinite(st).all()
+    ref = gpu_fleet(w, inp, 2)
+    ref.reset(None, 2)
+    ref.step(5)
+    np.testing.assert_array_equal(_np(ref.state()), st)
+    ref.close()
+    fl.close()
