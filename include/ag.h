@@ -424,8 +424,11 @@ ag_status ag_server_create(const ag_server_config* cfg, ag_server** out);
 
 /* Queues a request (thread-safe, non-blocking) and returns its id. The input
  * arrays (host or device) must stay valid until ag_server_wait has returned
- * for this id. AG_ERR_INVALID for a malformed request, AG_ERR_OOM if it could
- * never fit the budget, AG_ERR_STATE if the server has failed. */
+ * for this id. Their contents are not checked (submission stays cheap): they
+ * must meet the preconditions of ag_set_commands, ag_set_body and
+ * ag_set_obstacles. AG_ERR_INVALID for a malformed request (counts, NULL
+ * arrays, pitch), AG_ERR_OOM if it could never fit the budget, AG_ERR_STATE
+ * if the server has failed. */
 ag_status ag_server_submit(ag_server* s, const ag_request* req, uint64_t* id);
 
 /* Blocks until request `id` finishes or timeout_s seconds pass
