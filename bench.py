@@ -50,6 +50,14 @@ FLOP_PER_VEHICLE_STEP = 4588.0
 # drag, 40 % quad / 40 % hexa / 20 % octo) and the paper shape (attitude and
 # body velocity, SIE, quads, no boxes).
 FLOP_PER_VEHICLE_STEP_MIXED = 584.4
+# Bytes the unfused path moves per vehicle-step of the bench workload: per
+# substep the controller (state 52, mode 1, targets 16, body 16 in; command
+# 16 out), allocation (command 16, motors 16 in; motors 16, wrench 16 out)
+# and integrator (state 52, wrench 16, body 16 in; state 52 out), 301 B x 4;
+# per step the collision test (position 12, 16 boxes x 40 in; hit byte out)
+# and the reset pass (hit byte in).
+PLAIN_BYTES_PER_VEHICLE_STEP = 301 * 4 + 12 + 16 * 40 + 1 + 1
+HBM_PEAK_GBS = 6794.5  # the machine's measured copy bandwidth (MEASURED_PEAKS.json, hbm_gbs)
 FLOP_PER_VEHICLE_STEP_PAPER_SHAPE = 528.5
 # GB300 FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2,070 MHz
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
@@ -234,6 +242,8 @@ def gpu_arm(args) -> dict | None:
         secs_p, per_p = time_calls(fl, lambda: fl.step_plain(C), k_plain, world)
         plain_value = w.n_envs * C * k_plain * world / secs_p
         out["plain"] = {"value": plain_value, "unit": UNIT, "ms_per_step": secs_p * 1e3 / k_plain,
+                        "bytes_per_vehicle_step": PLAIN_BYTES_PER_VEHICLE_STEP,
+                        "hbm_frac": plain_value / world * PLAIN_BYTES_PER_VEHICLE_STEP / 1e9 / HBM_PEAK_GBS,
                         "launches_per_step": C * (3 * w.substeps_per_step + 2) + 1,
                         "fused_over_plain": value / plain_value}
 
