@@ -20,7 +20,8 @@ LIB_NAME = "libaerialgb.so"
 LIB_PATH = os.path.join(PKG, LIB_NAME)
 BUILD_DIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["ag_api.cu", "fleet_kernels.cu", "adjoint.cu", "serve.cu", "depth.cu", "task.cu"]
+CUDA_SOURCES = ["ag_api.cu", "ag_api_task.cu", "ag_api_adjoint.cu", "ag_api_noalloc.cu", "fleet_kernels.cu",
+                "adjoint.cu", "serve.cu", "depth.cu", "task.cu"]
 
 
 def _nvcc() -> str:

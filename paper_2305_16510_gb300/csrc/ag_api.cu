@@ -1,10 +1,12 @@
-// ag_api.cu — the extern "C" entry points declared in include/ag.h.
+// ag_api.cu — the core extern "C" entry points declared in include/ag.h:
+// context, inputs and outputs, steps, resets and the controller stage.
+// (ag_api_task.cu: depth images and the reach task; ag_api_adjoint.cu: the
+// differentiable rollout; ag_api_noalloc.cu: the allocation-free step.)
 //
 // Host side of libaerialgb: argument validation, device buffers, the
 // per-context sticky error state, the FP64 rotor-allocation matrices, and
 // the stream-ordered copies and launches. Nothing here computes a vehicle
-// state; every step of the simulation runs in the kernels of
-// fleet_kernels.cu.
+// state; every step of the simulation runs in the kernels.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -15,47 +17,15 @@
 
 #include <cuda_runtime.h>
 
-#include "adjoint_internal.h"
-#include "ag.h"
-#include "depth_internal.h"
-#include "fleet_internal.h"
-#include "task_internal.h"
-
-struct ag_ctx {
-  ag_config cfg;
-  cudaStream_t stream;
-  int device;
-  agk::FleetBuffers fb;
-  uint8_t* mask_dev;         // [n] staging for ag_reset masks
-  uint32_t* order_scratch;   // per-block key counts / offsets of the grouping permutation
-  uint64_t seed;             // Philox key of collision resets
-  bool failed;
-  std::string err;
-  size_t bytes;              // device bytes held
-  float A[3][4][8], Ap[3][8][4];
-  // differentiable rollout (allocated at the first ag_rollout_loss)
-  agk::AdjointBuffers adj;
-  size_t adj_ckpt_cap;       // checkpoints the ckpt buffer holds
-  int adj_tape_cap;          // steps the tape holds
-  bool adj_recorded;
-  agk::StepParams adj_P;     // parameters of the recorded rollout
-  // depth rendering staging (allocated on first use, grown as needed)
-  uint32_t* cam_ids;         // [n_envs]
-  float* depth_stage;        // device staging when the caller's buffer is on the host
-  size_t depth_stage_cap;    // floats
-  float* eval_state;         // [13][n_envs] states of ag_eval_controller (allocated on first use)
-  uint32_t* check_dev;       // [1] count of the setters' precondition checks
-  // reach-a-setpoint task (allocated at the first ag_reach_begin)
-  ag_reach_config reach;
-  float* reach_goals;        // [3][n_envs]
-  uint32_t* reach_steps;     // [n_envs]
-  bool reach_active;
-};
+#include "ctx_internal.h"
 
 namespace {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+namespace agh {
 
 ag_status fail_invalid(ag_ctx* ctx, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -117,6 +87,10 @@ void rotor_matrices(int n, double arm, double k_yaw, float A[4][8], float Ap[8][
     }
 }
 
+}  // namespace agh
+
+namespace {
+
 __global__ void k_fill_rows(float* dst, uint32_t n, float v0, float v1, float v2, float v3, int rows) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -148,7 +122,10 @@ __global__ void k_count_bad_boxes(const float* boxes, uint32_t n, uint32_t n_obs
   if (!box_ok(f)) atomicAdd(bad, 1u);
 }
 
-// Returns "" for a valid config, else a static message (no allocation).
+}  // namespace
+
+namespace agh {
+
 const char* validate(const ag_config* c) {
   if (!c) return "config is NULL";
   if (c->n_envs == 0) return "n_envs must be >= 1";
@@ -169,6 +146,10 @@ const char* validate(const ag_config* c) {
   return "";
 }
 
+}  // namespace agh
+
+namespace {
+
 size_t buffer_bytes(const ag_config* c) {
   size_t n = c->n_envs;
   size_t per = sizeof(float) * (13 + 8 + 4 + 4 + 4 + 4) + sizeof(uint32_t) * 4 + 3 /* modes, collided, hits */ + 1;
@@ -183,7 +164,7 @@ agk::StepParams agk::step_params_for(const ag_config& c, uint64_t seed) {
   for (int i = 0; i < 3; ++i) {
     P.kx[i] = c.kx[i]; P.kv[i] = c.kv[i]; P.kR[i] = c.kR[i]; P.kW[i] = c.kW[i];
   }
-  for (int t = 0; t < 3; ++t) rotor_matrices(t == 0 ? 4 : (t == 1 ? 6 : 8), c.arm, c.k_yaw, P.A[t], P.Ap[t]);
+  for (int t = 0; t < 3; ++t) agh::rotor_matrices(t == 0 ? 4 : (t == 1 ? 6 : 8), c.arm, c.k_yaw, P.A[t], P.Ap[t]);
   const double h = (double)c.dt / c.substeps_per_step;
   P.h = (float)h;
   P.alpha = c.motor_tau > 0.f ? (float)(1.0 - std::exp(-h / (double)c.motor_tau)) : 1.f;
@@ -195,7 +176,7 @@ agk::StepParams agk::step_params_for(const ag_config& c, uint64_t seed) {
   return P;
 }
 
-namespace {
+namespace agh {
 
 agk::StepParams step_params(const ag_ctx* ctx) {
   agk::StepParams P;
@@ -216,7 +197,6 @@ agk::StepParams step_params(const ag_ctx* ctx) {
   return P;
 }
 
-// common prologue: NULL ctx, sticky failure, device selection
 ag_status enter(ag_ctx* ctx) {
   if (!ctx) return AG_ERR_INVALID;
   if (ctx->failed) return AG_ERR_STATE;
@@ -225,6 +205,20 @@ ag_status enter(ag_ctx* ctx) {
   ctx->err.clear();
   return AG_OK;
 }
+
+bool on_device(const void* p) {
+  cudaPointerAttributes pa;
+  const bool dev = cudaPointerGetAttributes(&pa, p) == cudaSuccess &&
+                   (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  return dev;
+}
+
+}  // namespace agh
+
+namespace {
+
+using namespace agh;
 
 void free_adjoint(ag_ctx* ctx) {
   agk::AdjointBuffers& a = ctx->adj;
@@ -250,22 +244,6 @@ void free_all(ag_ctx* ctx) {
     if (p) cudaFree(p);
 }
 
-template <class T> cudaError_t alloc(ag_ctx* ctx, T** p, size_t count) {
-  if (count == 0) { *p = nullptr; return cudaSuccess; }
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e == cudaSuccess) ctx->bytes += count * sizeof(T);
-  return e;
-}
-
-// true for device or managed memory (a kernel can read it), false for host memory
-bool on_device(const void* p) {
-  cudaPointerAttributes pa;
-  const bool dev = cudaPointerGetAttributes(&pa, p) == cudaSuccess &&
-                   (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
-  cudaGetLastError();
-  return dev;
-}
-
 // Number of entries of a device array that break a setter's precondition
 // (counted by `launch` into ctx->check_dev; synchronises).
 template <class Launch>
@@ -280,6 +258,8 @@ ag_status count_bad_on_device(ag_ctx* ctx, Launch launch, uint32_t* bad) {
 }
 
 }  // namespace
+
+using namespace agh;
 
 extern "C" {
 
@@ -472,61 +452,6 @@ ag_status ag_get_obstacles(ag_ctx* ctx, float* boxes) {
                     "copy boxes out");
 }
 
-ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
-                          const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth) {
-  agk::NvtxRange range("ag_render_depth");
-  ag_status s = enter(ctx);
-  if (s != AG_OK) return s;
-  const uint32_t n = ctx->cfg.n_envs;
-  if (width == 0 || height == 0 || (uint64_t)width * height > (1u << 30))
-    return fail_invalid(ctx, "image size must be positive and at most 2^30 pixels");
-  if (!(hfov > 0.f && hfov < 3.14159f)) return fail_invalid(ctx, "hfov must lie in (0, pi)");
-  if (!(max_range > 0.f)) return fail_invalid(ctx, "max_range must be > 0");
-  if (n_cams == 0 || !depth) return fail_invalid(ctx, "n_cams must be >= 1 and depth non-NULL");
-  if (!env_ids && n_cams > n) return fail_invalid(ctx, "n_cams exceeds n_envs");
-  if (env_ids && n_cams > n) return fail_invalid(ctx, "at most n_envs cameras per call");
-  cudaStream_t st = ctx->stream;
-  const uint32_t* ids_dev = nullptr;
-  if (env_ids) {
-    if (!on_device(env_ids))
-      for (uint32_t j = 0; j < n_cams; ++j)
-        if (env_ids[j] >= n) return fail_invalid(ctx, "environment id out of range");
-    if (!ctx->cam_ids && (s = check_cuda(ctx, alloc(ctx, &ctx->cam_ids, n), "allocate camera ids")) != AG_OK) return s;
-    if ((s = check_cuda(ctx, cudaMemcpyAsync(ctx->cam_ids, env_ids, n_cams * sizeof(uint32_t), cudaMemcpyDefault, st),
-                        "copy camera ids")) != AG_OK) return s;
-    ids_dev = ctx->cam_ids;
-  }
-  const size_t count = (size_t)n_cams * width * height;
-  const bool out_on_device = on_device(depth);
-  float* out = depth;
-  if (!out_on_device) {
-    if (count > ctx->depth_stage_cap) {
-      if (ctx->depth_stage) { cudaStreamSynchronize(st); cudaFree(ctx->depth_stage); ctx->depth_stage = nullptr; }
-      ctx->depth_stage_cap = 0;
-      if ((s = check_cuda(ctx, alloc(ctx, &ctx->depth_stage, count), "allocate depth staging")) != AG_OK) return s;
-      ctx->depth_stage_cap = count;
-    }
-    out = ctx->depth_stage;
-  }
-  agk::DepthArgs a;
-  a.state = ctx->fb.state;
-  a.boxes = ctx->fb.boxes;
-  a.env_ids = ids_dev;
-  a.out = out;
-  a.n = n;
-  a.n_obs = ctx->cfg.n_obstacles;
-  a.n_cams = n_cams;
-  a.width = width;
-  a.height = height;
-  a.inv_f = (float)(std::tan(0.5 * (double)hfov) / (0.5 * width));
-  a.max_range = max_range;
-  for (int i = 0; i < 3; ++i) a.offset[i] = cam_offset ? cam_offset[i] : 0.f;
-  if ((s = check_cuda(ctx, agk::launch_render_depth(a, st), "depth launch")) != AG_OK) return s;
-  if (!out_on_device)
-    s = check_cuda(ctx, cudaMemcpyAsync(depth, out, count * sizeof(float), cudaMemcpyDeviceToHost, st), "copy depth out");
-  return s;
-}
-
 ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], const float env_max[3],
                                         const ag_box_randomization* per_box) {
   ag_status s = enter(ctx);
@@ -650,102 +575,6 @@ ag_status ag_reset(ag_ctx* ctx, const uint8_t* mask, uint64_t seed) {
                                            ctx->stream), "reset launch");
 }
 
-void ag_reach_config_default(ag_reach_config* c) {
-  if (!c) return;
-  std::memset(c, 0, sizeof(*c));
-  c->command_mode = AG_MODE_ATT_THRUST;
-  const float pi6 = 0.52359878f, mg = 0.75f * 9.81f;
-  const float scale[4] = {pi6, pi6, 1.0f, 0.5f * mg}, offset[4] = {0.f, 0.f, 0.f, mg};
-  for (int k = 0; k < 4; ++k) {
-    c->action_scale[k] = scale[k];
-    c->action_offset[k] = offset[k];
-  }
-  c->w_v = 0.1f;
-  c->w_omega = 0.01f;
-  c->crash = 10.f;
-  c->max_dist = 8.f;
-  c->max_steps = 500;
-}
-
-ag_status ag_reach_begin(ag_ctx* ctx, const ag_reach_config* cfg, const float* goals) {
-  agk::NvtxRange range("ag_reach_begin");
-  ag_status s = enter(ctx);
-  if (s != AG_OK) return s;
-  if (!cfg || !goals) return fail_invalid(ctx, "cfg and goals must be non-NULL");
-  if (cfg->command_mode != AG_MODE_ATT_THRUST && cfg->command_mode != AG_MODE_BODY_VEL)
-    return fail_invalid(ctx, "command_mode must be AG_MODE_ATT_THRUST or AG_MODE_BODY_VEL");
-  if (cfg->max_steps == 0) return fail_invalid(ctx, "max_steps must be >= 1");
-  if (!(cfg->w_v >= 0.f && cfg->w_omega >= 0.f && cfg->crash >= 0.f))
-    return fail_invalid(ctx, "weights and the crash penalty must be >= 0");
-  if (!(cfg->max_dist > 0.f)) return fail_invalid(ctx, "max_dist must be > 0");
-  for (int k = 0; k < 4; ++k)
-    if (!std::isfinite(cfg->action_scale[k]) || !std::isfinite(cfg->action_offset[k]))
-      return fail_invalid(ctx, "action scale and offset must be finite");
-  const size_t n = ctx->cfg.n_envs;
-  cudaStream_t st = ctx->stream;
-  if (!ctx->reach_goals && (s = check_cuda(ctx, alloc(ctx, &ctx->reach_goals, 3 * n), "allocate goals")) != AG_OK)
-    return s;
-  if (!ctx->reach_steps && (s = check_cuda(ctx, alloc(ctx, &ctx->reach_steps, n), "allocate step counters")) != AG_OK)
-    return s;
-  if ((s = check_cuda(ctx, cudaMemcpyAsync(ctx->reach_goals, goals, 3 * n * sizeof(float), cudaMemcpyDefault, st),
-                      "copy goals")) != AG_OK) return s;
-  if ((s = check_cuda(ctx, cudaMemsetAsync(ctx->reach_steps, 0, n * sizeof(uint32_t), st), "clear step counters")) !=
-      AG_OK) return s;
-  if ((s = check_cuda(ctx, cudaMemsetAsync(ctx->fb.modes, (int)cfg->command_mode, n, st), "set modes")) != AG_OK)
-    return s;
-  if ((s = check_cuda(ctx, agk::launch_build_order(ctx->fb, ctx->order_scratch, st), "build order")) != AG_OK)
-    return s;
-  ctx->reach = *cfg;
-  ctx->reach_active = true;
-  return AG_OK;
-}
-
-static agk::ReachArgs reach_args(ag_ctx* ctx, const float* actions, float* obs, float* reward, uint8_t* done) {
-  agk::ReachArgs a;
-  a.fb = ctx->fb;
-  a.actions = actions;
-  a.goals = ctx->reach_goals;
-  a.steps = ctx->reach_steps;
-  a.obs = obs;
-  a.reward = reward;
-  a.done = done;
-  const ag_reach_config& c = ctx->reach;
-  for (int k = 0; k < 4; ++k) {
-    a.scale[k] = c.action_scale[k];
-    a.offset[k] = c.action_offset[k];
-  }
-  a.w_v = c.w_v;
-  a.w_omega = c.w_omega;
-  a.crash = c.crash;
-  a.max_dist = c.max_dist;
-  a.max_steps = c.max_steps;
-  a.seed_lo = (uint32_t)(ctx->seed & 0xFFFFFFFFu);
-  a.seed_hi = (uint32_t)(ctx->seed >> 32);
-  return a;
-}
-
-ag_status ag_reach_step(ag_ctx* ctx, const float* actions, float* obs, float* reward, uint8_t* done) {
-  agk::NvtxRange range("ag_reach_step");
-  ag_status s = enter(ctx);
-  if (s != AG_OK) return s;
-  if (!ctx->reach_active) return AG_ERR_STATE;
-  if (!actions || !obs || !reward || !done) return fail_invalid(ctx, "actions, obs, reward and done must be non-NULL");
-  if (reinterpret_cast<uintptr_t>(actions) % 16 != 0) return fail_invalid(ctx, "actions must be 16-byte aligned");
-  const agk::ReachArgs a = reach_args(ctx, actions, obs, reward, done);
-  return check_cuda(ctx, agk::launch_reach_step(a, step_params(ctx), (int)ctx->cfg.integrator,
-                                                (int)ctx->cfg.substeps_per_step, ctx->stream), "task step launch");
-}
-
-ag_status ag_reach_observe(ag_ctx* ctx, float* obs) {
-  agk::NvtxRange range("ag_reach_observe");
-  ag_status s = enter(ctx);
-  if (s != AG_OK) return s;
-  if (!ctx->reach_active) return AG_ERR_STATE;
-  if (!obs) return fail_invalid(ctx, "obs must be non-NULL");
-  return check_cuda(ctx, agk::launch_reach_observe(reach_args(ctx, nullptr, obs, nullptr, nullptr), ctx->stream),
-                    "task observe launch");
-}
-
 ag_status ag_get_state(ag_ctx* ctx, float* state, uint8_t* collided, uint32_t* reset_ids, uint32_t* n_reset) {
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
@@ -812,261 +641,3 @@ const char* ag_last_error(const ag_ctx* ctx) {
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------
-// Differentiable rollout: gains, recorded forward, adjoint.
-namespace {
-
-// Grows the adjoint buffers for a record of n_steps steps with interval K.
-ag_status ensure_adjoint(ag_ctx* ctx, int n_steps, int K) {
-  agk::AdjointBuffers& a = ctx->adj;
-  const size_t n = ctx->cfg.n_envs;
-  const size_t n_ckpt = (size_t)(n_steps + K - 1) / K;
-  cudaError_t e = cudaSuccess;
-  if (!a.loss) {
-    float* pg = nullptr; float* lw = nullptr;
-    if (e == cudaSuccess) e = alloc(ctx, &pg, 3 * n);
-    if (e == cudaSuccess) e = alloc(ctx, &a.loss, n);
-    if (e == cudaSuccess) e = alloc(ctx, &a.saturated, n);
-    if (e == cudaSuccess) e = alloc(ctx, &lw, n);
-    if (e == cudaSuccess) e = alloc(ctx, &a.grad_x0, 13 * n);
-    if (e == cudaSuccess) e = alloc(ctx, &a.grad_gains_env, 12 * n);
-    if (e == cudaSuccess) e = alloc(ctx, &a.grad_targets, 4 * n);
-    if (e == cudaSuccess) e = alloc(ctx, &a.partial, 12 * (size_t)agk::kReduceParts);
-    if (e == cudaSuccess) e = alloc(ctx, &a.grad_gains, 12);
-    a.p_goal = pg;
-    a.loss_weights = lw;
-    if (e != cudaSuccess) { cudaGetLastError(); ctx->err = "adjoint buffers do not fit"; return AG_ERR_OOM; }
-  }
-  if (n_ckpt > ctx->adj_ckpt_cap) {
-    if (a.ckpt) { cudaStreamSynchronize(ctx->stream); cudaFree(a.ckpt); a.ckpt = nullptr; }
-    e = alloc(ctx, &a.ckpt, n_ckpt * 21 * n);
-    if (e != cudaSuccess) { cudaGetLastError(); ctx->adj_ckpt_cap = 0; ctx->err = "checkpoints do not fit"; return AG_ERR_OOM; }
-    ctx->adj_ckpt_cap = n_ckpt;
-  }
-  if (K > ctx->adj_tape_cap) {
-    if (a.tape) { cudaStreamSynchronize(ctx->stream); cudaFree(a.tape); a.tape = nullptr; }
-    e = alloc(ctx, &a.tape, (size_t)K * 21 * n);
-    if (e != cudaSuccess) { cudaGetLastError(); ctx->adj_tape_cap = 0; ctx->err = "tape does not fit"; return AG_ERR_OOM; }
-    ctx->adj_tape_cap = K;
-  }
-  return AG_OK;
-}
-
-}  // namespace
-
-extern "C" ag_status ag_set_gains(ag_ctx* ctx, const float* gains12) {
-  ag_status s = enter(ctx);
-  if (s != AG_OK) return s;
-  if (!gains12) return fail_invalid(ctx, "gains is NULL");
-  float g[12];
-  if ((s = check_cuda(ctx, cudaMemcpy(g, gains12, sizeof(g), cudaMemcpyDefault), "copy gains")) != AG_OK) return s;
-  for (int i = 0; i < 12; ++i)
-    if (!std::isfinite(g[i])) return fail_invalid(ctx, "gains must be finite");
-  for (int i = 0; i < 3; ++i) {
-    ctx->cfg.kx[i] = g[i]; ctx->cfg.kv[i] = g[3 + i]; ctx->cfg.kR[i] = g[6 + i]; ctx->cfg.kW[i] = g[9 + i];
-  }
-  return AG_OK;
-}
-
-extern "C" ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos, float w_omega, const float* p_goal,
-                                     float* loss, uint8_t* saturated) {
-  agk::NvtxRange range("ag_rollout_loss");
-  ag_status s = enter(ctx);
-  if (s != AG_OK) return s;
-  const ag_config& c = ctx->cfg;
-  if (c.integrator != AG_INTEG_SIE || c.substeps_per_step != 1 || c.n_obstacles != 0) {
-    ctx->err = "the differentiable rollout needs semi-implicit Euler, 1 substep per step and no obstacles";
-    return AG_ERR_UNSUPPORTED;
-  }
-  if (n_steps == 0 || !p_goal || !loss) return fail_invalid(ctx, "n_steps must be >= 1; p_goal and loss are required");
-  const size_t n = c.n_envs;
-  const int K = c.record_every ? (int)c.record_every : 32;
-  if ((s = ensure_adjoint(ctx, (int)n_steps, K)) != AG_OK) return s;
-  agk::AdjointBuffers& a = ctx->adj;
-  if ((s = check_cuda(ctx, cudaMemcpyAsync((void*)a.p_goal, p_goal, 3 * n * sizeof(float), cudaMemcpyDefault,
-                                           ctx->stream), "copy goals")) != AG_OK) return s;
-  a.state = ctx->fb.state; a.motors = ctx->fb.motors; a.body = ctx->fb.body; a.targets = ctx->fb.targets;
-  a.modes = ctx->fb.modes;
-  a.n = c.n_envs; a.n_quad = c.n_quad; a.n_hexa = c.n_hexa; a.n_octo = c.n_octo;
-  a.n_steps = (int)n_steps; a.K = K; a.w_pos = w_pos; a.w_omega = w_omega;
-  ctx->adj_P = step_params(ctx);
-  ctx->adj_recorded = false;
-  if ((s = check_cuda(ctx, agk::launch_record(a, ctx->adj_P, ctx->stream), "record launch")) != AG_OK) return s;
-  ctx->adj_recorded = true;
-  if ((s = check_cuda(ctx, cudaMemcpyAsync(loss, a.loss, n * sizeof(float), cudaMemcpyDefault, ctx->stream),
-                      "copy loss out")) != AG_OK) return s;
-  if (saturated)
-    s = check_cuda(ctx, cudaMemcpyAsync(saturated, a.saturated, n, cudaMemcpyDefault, ctx->stream), "copy flags out");
-  return s;
-}
-
-extern "C" ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, float* grad_gains,
-                                 float* grad_gains_per_env, float* grad_targets) {
-  agk::NvtxRange range("ag_backward");
-  ag_status s = enter(ctx);
-  if (s != AG_OK) return s;
-  if (!ctx->adj_recorded) {
-    ctx->err = "ag_backward needs a rollout recorded by ag_rollout_loss";
-    return AG_ERR_STATE;
-  }
-  if (!grad_x0 && !grad_gains && !grad_gains_per_env && !grad_targets) return AG_OK;
-  agk::AdjointBuffers a = ctx->adj;
-  const size_t n = ctx->cfg.n_envs;
-  if (loss_weights) {
-    if ((s = check_cuda(ctx, cudaMemcpyAsync((void*)a.loss_weights, loss_weights, n * sizeof(float),
-                                             cudaMemcpyDefault, ctx->stream), "copy weights")) != AG_OK) return s;
-  } else {
-    a.loss_weights = nullptr;
-  }
-  if ((s = check_cuda(ctx, agk::launch_adjoint(a, ctx->adj_P, ctx->stream), "adjoint launch")) != AG_OK) return s;
-  cudaStream_t st = ctx->stream;
-  if (grad_x0 && (s = check_cuda(ctx, cudaMemcpyAsync(grad_x0, a.grad_x0, 13 * n * sizeof(float), cudaMemcpyDefault,
-                                                      st), "copy grad x0")) != AG_OK) return s;
-  if (grad_gains && (s = check_cuda(ctx, cudaMemcpyAsync(grad_gains, a.grad_gains, 12 * sizeof(float),
-                                                         cudaMemcpyDefault, st), "copy grad gains")) != AG_OK) return s;
-  if (grad_gains_per_env && (s = check_cuda(ctx, cudaMemcpyAsync(grad_gains_per_env, a.grad_gains_env,
-                                                                  12 * n * sizeof(float), cudaMemcpyDefault, st),
-                                             "copy per-env grad gains")) != AG_OK) return s;
-  if (grad_targets)
-    s = check_cuda(ctx, cudaMemcpyAsync(grad_targets, a.grad_targets, 4 * n * sizeof(float), cudaMemcpyDefault, st),
-                   "copy grad targets");
-  return s;
-}
-
-// ---------------------------------------------------------------------------
-// Allocation-free unfused step (ag_step_plain_noalloc).
-//
-// The unfused path needs four scratch arrays between its stage kernels (the
-// commanded and the realised wrench, the per-step hit bytes and the per-call
-// reset counters). Here they live in one file-scope device array sized for
-// AG_NOALLOC_MAX_ENVS environments, so the call never allocates: every GPU
-// that loads this library holds the array until the process exits, and every
-// call on that GPU reuses it.
-#include <mutex>
-
-namespace {
-
-constexpr size_t kNoallocN = AG_NOALLOC_MAX_ENVS;
-constexpr size_t kNoallocOffCmd = 0;
-constexpr size_t kNoallocOffWrench = kNoallocOffCmd + 4 * kNoallocN * sizeof(float);
-constexpr size_t kNoallocOffResets = kNoallocOffWrench + 4 * kNoallocN * sizeof(float);
-constexpr size_t kNoallocOffHits = kNoallocOffResets + kNoallocN * sizeof(uint32_t);
-constexpr size_t kNoallocBytes = kNoallocOffHits + kNoallocN;  // 2,424,832 bytes for 65,536 envs
-static_assert(kNoallocOffWrench % 256 == 0 && kNoallocOffResets % 256 == 0 && kNoallocOffHits % 256 == 0,
-              "scratch sub-arrays must stay 256-byte aligned");
-
-constexpr int kNoallocMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-unsigned char* g_noalloc_base[kNoallocMaxDevices] = {};
-
-void noalloc_error(char* buf, size_t len, const char* msg) {
-  if (buf && len) std::snprintf(buf, len, "%s", msg);
-}
-
-bool is_device_pointer(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-}  // namespace
-
-// The scratch itself. Host code must not use this name as an address: it is a
-// host-side stand-in for the symbol; the device address comes from
-// cudaGetSymbolAddress below, once per device.
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
-
-extern "C" ag_status ag_step_plain_noalloc(const ag_config* cfg, void* cuda_stream, uint32_t n_substeps,
-                                           uint64_t seed, float* state, float* motors, const float* body,
-                                           const uint8_t* modes, const float* targets, const float* boxes,
-                                           uint32_t* epoch, uint8_t* collided, uint32_t* reset_ids,
-                                           uint32_t* n_reset, char* err, size_t err_len) {
-  noalloc_error(err, err_len, "");
-  const char* why = validate(cfg);
-  if (why[0] != '\0') {
-    noalloc_error(err, err_len, why);
-    return AG_ERR_INVALID;
-  }
-  if (cfg->n_envs > AG_NOALLOC_MAX_ENVS) {
-    noalloc_error(err, err_len, "n_envs exceeds AG_NOALLOC_MAX_ENVS (65536): use a context (ag_create) instead");
-    return AG_ERR_INVALID;
-  }
-  if (n_substeps == 0 || n_substeps % cfg->substeps_per_step != 0) {
-    noalloc_error(err, err_len, "n_substeps must be a positive multiple of substeps_per_step");
-    return AG_ERR_INVALID;
-  }
-  const void* required[] = {state, motors, body, modes, targets, epoch, collided, reset_ids, n_reset};
-  for (const void* p : required)
-    if (!p || !is_device_pointer(p)) {
-      noalloc_error(err, err_len, "every buffer must be a non-NULL device pointer");
-      return AG_ERR_INVALID;
-    }
-  if (cfg->n_obstacles > 0 && (!boxes || !is_device_pointer(boxes))) {
-    noalloc_error(err, err_len, "boxes must be a device pointer when n_obstacles > 0");
-    return AG_ERR_INVALID;
-  }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
-    noalloc_error(err, err_len, "no usable CUDA device");
-    return AG_ERR_CUDA;
-  }
-  unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_base[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        noalloc_error(err, err_len, cudaGetErrorString(e));
-        return AG_ERR_CUDA;
-      }
-      g_noalloc_base[dev] = static_cast<unsigned char*>(p);
-    }
-    base = g_noalloc_base[dev];
-  }
-  agk::FleetBuffers fb;
-  std::memset(&fb, 0, sizeof(fb));
-  fb.state = state;
-  fb.motors = motors;
-  fb.body = const_cast<float*>(body);
-  fb.modes = const_cast<uint8_t*>(modes);
-  fb.targets = const_cast<float*>(targets);
-  fb.boxes = const_cast<float*>(boxes);
-  fb.epoch = epoch;
-  fb.collided = collided;
-  fb.reset_ids = reset_ids;
-  fb.n_reset = n_reset;
-  fb.cmd = reinterpret_cast<float*>(base + kNoallocOffCmd);
-  fb.wrench = reinterpret_cast<float*>(base + kNoallocOffWrench);
-  fb.resets = reinterpret_cast<uint32_t*>(base + kNoallocOffResets);
-  fb.hits = base + kNoallocOffHits;
-  fb.n = cfg->n_envs;
-  fb.n_quad = cfg->n_quad;
-  fb.n_hexa = cfg->n_hexa;
-  fb.n_octo = cfg->n_octo;
-  fb.n_obs = cfg->n_obstacles;
-  agk::StepParams P;
-  for (int i = 0; i < 3; ++i) {
-    P.kx[i] = cfg->kx[i]; P.kv[i] = cfg->kv[i]; P.kR[i] = cfg->kR[i]; P.kW[i] = cfg->kW[i];
-  }
-  for (int t = 0; t < 3; ++t) rotor_matrices(t == 0 ? 4 : (t == 1 ? 6 : 8), cfg->arm, cfg->k_yaw, P.A[t], P.Ap[t]);
-  const double h = (double)cfg->dt / cfg->substeps_per_step;
-  P.h = (float)h;
-  P.alpha = cfg->motor_tau > 0.f ? (float)(1.0 - std::exp(-h / (double)cfg->motor_tau)) : 1.f;
-  P.drag = cfg->drag;
-  P.r2 = cfg->sphere_r * cfg->sphere_r;
-  P.u_max = cfg->u_max;
-  P.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
-  P.seed_hi = (uint32_t)(seed >> 32);
-  e = agk::launch_plain_step(fb, P, (int)cfg->integrator, (int)(n_substeps / cfg->substeps_per_step),
-                             (int)cfg->substeps_per_step, (cudaStream_t)cuda_stream);
-  if (e != cudaSuccess) {
-    noalloc_error(err, err_len, cudaGetErrorString(e));
-    return AG_ERR_CUDA;
-  }
-  return AG_OK;
-}
