@@ -399,16 +399,20 @@ def depth_part(seed: int, world: int) -> dict:
 def task_part(seed: int, world: int) -> dict:
     """Reach-a-setpoint task steps (ag_reach_step: actions to attitude
     commands, one fleet step, reward, termination, auto-reset, observations)
-    over 1,048,576 quads, semi-implicit Euler, 1 substep, no obstacles."""
+    over 1,048,576 quads, semi-implicit Euler, 1 substep, no obstacles; also
+    with 50 steps captured in a CUDA graph and replayed."""
     import torch
+    from paper_2305_16510_gb300 import _abi
     from paper_2305_16510_gb300.task import ReachEnv
     n = 1 << 20
     rng = np.random.default_rng(seed)
     goals = torch.from_numpy(rng.uniform(-1.0, 1.0, (3, n)).astype(np.float32))
-    env = ReachEnv(n, goals=goals, seed=seed)
-    env.reset()
-    actions = torch.from_numpy(rng.uniform(-0.3, 0.3, (n, 4)).astype(np.float32)).cuda()
-    from paper_2305_16510_gb300 import _abi
+    side = torch.cuda.Stream()          # graph capture needs a stream other than the legacy default one
+    with torch.cuda.stream(side):
+        env = ReachEnv(n, goals=goals, seed=seed, stream=side)
+        env.reset()
+        actions = torch.from_numpy(rng.uniform(-0.3, 0.3, (n, 4)).astype(np.float32)).cuda()
+    torch.cuda.synchronize()
 
     def step():
         _abi.ag_reach_step(env.fleet.ctx, actions, env.obs, env.reward, env.done)
@@ -416,12 +420,22 @@ def task_part(seed: int, world: int) -> dict:
     for _ in range(5):
         step()
     torch.cuda.synchronize()
-    k = 200
+    k, per_graph = 200, 50
     secs, per = time_calls(env.fleet, step, k, world)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        for _ in range(per_graph):
+            step()
+    with torch.cuda.stream(side):
+        g.replay()
+        torch.cuda.synchronize()
+        secs_g, _ = time_calls(env.fleet, g.replay, k // per_graph, world)
     env.close()
     return {"value": n * k * world / secs, "unit": "task env-steps/s", "ms_per_step": float(np.mean(per)),
             "workload": "reach-a-setpoint, 1,048,576 quads, attitude interface, SIE 1 substep, no obstacles, "
-                        "obs [n,13] + reward + done per step", "launches_per_step": 1}
+                        "obs [n,13] + reward + done per step", "launches_per_step": 1,
+            "cuda_graph": {"value": n * k * world / secs_g, "ms_per_step": secs_g * 1e3 / k,
+                           "steps_per_graph": per_graph}}
 
 
 # ----------------------------------------------------------------- adjoint --

@@ -321,7 +321,11 @@ ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, fl
  * step counter of every ended episode returns to 0. The observation then
  * describes the state the policy acts on next (after any reset):
  *   obs[i] = (p - g (3), v (3), q (w, x, y, z) with w >= 0 (4), Omega (3))
- * One kernel launch does all of it per environment; nothing synchronises.
+ * One kernel launch does all of it per environment; nothing synchronises
+ * and nothing is allocated after ag_reach_begin, so a training loop can
+ * capture ag_reach_step in a CUDA graph on the context's stream (a stream
+ * other than the legacy default one) and replay it; replays give the same
+ * bits as direct calls.
  * ------------------------------------------------------------------------ */
 typedef struct ag_reach_config {
   uint32_t command_mode;   /* AG_MODE_ATT_THRUST or AG_MODE_BODY_VEL */

@@ -207,3 +207,55 @@ def test_reach_full_size_sampled_against_oracle():
         steps = np.where(g_done == 1, 0, steps + 1).astype(np.uint32)
     assert ended == len(idx)          # every sampled episode ended at its second step
     env.close()
+
+
+def test_reach_steps_captured_in_a_cuda_graph_replay_bit_exactly():
+    """ag_reach_step issues one kernel on the context's stream and neither
+    allocates nor synchronises, so a training loop can capture it in a CUDA
+    graph: 8 captured steps replayed 3 times equal 24 direct steps bit for
+    bit, collision and time-limit resets included."""
+    w = W.Workload("reach_graph", 2048, 4, 1, 8, 2048, 0, 0)
+    cfg = _cfg(_abi.AG_MODE_ATT_THRUST, max_steps=5, max_dist=3.0)
+    rng = np.random.default_rng(3)
+    goals = torch.from_numpy(rng.uniform(-1, 1, (3, w.n_envs)).astype(np.float32)).cuda()
+    acts = [torch.from_numpy(rng.uniform(-1, 1, (w.n_envs, 4)).astype(np.float32)).cuda() for _ in range(8)]
+    from paper_2305_16510_gb300.fleet import Fleet
+    torch.cuda.synchronize()
+    results = []
+    for use_graph in (False, True):
+        side = torch.cuda.Stream()          # capture needs a stream other than the legacy default one
+        with torch.cuda.stream(side):
+            inp = W.make_inputs(w, 4)
+            fl = Fleet(w.n_envs, substeps_per_step=4, integrator=1, n_obstacles=8, seed=4, stream=side)
+            fl.set_body(inp.body)
+            fl.set_commands(inp.modes, inp.targets)
+            fl.set_obstacles(inp.boxes)
+            fl.reset(None, 4)
+            _abi.ag_reach_begin(fl.ctx, cfg, goals)
+            obs = torch.empty((w.n_envs, 13), device=fl.device)
+            rew = torch.empty((w.n_envs,), device=fl.device)
+            done = torch.empty((w.n_envs,), dtype=torch.uint8, device=fl.device)
+            dones = torch.zeros((w.n_envs,), dtype=torch.int32, device=fl.device)
+        torch.cuda.synchronize()
+
+        def steps():
+            for a in acts:
+                _abi.ag_reach_step(fl.ctx, a, obs, rew, done)
+                dones.add_(done)
+
+        if use_graph:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                steps()
+            for _ in range(3):
+                g.replay()
+        else:
+            with torch.cuda.stream(side):
+                for _ in range(3):
+                    steps()
+        torch.cuda.synchronize()
+        results.append((_np(fl.state()), _np(fl.epoch()), _np(obs), _np(rew), _np(dones)))
+        fl.close()
+    for a, b in zip(*results):
+        np.testing.assert_array_equal(a, b)
+    assert results[0][4].sum() > 0                 # episodes ended (and restarted) during the 24 steps
