@@ -22,14 +22,19 @@
 // three reciprocals and the slab intervals; records are read as four
 // broadcast 16-byte loads and reused for the thread's four pixels.
 //
-// Once per block, for each of its tiles, the block culls, conservatively, the
-// boxes that no ray of the tile can reach closer than max_range: the box's
-// bounding sphere (centre
+// Once per block, warp w culls for the block's tile w, conservatively, the
+// boxes that no ray of the tile can reach closer than max_range, and lists
+// the live ones (ballot and popc), so the tile's loop visits only those. A
+// box is culled when its bounding sphere (centre
 // s in the camera frame, radius |h| with a rounding margin) lies beyond
 // max_range along the axis, behind the camera, or outside one of the four
 // planes through the camera origin that bound the tile's rays (y = dy x and
 // z = dz x at the tile's extreme pixel centres). A culled box can change no
-// pixel of the tile, so the image is the same as without culling.
+// pixel of the tile, so the image is the same as without culling. When each
+// component of a live box's ray direction keeps one sign over the tile, the
+// near and far slab bound of every axis is known for the whole tile, and the
+// per-pixel min / max of the slab pairs is skipped (it would pick the same
+// products).
 #include <cmath>
 #include <cstdint>
 
@@ -118,10 +123,45 @@ __device__ __forceinline__ bool sphere_culled(float4 s, const TileRays& t, float
   return false;
 }
 
+// Flags of a live (tile, box) pair: kLive, and kFixedSigns when each
+// component of the box-frame ray direction M (1, y, z) keeps one sign over
+// the whole tile (it is linear in y and z, so the four corner rays decide,
+// with a margin far above float32 rounding); then bit kNegX + i says that
+// component i is negative, which fixes which slab bound is near and which is
+// far for every pixel of the tile.
+constexpr uint8_t kLive = 1, kFixedSigns = 2, kNegX = 2;
+
+__device__ __forceinline__ uint8_t slab_signs(const float4* rec, const TileRays& t) {
+  const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2];
+  // rows (M_i0, M_i1, M_i2) of M
+  const float m[3][3] = {{r0.x, r0.y, r0.z}, {r0.w, r1.x, r1.y}, {r1.z, r1.w, r2.x}};
+  const float ys[2] = {t.ylo, t.yhi}, zs[2] = {t.zlo, t.zhi};
+  uint8_t f = kLive | kFixedSigns;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    bool pos = true, neg = true;
+    const float scale = fabsf(m[i][0]) + fmaxf(fabsf(t.ylo), fabsf(t.yhi)) * fabsf(m[i][1]) +
+                        fmaxf(fabsf(t.zlo), fabsf(t.zhi)) * fabsf(m[i][2]);
+    const float margin = 1e-5f * scale;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float d = m[i][0] + ys[c & 1] * m[i][1] + zs[c >> 1] * m[i][2];
+      pos &= d > margin;
+      neg &= d < -margin;
+    }
+    if (!pos && !neg) return kLive;          // the sign changes (or nearly) inside the tile
+    if (neg) f |= (uint8_t)(1u << (kNegX + i));
+  }
+  return f;
+}
+
 __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
   __shared__ float4 recs[AG_MAX_OBSTACLES * 4];
   __shared__ float4 spheres[AG_MAX_OBSTACLES];
-  __shared__ uint8_t live[kDepthTilesPerBlock][AG_MAX_OBSTACLES];  // per tile of the block
+  // per tile of the block: the live boxes (index, flags) in box order, and their number
+  __shared__ uint8_t live_k[kDepthTilesPerBlock][AG_MAX_OBSTACLES];
+  __shared__ uint8_t live_f[kDepthTilesPerBlock][AG_MAX_OBSTACLES];
+  __shared__ int n_live[kDepthTilesPerBlock];
   // block -> (camera, group of kDepthTilesPerBlock consecutive tiles); cameras cam0, cam0 + 1, ...
   const uint32_t tiles_x = (a.width + kDepthTile - 1) / kDepthTile;
   const uint32_t tiles = tiles_x * ((a.height + kDepthTile - 1) / kDepthTile);
@@ -143,27 +183,42 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
     }
   }
   __syncthreads();
-  // ... then the cull flags of every (tile, box) pair of the block
-  const int pairs = (int)(t_end - t_begin) * n_obs;
-  for (int q = threadIdx.x; q < pairs; q += kDepthThreads) {
-    const uint32_t tl = (uint32_t)(q / n_obs), k = (uint32_t)(q % n_obs), t = t_begin + tl;
-    const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
-    const uint32_t x1 = min(x0 + kDepthTile, a.width) - 1, y1 = min(y0 + kDepthTile, a.height) - 1;
-    TileRays r;
-    r.yhi = -((float)x0 + 0.5f - half_w) * a.inv_f;
-    r.ylo = -((float)x1 + 0.5f - half_w) * a.inv_f;
-    r.zhi = -((float)y0 + 0.5f - half_h) * a.inv_f;
-    r.zlo = -((float)y1 + 0.5f - half_h) * a.inv_f;
-    r.nyhi = sqrtf(1.f + r.yhi * r.yhi);
-    r.nylo = sqrtf(1.f + r.ylo * r.ylo);
-    r.nzhi = sqrtf(1.f + r.zhi * r.zhi);
-    r.nzlo = sqrtf(1.f + r.zlo * r.zlo);
-    live[tl][k] = sphere_culled(spheres[k], r, a.max_range) ? 0 : 1;
+  // ... then warp w culls the boxes for tile w of the block and lists the live ones
+  static_assert(kDepthThreads / 32 == kDepthTilesPerBlock, "one warp per tile");
+  {
+    const uint32_t w = threadIdx.x / 32, lane = threadIdx.x % 32, t = t_begin + w;
+    if (t < t_end) {
+      const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
+      const uint32_t x1 = min(x0 + kDepthTile, a.width) - 1, y1 = min(y0 + kDepthTile, a.height) - 1;
+      TileRays r;
+      r.yhi = -((float)x0 + 0.5f - half_w) * a.inv_f;
+      r.ylo = -((float)x1 + 0.5f - half_w) * a.inv_f;
+      r.zhi = -((float)y0 + 0.5f - half_h) * a.inv_f;
+      r.zlo = -((float)y1 + 0.5f - half_h) * a.inv_f;
+      r.nyhi = sqrtf(1.f + r.yhi * r.yhi);
+      r.nylo = sqrtf(1.f + r.ylo * r.ylo);
+      r.nzhi = sqrtf(1.f + r.zhi * r.zhi);
+      r.nzlo = sqrtf(1.f + r.zlo * r.zlo);
+      int count = 0;
+      for (int k0 = 0; k0 < n_obs; k0 += 32) {  // warp-uniform loop
+        const int k = k0 + (int)lane;
+        uint8_t f = 0;
+        if (k < n_obs && !sphere_culled(spheres[k], r, a.max_range)) f = slab_signs(recs + 4 * k, r);
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, f != 0);
+        if (f) {
+          const int at = count + __popc(m & ((1u << lane) - 1u));
+          live_k[w][at] = (uint8_t)k;
+          live_f[w][at] = f;
+        }
+        count += __popc(m);
+      }
+      if (lane == 0) n_live[w] = count;
+    }
   }
   __syncthreads();
   for (uint32_t t = t_begin; t < t_end; ++t) {
     const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
-    const uint8_t* lv = live[t - t_begin];
+    const int tl = (int)(t - t_begin);
     const uint32_t col = x0 + tx;
     const float dy = -((float)col + 0.5f - half_w) * a.inv_f;
     float dz[kDepthPix], best[kDepthPix];
@@ -172,11 +227,30 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
       dz[p] = -((float)(y0 + ty + p * kDepthRows) + 0.5f - half_h) * a.inv_f;
       best[p] = a.max_range;
     }
-    for (int k = 0; k < n_obs; ++k) {
-      if (!lv[k]) continue;  // the same for the whole block
+    for (int j = 0; j < n_live[tl]; ++j) {  // the same for the whole block
+      const int k = live_k[tl][j];
+      const uint8_t flags = live_f[tl][j];
       const float4 r0 = recs[4 * k], r1 = recs[4 * k + 1], r2 = recs[4 * k + 2], r3 = recs[4 * k + 3];
       // the column's part of M (1, dy, dz), shared by the thread's four pixels
       const float cx = fmaf(dy, r0.y, r0.x), cy = fmaf(dy, r1.x, r0.w), cz = fmaf(dy, r1.w, r1.z);
+      if (flags & kFixedSigns) {
+        // slab bounds lo = (r2.y, r2.z, r2.w), hi = (r3.x, r3.y, r3.z): near is lo for a positive
+        // direction component, hi for a negative one (the same min / max as below, known in advance)
+        const bool nx = flags & (1u << kNegX), ny = flags & (2u << kNegX), nz = flags & (4u << kNegX);
+        const float near_x = nx ? r3.x : r2.y, far_x = nx ? r2.y : r3.x;
+        const float near_y = ny ? r3.y : r2.z, far_y = ny ? r2.z : r3.y;
+        const float near_z = nz ? r3.z : r2.w, far_z = nz ? r2.w : r3.z;
+#pragma unroll
+        for (int p = 0; p < kDepthPix; ++p) {
+          const float ix = __fdividef(1.f, fmaf(dz[p], r0.z, cx));
+          const float iy = __fdividef(1.f, fmaf(dz[p], r1.y, cy));
+          const float iz = __fdividef(1.f, fmaf(dz[p], r2.x, cz));
+          const float t_in = fmaxf(fmaxf(0.f, near_x * ix), fmaxf(near_y * iy, near_z * iz));
+          const float t_out = fminf(fminf(best[p], far_x * ix), fminf(far_y * iy, far_z * iz));
+          if (t_in <= t_out) best[p] = t_in;
+        }
+        continue;
+      }
 #pragma unroll
       for (int p = 0; p < kDepthPix; ++p) {
         const float ix = __fdividef(1.f, fmaf(dz[p], r0.z, cx));
