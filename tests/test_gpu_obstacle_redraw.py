@@ -117,3 +117,44 @@ def test_disable_keeps_boxes():
         fl.set_obstacle_randomization(ENV_MIN, ENV_MAX, bad)
     assert e.value.status == _abi.AG_ERR_INVALID
     fl.close()
+
+
+@pytest.mark.parametrize("identity_order", [False, True], ids=["grouped", "ungrouped"])
+def test_boxes_redrawn_mid_launch_are_the_ones_tested_next(identity_order, monkeypatch):
+    """One fused launch of 30 steps over a quad / hexa / octo fleet with 12
+    boxes (pair 0 in registers, five pairs staged in shared memory): a box
+    re-drawn by a collision reset inside the launch must be the box the later
+    steps of that launch test. The oracle steps the same fleet 30 times; envs
+    whose distance to a box comes within 1e-5 m^2 of the radius at any step
+    (float32 / float64 near-ties) are left out."""
+    if identity_order:
+        monkeypatch.setenv("AG_FUSED_ORDER", "identity")
+    w = W.Workload("redraw_ms", 2000, 4, 1, 12, 800, 800, 400, mode_mix=(0, 1, 2))
+    fl, inp, world = _pair(w, 57)
+    fl.reset(None, 57)
+    s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
+    b0 = _np(fl.obstacles())
+    fl.step(30)
+    s1, b1, e1 = _np(fl.state()), _np(fl.obstacles()), _np(fl.epoch()).astype(np.uint32)
+    col = _np(fl.events()[0])
+    fl.close()
+    cur = W.Inputs(inp.modes, inp.targets, inp.body, b0)
+    orc = oracle_fleet_from(w, cur, s0, m0, e0, 57)
+    world_free = O.World(**{**world.__dict__, "n_obs": 0, "box_specs": None})
+    ok = np.ones(w.n_envs, bool)
+    any_hit = np.zeros(w.n_envs, np.uint8)
+    for _ in range(30):
+        pre = oracle_fleet_from(w, W.Inputs(inp.modes, inp.targets, inp.body, None), orc.state, orc.motors,
+                                orc.epoch, 57)
+        O.rollout(world_free, pre, 1)
+        ok &= np.abs(box_margin(pre.state[0:3], orc.boxes)) >= 1e-5
+        c, _ = O.rollout(world, orc, 1)
+        any_hit |= c
+    assert ok.mean() > 0.97
+    redrawn = ok & (e1 - e0 >= 2)          # reset twice or more: a re-drawn box was hit again
+    assert (ok & (e1 > e0)).sum() > 20 and redrawn.sum() > 0
+    np.testing.assert_array_equal(e1[ok], orc.epoch[ok])
+    np.testing.assert_array_equal(col[ok], any_hit[ok])
+    np.testing.assert_array_equal(b1[:, :, ok], orc.boxes[:, :, ok].astype(np.float32))
+    dp, _, dang, _ = max_state_errors(s1[:, ok], orc.state[:, ok])
+    assert dp.max() <= 1e-4 * (1 + np.abs(orc.state[0:3, ok]).max()) and dang.max() <= 1e-4
