@@ -116,25 +116,27 @@ __global__ void __launch_bounds__(kTaskBlock, BOXES ? 3 : 8) k_reach_step(ReachA
     for (int k = 0; k < 4; ++k) t[k] = fmaf(a.scale[k], fminf(fmaxf(v[k], -1.f), 1.f), a.offset[k]);
     const Command cm = prepare_command(fb.modes[i], t[0], t[1], t[2], t[3]);
     const int nrot = rotor_count(fb, i);
+    // environment i's place in the slot-ordered box copy (a re-draw updates it there)
+    const uint32_t slot = fb.slot_of ? fb.slot_of[i] : i;
     const int n_obs = (int)fb.n_obs;
     bool hit = false;
     VState s;
     if (BOXES) {
       EnvBoxPairs bx{fb.boxes, n, i};
       if (nrot == 4)
-        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
       else if (nrot == 6)
-        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
       else
-        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
     } else {
       NoBoxSource none;
       if (nrot == 4)
-        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
       else if (nrot == 6)
-        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
       else
-        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, i, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
     }
     fb.collided[i] = hit ? 1 : 0;
 #pragma unroll

@@ -48,20 +48,33 @@ def _params(c):
 
 CASES = [
     # RK4, 4 substeps, boxes (collisions end episodes), attitude interface
-    (W.Workload("reach_att", 3000, 4, 1, 8, 3000, 0, 0), _abi.AG_MODE_ATT_THRUST),
+    (W.Workload("reach_att", 3000, 4, 1, 8, 3000, 0, 0), _abi.AG_MODE_ATT_THRUST, False),
+    # the same with obstacle re-placement on every reset, quad / hexa / octo
+    (W.Workload("reach_redraw", 3000, 4, 1, 8, 1200, 1200, 600), _abi.AG_MODE_ATT_THRUST, True),
     # semi-implicit Euler, quad / hexa / octo, no boxes, velocity interface
-    (W.Workload("reach_vel", 2500, 1, 0, 0, 1000, 1000, 500, drag=0.1), _abi.AG_MODE_BODY_VEL),
+    (W.Workload("reach_vel", 2500, 1, 0, 0, 1000, 1000, 500, drag=0.1), _abi.AG_MODE_BODY_VEL, False),
 ]
+ENV_MIN, ENV_MAX = (-5.0, -5.0, -5.0), (5.0, 5.0, 5.0)
 
 
-@pytest.mark.parametrize("w,mode", CASES, ids=[c[0].name for c in CASES])
-def test_reach_step_matches_oracle(w, mode):
+def _box_specs(n_obs):
+    kw = [dict(pos_min=(0.2, 0.2, 0.2), pos_max=(0.8, 0.8, 0.8), euler_min=(-1, -1, -3), euler_max=(1, 1, 3),
+               lock=0, fixed=[0.0] * 6) for _ in range(n_obs)]
+    return [_abi.box_randomization(**k) for k in kw], [O.box_rand(**k) for k in kw]
+
+
+@pytest.mark.parametrize("w,mode,redraw", CASES, ids=[c[0].name for c in CASES])
+def test_reach_step_matches_oracle(w, mode, redraw):
     from harness import gpu_fleet
     seed = 23
     inp = W.make_inputs(w, seed)
     fl = gpu_fleet(w, inp, seed)
     world = oracle_world(w)
-    world_free = O.World(**{**world.__dict__, "n_obs": 0})
+    if redraw:
+        sg, so = _box_specs(w.n_obstacles)
+        fl.set_obstacle_randomization(ENV_MIN, ENV_MAX, sg)
+        world = O.World(**{**world.__dict__, "env_min": ENV_MIN, "env_max": ENV_MAX, "box_specs": so})
+    world_free = O.World(**{**world.__dict__, "n_obs": 0, "box_specs": None})
     rng = np.random.default_rng(5)
     goals = rng.uniform(-1.0, 1.0, (3, w.n_envs)).astype(np.float32)
     cfg = _cfg(mode, max_steps=3, max_dist=3.0)
@@ -77,6 +90,7 @@ def test_reach_step_matches_oracle(w, mode):
     seen = {"collided": 0, "far": 0, "timeout": 0}
     for _ in range(7):
         s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
+        b0 = _np(fl.obstacles()) if w.n_obstacles else None
         act = rng.uniform(-1.3, 1.3, (w.n_envs, 4)).astype(np.float32)
         _abi.ag_reach_step(fl.ctx, torch.from_numpy(act).to(dev), obs, rew, done)
         g_obs, g_rew, g_done = _np(obs), _np(rew), _np(done)
@@ -84,7 +98,7 @@ def test_reach_step_matches_oracle(w, mode):
         g_epoch = _np(fl.epoch())
         # oracle: commands, one step, score, end, re-draw, observe
         tgt = (offset[:, None] + scale[:, None] * np.clip(act.T.astype(np.float64), -1.0, 1.0))
-        cur = W.Inputs(modes, tgt, inp.body, inp.boxes)
+        cur = W.Inputs(modes, tgt, inp.body, b0)
         orc = oracle_fleet_from(w, cur, s0, m0, e0, seed)
         ocol, _ = O.rollout(world, orc, 1)
         nxt = steps + 1
@@ -97,11 +111,13 @@ def test_reach_step_matches_oracle(w, mode):
         if w.n_obstacles:
             pre = oracle_fleet_from(w, W.Inputs(modes, tgt, inp.body, None), s0, m0, e0, seed)
             O.rollout(world_free, pre, 1)
-            ok &= np.abs(box_margin(pre.state[0:3], inp.boxes.astype(np.float64))) >= 1e-5
+            ok &= np.abs(box_margin(pre.state[0:3], b0.astype(np.float64))) >= 1e-5
         assert ok.mean() > 0.99
         np.testing.assert_array_equal(g_col[ok], ocol[ok])
         np.testing.assert_array_equal(g_done[ok], o_done[ok])
         np.testing.assert_array_equal(g_epoch[ok], orc.epoch[ok])
+        if w.n_obstacles:   # re-drawn (or kept) boxes, bit for bit
+            np.testing.assert_array_equal(_np(fl.obstacles())[:, :, ok], orc.boxes[:, :, ok].astype(np.float32))
         hit = ok & (ocol == 1)
         assert np.all(g_rew[hit] == np.float32(-cfg.crash))
         free = ok & (ocol == 0)
