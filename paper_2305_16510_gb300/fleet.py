@@ -93,6 +93,15 @@ class Fleet:
         self._keep_ids = ids
         return out
 
+    def eval_controller(self, state=None) -> torch.Tensor:
+        """float32 [4, n] commanded (f, M_x, M_y, M_z) of every environment's
+        controller at `state` [13, n] (None = the current states); see ag_eval_controller."""
+        s = None if state is None else self._dev(state, torch.float32)
+        out = torch.empty((4, self.n), dtype=torch.float32, device=self.device)
+        _abi.ag_eval_controller(self.ctx, s, out)
+        self._keep_eval = s
+        return out
+
     def set_body(self, body) -> None:
         b = self._dev(body, torch.float32)
         _abi.ag_set_body(self.ctx, b)

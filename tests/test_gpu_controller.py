@@ -72,6 +72,7 @@ def test_controller_matches_oracle_in_every_mode():
     out2 = torch.empty((4, n), device=fl.device)
     _abi.ag_eval_controller(fl.ctx, None, out2)
     np.testing.assert_array_equal(out2.cpu().numpy(), got.astype(np.float32))
+    np.testing.assert_array_equal(fl.eval_controller().cpu().numpy(), got.astype(np.float32))
     fl.close()
 
     ref = np.zeros((4, n))
