@@ -307,16 +307,16 @@ def test_invalid_arguments_leave_context_usable():
 
 # ----------------------------------------- full size, sampled, bench launch --
 def test_full_size_obstacle_fleet_sampled_against_oracle():
-    """1,048,576 quads, 16 boxes each, one ag_step of 100 steps (the launch the
-    bench times); 384 sampled envs are re-simulated by the oracle step by step
-    from the same initial draw, near-tie envs excluded."""
+    """1,048,576 quads, 16 boxes each, one ag_step of 1,000 steps (the launch
+    the bench times); 384 sampled envs are re-simulated by the oracle step by
+    step from the same initial draw, near-tie envs excluded."""
     w = W.WORKLOADS["obstacles"]
     seed = 1
     inp = W.make_inputs(w, seed)
     fl = gpu_fleet(w, inp, seed)
     fl.reset(None, seed)
     s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
-    fl.step(100)
+    fl.step(1000)
     s1 = _np(fl.state())
     col = _np(fl.events()[0])
     e1 = _np(fl.epoch()).astype(np.uint32)
@@ -328,7 +328,7 @@ def test_full_size_obstacle_fleet_sampled_against_oracle():
     orc = oracle_fleet_from(ws, ins, s0[:, idx], m0[:, idx], e0[idx], seed)
     ok = np.ones(len(idx), bool)
     any_hit = np.zeros(len(idx), np.uint8)
-    for _ in range(100):
+    for _ in range(1000):
         # near-tie check on the pre-collision position of this step
         pre = oracle_fleet_from(ws, ins, orc.state, orc.motors, orc.epoch, seed)
         pre.boxes = None
@@ -347,9 +347,9 @@ def test_full_size_obstacle_fleet_sampled_against_oracle():
 
 def test_full_size_mixed_fleet_with_reset_masks_sampled_against_oracle():
     """4,194,304 vehicles (40 % quad, 40 % hexa, 20 % octo), randomised mass and
-    inertia, drag, body-velocity commands: 150 steps in calls of 50 with a 1 %
-    Bernoulli reset mask after each call. The reset words of the whole fleet
-    are compared bit for bit; 384 sampled envs are re-simulated by the oracle."""
+    inertia, drag, body-velocity commands: the workload's 500 steps in calls of
+    50 with a 1 % Bernoulli reset mask after each call. The reset words are
+    compared bit for bit; 384 sampled envs are re-simulated by the oracle."""
     w = W.WORKLOADS["mixed"]
     seed = 4
     inp = W.make_inputs(w, seed)
@@ -362,7 +362,7 @@ def test_full_size_mixed_fleet_with_reset_masks_sampled_against_oracle():
     orc = oracle_fleet_from(ws, ins, s0[:, idx], m0[:, idx], e0[idx], seed)
     world = oracle_world(ws)
     rng = np.random.default_rng(6)
-    for call in range(3):
+    for call in range(10):
         fl.step(50)
         O.rollout(world, orc, 50)
         mask = W.reset_mask(w.n_envs, 0.01, rng)
