@@ -18,6 +18,11 @@
 //   * Sec. I / IV-B last sentence: force and torque applied to a rigid body;
 //     the 6-DoF dynamics, rotor allocation, motor lag, collision and reset
 //     are the readings listed in each function's comment.
+//   * Sec. III (depth cameras) and Sec. I / VII (kernel-based ray casting):
+//     ray_box_depth, the slab method for a pinhole camera's rays.
+//   * Sec. V (obstacle poses re-drawn on reset): philox_sampler.hpp.
+//   * Sec. I (learning to reach a goal setpoint): the task's observation,
+//     reward and termination in oracle_capi.cpp (orc_reach_task).
 //
 // Every function is a template on the scalar type T so the same code runs
 // in double (the oracle), in an op-counting scalar (algorithmic FLOPs per
