@@ -40,7 +40,7 @@ struct FleetBuffers {
   uint32_t* order;     // [n]     thread slot -> env, grouped by rotor type and mode (NULL = identity)
   float2* boxes_slot;  // [ceil(n_obs/2)][10][n] the boxes in slot order, in pairs: element
                        // (j*10 + f)*n + i = (field f of box 2j, of box 2j+1) of env order[i],
-                       // with the orientation's vector part (fields 7-9) doubled
+                       // in the staged form of staged_field (-c, -h, -w, 2u)
   uint32_t* slot_of;   // [n]     inverse of order (NULL when no obstacle re-draw is needed)
   const BoxRandDev* box_rand;  // [n_obs] obstacle re-draw on reset (NULL = boxes keep their poses)
   uint32_t n, n_quad, n_hexa, n_octo, n_obs;

@@ -94,31 +94,33 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float box_pad_field(int f) { return f < 3 ? 1e30f : (f == 6 ? 1.f : 0.f); }
 
 // Staged form of box field f in the pair copies (the slot-ordered copy and
-// each thread's staged copy): the orientation's vector part u (fields 7-9)
-// is held doubled, which is exact, so that pair_hits needs no factor 2.
-__device__ __forceinline__ float staged_field(int f, float v) { return f >= 7 ? 2.f * v : v; }
+// each thread's staged copy): the centre, the half-extents and the
+// orientation's scalar part are held negated (-c, -h, -w) and its vector
+// part doubled (2u). Both are exact, and pair_hits then needs no negation
+// and no factor 2.
+__device__ __forceinline__ float staged_field(int f, float v) { return f >= 7 ? 2.f * v : -v; }
 
 // Sphere (squared radius r2, centre p) against two boxes at once; the ten
-// float2 hold (box a, box b) of: centre x y z, half-extents x y z, and the
-// orientation q = (w, u) staged as (w, 2u). With v = p - c and t = 2 u x v,
-// the box-frame point d = R_b^T v = v - w t + u x t is computed as
-// (v - w t) + 1/2 ((2u) x t); doubling and halving are exact, so d rounds as
-// the plain form would.
-__device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float r2, float2 cx, float2 cy, float2 cz,
-                                          float2 hx, float2 hy, float2 hz, float2 qw, float2 ux2, float2 uy2,
-                                          float2 uz2) {
-  const float2 vx = add2(px, neg2(cx)), vy = add2(py, neg2(cy)), vz = add2(pz, neg2(cz));
+// float2 hold (box a, box b) of the staged fields (see staged_field): -c,
+// -h, -w and 2u. With v = p - c and t = 2 u x v, the box-frame point
+// d = R_b^T v = v - w t + u x t is computed as (v - w t) + 1/2 ((2u) x t);
+// negation, doubling and halving are exact, so d rounds as the plain form
+// would.
+__device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float r2, float2 ncx, float2 ncy,
+                                          float2 ncz, float2 nhx, float2 nhy, float2 nhz, float2 nqw, float2 ux2,
+                                          float2 uy2, float2 uz2) {
+  const float2 vx = add2(px, ncx), vy = add2(py, ncy), vz = add2(pz, ncz);
   const float2 tx = fma2(uy2, vz, neg2(mul2(uz2, vy)));
   const float2 ty = fma2(uz2, vx, neg2(mul2(ux2, vz)));
   const float2 tz = fma2(ux2, vy, neg2(mul2(uy2, vx)));
   const float2 half = dup2(0.5f);
-  const float2 dx = fma2(half, fma2(uy2, tz, neg2(mul2(uz2, ty))), fma2(neg2(qw), tx, vx));
-  const float2 dy = fma2(half, fma2(uz2, tx, neg2(mul2(ux2, tz))), fma2(neg2(qw), ty, vy));
-  const float2 dz = fma2(half, fma2(ux2, ty, neg2(mul2(uy2, tx))), fma2(neg2(qw), tz, vz));
+  const float2 dx = fma2(half, fma2(uy2, tz, neg2(mul2(uz2, ty))), fma2(nqw, tx, vx));
+  const float2 dy = fma2(half, fma2(uz2, tx, neg2(mul2(ux2, tz))), fma2(nqw, ty, vy));
+  const float2 dz = fma2(half, fma2(ux2, ty, neg2(mul2(uy2, tx))), fma2(nqw, tz, vz));
   // excess over the half-extents, clamped at 0
-  const float2 ex = add2(make_float2(fabsf(dx.x), fabsf(dx.y)), neg2(hx));
-  const float2 ey = add2(make_float2(fabsf(dy.x), fabsf(dy.y)), neg2(hy));
-  const float2 ez = add2(make_float2(fabsf(dz.x), fabsf(dz.y)), neg2(hz));
+  const float2 ex = add2(make_float2(fabsf(dx.x), fabsf(dx.y)), nhx);
+  const float2 ey = add2(make_float2(fabsf(dy.x), fabsf(dy.y)), nhy);
+  const float2 ez = add2(make_float2(fabsf(dz.x), fabsf(dz.y)), nhz);
   const float2 mx = make_float2(fmaxf(ex.x, 0.f), fmaxf(ex.y, 0.f));
   const float2 my = make_float2(fmaxf(ey.x, 0.f), fmaxf(ey.y, 0.f));
   const float2 mz = make_float2(fmaxf(ez.x, 0.f), fmaxf(ez.y, 0.f));
