@@ -70,7 +70,7 @@ BYTES_PER_VEHICLE_LAUNCH = 4 * (26 + 8 + 4 + 4) + 1 + 8 + 4 * 160 + 1 + 4
 # dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu capture of
 # exactly this launch (795.15 MB + 69.06 MB). It scales with the fleet size
 # (each env is loaded and stored once per launch), not with the step count.
-TRAFFIC_BYTES_FULL_LAUNCH = 795.15e6 + 69.06e6
+TRAFFIC_BYTES_FULL_LAUNCH = 796.32e6 + 68.94e6
 
 
 def dist_env():
