@@ -233,6 +233,10 @@ def gpu_arm(args) -> dict | None:
     achieved_tflops = w.n_envs * C * FLOP_PER_VEHICLE_STEP / (launch_ms * 1e-3) / 1e12
     _, n_reset = fl.events()
     out = {}
+    # check of the derived ALU peak: an FMA-chain kernel of the library, run
+    # after the timed region on the same stream (about 0.2 s)
+    from paper_2305_16510_gb300 import _abi
+    fma_chain = _abi.ag_measure_fp32_peak(fl.stream.cuda_stream, iters=10000, reps=5)
 
     # ---- unfused comparison path (same fleet, same call size)
     if "plain" in parts:
@@ -249,7 +253,6 @@ def gpu_arm(args) -> dict | None:
 
     # ---- end to end through the C-ABI with host buffers: per call, upload the
     # commands from pinned host memory, step, read the state back
-    from paper_2305_16510_gb300 import _abi
     modes_h = torch.from_numpy(inp.modes).pin_memory()
     targets_h = torch.from_numpy(inp.targets).pin_memory()
     state_h = torch.empty((13, w.n_envs), dtype=torch.float32).pin_memory()
@@ -324,7 +327,13 @@ def gpu_arm(args) -> dict | None:
                      "traffic": TRAFFIC_BYTES_FULL_LAUNCH if w.n_envs == 1 << 20 else None,
                      "kernel": "k_fused_step<RK4, quad>", "launch_ms": launch_ms,
                      "flop_per_vehicle_step": FLOP_PER_VEHICLE_STEP,
-                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",
+                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz (MEASURED_PEAKS has no "
+                                    "FP32 figure)",
+                     "fma_chain_check": {
+                         "scalar_tflops": fma_chain["scalar_tflops"], "packed_tflops": fma_chain["packed_tflops"],
+                         "frac_of_packed": achieved_tflops / fma_chain["packed_tflops"],
+                         "what": "measured FMA-chain kernels (ag_measure_fp32_peak: scalar fmaf and packed "
+                                 "__ffma2_rn, best of 5, grid = SMs x resident blocks), run after the timed region"},
                      "algorithmic_bytes_per_launch": BYTES_PER_VEHICLE_LAUNCH * w.n_envs},
         "gpu_launches": args.steps,
         "clocks": clocks,

@@ -71,10 +71,16 @@ class ag_server_stats(ctypes.Structure):
                 ("hbm_used_bytes", ctypes.c_uint64)]
 
 
+class ag_fp32_peak(ctypes.Structure):
+    _fields_ = [("scalar_tflops", ctypes.c_double), ("packed_tflops", ctypes.c_double),
+                ("scalar_ms", ctypes.c_double), ("packed_ms", ctypes.c_double), ("grid", ctypes.c_uint32),
+                ("block", ctypes.c_uint32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
-# every symbol include/ag.h declares, with (restype, argtypes)
+# every symbol include/*.h declares, with (restype, argtypes)
 _vp = ctypes.c_void_p
 SIGNATURES = {
     "ag_abi_version": (ctypes.c_int, []),
@@ -94,6 +100,7 @@ SIGNATURES = {
     "ag_reset": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
     "ag_eval_controller": (ctypes.c_int, [_vp, _vp, _vp]),
     "ag_inject_failure": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "ag_measure_fp32_peak": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ag_fp32_peak)]),
     "ag_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),
     "ag_get_motors": (ctypes.c_int, [_vp, _vp, _vp]),
     "ag_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -246,6 +253,15 @@ def ag_step_plain(ctx: int, n_substeps: int) -> None:
 
 def ag_inject_failure(ctx: int, why: str | None = None) -> None:
     _check(lib().ag_inject_failure(ctx, why.encode() if why else None), "ag_inject_failure", ctx)
+
+
+def ag_measure_fp32_peak(stream: int = 0, iters: int = 10000, reps: int = 5, out=None) -> dict:
+    """FP32 FMA-chain throughput of the current device (include/ag_measure.h).
+    `out` may be given to receive the raw struct (used to pass NULL in tests)."""
+    r = ag_fp32_peak()
+    rc = lib().ag_measure_fp32_peak(stream or None, iters, reps, ctypes.byref(r) if out is None else out)
+    _check(rc, "ag_measure_fp32_peak", None)
+    return {k: getattr(r, k) for k, _ in ag_fp32_peak._fields_}
 
 
 def ag_eval_controller(ctx: int, state, wrench) -> None:

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(PKG, LIB_NAME)
 BUILD_DIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["ag_api.cu", "ag_api_task.cu", "ag_api_adjoint.cu", "ag_api_noalloc.cu", "fleet_kernels.cu",
-                "adjoint.cu", "serve.cu", "depth.cu", "task.cu"]
+                "adjoint.cu", "serve.cu", "depth.cu", "task.cu", "measure.cu"]
 
 
 def _nvcc() -> str:

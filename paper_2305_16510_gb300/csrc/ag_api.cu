@@ -27,6 +27,8 @@ thread_local std::string g_create_error;
 
 namespace agh {
 
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+
 ag_status fail_invalid(ag_ctx* ctx, const std::string& msg) {
   if (ctx) ctx->err = msg;
   else g_create_error = msg;

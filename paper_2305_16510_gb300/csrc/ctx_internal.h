@@ -48,6 +48,8 @@ namespace agh {
 
 // AG_ERR_INVALID with a message (ctx NULL: the message of a failed ag_create).
 ag_status fail_invalid(ag_ctx* ctx, const std::string& msg);
+// Sets the message ag_last_error(NULL) returns (calls without a context).
+void set_global_error(const std::string& msg);
 // AG_OK for cudaSuccess; else the context becomes failed (sticky) with the message.
 ag_status check_cuda(ag_ctx* ctx, cudaError_t e, const char* what);
 // Common prologue of every call on a context: NULL ctx, sticky failure, device selection.

@@ -84,3 +84,13 @@ def test_header_is_plain_c():
     r = subprocess.run(["gcc", "-std=c99", "-fsyntax-only", "-x", "c", os.path.join(ROOT, "include", "ag.h")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_measure_fp32_peak_rejects_bad_arguments(lib):
+    # argument checks come before any CUDA call, so they run without a GPU
+    for kw in ({"iters": 0}, {"iters": 1000001}, {"reps": 0}, {"reps": 101}):
+        with pytest.raises(_abi.AgError) as e:
+            _abi.ag_measure_fp32_peak(**kw)
+        assert e.value.status == _abi.AG_ERR_INVALID
+    assert lib.ag_measure_fp32_peak(None, 10, 1, None) == _abi.AG_ERR_INVALID
+    assert b"out is NULL" in lib.ag_last_error(None)
