@@ -53,6 +53,10 @@ CASES = [
     (W.Workload("reach_redraw", 3000, 4, 1, 8, 1200, 1200, 600), _abi.AG_MODE_ATT_THRUST, True),
     # semi-implicit Euler, quad / hexa / octo, no boxes, velocity interface
     (W.Workload("reach_vel", 2500, 1, 0, 0, 1000, 1000, 500, drag=0.1), _abi.AG_MODE_BODY_VEL, False),
+    # an odd fleet size (1001 = 7 x 128 + 105: a ragged last block), quad / hexa
+    (W.Workload("reach_vel_odd", 1001, 1, 0, 0, 501, 500, 0), _abi.AG_MODE_BODY_VEL, False),
+    # quad / hexa without boxes, full blocks only (2048 = 16 x 128), RK4 x 2, attitude interface
+    (W.Workload("reach_att_hexa", 2048, 2, 1, 0, 1024, 1024, 0), _abi.AG_MODE_ATT_THRUST, False),
 ]
 ENV_MIN, ENV_MAX = (-5.0, -5.0, -5.0), (5.0, 5.0, 5.0)
 
