@@ -68,9 +68,17 @@ ALU_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 BYTES_PER_VEHICLE_LAUNCH = 4 * (26 + 8 + 4 + 4) + 1 + 8 + 4 * 160 + 1 + 4
 # DRAM traffic of one full-size fused launch (1,048,576 envs, 1,000 steps):
 # dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu capture of
-# exactly this launch (795.15 MB + 69.06 MB). It scales with the fleet size
+# exactly this launch (796.32 MB + 68.94 MB). It scales with the fleet size
 # (each env is loaded and stored once per launch), not with the step count.
 TRAFFIC_BYTES_FULL_LAUNCH = 796.32e6 + 68.94e6
+# Algorithmic bytes of one reach-task step per quad: read action 16, goal 12,
+# step counter 4, state 52, motors 16, body 16, epoch 4, mode 1 (121 B);
+# written state 52, motors 16, epoch 4, collided flag 1, command 16,
+# reward 4, done 1, step counter 4, observation 52 (150 B).
+TASK_BYTES_PER_ENV_STEP = (16 + 12 + 4 + 52 + 16 + 16 + 4 + 1) + (52 + 16 + 4 + 1 + 16 + 4 + 1 + 4 + 52)
+# Algorithmic bytes of one depth frame: the float32 270 x 480 image written
+# (the boxes and poses read are under 1 KB per camera).
+DEPTH_BYTES_PER_FRAME = 270 * 480 * 4
 
 
 def dist_env():
@@ -400,6 +408,8 @@ def depth_part(seed: int, world: int) -> dict:
     frames = 1024 * k * world
     return {"value": frames / secs, "unit": "depth frames/s", "ms_per_1024_frames": float(np.mean(per)),
             "pixel_box_pairs_per_s": frames * 270 * 480 * 16 / secs,  # culled pairs included
+            "hbm_frac": frames / secs / world * DEPTH_BYTES_PER_FRAME / 1e9 / HBM_PEAK_GBS,
+            "bound": "issue (ALU pipe: slab min/max and compares), not HBM",
             "workload": "1,024 robots x 270 x 480 depth camera, 16 oriented boxes per environment, 87 deg hfov",
             "paper_value": 1800.0, "paper_hardware": "2x RTX 3090, Isaac Gym camera sensors (graphics renderer)"}
 
@@ -441,6 +451,8 @@ def task_part(seed: int, world: int) -> dict:
         secs_g, _ = time_calls(env.fleet, g.replay, k // per_graph, world)
     env.close()
     return {"value": n * k * world / secs, "unit": "task env-steps/s", "ms_per_step": float(np.mean(per)),
+            "bytes_per_env_step": TASK_BYTES_PER_ENV_STEP,
+            "hbm_frac": n * k / secs * TASK_BYTES_PER_ENV_STEP / 1e9 / HBM_PEAK_GBS,
             "workload": "reach-a-setpoint, 1,048,576 quads, attitude interface, SIE 1 substep, no obstacles, "
                         "obs [n,13] + reward + done per step", "launches_per_step": 1,
             "cuda_graph": {"value": n * k * world / secs_g, "ms_per_step": secs_g * 1e3 / k,
