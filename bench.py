@@ -408,7 +408,7 @@ def depth_part(seed: int, world: int) -> dict:
     frames = 1024 * k * world
     return {"value": frames / secs, "unit": "depth frames/s", "ms_per_1024_frames": float(np.mean(per)),
             "pixel_box_pairs_per_s": frames * 270 * 480 * 16 / secs,  # culled pairs included
-            "hbm_frac": frames / secs / world * DEPTH_BYTES_PER_FRAME / 1e9 / HBM_PEAK_GBS,
+            "hbm_frac": 1024 * DEPTH_BYTES_PER_FRAME / (float(np.mean(per)) * 1e-3) / 1e9 / HBM_PEAK_GBS,
             "bound": "issue (ALU pipe: slab min/max and compares), not HBM",
             "workload": "1,024 robots x 270 x 480 depth camera, 16 oriented boxes per environment, 87 deg hfov",
             "paper_value": 1800.0, "paper_hardware": "2x RTX 3090, Isaac Gym camera sensors (graphics renderer)"}
@@ -452,7 +452,8 @@ def task_part(seed: int, world: int) -> dict:
     env.close()
     return {"value": n * k * world / secs, "unit": "task env-steps/s", "ms_per_step": float(np.mean(per)),
             "bytes_per_env_step": TASK_BYTES_PER_ENV_STEP,
-            "hbm_frac": n * k / secs * TASK_BYTES_PER_ENV_STEP / 1e9 / HBM_PEAK_GBS,
+            # algorithmic bytes of one launch over its mean CUDA-event duration
+            "hbm_frac": n * TASK_BYTES_PER_ENV_STEP / (float(np.mean(per)) * 1e-3) / 1e9 / HBM_PEAK_GBS,
             "workload": "reach-a-setpoint, 1,048,576 quads, attitude interface, SIE 1 substep, no obstacles, "
                         "obs [n,13] + reward + done per step", "launches_per_step": 1,
             "cuda_graph": {"value": n * k * world / secs_g, "ms_per_step": secs_g * 1e3 / k,
