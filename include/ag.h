@@ -43,6 +43,10 @@ extern "C" {
 
 #define AG_ABI_VERSION 2
 #define AG_MAX_OBSTACLES 64
+/* Largest fleet of one context or one serving request: every field index
+ * r * n_envs + i of the structure-of-arrays buffers (at most 13 rows) fits
+ * in 32 bits, which the kernels' index arithmetic uses. */
+#define AG_MAX_ENVS (1u << 28)
 #define AG_STATE_DIM 13  /* p.xyz, v.xyz, q.wxyz, Omega.xyz */
 #define AG_MAX_ROTORS 8
 
@@ -76,7 +80,7 @@ typedef enum {
 typedef enum { AG_INTEG_SIE = 0 /* semi-implicit Euler */, AG_INTEG_RK4 = 1 } ag_integrator;
 
 typedef struct {
-  uint32_t n_envs;            /* >= 1 */
+  uint32_t n_envs;            /* 1 .. AG_MAX_ENVS */
   uint32_t substeps_per_step; /* controller + integrator updates per step (>= 1) */
   uint32_t integrator;        /* ag_integrator */
   uint32_t n_obstacles;       /* boxes per environment, 0..AG_MAX_OBSTACLES */
@@ -430,8 +434,9 @@ ag_status ag_server_create(const ag_server_config* cfg, ag_server** out);
  * arrays (host or device) must stay valid until ag_server_wait has returned
  * for this id. Their contents are not checked (submission stays cheap): they
  * must meet the preconditions of ag_set_commands, ag_set_body and
- * ag_set_obstacles. AG_ERR_INVALID for a malformed request (counts, NULL
- * arrays, pitch), AG_ERR_OOM if it could never fit the budget, AG_ERR_STATE
+ * ag_set_obstacles. AG_ERR_INVALID for a malformed request (n_envs outside
+ * 1 .. AG_MAX_ENVS, other counts, NULL arrays, pitch), AG_ERR_OOM if it
+ * could never fit the budget, AG_ERR_STATE
  * if the server has failed. */
 ag_status ag_server_submit(ag_server* s, const ag_request* req, uint64_t* id);
 

@@ -19,6 +19,7 @@ AG_OK, AG_ERR_INVALID, AG_ERR_OOM, AG_ERR_CUDA, AG_ERR_STATE, AG_ERR_TIMEOUT, AG
 AG_MODE_POSITION, AG_MODE_BODY_VEL, AG_MODE_ATT_THRUST, AG_MODE_WRENCH = range(4)
 AG_INTEG_SIE, AG_INTEG_RK4 = 0, 1
 AG_MAX_OBSTACLES = 64
+AG_MAX_ENVS = 1 << 28
 STATUS_NAMES = {0: "AG_OK", 1: "AG_ERR_INVALID", 2: "AG_ERR_OOM", 3: "AG_ERR_CUDA", 4: "AG_ERR_STATE",
                 5: "AG_ERR_TIMEOUT", 6: "AG_ERR_UNSUPPORTED"}
 

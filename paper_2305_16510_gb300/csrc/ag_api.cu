@@ -131,7 +131,7 @@ namespace agh {
 const char* validate(const ag_config* c) {
   if (!c) return "config is NULL";
   if (c->n_envs == 0) return "n_envs must be >= 1";
-  if (c->n_envs > (1u << 30)) return "n_envs must be <= 2^30";
+  if (c->n_envs > AG_MAX_ENVS) return "n_envs must be <= AG_MAX_ENVS (2^28)";
   if (c->substeps_per_step == 0) return "substeps_per_step must be >= 1";
   if (c->integrator > 1) return "integrator must be 0 (semi-implicit Euler) or 1 (RK4)";
   if (c->n_obstacles > AG_MAX_OBSTACLES) return "n_obstacles exceeds AG_MAX_OBSTACLES";

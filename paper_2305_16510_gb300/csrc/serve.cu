@@ -438,7 +438,8 @@ ag_status ag_server_create(const ag_server_config* cfg, ag_server** out) {
 
 ag_status ag_server_submit(ag_server* s, const ag_request* req, uint64_t* id) {
   if (!s || !req || !id) return AG_ERR_INVALID;
-  if (req->n_envs == 0 || req->n_steps == 0 || req->n_obstacles > AG_MAX_OBSTACLES || !req->modes || !req->targets ||
+  if (req->n_envs == 0 || req->n_envs > AG_MAX_ENVS || req->n_steps == 0 || req->n_obstacles > AG_MAX_OBSTACLES ||
+      !req->modes || !req->targets ||
       (req->n_obstacles && !req->boxes) || (req->pitch && req->pitch < req->n_envs))
     return AG_ERR_INVALID;
   if (agk::request_bytes(req->n_envs, req->n_obstacles) > s->cfg.hbm_budget_bytes) return AG_ERR_OOM;

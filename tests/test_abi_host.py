@@ -42,6 +42,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_abi_version_and_defaults(lib):
     header = open(os.path.join(ROOT, "include", "ag.h")).read()
+    assert "#define AG_MAX_ENVS (1u << 28)" in header and _abi.AG_MAX_ENVS == 1 << 28
+    assert f"#define AG_MAX_OBSTACLES {_abi.AG_MAX_OBSTACLES}" in header
     assert f"#define AG_ABI_VERSION {_abi.ABI_VERSION}" in header
     assert _abi.ag_abi_version() == _abi.ABI_VERSION
     c = _abi.ag_config_default()
@@ -53,6 +55,7 @@ def test_abi_version_and_defaults(lib):
 
 @pytest.mark.parametrize("field,value,msg", [
     ("n_envs", 0, "n_envs"),
+    ("n_envs", (1 << 28) + 1, "AG_MAX_ENVS"),   # larger fleets would overflow 32-bit field indices
     ("substeps_per_step", 0, "substeps_per_step"),
     ("integrator", 7, "integrator"),
     ("n_obstacles", 65, "n_obstacles"),

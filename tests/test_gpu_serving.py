@@ -135,11 +135,12 @@ def test_bounded_wait_and_invalid_requests(pool):
             s.wait(rid, timeout_s=0.0005)
         assert e.value.status == _abi.AG_ERR_TIMEOUT
         s.wait(rid, timeout_s=600)       # still there, completes
-        bad = rp.request(10, 10, 0, seed=1)
-        bad.n_envs = 0
-        with pytest.raises(_abi.AgError) as e:
-            s.submit(bad)
-        assert e.value.status == _abi.AG_ERR_INVALID
+        for n_bad in (0, _abi.AG_MAX_ENVS + 1):   # counts are checked before any array is read
+            bad = rp.request(10, 10, 0, seed=1)
+            bad.n_envs = n_bad
+            with pytest.raises(_abi.AgError) as e:
+                s.submit(bad)
+            assert e.value.status == _abi.AG_ERR_INVALID
     with _server(max_active=4, chunk_steps=10, hbm_budget_bytes=8 << 20) as s:
         with pytest.raises(_abi.AgError) as e:
             s.submit(rp.request(N_POOL, 10, 32, seed=1))
