@@ -81,11 +81,11 @@ typedef enum { AG_INTEG_SIE = 0 /* semi-implicit Euler */, AG_INTEG_RK4 = 1 } ag
 
 typedef struct {
   uint32_t n_envs;            /* 1 .. AG_MAX_ENVS */
-  uint32_t substeps_per_step; /* controller + integrator updates per step (>= 1) */
+  uint32_t substeps_per_step; /* controller + integrator updates per step (1 .. 65536) */
   uint32_t integrator;        /* ag_integrator */
   uint32_t n_obstacles;       /* boxes per environment, 0..AG_MAX_OBSTACLES */
   uint32_t n_quad, n_hexa, n_octo; /* contiguous type ranges in this order; sum == n_envs */
-  uint32_t record_every;      /* checkpoint interval K of ag_rollout_loss (0 = 32 steps) */
+  uint32_t record_every;      /* checkpoint interval K of ag_rollout_loss (0 = 32 steps; <= 65536) */
   float dt;          /* step length [s]; a substep is dt / substeps_per_step */
   float motor_tau;   /* first-order motor time constant [s]; 0 = no lag */
   float drag;        /* linear drag coefficient [N s / m], world frame */
@@ -193,7 +193,8 @@ ag_status ag_set_body(ag_ctx* ctx, const float* body);
  * environment that touches one is reset in place (epoch + 1, Philox draw of
  * a new state, as ag_reset). Afterwards the collided flags mark environments
  * that hit a box in any step of this call and the reset list holds each
- * environment reset during this call once (order unspecified). */
+ * environment reset during this call once (order unspecified).
+ * AG_ERR_INVALID unless n_substeps / substeps_per_step is in 1 .. 2^31 - 1. */
 ag_status ag_step(ag_ctx* ctx, uint32_t n_substeps);
 
 /* Same results as ag_step, computed by one kernel launch per stage per
@@ -287,8 +288,10 @@ ag_status ag_set_gains(ag_ctx* ctx, const float* gains12);
  * NULL) flags environments in which some motor command was clamped during
  * the rollout; there the gradient uses the clamp's subgradient 0. Requires
  * semi-implicit Euler, one substep per step and no obstacles (else
- * AG_ERR_UNSUPPORTED). Does not synchronise. Commands, body parameters and
- * gains must not change until ag_backward has run. */
+ * AG_ERR_UNSUPPORTED); AG_ERR_INVALID for n_steps outside 1 .. 2^30, NULL
+ * p_goal or loss; AG_ERR_OOM (context still usable) when the checkpoints do
+ * not fit. Does not synchronise. Commands, body parameters and gains must not
+ * change until ag_backward has run. */
 ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos, float w_omega, const float* p_goal,
                           float* loss, uint8_t* saturated);
 
@@ -395,7 +398,7 @@ typedef struct ag_server ag_server;
 typedef struct {
   ag_config physics;         /* per-step physics of every request */
   uint32_t max_active;       /* requests on the device at once, 1..AG_SERVER_MAX_ACTIVE */
-  uint32_t chunk_steps;      /* steps per launch (>= 1) */
+  uint32_t chunk_steps;      /* steps per launch (1 .. 2^30) */
   uint64_t hbm_budget_bytes; /* device memory for request buffers (>= 1 MiB) */
 } ag_server_config;
 

@@ -132,7 +132,8 @@ const char* validate(const ag_config* c) {
   if (!c) return "config is NULL";
   if (c->n_envs == 0) return "n_envs must be >= 1";
   if (c->n_envs > AG_MAX_ENVS) return "n_envs must be <= AG_MAX_ENVS (2^28)";
-  if (c->substeps_per_step == 0) return "substeps_per_step must be >= 1";
+  if (c->substeps_per_step == 0 || c->substeps_per_step > 65536) return "substeps_per_step must be in 1..65536";
+  if (c->record_every > 65536) return "record_every must be <= 65536";
   if (c->integrator > 1) return "integrator must be 0 (semi-implicit Euler) or 1 (RK4)";
   if (c->n_obstacles > AG_MAX_OBSTACLES) return "n_obstacles exceeds AG_MAX_OBSTACLES";
   if ((uint64_t)c->n_quad + c->n_hexa + c->n_octo != c->n_envs) return "n_quad + n_hexa + n_octo must equal n_envs";
@@ -523,6 +524,7 @@ static ag_status step_common(ag_ctx* ctx, uint32_t n_substeps, bool fused) {
   const uint32_t sps = ctx->cfg.substeps_per_step;
   if (n_substeps == 0 || n_substeps % sps != 0)
     return fail_invalid(ctx, "n_substeps must be a positive multiple of substeps_per_step");
+  if (n_substeps / sps > (uint32_t)INT32_MAX) return fail_invalid(ctx, "at most 2^31 - 1 steps per call");
   agk::StepParams P = step_params(ctx);
   const int n_steps = (int)(n_substeps / sps);
   cudaError_t e = fused ? agk::launch_fused_step(ctx->fb, P, (int)ctx->cfg.integrator, n_steps, (int)sps, ctx->stream)

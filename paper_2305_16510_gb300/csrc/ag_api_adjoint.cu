@@ -76,7 +76,8 @@ extern "C" ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos,
     ctx->err = "the differentiable rollout needs semi-implicit Euler, 1 substep per step and no obstacles";
     return AG_ERR_UNSUPPORTED;
   }
-  if (n_steps == 0 || !p_goal || !loss) return fail_invalid(ctx, "n_steps must be >= 1; p_goal and loss are required");
+  if (n_steps == 0 || n_steps > (1u << 30) || !p_goal || !loss)
+    return fail_invalid(ctx, "n_steps must be in 1..2^30; p_goal and loss are required");
   const size_t n = c.n_envs;
   const int K = c.record_every ? (int)c.record_every : 32;
   if ((s = ensure_adjoint(ctx, (int)n_steps, K)) != AG_OK) return s;

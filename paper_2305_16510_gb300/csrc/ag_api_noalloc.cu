@@ -62,8 +62,9 @@ extern "C" ag_status ag_step_plain_noalloc(const ag_config* cfg, void* cuda_stre
     noalloc_error(err, err_len, "n_envs exceeds AG_NOALLOC_MAX_ENVS (65536): use a context (ag_create) instead");
     return AG_ERR_INVALID;
   }
-  if (n_substeps == 0 || n_substeps % cfg->substeps_per_step != 0) {
-    noalloc_error(err, err_len, "n_substeps must be a positive multiple of substeps_per_step");
+  if (n_substeps == 0 || n_substeps % cfg->substeps_per_step != 0 ||
+      n_substeps / cfg->substeps_per_step > (uint32_t)INT32_MAX) {
+    noalloc_error(err, err_len, "n_substeps must be a positive multiple of substeps_per_step (at most 2^31 - 1 steps)");
     return AG_ERR_INVALID;
   }
   const void* required[] = {state, motors, body, modes, targets, epoch, collided, reset_ids, n_reset};

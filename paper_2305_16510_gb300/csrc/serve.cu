@@ -400,7 +400,8 @@ ag_status ag_server_create(const ag_server_config* cfg, ag_server** out) {
   if (!out || !cfg) return AG_ERR_INVALID;
   *out = nullptr;
   if (cfg->max_active == 0 || cfg->max_active > AG_SERVER_MAX_ACTIVE || cfg->chunk_steps == 0 ||
-      cfg->hbm_budget_bytes < (1u << 20) || cfg->physics.substeps_per_step == 0 || cfg->physics.integrator > 1 ||
+      cfg->chunk_steps > (1u << 30) || cfg->hbm_budget_bytes < (1u << 20) || cfg->physics.substeps_per_step == 0 ||
+      cfg->physics.substeps_per_step > 65536 || cfg->physics.integrator > 1 ||
       !(cfg->physics.dt > 0.f) || !(cfg->physics.u_max > 0.f) || !(cfg->physics.mass > 0.f))
     return AG_ERR_INVALID;
   ag_server* s = new (std::nothrow) ag_server();

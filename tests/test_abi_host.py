@@ -57,6 +57,8 @@ def test_abi_version_and_defaults(lib):
     ("n_envs", 0, "n_envs"),
     ("n_envs", (1 << 28) + 1, "AG_MAX_ENVS"),   # larger fleets would overflow 32-bit field indices
     ("substeps_per_step", 0, "substeps_per_step"),
+    ("substeps_per_step", 65537, "substeps_per_step"),
+    ("record_every", 65537, "record_every"),
     ("integrator", 7, "integrator"),
     ("n_obstacles", 65, "n_obstacles"),
     ("n_quad", 5, "n_quad + n_hexa + n_octo"),

@@ -292,6 +292,20 @@ def test_invalid_arguments_leave_context_usable():
     assert e.value.status == _abi.AG_ERR_INVALID
     with pytest.raises(_abi.AgError):
         _abi.ag_step(fl.ctx, 0)
+    # step counts that do not fit the kernels' int step counter
+    from paper_2305_16510_gb300.fleet import Fleet
+    one = Fleet(64)
+    for n_sub in (1 << 31, (1 << 32) - 1):
+        with pytest.raises(_abi.AgError) as e:
+            _abi.ag_step(one.ctx, n_sub)
+        assert e.value.status == _abi.AG_ERR_INVALID
+    goal, loss = torch.zeros((3, 64), device=one.device), torch.empty(64, device=one.device)
+    with pytest.raises(_abi.AgError) as e:
+        _abi.ag_rollout_loss(one.ctx, (1 << 30) + 1, 1.0, 0.01, goal, loss)
+    assert e.value.status == _abi.AG_ERR_INVALID
+    one.step(1)
+    assert np.isfinite(_np(one.state())).all()
+    one.close()
     fl.reset(None, 1)
     fl.step(2)
     assert np.isfinite(_np(fl.state())).all()
