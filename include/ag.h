@@ -174,7 +174,9 @@ ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], con
  * optical axis to the nearest box surface in front of the camera (0 inside a
  * box), or max_range if none is closer. depth: float[n_cams][height][width],
  * host or device. AG_ERR_INVALID for an empty image, hfov outside (0, pi),
- * max_range <= 0 or an environment id out of range (host arrays only). */
+ * max_range <= 0 or an environment id out of range in a host array; an id
+ * out of range in a device array is not read through: that camera's image
+ * is all NaN. */
 ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
                           const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth);
 

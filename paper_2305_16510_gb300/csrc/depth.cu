@@ -170,10 +170,12 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
   const uint32_t t_begin = (blockIdx.x % groups) * kDepthTilesPerBlock;
   const uint32_t t_end = min(t_begin + kDepthTilesPerBlock, tiles);
   const uint32_t env = a.env_ids ? a.env_ids[j] : j;
+  // a camera id outside the fleet reads nothing and yields a NaN image
+  const bool bad_env = env >= a.n;
   const uint32_t n_pix = a.width * a.height;
   const uint32_t tx = threadIdx.x & (kDepthTile - 1), ty = threadIdx.x / kDepthTile;
   const float half_w = 0.5f * (float)a.width, half_h = 0.5f * (float)a.height;
-  const int n_obs = (int)a.n_obs;  // at most AG_MAX_OBSTACLES (checked when the context is created)
+  const int n_obs = bad_env ? 0 : (int)a.n_obs;  // at most AG_MAX_OBSTACLES (checked when the context is created)
   // once per block: each box's record and its bounding sphere in the camera frame ...
   if ((int)threadIdx.x < n_obs) {
     const CamPose cam = camera_pose(a, env);
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
 #pragma unroll
     for (int p = 0; p < kDepthPix; ++p) {
       dz[p] = -((float)(y0 + ty + p * kDepthRows) + 0.5f - half_h) * a.inv_f;
-      best[p] = a.max_range;
+      best[p] = bad_env ? __int_as_float(0x7fc00000) : a.max_range;  // no box is tested for a bad id
     }
     for (int j = 0; j < n_live[tl]; ++j) {  // the same for the whole block
       const int k = live_k[tl][j];

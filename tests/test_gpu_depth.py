@@ -58,6 +58,14 @@ def test_depth_matches_oracle_small_images():
     assert e.value.status == _abi.AG_ERR_INVALID
     with pytest.raises(_abi.AgError):
         _abi.ag_render_depth(fl.ctx, 8, 8, hfov, rng_max, None, np.array([5000], np.uint32), 1, host)
+    # ids out of range in a device array are not read through: those images are NaN, the others unchanged
+    dev_ids = torch.tensor([3, 300, 7, -1, 299], dtype=torch.int32, device=fl.device)  # -1: id 2^32 - 1
+    img = _np(fl.render_depth(48, 32, hfov, rng_max, env_ids=dev_ids))
+    assert np.isnan(img[1]).all() and np.isnan(img[3]).all()
+    good = [0, 2, 4]
+    ref = O.render_depth(_np(fl.state()), _np(fl.obstacles()), np.array([3, 7, 299]), 48, 32, hfov, rng_max)
+    assert not np.isnan(img[good]).any()
+    _compare(img[good], ref, 0.002)
     fl.close()
 
 
