@@ -589,6 +589,22 @@ def test_op_counts_are_plausible():
     assert 20 < per_box < 120
 
 
+def test_op_count_of_one_box_test_matches_a_hand_count():
+    # d = R_b^T (p - c), e = d - clamp(d, -h, h), hit iff e.e <= r^2, with R_b
+    # formed from the unit quaternion: each diagonal entry 1 - 2 (a a + b b) is
+    # 3 mul + 2 add, each off-diagonal 2 (a b -+ c d) is 3 mul + 1 add (27 mul,
+    # 12 add); p - c 3 add; R_b^T v 9 mul + 6 add; e 3 add; e.e 3 mul + 2 add;
+    # r^2 1 mul. Comparisons (the clamp) are counted apart and left out.
+    world = O.World(n_envs=1)
+    c0 = O.count_ops(world, O.MODE_WRENCH, 0)
+    c1 = O.count_ops(world, O.MODE_WRENCH, 1)
+    c5 = O.count_ops(world, O.MODE_WRENCH, 5)
+    for c in (c1, c5):
+        k = 1 if c is c1 else 5
+        assert (c["add"] - c0["add"]) == 26 * k and (c["mul"] - c0["mul"]) == 40 * k
+        assert (c["div"], c["sqrt"], c["trans"]) == (c0["div"], c0["sqrt"], c0["trans"])
+
+
 # ------------------------------------------------- obstacle pose re-draw --
 ENV_MIN, ENV_MAX = (-5.0, -4.0, 0.0), (5.0, 4.0, 3.0)
 
