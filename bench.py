@@ -57,7 +57,7 @@ FLOP_PER_VEHICLE_STEP_MIXED = 584.4
 # per step the collision test (position 12, 16 boxes x 40 in; hit byte out)
 # and the reset pass (hit byte in).
 PLAIN_BYTES_PER_VEHICLE_STEP = 301 * 4 + 12 + 16 * 40 + 1 + 1
-HBM_PEAK_GBS = 6794.5  # the machine's measured copy bandwidth (MEASURED_PEAKS.json, hbm_gbs)
+HBM_PEAK_GBS = 6794.5  # measured GB300 copy bandwidth (MEASURED_PEAKS.json, hbm_gbs)
 FLOP_PER_VEHICLE_STEP_PAPER_SHAPE = 528.5
 # GB300 FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2,070 MHz
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0

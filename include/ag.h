@@ -59,7 +59,7 @@ typedef enum {
   AG_ERR_CUDA = 3,        /* a CUDA call failed; the context is now failed */
   AG_ERR_STATE = 4,       /* the context failed earlier */
   AG_ERR_TIMEOUT = 5,     /* a bounded wait expired */
-  AG_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+  AG_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
 } ag_status;
 
 /* Command interface of one environment (Sec. IV). Targets are four floats:
