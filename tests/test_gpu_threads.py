@@ -34,7 +34,7 @@ def _built():
     build.build()
 
 
-def _work(w, seed):
+def _run_context(w, seed):
     """Reset, fused and unfused steps, a masked reset and a depth render on a
     context of its own, on a stream of its own; returns the results on the host."""
     side = torch.cuda.Stream()
@@ -59,13 +59,13 @@ def _work(w, seed):
 
 def test_contexts_in_concurrent_threads_match_sequential_runs():
     seeds = [31 + k for k in range(len(CONFIGS))]
-    sequential = [_work(w, s) for w, s in zip(CONFIGS, seeds)]
+    sequential = [_run_context(w, s) for w, s in zip(CONFIGS, seeds)]
     for _ in range(3):           # a few rounds, to give interleavings a chance
         results, errors = [None] * len(CONFIGS), []
 
         def run(k):
             try:
-                results[k] = _work(CONFIGS[k], seeds[k])
+                results[k] = _run_context(CONFIGS[k], seeds[k])
             except BaseException as e:       # re-raised below, on the test's thread
                 errors.append(e)
 
