@@ -60,7 +60,7 @@ def _run_context(w, seed):
 def test_contexts_in_concurrent_threads_match_sequential_runs():
     seeds = [31 + k for k in range(len(CONFIGS))]
     sequential = [_run_context(w, s) for w, s in zip(CONFIGS, seeds)]
-    for _ in range(3):           # a few rounds, to give interleavings a chance
+    for _ in range(3):           # repeated, to give interleavings a chance
         results, errors = [None] * len(CONFIGS), []
 
         def run(k):
