@@ -116,13 +116,14 @@ void ag_config_default(ag_config* cfg);
 ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out);
 
 /* Frees every buffer of the context (synchronises its stream first). NULL is
- * accepted. */
+ * accepted. Always AG_OK, also for a failed context. */
 ag_status ag_destroy(ag_ctx* ctx);
 
 /* Copies the command of every environment: modes uint8[n_envs] (ag_mode
  * values; any value above 3 acts as AG_MODE_WRENCH) and targets
  * float[4][n_envs] as described at ag_mode. Either pointer may be NULL to
- * keep the current one. */
+ * keep the current one. Values are not checked (a NaN target propagates into
+ * that environment's state only). AG_ERR_CUDA if a copy fails. */
 ag_status ag_set_commands(ag_ctx* ctx, const uint8_t* modes, const float* targets);
 
 /* Copies the static obstacles: float[n_obstacles][10][n_envs], per box the
@@ -134,7 +135,9 @@ ag_status ag_set_commands(ag_ctx* ctx, const uint8_t* modes, const float* target
 ag_status ag_set_obstacles(ag_ctx* ctx, const float* boxes);
 
 /* Copies out the current obstacles float[n_obstacles][10][n_envs] (layout of
- * ag_set_obstacles); they change only when obstacle re-placement is on. */
+ * ag_set_obstacles); they change only when obstacle re-placement is on.
+ * AG_ERR_INVALID for a NULL boxes pointer; nothing is copied when the
+ * context has no obstacles. */
 ag_status ag_get_obstacles(ag_ctx* ctx, float* boxes);
 
 /* Re-placement of one obstacle when its environment resets (Sec. V: the
@@ -158,7 +161,8 @@ typedef struct {
  * half-extents are kept. The draws are Philox4x32-10 keyed by the reset seed
  * with counters (env, epoch, k, 1) and (env, epoch, k, 2), transformed in
  * strict binary32, so they are reproducible bit for bit. Host pointers;
- * AG_ERR_INVALID for bounds outside [0, 1] or angles outside [-pi, pi]. */
+ * AG_ERR_INVALID for bounds outside [0, 1] or angles outside [-pi, pi];
+ * AG_ERR_OOM (context still usable) if the specification does not fit. */
 ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], const float env_max[3],
                                         const ag_box_randomization* per_box);
 
@@ -176,7 +180,8 @@ ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], con
  * host or device. AG_ERR_INVALID for an empty image, hfov outside (0, pi),
  * max_range <= 0 or an environment id out of range in a host array; an id
  * out of range in a device array is not read through: that camera's image
- * is all NaN. */
+ * is all NaN. AG_ERR_OOM (context still usable) if the staging buffer of a
+ * host destination does not fit. */
 ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
                           const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth);
 
@@ -203,7 +208,7 @@ ag_status ag_step(ag_ctx* ctx, uint32_t n_substeps);
  * substep (controller, allocation, integrator) and per step (collision,
  * reset), with every intermediate written to and read back from device
  * memory. It is the unfused comparison point; results agree with ag_step to
- * float32 rounding. */
+ * float32 rounding. Errors as ag_step. */
 ag_status ag_step_plain(ag_ctx* ctx, uint32_t n_substeps);
 
 /* The controller stage alone (Sec. IV): for every environment, its command
@@ -211,7 +216,9 @@ ag_status ag_step_plain(ag_ctx* ctx, uint32_t n_substeps);
  * commanded collective thrust and moments float[4][n_envs] (f, M_x, M_y,
  * M_z) at the states float[13][n_envs] (NULL = the current states; q need
  * not be unit). Host or device pointers; nothing else changes. For
- * inspecting what the controller asks for, and for testing it on its own. */
+ * inspecting what the controller asks for, and for testing it on its own.
+ * AG_ERR_INVALID for a NULL wrench; AG_ERR_OOM if the staging buffer for a
+ * given state does not fit. */
 ag_status ag_eval_controller(ag_ctx* ctx, const float* state, float* wrench);
 
 /* Resets the environments whose mask byte is non-zero (mask NULL = all):
@@ -221,23 +228,26 @@ ag_status ag_eval_controller(ag_ctx* ctx, const float* state, float* wrench);
  * with key = seed and counter (env, epoch, slot, 0), transformed in strict
  * binary32 arithmetic, so it is reproducible bit for bit. `seed` also becomes
  * the key of later collision resets. Writes the reset list and clears the
- * collided flags. */
+ * collided flags. The mask (host or device) is copied; AG_ERR_CUDA if the
+ * copy or the launch fails. */
 ag_status ag_reset(ag_ctx* ctx, const uint8_t* mask, uint64_t seed);
 
 /* Copies out the state float[13][n_envs] (p, v, q, Omega), the collided
  * flags uint8[n_envs] and the reset list uint32[n_envs] (its first
  * *n_reset entries are valid) of the last ag_step / ag_reset. Any pointer may
- * be NULL. A non-NULL n_reset synchronises the stream. */
+ * be NULL. A non-NULL n_reset synchronises the stream. AG_ERR_CUDA if a copy
+ * fails. */
 ag_status ag_get_state(ag_ctx* ctx, float* state, uint8_t* collided, uint32_t* reset_ids, uint32_t* n_reset);
 
 /* Copies out the motor thrusts float[8][n_envs] (rows >= n_rot unused) and
- * the reset epochs uint32[n_envs]. Either pointer may be NULL. */
+ * the reset epochs uint32[n_envs]. Either pointer may be NULL. AG_ERR_CUDA if
+ * a copy fails. */
 ag_status ag_get_motors(ag_ctx* ctx, float* motors, uint32_t* epoch);
 
 /* Overwrites the state float[13][n_envs]; motors float[8][n_envs] and
  * epoch uint32[n_envs] may be NULL to keep the current values. With
  * ag_get_state / ag_get_motors this checkpoints and resumes a fleet bit for
- * bit. */
+ * bit. Values are not checked. AG_ERR_INVALID for a NULL state. */
 ag_status ag_set_state(ag_ctx* ctx, const float* state, const float* motors, const uint32_t* epoch);
 
 /* Allocation-free unfused step: the same computation as ag_step_plain,
@@ -275,7 +285,8 @@ ag_status ag_step_plain_noalloc(const ag_config* cfg, void* cuda_stream, uint32_
 
 /* Sets the 12 diagonal controller gains (k_x, k_v, k_R, k_Omega, three each,
  * in that order) used by every later launch. gains12 may be a host or device
- * pointer (the call synchronises the copy). */
+ * pointer (the call synchronises the copy). AG_ERR_INVALID (gains unchanged)
+ * for NULL or a non-finite gain. */
 ag_status ag_set_gains(ag_ctx* ctx, const float* gains12);
 
 /* Differentiable rollout, forward half. Advances every environment n_steps
@@ -356,7 +367,8 @@ void ag_reach_config_default(ag_reach_config* cfg);
  * goals float[3][n_envs] (host or device) are copied and every step counter
  * is set to 0. States are left as they are (call ag_reset first for fresh
  * episodes). AG_ERR_INVALID for another mode, max_steps 0, a negative weight
- * or penalty, max_dist <= 0 or goals NULL. */
+ * or penalty, max_dist <= 0 or goals NULL; AG_ERR_OOM (context still usable)
+ * if the goals and step counters do not fit. */
 ag_status ag_reach_begin(ag_ctx* ctx, const ag_reach_config* cfg, const float* goals);
 
 /* One task step. actions: device float[n_envs][4], 16-byte aligned. obs:
@@ -453,17 +465,19 @@ ag_status ag_server_submit(ag_server* s, const ag_request* req, uint64_t* id);
 ag_status ag_server_wait(ag_server* s, uint64_t id, double timeout_s, float* final_state, uint32_t* epoch,
                          double* latency_ms);
 
-/* Snapshot of the server's counters. */
+/* Snapshot of the server's counters (thread-safe). AG_ERR_INVALID for a NULL
+ * server or out. */
 ag_status ag_server_get_stats(ag_server* s, ag_server_stats* out);
 
 /* Stops the loop after the requests on the device finish, abandons queued
- * ones, and frees everything. */
+ * ones, and frees everything. NULL is accepted; always AG_OK. */
 ag_status ag_server_destroy(ag_server* s);
 
 /* Waits for all work queued on the context's stream. */
 ag_status ag_synchronize(ag_ctx* ctx);
 
-/* Number of environments / the configuration the context was created with. */
+/* Number of environments / the configuration the context was created with
+ * (the gains as last set). AG_ERR_INVALID for a NULL ctx or out. */
 ag_status ag_get_config(const ag_ctx* ctx, ag_config* out);
 
 /* Fault injection for testing a caller's error handling: marks the context

@@ -489,7 +489,7 @@ ag_status ag_set_obstacle_randomization(ag_ctx* ctx, const float env_min[3], con
   }
   if (!f.box_rand) {
     agk::BoxRandDev* p = nullptr;
-    if ((s = check_cuda(ctx, alloc(ctx, &p, n_obs), "allocate obstacle spec")) != AG_OK) return s;
+    if ((s = alloc_or_oom(ctx, &p, n_obs, "the obstacle spec")) != AG_OK) return s;
     f.box_rand = p;
   }
   return check_cuda(ctx, cudaMemcpy((void*)f.box_rand, spec.data(), n_obs * sizeof(agk::BoxRandDev),
@@ -552,7 +552,7 @@ ag_status ag_eval_controller(ag_ctx* ctx, const float* state, float* wrench) {
   agk::FleetBuffers fb = ctx->fb;
   if (state) {
     if (!ctx->eval_state &&
-        (s = check_cuda(ctx, alloc(ctx, &ctx->eval_state, 13 * n), "allocate controller states")) != AG_OK) return s;
+        (s = alloc_or_oom(ctx, &ctx->eval_state, 13 * n, "the controller states")) != AG_OK) return s;
     if ((s = check_cuda(ctx, cudaMemcpyAsync(ctx->eval_state, state, 13 * n * sizeof(float), cudaMemcpyDefault, st),
                         "copy controller states")) != AG_OK) return s;
     fb.state = ctx->eval_state;

@@ -32,7 +32,7 @@ ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hf
     if (!on_device(env_ids))
       for (uint32_t j = 0; j < n_cams; ++j)
         if (env_ids[j] >= n) return fail_invalid(ctx, "environment id out of range");
-    if (!ctx->cam_ids && (s = check_cuda(ctx, alloc(ctx, &ctx->cam_ids, n), "allocate camera ids")) != AG_OK) return s;
+    if (!ctx->cam_ids && (s = alloc_or_oom(ctx, &ctx->cam_ids, n, "the camera ids")) != AG_OK) return s;
     if ((s = check_cuda(ctx, cudaMemcpyAsync(ctx->cam_ids, env_ids, n_cams * sizeof(uint32_t), cudaMemcpyDefault, st),
                         "copy camera ids")) != AG_OK) return s;
     ids_dev = ctx->cam_ids;
@@ -44,7 +44,7 @@ ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hf
     if (count > ctx->depth_stage_cap) {
       if (ctx->depth_stage) { cudaStreamSynchronize(st); cudaFree(ctx->depth_stage); ctx->depth_stage = nullptr; }
       ctx->depth_stage_cap = 0;
-      if ((s = check_cuda(ctx, alloc(ctx, &ctx->depth_stage, count), "allocate depth staging")) != AG_OK) return s;
+      if ((s = alloc_or_oom(ctx, &ctx->depth_stage, count, "the depth staging buffer")) != AG_OK) return s;
       ctx->depth_stage_cap = count;
     }
     out = ctx->depth_stage;
@@ -101,9 +101,9 @@ ag_status ag_reach_begin(ag_ctx* ctx, const ag_reach_config* cfg, const float* g
       return fail_invalid(ctx, "action scale and offset must be finite");
   const size_t n = ctx->cfg.n_envs;
   cudaStream_t st = ctx->stream;
-  if (!ctx->reach_goals && (s = check_cuda(ctx, alloc(ctx, &ctx->reach_goals, 3 * n), "allocate goals")) != AG_OK)
+  if (!ctx->reach_goals && (s = alloc_or_oom(ctx, &ctx->reach_goals, 3 * n, "the goals")) != AG_OK)
     return s;
-  if (!ctx->reach_steps && (s = check_cuda(ctx, alloc(ctx, &ctx->reach_steps, n), "allocate step counters")) != AG_OK)
+  if (!ctx->reach_steps && (s = alloc_or_oom(ctx, &ctx->reach_steps, n, "the step counters")) != AG_OK)
     return s;
   if ((s = check_cuda(ctx, cudaMemcpyAsync(ctx->reach_goals, goals, 3 * n * sizeof(float), cudaMemcpyDefault, st),
                       "copy goals")) != AG_OK) return s;

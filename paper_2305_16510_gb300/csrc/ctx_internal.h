@@ -71,4 +71,15 @@ template <class T> cudaError_t alloc(ag_ctx* ctx, T** p, size_t count) {
   return e;
 }
 
+// Allocation made on first use of a feature: AG_OK, or AG_ERR_OOM with the
+// message "<what> does not fit" and the context left usable (an out-of-memory
+// cudaMalloc leaves no sticky error).
+template <class T> ag_status alloc_or_oom(ag_ctx* ctx, T** p, size_t count, const char* what) {
+  if (alloc(ctx, p, count) == cudaSuccess) return AG_OK;
+  cudaGetLastError();
+  *p = nullptr;
+  ctx->err = std::string(what) + " does not fit";
+  return AG_ERR_OOM;
+}
+
 }  // namespace agh

@@ -58,6 +58,14 @@ def test_depth_matches_oracle_small_images():
     assert e.value.status == _abi.AG_ERR_INVALID
     with pytest.raises(_abi.AgError):
         _abi.ag_render_depth(fl.ctx, 8, 8, hfov, rng_max, None, np.array([5000], np.uint32), 1, host)
+    # a host destination whose staging buffer cannot fit (300 x 2^30 floats, 1.3 TB): AG_ERR_OOM before
+    # anything is copied, and the context stays usable
+    with pytest.raises(_abi.AgError) as e:
+        _abi.ag_render_depth(fl.ctx, 1 << 15, 1 << 15, hfov, rng_max, None, None, 300, host)
+    assert e.value.status == _abi.AG_ERR_OOM
+    _abi.ag_render_depth(fl.ctx, 48, 32, hfov, rng_max, None, None, 8, host)
+    fl.synchronize()
+    _compare(host, ref, 0.002)
     # ids out of range in a device array are not read through: those images are NaN, the others unchanged
     dev_ids = torch.tensor([3, 300, 7, -1, 299], dtype=torch.int32, device=fl.device)  # -1: id 2^32 - 1
     img = _np(fl.render_depth(48, 32, hfov, rng_max, env_ids=dev_ids))
