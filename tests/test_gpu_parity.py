@@ -11,6 +11,7 @@ and float64 may decide differently; they are counted and excluded.
 import numpy as np
 import pytest
 import torch
+from scipy.spatial.transform import Rotation
 
 import oracle as O
 from harness import (attitude_error, box_margin, gpu_fleet, max_state_errors, oracle_fleet_from, oracle_world,
@@ -148,6 +149,53 @@ def test_wrench_mode_free_fall_and_hover_fixed_point():
     fl.set_state(st, mot)
     fl.step(100)
     np.testing.assert_allclose(_np(fl.state()), st, atol=2e-5)
+    fl.close()
+
+
+def test_torque_free_rk4_conserves_momentum_and_energy_and_falls_on_the_parabola():
+    """Pinned by the physics, not the oracle: with zero wrench and an
+    asymmetric inertia the world angular momentum R J Omega and the kinetic
+    energy 1/2 Omega^T J Omega are invariants, and the centre of mass follows
+    p0 + v0 t - 1/2 g t^2 e3, which RK4 integrates exactly. 1,000 steps of
+    4 RK4 substeps in float32."""
+    from paper_2305_16510_gb300.fleet import Fleet
+    n, steps, dt = 512, 1000, 0.01
+    rng = np.random.default_rng(77)
+    fl = Fleet(n, substeps_per_step=4, integrator=_abi.AG_INTEG_RK4, motor_tau=0.0)
+    J = np.array([0.007, 0.009, 0.012])
+    fl.set_body(np.tile(np.array([[0.75], [J[0]], [J[1]], [J[2]]], np.float32), (1, n)))
+    fl.set_commands(np.full(n, W.MODE_WRENCH, np.uint8), np.zeros((4, n), np.float32))
+    st = np.zeros((13, n), np.float32)
+    st[0:3] = rng.uniform(-2, 2, (3, n))
+    st[3:6] = rng.normal(0, 1.0, (3, n))
+    q = rng.normal(size=(4, n))
+    st[6:10] = q / np.linalg.norm(q, axis=0)
+    st[10:13] = rng.normal(0, 1.5, (3, n))
+    fl.set_state(st, np.zeros((8, n), np.float32))
+
+    def invariants(s):
+        s = s.astype(np.float64)
+        R = Rotation.from_quat(np.stack([s[7], s[8], s[9], s[6]], axis=1)).as_matrix()
+        Jw = J[:, None] * s[10:13]
+        return np.einsum("nij,jn->in", R, Jw), 0.5 * np.sum(s[10:13] * Jw, axis=0)
+
+    L0, E0 = invariants(st)
+    fl.step(steps)
+    s1 = _np(fl.state())
+    L1, E1 = invariants(s1)
+    # float32 rounding over 4,000 substeps; a modelling error (a dropped gyroscopic term, a wrong
+    # sign) misses these by orders of magnitude
+    assert np.all(np.linalg.norm(L1 - L0, axis=0) <= 5e-4 * np.linalg.norm(L0, axis=0))
+    assert np.all(np.abs(E1 - E0) <= 5e-4 * E0)
+    np.testing.assert_allclose(np.linalg.norm(s1[6:10].astype(np.float64), axis=0), 1.0, atol=1e-6)
+    t = steps * dt
+    p_exact = st[0:3].astype(np.float64) + st[3:6].astype(np.float64) * t
+    p_exact[2] -= 0.5 * 9.81 * t * t
+    v_exact = st[3:6].astype(np.float64)
+    v_exact[2] -= 9.81 * t
+    # |p| reaches ~500 m: 4,000 float32 additions at that size round to ~2e-4 of it
+    assert np.all(np.abs(s1[0:3] - p_exact) <= 2e-4 * (1 + np.abs(p_exact)))
+    assert np.all(np.abs(s1[3:6] - v_exact) <= 2e-4 * (1 + np.abs(v_exact)))
     fl.close()
 
 
