@@ -199,6 +199,44 @@ def test_torque_free_rk4_conserves_momentum_and_energy_and_falls_on_the_parabola
     fl.close()
 
 
+def test_position_control_converges_from_small_errors_on_every_airframe():
+    """Pinned by the control law's stability (Lee et al. 2011, the position
+    controller of Sec. I): from 0.1 m and 5 deg off a hover setpoint, quad,
+    hexa and octo fleets settle within 1e-3 m and 1e-3 (|e_R|) in 10 s."""
+    from paper_2305_16510_gb300.fleet import Fleet
+    n_q, n_h, n_o = 2048, 1024, 1024
+    n = n_q + n_h + n_o
+    rng = np.random.default_rng(12)
+    fl = Fleet(n, n_hexa=n_h, n_octo=n_o)
+    pd = rng.uniform(-3, 3, (3, n))
+    psi_d = rng.uniform(-3, 3, n)
+    e = rng.normal(size=(3, n))
+    e *= 0.1 / np.linalg.norm(e, axis=0)
+    ax = rng.normal(size=(n, 3))
+    ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    R0 = Rotation.from_euler("Z", psi_d[:, None]) * Rotation.from_rotvec(np.radians(5) * ax)
+    q = R0.as_quat()                              # x, y, z, w
+    st = np.zeros((13, n), np.float32)
+    st[0:3] = pd + e
+    st[6], st[7], st[8], st[9] = q[:, 3], q[:, 0], q[:, 1], q[:, 2]
+    mot = np.zeros((8, n), np.float32)
+    n_rot = np.array([4] * n_q + [6] * n_h + [8] * n_o)
+    for k in range(8):
+        mot[k] = np.where(k < n_rot, 0.75 * 9.81 / n_rot, 0.0)
+    tg = np.vstack([pd, psi_d[None]]).astype(np.float32)
+    fl.set_commands(np.zeros(n, np.uint8), tg)
+    fl.set_state(st, mot)
+    fl.step(1000)
+    s1 = _np(fl.state()).astype(np.float64)
+    assert np.max(np.linalg.norm(s1[0:3] - pd, axis=0)) < 1e-3
+    R = Rotation.from_quat(np.stack([s1[7], s1[8], s1[9], s1[6]], axis=1)).as_matrix()
+    Rd = Rotation.from_euler("Z", psi_d[:, None]).as_matrix()
+    E = np.einsum("nji,njk->nik", Rd, R) - np.einsum("nji,njk->nik", R, Rd)
+    eR = 0.5 * np.stack([E[:, 2, 1], E[:, 0, 2], E[:, 1, 0]], axis=1)
+    assert np.max(np.linalg.norm(eR, axis=1)) < 1e-3
+    fl.close()
+
+
 # -------------------------------------------------------------- obstacles --
 def _teacher_forced_steps(w, seed, n_calls, plain=False):
     """One step per call; after each call the oracle advances the GPU's
