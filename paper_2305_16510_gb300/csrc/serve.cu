@@ -160,6 +160,7 @@ struct ag_server {
   ag_server_config cfg;
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;  // results of retired requests, beside the next chunk
   // two chunks can be in flight: chunk k uses buffer k % 2
   cudaEvent_t chunk_start[2] = {nullptr, nullptr}, chunk_done[2] = {nullptr, nullptr};
   unsigned char* slab = nullptr;
@@ -263,14 +264,16 @@ void fail_server(ag_server* s, cudaError_t e, const char* what) {
 // A chunk handed to the device and not yet retired.
 struct InFlight {
   bool valid = false;
-  std::vector<ServeRequest*> finishing;  // requests whose last steps (and result copies) it holds
+  std::vector<ServeRequest*> finishing;  // requests whose last steps it holds
   double vehicle_steps = 0.0;
 };
 
 // The loop keeps the device fed: it enqueues chunk k (after any uploads of
 // newly admitted requests) and only then waits for chunk k - 1 and retires
 // the requests that finished in it, so the next chunk is already queued
-// while the host does its bookkeeping.
+// while the host does its bookkeeping. A retired request's final state is
+// copied back then, on a stream of its own, while chunk k runs: its slab
+// region is released only after that copy.
 void serve_loop(ag_server* s) {
   cudaSetDevice(s->device);
   const int substeps = (int)s->cfg.physics.substeps_per_step;
@@ -341,16 +344,6 @@ void serve_loop(ag_server* s) {
         }
         e = cudaGetLastError();
       }
-      // results of the requests that finish in this chunk
-      for (ServeRequest* r : f.finishing) {
-        if (e != cudaSuccess) break;
-        const size_t n = r->in.n_envs;
-        r->final_state.resize(13 * n);
-        r->final_epoch.resize(n);
-        e = cudaMemcpyAsync(r->final_state.data(), r->fb.state, 13 * n * 4, cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(r->final_epoch.data(), r->fb.epoch, n * 4, cudaMemcpyDeviceToHost, s->stream);
-      }
       if (e == cudaSuccess) e = cudaEventRecord(s->chunk_done[b], s->stream);
       if (e != cudaSuccess) { fail_server(s, e, "serve launch"); return; }
       f.valid = true;
@@ -361,6 +354,18 @@ void serve_loop(ag_server* s) {
     float ms = 0.f;
     e = cudaEventSynchronize(s->chunk_done[b ^ 1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->chunk_start[b ^ 1], s->chunk_done[b ^ 1]);
+    // the results of the requests that finished in chunk k - 1 (pageable
+    // destinations: each copy returns once it is done)
+    for (ServeRequest* r : prev.finishing) {
+      if (e != cudaSuccess) break;
+      const size_t n = r->in.n_envs;
+      r->final_state.resize(13 * n);
+      r->final_epoch.resize(n);
+      e = cudaMemcpyAsync(r->final_state.data(), r->fb.state, 13 * n * 4, cudaMemcpyDeviceToHost, s->copy_stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r->final_epoch.data(), r->fb.epoch, n * 4, cudaMemcpyDeviceToHost, s->copy_stream);
+    }
+    if (e == cudaSuccess && !prev.finishing.empty()) e = cudaStreamSynchronize(s->copy_stream);
     if (e != cudaSuccess) { fail_server(s, e, "serve retire"); return; }
     {
       std::lock_guard<std::mutex> lk(s->mu);
@@ -409,6 +414,7 @@ ag_status ag_server_create(const ag_server_config* cfg, ag_server** out) {
   s->cfg = *cfg;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
   for (int b = 0; b < 2; ++b) {
     if (e == cudaSuccess) e = cudaEventCreate(&s->chunk_done[b]);
     if (e == cudaSuccess) e = cudaEventCreate(&s->chunk_start[b]);
@@ -426,6 +432,7 @@ ag_status ag_server_create(const ag_server_config* cfg, ag_server** out) {
       if (s->chunk_start[b]) cudaEventDestroy(s->chunk_start[b]);
     }
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     delete s;
     return e == cudaErrorMemoryAllocation ? AG_ERR_OOM : AG_ERR_CUDA;
   }
@@ -520,6 +527,8 @@ ag_status ag_server_destroy(ag_server* s) {
     cudaEventDestroy(s->chunk_start[b]);
   }
   cudaStreamDestroy(s->stream);
+  cudaStreamSynchronize(s->copy_stream);
+  cudaStreamDestroy(s->copy_stream);
   delete s;
   return AG_OK;
 }
