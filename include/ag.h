@@ -449,7 +449,9 @@ ag_status ag_server_create(const ag_server_config* cfg, ag_server** out);
 
 /* Queues a request (thread-safe, non-blocking) and returns its id. The input
  * arrays (host or device) must stay valid until ag_server_wait has returned
- * for this id. Their contents are not checked (submission stays cheap): they
+ * for this id. The loop uploads them when it admits the request: device (or
+ * pinned) arrays are copied asynchronously, while pageable host arrays make
+ * the loop wait for their copy before it queues the next chunk. Their contents are not checked (submission stays cheap): they
  * must meet the preconditions of ag_set_commands, ag_set_body and
  * ag_set_obstacles. AG_ERR_INVALID for a malformed request (n_envs outside
  * 1 .. AG_MAX_ENVS, other counts, NULL arrays, pitch), AG_ERR_OOM if it
