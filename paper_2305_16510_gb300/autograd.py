@@ -19,6 +19,10 @@ class RolloutLoss(torch.autograd.Function):
     differentiable too; None keeps the fleet's commands); the fleet, its
     initial motors [8, n], the horizon, the goals [3, n] and the weights are
     constants. Returns float32 [n] on the fleet's device.
+
+    The library keeps one recorded rollout per fleet: a second forward on the
+    same fleet replaces the first one's tape, and the first one's backward
+    then raises instead of returning the gradients of the other rollout.
     """
 
     @staticmethod
@@ -30,6 +34,8 @@ class RolloutLoss(torch.autograd.Function):
         loss = torch.empty(fleet.n, dtype=torch.float32, device=fleet.device)
         goal = p_goal.to(device=fleet.device, dtype=torch.float32).contiguous()
         _abi.ag_rollout_loss(fleet.ctx, n_steps, w_pos, w_omega, goal, loss)
+        fleet._recording = getattr(fleet, "_recording", 0) + 1
+        ctx.recording = fleet._recording
         ctx.fleet = fleet
         ctx.gains_device = gains.device
         ctx.has_targets = targets is not None
@@ -39,6 +45,9 @@ class RolloutLoss(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_loss):
         fleet = ctx.fleet
+        if getattr(fleet, "_recording", 0) != ctx.recording:
+            raise RuntimeError("the fleet recorded another rollout after this loss was computed: its backward "
+                               "would differentiate that rollout instead")
         gx = torch.empty((13, fleet.n), dtype=torch.float32, device=fleet.device)
         gg = torch.empty((12,), dtype=torch.float32, device=fleet.device)
         gt = torch.empty((4, fleet.n), dtype=torch.float32, device=fleet.device) if ctx.has_targets else None

@@ -27,7 +27,9 @@ class ReachEnv:
     environment whose episode ended has already been reset and ``obs`` shows
     its new episode. ``info["collided"]`` marks the episodes that ended in a
     collision. Actions lie in [-1, 1] (clamped) and map to commands through
-    ``task.action_scale`` and ``task.action_offset``.
+    ``task.action_scale`` and ``task.action_offset``. The returned tensors are
+    the environment's own buffers, overwritten by the next step (so that a
+    step allocates nothing): clone what must outlive it.
     """
 
     def __init__(self, n_envs: int, goals=None, task: _abi.ag_reach_config | None = None, seed: int = 1,

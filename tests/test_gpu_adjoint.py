@@ -182,6 +182,15 @@ def test_autograd_function_matches_ag_backward():
     out.sum().backward()
     np.testing.assert_allclose(_np(x0_t.grad), gx, rtol=1e-6, atol=1e-6 * np.abs(gx).max())
     np.testing.assert_allclose(_np(gains_t.grad), gg, rtol=1e-6)
+    # a second recording on the same fleet: the first loss's backward refuses, the second's works
+    xa = torch.from_numpy(x0).cuda().requires_grad_(True)
+    xb = torch.from_numpy(x0).cuda().requires_grad_(True)
+    out_a = rollout_loss(fl, xa, gains_t.detach(), m0_t, H, goal, W_POS, W_OMEGA)
+    out_b = rollout_loss(fl, xb, gains_t.detach(), m0_t, H, goal, W_POS, W_OMEGA)
+    with pytest.raises(RuntimeError, match="recorded another rollout"):
+        out_a.sum().backward()
+    out_b.sum().backward()
+    np.testing.assert_allclose(_np(xb.grad), gx, rtol=1e-6, atol=1e-6 * np.abs(gx).max())
     fl.close()
 
 
