@@ -11,7 +11,15 @@ from . import _abi
 
 
 class Fleet:
-    """One ag_ctx. Arrays are structure-of-arrays over environments."""
+    """One ag_ctx. Arrays are structure-of-arrays over environments.
+
+    Every call runs on the context's stream: torch's current stream when the
+    fleet is created, unless ``stream`` is given. Inputs that need a dtype or
+    device conversion are converted by torch on its current stream, and the
+    tensors the getters return are read back by torch on it too; with a
+    ``stream`` of its own, use the fleet under ``torch.cuda.stream(fleet.stream)``
+    so that both orders agree.
+    """
 
     def __init__(self, n_envs: int, *, substeps_per_step: int = 1, integrator: int = _abi.AG_INTEG_SIE,
                  n_obstacles: int = 0, n_hexa: int = 0, n_octo: int = 0, dt: float = 0.01,
