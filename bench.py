@@ -613,6 +613,110 @@ def oracle_rate(n_envs: int, n_steps: int, threads: int, seed: int = 1) -> tuple
     return n_envs * n_steps / dt, dt
 
 
+def _oracle_fleet(w, seed: int):
+    """Oracle world and fleet of a workload, reset with its Philox draw."""
+    import oracle as O
+    from paper_2305_16510_gb300 import workloads as W
+    inp = W.make_inputs(w, seed)
+    world = O.World(n_envs=w.n_envs, substeps_per_step=w.substeps_per_step, integrator=w.integrator,
+                    n_obs=w.n_obstacles, n_quad=w.n_quad, n_hexa=w.n_hexa, n_octo=w.n_octo, dt=w.dt,
+                    motor_tau=w.motor_tau, drag=w.drag)
+    fl = O.make_fleet(world, body=inp.body.astype(np.float64), modes=inp.modes,
+                      targets=inp.targets.astype(np.float64),
+                      boxes=None if inp.boxes is None else inp.boxes.astype(np.float64), seed=seed)
+    O.reset(world, fl, None, seed)
+    return world, fl, inp
+
+
+def cpu_baseline_rows(parts, target_s: float = 3.0) -> dict:
+    """The oracle, as it stands, on bounded samples of the other measured
+    workloads (about target_s seconds each), in those lines' units."""
+    import math
+    import oracle as O
+    from paper_2305_16510_gb300 import workloads as W
+    threads = os.cpu_count() or 1
+    rows = {}
+    if "mixed" in parts:           # quad / hexa / octo, drag, randomised bodies, SIE (no reset masks)
+        w = W.scaled(W.WORKLOADS["mixed"], 8192)
+        world, fl, _ = _oracle_fleet(w, 1)
+        t0 = time.perf_counter()
+        O.rollout(world, fl, 10, n_threads=threads)
+        k = max(10, int(10 * target_s / (time.perf_counter() - t0)))
+        t0 = time.perf_counter()
+        O.rollout(world, fl, k, n_threads=threads)
+        dt = time.perf_counter() - t0
+        rows["mixed"] = {"value": w.n_envs * k / dt, "unit": UNIT, "cores": threads,
+                         "sample": f"{w.n_envs} envs x {k} steps ({dt:.1f} s, FP64)"}
+    if "depth" in parts:           # 270 x 480, 87 deg, 10 m, 16 boxes per environment
+        w = W.scaled(W.WORKLOADS[WORKLOAD], 64)
+        world, fl, _ = _oracle_fleet(w, 1)
+        t0 = time.perf_counter()
+        O.render_depth(fl.state, fl.boxes, [0], 480, 270, math.radians(87), 10.0)
+        k = max(1, min(64, int(target_s / (time.perf_counter() - t0))))
+        t0 = time.perf_counter()
+        O.render_depth(fl.state, fl.boxes, list(range(k)), 480, 270, math.radians(87), 10.0)
+        dt = time.perf_counter() - t0
+        rows["depth"] = {"value": k / dt, "unit": "depth frames/s", "cores": 1,
+                         "sample": f"{k} cameras x 270 x 480, 16 boxes ({dt:.1f} s, FP64, 1 thread)"}
+    if "task" in parts:            # reach task: commands, one SIE step, score, re-draw, observe
+        n = 8192
+        w = W.Workload("reach", n, 1, 0, 0, n, 0, 0, mode_mix=(W.MODE_ATT_THRUST,))
+        world, fl, _ = _oracle_fleet(w, 1)
+        rng = np.random.default_rng(1)
+        goals = rng.uniform(-1.0, 1.0, (3, n))
+        from paper_2305_16510_gb300 import _abi
+        cfg = _abi.ag_reach_config_default()
+        scale, offset = np.array(cfg.action_scale[:]), np.array(cfg.action_offset[:])
+        steps = np.zeros(n, np.uint32)
+
+        def task_step():
+            nonlocal steps
+            act = rng.uniform(-1.0, 1.0, (4, n))
+            fl.targets[:] = offset[:, None] + scale[:, None] * np.clip(act, -1.0, 1.0)
+            col, _ = O.rollout(world, fl, 1, n_threads=threads)
+            _, _, done = O.reach_task(fl.state, goals, col, steps + 1)
+            O.reset(world, fl, (done == 1) & (col == 0), 1)
+            O.reach_task(fl.state, goals, col, steps + 1)
+            steps = np.where(done == 1, 0, steps + 1).astype(np.uint32)
+
+        t0 = time.perf_counter()
+        task_step()
+        k = max(2, int(target_s / (time.perf_counter() - t0)))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            task_step()
+        dt = time.perf_counter() - t0
+        rows["task"] = {"value": n * k / dt, "unit": "task env-steps/s", "cores": threads,
+                        "sample": f"{n} envs x {k} task steps ({dt:.1f} s, FP64, rollout on {threads} threads)"}
+    if "adjoint" in parts:         # the oracle's gradient: forward-mode passes, one per direction
+        w = W.WORKLOADS["adjoint"]
+        n, H = 512, w.horizon
+        wv = W.scaled(w, n)
+        world, fl, inp = _oracle_fleet(wv, 1)
+        gains = world.gains12()
+        goal = inp.targets[0:3].astype(np.float64)
+        eye13, eye12 = np.eye(13), np.eye(12)
+
+        def gradient(i):
+            args = (world, 4, int(fl.modes[i]), fl.targets[:, i], fl.body[:, i], fl.state[:, i], fl.motors[:4, i])
+            for d in range(13):
+                O.vehicle_loss_jvp(*args, gains, eye13[d], np.zeros(12), H, goal[:, i])
+            for d in range(12):
+                O.vehicle_loss_jvp(*args, gains, np.zeros(13), eye12[d], H, goal[:, i])
+
+        t0 = time.perf_counter()
+        gradient(0)
+        k = max(1, min(n, int(target_s / (time.perf_counter() - t0))))
+        t0 = time.perf_counter()
+        for i in range(k):
+            gradient(i)
+        dt = time.perf_counter() - t0
+        rows["adjoint"] = {"value": k * H / dt, "unit": "vehicle-steps/s (forward + gradient)", "cores": 1,
+                           "sample": f"{k} vehicles x {H} steps, 25 forward-mode passes each (13 state + 12 gain "
+                                     f"directions; the oracle has no reverse mode) ({dt:.1f} s, FP64, 1 thread)"}
+    return rows
+
+
 def cpu_baseline(target_s: float = 12.0) -> dict:
     threads = os.cpu_count() or 1
     n_envs = 8192
@@ -680,6 +784,7 @@ def main():
     world, _, _ = dist_env()
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline"]["rows"] = cpu_baseline_rows(set(args.parts.split(",")))
     print(json.dumps(out), flush=True)
 
 
