@@ -561,9 +561,15 @@ def run_trace(server, pool, trace, warm: int, cap_s: float) -> dict:
     t_end = max(done_at[i] for i in meas)
     work = sum(trace[i]["n"] * trace[i]["h"] for i in meas)
     L = np.array([lat[i] for i in meas])
+    edges = [0, 5, 10, 20, 50, 100, 200, 500, 1000, 2000, np.inf]
+    counts, _ = np.histogram(L, bins=edges)
     return {"value": work / (t_end - t_begin), "unit": UNIT, "p50_ms": float(np.percentile(L, 50)),
             "p99_ms": float(np.percentile(L, 99)), "mean_ms": float(L.mean()), "completed": len(meas),
-            "measured_of": len(trace) - warm, "submitted": submitted, "window_s": t_end - t_begin}
+            "measured_of": len(trace) - warm, "submitted": submitted, "window_s": t_end - t_begin,
+            "latency_ms": {"p10": float(np.percentile(L, 10)), "p25": float(np.percentile(L, 25)),
+                           "p75": float(np.percentile(L, 75)), "p90": float(np.percentile(L, 90)),
+                           "max": float(L.max()),
+                           "histogram": {f"{edges[k]}-{edges[k + 1]}": int(counts[k]) for k in range(len(counts))}}}
 
 
 def serving_part(seed: int) -> dict:
