@@ -77,6 +77,16 @@ def test_depth_matches_oracle_small_images():
     fl.close()
 
 
+def test_depth_without_boxes_is_max_range_everywhere():
+    from paper_2305_16510_gb300.fleet import Fleet
+    fl = Fleet(40)
+    fl.reset(None, 3)
+    img = _np(fl.render_depth(33, 17, math.radians(87), 7.5, cam_offset=(0.1, 0.0, 0.0)))
+    assert img.shape == (40, 17, 33)
+    assert np.all(img == np.float32(7.5))
+    fl.close()
+
+
 def test_depth_paper_resolution_1024_robots_sampled():
     # 2^10 robots with 270 x 480 depth cameras (the paper's depth-camera
     # workload); 3 sampled cameras are re-rendered by the oracle
