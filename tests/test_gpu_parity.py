@@ -199,6 +199,48 @@ def test_torque_free_rk4_conserves_momentum_and_energy_and_falls_on_the_parabola
     fl.close()
 
 
+def test_yaw_torque_spins_a_level_hover_with_constant_angular_acceleration():
+    """Pinned by the physics: a level vehicle commanded f = m g and a small
+    yaw moment M_z (wrench mode, no motor lag) keeps its position and turns
+    about +z with psi(t) = psi0 + w0 t + 1/2 (M_z / J_z) t^2, on quad, hexa and
+    octo airframes. Bounds: with A and its pseudo-inverse rounded to float32,
+    A A^+ - I is ~1e-7, so the 7.4 N thrust leaks ~7e-7 N m into each moment.
+    Open loop over 2 s that is ~1e-4 rad/s of yaw rate, ~1e-4 of tilt and
+    ~1e-3 m of drift; the bounds below sit ~10x above. A wrong torque sign or
+    scale misses them by orders of magnitude."""
+    from paper_2305_16510_gb300.fleet import Fleet
+    n_q, n_h, n_o = 256, 256, 256
+    n = n_q + n_h + n_o
+    rng = np.random.default_rng(21)
+    fl = Fleet(n, n_hexa=n_h, n_octo=n_o, substeps_per_step=4, integrator=_abi.AG_INTEG_RK4, motor_tau=0.0)
+    m, jz = 0.75, 0.012
+    psi0 = rng.uniform(-1, 1, n)
+    w0 = rng.uniform(-1, 1, n)
+    mz = rng.uniform(-2e-3, 2e-3, n)
+    tg = np.zeros((4, n), np.float32)
+    tg[0] = m * 9.81
+    tg[3] = mz
+    fl.set_commands(np.full(n, W.MODE_WRENCH, np.uint8), tg)
+    st = np.zeros((13, n), np.float32)
+    st[0:3] = rng.uniform(-2, 2, (3, n))
+    st[6], st[9] = np.cos(psi0 / 2), np.sin(psi0 / 2)
+    st[12] = w0
+    fl.set_state(st, np.zeros((8, n), np.float32))
+    steps = 200                                      # 2 s
+    fl.step(steps)
+    s1 = _np(fl.state()).astype(np.float64)
+    t = steps * 0.01
+    alpha = tg[3].astype(np.float64) / jz
+    psi = 2 * np.arctan2(s1[9], s1[6])
+    want = psi0 + w0 * t + 0.5 * alpha * t * t
+    err = np.angle(np.exp(1j * (psi - want)))       # wrapped to (-pi, pi]
+    assert np.max(np.abs(err)) < 1e-4, np.max(np.abs(err))
+    np.testing.assert_allclose(s1[12], w0 + alpha * t, atol=1e-3)
+    np.testing.assert_allclose(s1[7:9], 0.0, atol=1e-3)             # stays level
+    np.testing.assert_allclose(s1[0:3], st[0:3], atol=1e-2)         # hovers in place
+    fl.close()
+
+
 def test_position_control_converges_from_small_errors_on_every_airframe():
     """Pinned by the control law's stability (Lee et al. 2011, the position
     controller of Sec. I): from 0.1 m and 5 deg off a hover setpoint, quad,
