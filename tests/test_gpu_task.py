@@ -186,6 +186,43 @@ def test_reach_errors():
     fl.close()
 
 
+@pytest.mark.parametrize("n", [1, 3, 33])
+def test_reach_step_on_tiny_and_ragged_fleets(n):
+    """Fleets smaller than a warp or one lane past it: one task step against
+    the oracle's composition (the observation rows of a partly empty warp)."""
+    from harness import gpu_fleet
+    seed = 8
+    w = W.Workload("reach_small", n, 1, 0, 0, n, 0, 0)
+    inp = W.make_inputs(w, seed)
+    fl = gpu_fleet(w, inp, seed)
+    world = oracle_world(w)
+    rng = np.random.default_rng(n)
+    goals = rng.uniform(-1.0, 1.0, (3, n)).astype(np.float32)
+    cfg = _cfg(_abi.AG_MODE_ATT_THRUST, max_steps=1, max_dist=3.0)
+    fl.reset(None, seed)
+    _abi.ag_reach_begin(fl.ctx, cfg, torch.from_numpy(goals).cuda())
+    dev = fl.device
+    obs = torch.full((n, 13), np.nan, device=dev)
+    rew = torch.empty((n,), device=dev)
+    done = torch.empty((n,), dtype=torch.uint8, device=dev)
+    s0, m0, e0 = _np(fl.state()), _np(fl.motors()), _np(fl.epoch()).astype(np.uint32)
+    act = rng.uniform(-1.0, 1.0, (n, 4)).astype(np.float32)
+    _abi.ag_reach_step(fl.ctx, torch.from_numpy(act).to(dev), obs, rew, done)
+    scale, offset = np.array(cfg.action_scale[:]), np.array(cfg.action_offset[:])
+    tgt = offset[:, None] + scale[:, None] * np.clip(act.T.astype(np.float64), -1.0, 1.0)
+    orc = oracle_fleet_from(w, W.Inputs(np.full(n, _abi.AG_MODE_ATT_THRUST, np.uint8), tgt, inp.body, None),
+                            s0, m0, e0, seed)
+    ocol, _ = O.rollout(world, orc, 1)
+    ones = np.ones(n, np.uint32)
+    _, o_rew, o_done = O.reach_task(orc.state, goals, ocol, ones, **_params(cfg))
+    O.reset(world, orc, (o_done == 1) & (ocol == 0), seed)
+    o_obs = O.reach_task(orc.state, goals, ocol, ones, **_params(cfg))[0].T
+    np.testing.assert_array_equal(_np(done), o_done)          # max_steps 1: every episode ends
+    np.testing.assert_allclose(_np(rew), o_rew, rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(_np(obs), o_obs, atol=2e-6)    # restarted from the reset draw
+    fl.close()
+
+
 def test_reach_full_size_sampled_against_oracle():
     """The bench's task workload (1,048,576 quads, attitude interface, SIE, no
     obstacles) for three task steps with a step limit of 2, so every episode
