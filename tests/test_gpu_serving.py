@@ -69,6 +69,27 @@ def test_request_is_bit_identical_alone_in_a_mix_and_one_per_launch(pool):
     np.testing.assert_array_equal(ep_one, ep_alone)
 
 
+def test_tiny_and_odd_requests_are_bit_identical_alone_and_in_a_mix(pool):
+    """Requests smaller than a block or a warp, odd box counts (a padded pair)
+    and unaligned pool offsets: each result alone equals its result in a mix."""
+    rp, _ = pool
+    shapes = [(1, 60, 0), (2, 75, 1), (31, 50, 3), (33, 120, 8), (129, 90, 32)]
+    reqs = [dict(n_envs=n, n_steps=h, n_obstacles=o, seed=500 + k, offset=17 * k + 3)
+            for k, (n, h, o) in enumerate(shapes)]
+    alone = []
+    with _server(max_active=8, chunk_steps=50) as s:
+        for r in reqs:
+            st, ep, _ = s.wait(s.submit(rp.request(**r)))
+            alone.append((st, ep))
+    with _server(max_active=8, chunk_steps=50) as s:
+        ids = [s.submit(rp.request(**r)) for r in reqs]
+        mixed = [s.wait(i)[:2] for i in ids]
+    for (n, h, o), (a_st, a_ep), (m_st, m_ep) in zip(shapes, alone, mixed):
+        assert a_st.shape == (13, n) and np.isfinite(a_st).all()
+        np.testing.assert_array_equal(m_st, a_st, err_msg=f"n={n} boxes={o}")
+        np.testing.assert_array_equal(m_ep, a_ep)
+
+
 def test_served_request_matches_the_oracle(pool):
     rp, inp = pool
     n, steps, seed, off = 600, 60, 5, 1234
