@@ -201,7 +201,10 @@ ag_status ag_set_body(ag_ctx* ctx, const float* body);
  * a new state, as ag_reset). Afterwards the collided flags mark environments
  * that hit a box in any step of this call and the reset list holds each
  * environment reset during this call once (order unspecified).
- * AG_ERR_INVALID unless n_substeps / substeps_per_step is in 1 .. 2^31 - 1. */
+ * AG_ERR_INVALID unless n_substeps / substeps_per_step is in 1 .. 2^31 - 1.
+ * The call allocates nothing and never synchronises, so a loop of calls can
+ * be captured in a CUDA graph on the context's stream (make one call outside
+ * the capture first: it sets the kernel's shared-memory attribute). */
 ag_status ag_step(ag_ctx* ctx, uint32_t n_substeps);
 
 /* Same results as ag_step, computed by one kernel launch per stage per
