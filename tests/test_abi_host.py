@@ -99,3 +99,71 @@ def test_measure_fp32_peak_rejects_bad_arguments(lib):
         assert e.value.status == _abi.AG_ERR_INVALID
     assert lib.ag_measure_fp32_peak(None, 10, 1, None) == _abi.AG_ERR_INVALID
     assert b"out is NULL" in lib.ag_last_error(None)
+
+
+def _config_is_valid(c) -> bool:
+    """The rules include/ag.h states for ag_config, written out independently."""
+    import math
+    finite_pos = lambda x: math.isfinite(x) and x > 0
+    return (1 <= c.n_envs <= (1 << 28) and 1 <= c.substeps_per_step <= 65536 and c.integrator <= 1
+            and c.n_obstacles <= 64 and c.n_quad + c.n_hexa + c.n_octo == c.n_envs and c.record_every <= 65536
+            and finite_pos(c.dt) and c.motor_tau >= 0 and c.drag >= 0 and c.sphere_r >= 0 and c.u_max > 0
+            and c.arm > 0 and c.k_yaw > 0 and c.mass > 0 and all(x > 0 for x in c.inertia))
+
+
+def test_config_validation_follows_the_documented_rules(lib):
+    """Random valid configurations with at most one documented rule broken:
+    ag_create refuses exactly the broken ones (AG_ERR_INVALID, before any
+    device call). Valid ones get to the device step: without a GPU that is
+    AG_ERR_CUDA ("no CUDA device"); with one, a small context is created and
+    destroyed."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+    pos = st.sampled_from([1e-3, 0.01, 0.13, 0.5, 5.0])
+    breaks = {
+        None: lambda c: None,
+        "n_envs 0": lambda c: setattr(c, "n_envs", 0),
+        "n_envs above AG_MAX_ENVS": lambda c: setattr(c, "n_envs", (1 << 28) + 1),
+        "substeps 0": lambda c: setattr(c, "substeps_per_step", 0),
+        "substeps above 65536": lambda c: setattr(c, "substeps_per_step", 65537),
+        "integrator 2": lambda c: setattr(c, "integrator", 2),
+        "65 boxes": lambda c: setattr(c, "n_obstacles", 65),
+        "type counts": lambda c: setattr(c, "n_quad", c.n_quad + 1),
+        "record_every": lambda c: setattr(c, "record_every", 65537),
+        "dt 0": lambda c: setattr(c, "dt", 0.0),
+        "dt inf": lambda c: setattr(c, "dt", float("inf")),
+        "dt nan": lambda c: setattr(c, "dt", float("nan")),
+        "tau < 0": lambda c: setattr(c, "motor_tau", -0.01),
+        "drag < 0": lambda c: setattr(c, "drag", -0.1),
+        "radius < 0": lambda c: setattr(c, "sphere_r", -0.2),
+        "u_max 0": lambda c: setattr(c, "u_max", 0.0),
+        "arm nan": lambda c: setattr(c, "arm", float("nan")),
+        "k_yaw < 0": lambda c: setattr(c, "k_yaw", -0.016),
+        "mass 0": lambda c: setattr(c, "mass", 0.0),
+        "inertia nan": lambda c: c.inertia.__setitem__(1, float("nan")),
+    }
+
+    @hyp.settings(max_examples=150, deadline=None, derandomize=True)
+    @hyp.given(n=st.sampled_from([1, 7, 33, 4096]), sub=st.sampled_from([1, 4, 65536]), integ=st.sampled_from([0, 1]),
+               obs=st.sampled_from([0, 3, 64]), mixed=st.booleans(), rec=st.sampled_from([0, 32, 65536]),
+               dt=pos, tau=st.sampled_from([0.0, 0.03]), drag=st.sampled_from([0.0, 0.1]), umax=pos, arm=pos,
+               kyaw=pos, mass=pos, which=st.sampled_from([None] * 10 + list(breaks)))  # ~1/3 valid
+    def check(n, sub, integ, obs, mixed, rec, dt, tau, drag, umax, arm, kyaw, mass, which):
+        c = _abi.ag_config_default()
+        c.n_envs, c.substeps_per_step, c.integrator, c.n_obstacles, c.record_every = n, sub, integ, obs, rec
+        c.n_hexa, c.n_octo = (n // 3, n // 4) if mixed else (0, 0)
+        c.n_quad = n - c.n_hexa - c.n_octo
+        c.dt, c.motor_tau, c.drag, c.u_max, c.arm, c.k_yaw, c.mass = dt, tau, drag, umax, arm, kyaw, mass
+        breaks[which](c)
+        valid = _config_is_valid(c)
+        assert valid == (which is None), which          # the rule list itself agrees with the break
+        try:
+            ctx = _abi.ag_create(c)
+        except _abi.AgError as e:
+            expect = _abi.AG_ERR_CUDA if valid else _abi.AG_ERR_INVALID
+            assert e.status == expect, (which, e.status, str(e))
+            return
+        assert valid, which
+        _abi.ag_destroy(ctx)
+
+    check()
