@@ -224,7 +224,7 @@ def gpu_arm(args) -> dict | None:
         w = W.scaled(w, args.envs)
     C = args.steps_per_call
     parts = set(args.parts.split(","))
-    seed = 1 + rank
+    seed = args.seed + rank
     inp = W.make_inputs(w, seed)
     fl = make_fleet(w, inp, seed)
     n_sub = C * w.substeps_per_step
@@ -776,6 +776,7 @@ def main():
     ap.add_argument("--envs", type=int, default=0, help="reduced fleet size (default: the full workload)")
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
     ap.add_argument("--parts", default="fused,plain,e2e,paper,mixed,depth,task,adjoint,serve")
+    ap.add_argument("--seed", type=int, default=1, help="input seed of rank 0 (rank r uses seed + r)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
