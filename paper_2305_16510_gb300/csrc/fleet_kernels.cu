@@ -35,10 +35,14 @@ constexpr size_t kFusedSmemCap = 200 * 1024;
 // consecutive and conflict-free. A thread reads only what it wrote, so no
 // barrier is needed.
 // BOXES = false (no obstacles) keeps the kernel within 128 registers, so
-// more warps are resident when there is no staging to pay for.
+// more warps are resident when there is no staging to pay for. A quad-only
+// semi-implicit-Euler fleet without obstacles needs about 70 (no spills),
+// and its bound of 7 blocks per SM lets a 131,072-vehicle fleet run in one
+// wave; fleets with hexa and octo rotors keep the looser bound, which
+// measured faster for them.
 template <int INTEG, bool QUAD_ONLY, bool DRAG, bool BOXES>
-__global__ void __launch_bounds__(128, BOXES ? 3 : 4) k_fused_step(FleetBuffers fb, StepParams P, int n_steps,
-                                                                  int substeps) {
+__global__ void __launch_bounds__(128, BOXES ? 3 : ((QUAD_ONLY && INTEG == kIntegSIE) ? 7 : 4))
+    k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
   extern __shared__ float2 sm_pairs[];  // [ceil(n_obs / 2) - 1][10][blockDim.x] box pairs 1..
   const int B = blockDim.x;
   const uint32_t slot = blockIdx.x * B + threadIdx.x;
