@@ -766,7 +766,10 @@ def reference_arm(args) -> dict | None:
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def main():
+PARTS = ("fused", "plain", "e2e", "paper", "mixed", "depth", "task", "adjoint", "serve")
+
+
+def make_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -775,9 +778,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--envs", type=int, default=0, help="reduced fleet size (default: the full workload)")
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
-    ap.add_argument("--parts", default="fused,plain,e2e,paper,mixed,depth,task,adjoint,serve")
+    ap.add_argument("--parts", default=",".join(PARTS))
     ap.add_argument("--seed", type=int, default=1, help="input seed of rank 0 (rank r uses seed + r)")
+    return ap
+
+
+def main():
+    ap = make_parser()
     args = ap.parse_args()
+    unknown = set(args.parts.split(",")) - set(PARTS)
+    if unknown:
+        ap.error(f"unknown --parts: {sorted(unknown)} (choose from {', '.join(PARTS)})")
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
