@@ -253,8 +253,8 @@ ag_status ag_get_motors(ag_ctx* ctx, float* motors, uint32_t* epoch);
  * bit. Values are not checked. AG_ERR_INVALID for a NULL state. */
 ag_status ag_set_state(ag_ctx* ctx, const float* state, const float* motors, const uint32_t* epoch);
 
-/* Allocation-free unfused step: the same computation as ag_step_plain,
- * without a context and without allocating any device memory.
+/* Allocation-free unfused step: the computation of ag_step_plain, without a
+ * context and without allocating any device memory.
  *
  * The paper has no counterpart; this entry point exists for callers that
  * cannot call cudaMalloc: for example a simulator embedded in a real-time
@@ -269,14 +269,26 @@ ag_status ag_set_state(ag_ctx* ctx, const float* state, const float* motors, con
  * wrenches, hit bytes and reset counters live in a static device array sized
  * for AG_NOALLOC_MAX_ENVS environments (2,424,832 bytes), which every GPU that
  * loads the library holds until the process exits.
+ *   - Two differences from a context's ag_step_plain: a collision reset never
+ *     re-draws the environment's obstacles (there is no
+ *     ag_set_obstacle_randomization here), and the body array is not checked
+ *     (ag_set_body rejects non-finite or non-positive masses and inertias;
+ *     here they are the caller's precondition).
  *   - n_envs > AG_NOALLOC_MAX_ENVS, an invalid config, an n_substeps that is
- *     not a positive multiple of substeps_per_step, or a NULL / non-device
- *     pointer returns AG_ERR_INVALID; a CUDA failure returns AG_ERR_CUDA.
- *     The reason is written to err (err_len bytes, may be NULL).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture
- *     begins.
- *   - Every call on a device shares the one array and leaves its contents
+ *     not a positive multiple of substeps_per_step, a NULL pointer, a pointer
+ *     to host memory or to another device's memory, or a stream of another
+ *     device returns AG_ERR_INVALID ("another device" means other than the
+ *     current one, cudaGetDevice). A CUDA failure returns AG_ERR_CUDA. The
+ *     reason is written to err (err_len bytes, may be NULL).
+ *   - The array's address belongs to the CUDA context current at the call
+ *     (the primary context, or a context the host application made current).
+ *     Every call outside stream capture looks the address up in that context
+ *     (cudaGetSymbolAddress; the first lookup in a context loads the module)
+ *     and remembers it for that context. A call on a stream that is being
+ *     captured uses the remembered address, so make one call in each context
+ *     (and again after cudaDeviceReset) before any capture begins; without
+ *     one the call returns AG_ERR_STATE.
+ *   - Every call in a context shares the one array and leaves its contents
  *     behind; the call clears what must start at zero itself. Two calls whose
  *     work overlaps on the GPU (for example on two streams) race on the array
  *     and give undefined results: order them on one stream. */

@@ -2,7 +2,9 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "ctx_internal.h"
@@ -18,7 +20,6 @@ using namespace agh;
 // AG_NOALLOC_MAX_ENVS environments, so the call never allocates: every GPU
 // that loads this library holds the array until the process exits, and every
 // call on that GPU reuses it.
-#include <mutex>
 
 namespace {
 
@@ -31,21 +32,116 @@ constexpr size_t kNoallocBytes = kNoallocOffHits + kNoallocN;  // 2,424,832 byte
 static_assert(kNoallocOffWrench % 256 == 0 && kNoallocOffResets % 256 == 0 && kNoallocOffHits % 256 == 0,
               "scratch sub-arrays must stay 256-byte aligned");
 
-constexpr int kNoallocMaxDevices = 64;
+// The array's device address belongs to the CUDA context that loaded this
+// module, not to the device: a host application may make its own driver-API
+// context current, and cudaDeviceReset replaces the primary context. So the
+// address is looked up again on every call made outside stream capture, and
+// remembered per context for calls made while a stream is being captured
+// (where a first lookup could load the module into the context).
+constexpr int kNoallocMaxContexts = 64;
+struct ScratchEntry {
+  CUcontext ctx;
+  unsigned char* base;
+};
 std::mutex g_noalloc_mutex;
-unsigned char* g_noalloc_base[kNoallocMaxDevices] = {};
+ScratchEntry g_noalloc_cache[kNoallocMaxContexts] = {};
+int g_noalloc_cache_n = 0;
+int g_noalloc_cache_next = 0;  // entry replaced when all are taken (round robin)
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
 
 void noalloc_error(char* buf, size_t len, const char* msg) {
   if (buf && len) std::snprintf(buf, len, "%s", msg);
 }
 
+// The context current on this thread, through the driver entry point the
+// runtime hands out (the library links no libcuda of its own). nullptr on
+// failure.
+CUcontext current_context() {
+  if (!g_ctx_get_current) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+  }
+  CUcontext c = nullptr;
+  if (g_ctx_get_current(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+// The device a kernel buffer lives on; -1 for host memory or an unknown
+// pointer. Managed memory reports the device it was allocated against.
+int device_of(const void* p) {
+  cudaPointerAttributes pa;
+  int dev = -1;
+  if (cudaPointerGetAttributes(&pa, p) == cudaSuccess &&
+      (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged))
+    dev = pa.device;
+  cudaGetLastError();
+  return dev;
+}
 
 }  // namespace
 
 // The scratch itself. Host code must not use this name as an address: it is a
 // host-side stand-in for the symbol; the device address comes from
-// cudaGetSymbolAddress below, once per device.
+// cudaGetSymbolAddress, in the context that is current for the call.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+namespace {
+
+// Device address of the scratch array in the current context (see above).
+ag_status scratch_base(cudaStream_t stream, unsigned char** base, char* err, size_t err_len) {
+  CUcontext ctx = current_context();
+  if (!ctx) {
+    noalloc_error(err, err_len, "no current CUDA context");
+    return AG_ERR_CUDA;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    noalloc_error(err, err_len, "cudaStreamIsCapturing failed on the stream");
+    return AG_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  int slot = -1;
+  for (int i = 0; i < g_noalloc_cache_n; ++i)
+    if (g_noalloc_cache[i].ctx == ctx) slot = i;
+  if (cap != cudaStreamCaptureStatusNone) {
+    if (slot < 0) {
+      noalloc_error(err, err_len, "the first call in a CUDA context must come before any stream capture");
+      return AG_ERR_STATE;
+    }
+    *base = g_noalloc_cache[slot].base;
+    return AG_OK;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    noalloc_error(err, err_len, cudaGetErrorString(e));
+    return AG_ERR_CUDA;
+  }
+  if (slot < 0) {
+    if (g_noalloc_cache_n < kNoallocMaxContexts) {
+      slot = g_noalloc_cache_n++;
+    } else {
+      slot = g_noalloc_cache_next;
+      g_noalloc_cache_next = (g_noalloc_cache_next + 1) % kNoallocMaxContexts;
+    }
+    g_noalloc_cache[slot].ctx = ctx;
+  }
+  g_noalloc_cache[slot].base = static_cast<unsigned char*>(p);
+  *base = g_noalloc_cache[slot].base;
+  return AG_OK;
+}
+
+}  // namespace
 
 extern "C" ag_status ag_step_plain_noalloc(const ag_config* cfg, void* cuda_stream, uint32_t n_substeps,
                                            uint64_t seed, float* state, float* motors, const float* body,
@@ -67,36 +163,35 @@ extern "C" ag_status ag_step_plain_noalloc(const ag_config* cfg, void* cuda_stre
     noalloc_error(err, err_len, "n_substeps must be a positive multiple of substeps_per_step (at most 2^31 - 1 steps)");
     return AG_ERR_INVALID;
   }
-  const void* required[] = {state, motors, body, modes, targets, epoch, collided, reset_ids, n_reset};
-  for (const void* p : required)
-    if (!p || !on_device(p)) {
-      noalloc_error(err, err_len, "every buffer must be a non-NULL device pointer");
-      return AG_ERR_INVALID;
-    }
-  if (cfg->n_obstacles > 0 && (!boxes || !on_device(boxes))) {
-    noalloc_error(err, err_len, "boxes must be a device pointer when n_obstacles > 0");
-    return AG_ERR_INVALID;
-  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
     noalloc_error(err, err_len, "no usable CUDA device");
     return AG_ERR_CUDA;
   }
-  unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_base[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        noalloc_error(err, err_len, cudaGetErrorString(e));
-        return AG_ERR_CUDA;
-      }
-      g_noalloc_base[dev] = static_cast<unsigned char*>(p);
+  const cudaStream_t stream = (cudaStream_t)cuda_stream;
+  if (stream) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(stream, &sdev) != cudaSuccess || sdev != dev) {
+      cudaGetLastError();
+      noalloc_error(err, err_len, "the stream does not belong to the current device");
+      return AG_ERR_INVALID;
     }
-    base = g_noalloc_base[dev];
   }
+  const void* required[] = {state, motors, body, modes, targets, epoch, collided, reset_ids, n_reset};
+  for (const void* p : required)
+    if (!p || device_of(p) != dev) {
+      noalloc_error(err, err_len, "every buffer must be a non-NULL pointer to memory of the current device");
+      return AG_ERR_INVALID;
+    }
+  if (cfg->n_obstacles > 0 && (!boxes || device_of(boxes) != dev)) {
+    noalloc_error(err, err_len, "boxes must point to memory of the current device when n_obstacles > 0");
+    return AG_ERR_INVALID;
+  }
+  unsigned char* base = nullptr;
+  const ag_status s = scratch_base(stream, &base, err, err_len);
+  if (s != AG_OK) return s;
   agk::FleetBuffers fb;
   std::memset(&fb, 0, sizeof(fb));
   fb.state = state;
@@ -118,21 +213,9 @@ extern "C" ag_status ag_step_plain_noalloc(const ag_config* cfg, void* cuda_stre
   fb.n_hexa = cfg->n_hexa;
   fb.n_octo = cfg->n_octo;
   fb.n_obs = cfg->n_obstacles;
-  agk::StepParams P;
-  for (int i = 0; i < 3; ++i) {
-    P.kx[i] = cfg->kx[i]; P.kv[i] = cfg->kv[i]; P.kR[i] = cfg->kR[i]; P.kW[i] = cfg->kW[i];
-  }
-  for (int t = 0; t < 3; ++t) rotor_matrices(t == 0 ? 4 : (t == 1 ? 6 : 8), cfg->arm, cfg->k_yaw, P.A[t], P.Ap[t]);
-  const double h = (double)cfg->dt / cfg->substeps_per_step;
-  P.h = (float)h;
-  P.alpha = cfg->motor_tau > 0.f ? (float)(1.0 - std::exp(-h / (double)cfg->motor_tau)) : 1.f;
-  P.drag = cfg->drag;
-  P.r2 = cfg->sphere_r * cfg->sphere_r;
-  P.u_max = cfg->u_max;
-  P.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
-  P.seed_hi = (uint32_t)(seed >> 32);
+  const agk::StepParams P = agk::step_params_for(*cfg, seed);
   e = agk::launch_plain_step(fb, P, (int)cfg->integrator, (int)(n_substeps / cfg->substeps_per_step),
-                             (int)cfg->substeps_per_step, (cudaStream_t)cuda_stream);
+                             (int)cfg->substeps_per_step, stream);
   if (e != cudaSuccess) {
     noalloc_error(err, err_len, cudaGetErrorString(e));
     return AG_ERR_CUDA;
