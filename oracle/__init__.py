@@ -94,6 +94,9 @@ def _declare(L: ctypes.CDLL) -> None:
     L.orc_log_u01.argtypes = [ctypes.c_uint32]
     L.orc_log_u01.restype = ctypes.c_float
     L.orc_count_ops.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p]
+    L.orc_count_depth_ops.argtypes = [_i64p, _i64p, _i64p]
+    L.orc_count_reverse_ops.argtypes = [vp, ctypes.c_int, ctypes.c_int, _i64p, _i64p]
+    L.orc_count_reverse_primitive.argtypes = [ctypes.c_int, _i64p, _i64p]
     L.orc_vehicle_loss.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.c_int, _dp,
                                    ctypes.c_double, ctypes.c_double]
     L.orc_vehicle_loss.restype = ctypes.c_double
@@ -413,6 +416,35 @@ def count_ops(world: World, mode: int, n_obs: int, n_rot: int = 4) -> dict:
     w = world.c()
     lib().orc_count_ops(ctypes.byref(w), int(mode), int(n_obs), int(n_rot), _ptr(out, _i64p))
     return dict(zip(["add", "mul", "div", "sqrt", "trans", "cmp"], (int(x) for x in out)))
+
+
+_FWD_KEYS = ["add", "mul", "div", "sqrt", "trans", "cmp"]
+_REV_KEYS = ["add", "mul", "div", "sqrt", "trans"]
+
+
+def count_depth_ops() -> dict:
+    """Operations of the depth caster by what they repeat over: 'ray' per
+    pixel, 'box' per (camera, box) pair, 'pair' per (pixel, box) pair."""
+    outs = [np.zeros(6, dtype=np.int64) for _ in range(3)]
+    lib().orc_count_depth_ops(*(_ptr(o, _i64p) for o in outs))
+    return {k: dict(zip(_FWD_KEYS, (int(x) for x in o))) for k, o in zip(("ray", "box", "pair"), outs)}
+
+
+def count_reverse_ops(world: World, mode: int, n_rot: int = 4) -> tuple[dict, dict]:
+    """(forward, reverse) operations of one step of the rollout objective with
+    state, motors, gains and targets active (see CntRev in scalars.hpp)."""
+    fwd, rev = np.zeros(6, dtype=np.int64), np.zeros(5, dtype=np.int64)
+    w = world.c()
+    lib().orc_count_reverse_ops(ctypes.byref(w), int(mode), int(n_rot), _ptr(fwd, _i64p), _ptr(rev, _i64p))
+    return dict(zip(_FWD_KEYS, (int(x) for x in fwd))), dict(zip(_REV_KEYS, (int(x) for x in rev)))
+
+
+def count_reverse_primitive(which: int) -> tuple[dict, dict]:
+    """(forward, reverse) operations of 0 dot(a, b), 1 quat_normalize(q) or
+    2 cross(a, b) with every input active."""
+    fwd, rev = np.zeros(6, dtype=np.int64), np.zeros(5, dtype=np.int64)
+    lib().orc_count_reverse_primitive(int(which), _ptr(fwd, _i64p), _ptr(rev, _i64p))
+    return dict(zip(_FWD_KEYS, (int(x) for x in fwd))), dict(zip(_REV_KEYS, (int(x) for x in rev)))
 
 
 def vehicle_loss(world: World, n_rot, mode, tgt4, body4, state13, motors, gains12, horizon, p_goal,

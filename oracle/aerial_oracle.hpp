@@ -557,12 +557,26 @@ bool sphere_hits_box(Vec3<T> p, T r, Vec3<T> c, Vec3<T> h, Quat<T> qb) {
 // closer. A ray enters the box {|x_i| <= h_i} (box frame) by the slab method:
 // t_in = max_i min(t_i-, t_i+), t_out = min_i max(t_i-, t_i+) with
 // t_i-+ = (-+h_i - o_i) / d_i, and hits it iff t_out >= max(t_in, 0).
-template <class T>
-T ray_box_depth(Vec3<T> o, Vec3<T> d, Vec3<T> c, Vec3<T> h, Quat<T> qb, T max_range) {
-  Mat3<T> Rt = transpose(unit_quat_to_rot(qb));
-  Vec3<T> ob = matvec(Rt, o - c);
-  Vec3<T> db = matvec(Rt, d);
-  T oi[3] = {ob.x, ob.y, ob.z}, di[3] = {db.x, db.y, db.z}, hi[3] = {h.x, h.y, h.z};
+//
+// The work splits into a part per (camera, box) pair, which does not depend on
+// the pixel (the box's rotation R_b^T and the camera origin in the box frame),
+// and the part per (pixel, box) pair (the ray direction in the box frame and
+// the slab intervals). ray_box_depth is the two in sequence.
+template <class T> struct BoxInCamera {
+  Mat3<T> Rt;   // R_b^T: world -> box frame
+  Vec3<T> ob;   // camera origin in the box frame
+};
+
+template <class T> BoxInCamera<T> box_in_camera(Vec3<T> o, Vec3<T> c, Quat<T> qb) {
+  BoxInCamera<T> bc;
+  bc.Rt = transpose(unit_quat_to_rot(qb));
+  bc.ob = matvec(bc.Rt, o - c);
+  return bc;
+}
+
+template <class T> T ray_slab_depth(const BoxInCamera<T>& bc, Vec3<T> d, Vec3<T> h, T max_range) {
+  Vec3<T> db = matvec(bc.Rt, d);
+  T oi[3] = {bc.ob.x, bc.ob.y, bc.ob.z}, di[3] = {db.x, db.y, db.z}, hi[3] = {h.x, h.y, h.z};
   T t_in = T(-1e300), t_out = T(1e300);
   for (int i = 0; i < 3; ++i) {
     if (di[i] == T(0)) {
@@ -577,6 +591,11 @@ T ray_box_depth(Vec3<T> o, Vec3<T> d, Vec3<T> c, Vec3<T> h, Quat<T> qb, T max_ra
   T t0 = t_in < T(0) ? T(0) : t_in;
   if (t_out < t0) return max_range;
   return t0 < max_range ? t0 : max_range;
+}
+
+template <class T>
+T ray_box_depth(Vec3<T> o, Vec3<T> d, Vec3<T> c, Vec3<T> h, Quat<T> qb, T max_range) {
+  return ray_slab_depth(box_in_camera(o, c, qb), d, h, max_range);
 }
 
 }  // namespace orc

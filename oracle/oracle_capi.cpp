@@ -434,6 +434,95 @@ void orc_count_ops(const void* world, int mode, int n_obs, int n_rot, long long 
   counts[3] = oc.sqrt; counts[4] = oc.trans; counts[5] = oc.cmp;
 }
 
+void put_counts(long long out[6]) {
+  OpCounts oc = op_counts();
+  out[0] = oc.add; out[1] = oc.mul; out[2] = oc.div; out[3] = oc.sqrt; out[4] = oc.trans; out[5] = oc.cmp;
+}
+
+// Operation counts of the depth camera (ray_box_depth, orc_render_depth),
+// split by what each part is repeated over: `ray` per pixel (its world-frame
+// ray R d_c), `box` per (camera, box) pair (box_in_camera), `pair` per
+// (pixel, box) pair (ray_slab_depth, for a ray with no zero component that
+// hits the box). Each is {add, mul, div, sqrt, trans, cmp}.
+void orc_count_depth_ops(long long ray[6], long long box[6], long long pair[6]) {
+  const double W = 480.0, H = 270.0, f = 0.5 * W / std::tan(0.5 * 1.5);
+  Quat<Cnt> qc = {Cnt(0.9), Cnt(0.1), Cnt(-0.2), Cnt(0.3)};
+  Mat3<Cnt> R = quat_to_rot(qc);
+  Vec3<Cnt> o = {Cnt(0.1), Cnt(0.2), Cnt(0.3)};
+  op_counts() = OpCounts{0, 0, 0, 0, 0, 0};
+  const Cnt c = Cnt(100.0), r = Cnt(50.0);
+  Vec3<Cnt> dc = {Cnt(1.0), -(c + Cnt(0.5) - Cnt(0.5 * W)) / Cnt(f), -(r + Cnt(0.5) - Cnt(0.5 * H)) / Cnt(f)};
+  Vec3<Cnt> d = matvec(R, dc);
+  put_counts(ray);
+  op_counts() = OpCounts{0, 0, 0, 0, 0, 0};
+  BoxInCamera<Cnt> bc = box_in_camera(o, Vec3<Cnt>{Cnt(3.0), Cnt(0.4), Cnt(0.2)},
+                                      Quat<Cnt>{Cnt(0.9), Cnt(0.1), Cnt(0.3), Cnt(0.3)});
+  put_counts(box);
+  op_counts() = OpCounts{0, 0, 0, 0, 0, 0};
+  Cnt t = ray_slab_depth(bc, Vec3<Cnt>{Cnt(1.0), Cnt(0.1), Cnt(0.05)}, Vec3<Cnt>{Cnt(0.5), Cnt(0.5), Cnt(0.5)},
+                         Cnt(10.0));
+  put_counts(pair);
+  (void)d; (void)t;
+}
+
+void put_rev(long long out[5]) {
+  RevCounts rc = rev_counts();
+  out[0] = rc.add; out[1] = rc.mul; out[2] = rc.div; out[3] = rc.sqrt; out[4] = rc.trans;
+}
+
+// Forward and reverse-mode operation counts of ONE step of the
+// differentiable-rollout objective (vehicle_loss over one step: controller
+// of `mode`, allocation, clamp, lag, semi-implicit Euler, and the step's loss
+// term) for a vehicle near hover with the state, motors, 12 gains and 4
+// targets active. fwd = {add, mul, div, sqrt, trans, cmp} of the step; rev =
+// {add, mul, div, sqrt, trans} of its adjoint (see CntRev).
+void orc_count_reverse_ops(const void* world, int mode, int n_rot, long long fwd[6], long long rev[5]) {
+  World w = world_of(world);
+  Rotors rot = make_rotors(n_rot, w.arm, w.k_yaw);
+  Gains<CntRev> g;
+  g.kx = {CntRev(w.kx[0], true), CntRev(w.kx[1], true), CntRev(w.kx[2], true)};
+  g.kv = {CntRev(w.kv[0], true), CntRev(w.kv[1], true), CntRev(w.kv[2], true)};
+  g.kR = {CntRev(w.kR[0], true), CntRev(w.kR[1], true), CntRev(w.kR[2], true)};
+  g.kW = {CntRev(w.kW[0], true), CntRev(w.kW[1], true), CntRev(w.kW[2], true)};
+  Body<CntRev> b = {CntRev(0.75), {CntRev(0.007), CntRev(0.007), CntRev(0.012)}};
+  State<CntRev> s;
+  s.p = {CntRev(0.3, true), CntRev(-0.2, true), CntRev(0.1, true)};
+  s.v = {CntRev(0.1, true), CntRev(0.2, true), CntRev(-0.1, true)};
+  s.q = {CntRev(0.99, true), CntRev(0.05, true), CntRev(-0.08, true), CntRev(0.1, true)};
+  s.w = {CntRev(0.1, true), CntRev(-0.2, true), CntRev(0.05, true)};
+  CntRev u[8];
+  for (int k = 0; k < 8; ++k) u[k] = CntRev(1.8, true);
+  double t4[4];
+  if (mode == MODE_POSITION) { t4[0] = 1.0; t4[1] = -1.0; t4[2] = 0.5; t4[3] = 0.3; }
+  else if (mode == MODE_BODY_VEL) { t4[0] = 0.5; t4[1] = -0.5; t4[2] = 0.2; t4[3] = 0.1; }
+  else if (mode == MODE_ATT_THRUST) { t4[0] = 0.1; t4[1] = -0.1; t4[2] = 0.2; t4[3] = 7.0; }
+  else { t4[0] = 7.0; t4[1] = 0.0; t4[2] = 0.0; t4[3] = 0.0; }
+  CntRev tgt[4];
+  for (int k = 0; k < 4; ++k) tgt[k] = CntRev(t4[k], true);
+  const double goal[3] = {0.5, -0.5, 0.2};
+  op_counts() = OpCounts{0, 0, 0, 0, 0, 0};
+  rev_counts() = RevCounts{0, 0, 0, 0, 0};
+  vehicle_loss(w, rot, mode, tgt, b, s, u, g, 1, goal, 1.0, 0.01);
+  put_counts(fwd);
+  put_rev(rev);
+}
+
+// The same counts for one small building block with every input active, to
+// check CntRev against counts made by hand: which = 0 dot(a, b) of two
+// 3-vectors, 1 quat_normalize(q), 2 cross(a, b).
+void orc_count_reverse_primitive(int which, long long fwd[6], long long rev[5]) {
+  Vec3<CntRev> a = {CntRev(0.3, true), CntRev(-0.2, true), CntRev(0.1, true)};
+  Vec3<CntRev> bb = {CntRev(0.7, true), CntRev(0.4, true), CntRev(-0.5, true)};
+  Quat<CntRev> q = {CntRev(0.9, true), CntRev(0.1, true), CntRev(-0.2, true), CntRev(0.3, true)};
+  op_counts() = OpCounts{0, 0, 0, 0, 0, 0};
+  rev_counts() = RevCounts{0, 0, 0, 0, 0};
+  if (which == 0) (void)dot(a, bb);
+  else if (which == 1) (void)quat_normalize(q);
+  else (void)cross(a, bb);
+  put_counts(fwd);
+  put_rev(rev);
+}
+
 // Loss of one vehicle (see vehicle_loss) in FP64. gains12 = (k_x, k_v, k_R,
 // k_Omega) diagonals; state13 / motors (n_rot entries) are the initial state.
 double orc_vehicle_loss(const void* world, int n_rot, int mode, const double tgt[4], const double body4[4],

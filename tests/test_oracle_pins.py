@@ -605,6 +605,58 @@ def test_op_count_of_one_box_test_matches_a_hand_count():
         assert (c["div"], c["sqrt"], c["trans"]) == (c0["div"], c0["sqrt"], c0["trans"])
 
 
+def test_depth_op_counts_match_a_hand_count():
+    # per (pixel, box) pair (ray_slab_depth): d_b = R_b^T d 9 mul + 6 add; per axis
+    # t1 = (-h - o) / d and t2 = (h - o) / d, 2 add + 2 div (the sign flip is free):
+    # 12 add, 9 mul, 6 div; comparisons: d == 0, two for t1 < t2, t_in < lo, up < t_out
+    # per axis (15), then t_in < 0, t_out < t0, t0 < max_range (3).
+    # per (camera, box): R_b 27 mul + 12 add, o - c 3 add, R_b^T (o - c) 9 mul + 6 add.
+    # per pixel: the two centred pixel coordinates 2 add + 1 div each, R d_c 9 mul + 6 add.
+    c = O.count_depth_ops()
+    assert c["pair"] == {"add": 12, "mul": 9, "div": 6, "sqrt": 0, "trans": 0, "cmp": 18}
+    assert c["box"] == {"add": 21, "mul": 36, "div": 0, "sqrt": 0, "trans": 0, "cmp": 0}
+    assert c["ray"] == {"add": 10, "mul": 9, "div": 2, "sqrt": 0, "trans": 0, "cmp": 0}
+
+
+def test_reverse_op_counter_matches_hand_counts():
+    # Every adjoint rule accumulates into each active operand (one add per
+    # accumulation). dot(a, b) = a.x b.x + a.y b.y + a.z b.z, all active:
+    # forward 3 mul + 2 add; reverse: each product 2 x (1 mul + 1 add), each
+    # sum 2 x 1 add -> 6 mul, 10 add.
+    fwd, rev = O.count_reverse_primitive(0)
+    assert (fwd["mul"], fwd["add"]) == (3, 2)
+    assert rev == {"add": 10, "mul": 6, "div": 0, "sqrt": 0, "trans": 0}
+    # quat_normalize: n = sqrt(w w + x x + y y + z z), q / n: forward 4 mul +
+    # 3 add + 1 sqrt + 4 div. Reverse: 4 squares (both operands the same active
+    # value) 8 mul + 8 add; 3 sums 6 add; sqrt 1 mul + 1 div + 1 add; 4 quotients
+    # with both operands active 4 x (1 div + 1 mul + 2 add).
+    fwd, rev = O.count_reverse_primitive(1)
+    assert (fwd["mul"], fwd["add"], fwd["sqrt"], fwd["div"]) == (4, 3, 1, 4)
+    assert rev == {"add": 23, "mul": 13, "div": 5, "sqrt": 0, "trans": 0}
+    # cross(a, b): 6 products and 3 differences: reverse 12 mul + 12 add + 6 add.
+    fwd, rev = O.count_reverse_primitive(2)
+    assert (fwd["mul"], fwd["add"]) == (6, 3)
+    assert rev == {"add": 18, "mul": 12, "div": 0, "sqrt": 0, "trans": 0}
+
+
+def test_reverse_count_of_a_step_sees_every_mode_and_airframe():
+    # The adjoint of a step is a few times the step itself (the cheap-gradient
+    # principle bounds reverse mode by a small constant times the function),
+    # it grows with the rotor count, and the trig of the angle modes appears.
+    world = O.World(n_envs=1)
+    for mode in (O.MODE_POSITION, O.MODE_BODY_VEL, O.MODE_ATT_THRUST, O.MODE_WRENCH):
+        tot = {}
+        for n_rot in (4, 6, 8):
+            fwd, rev = O.count_reverse_ops(world, mode, n_rot)
+            f = fwd["add"] + fwd["mul"] + fwd["div"] + fwd["sqrt"] + fwd["trans"]
+            r = rev["add"] + rev["mul"] + rev["div"] + rev["sqrt"] + rev["trans"]
+            assert 1.5 * f < r < 5 * f
+            tot[n_rot] = r
+        assert tot[4] < tot[6] < tot[8]
+        _, rev = O.count_reverse_ops(world, mode, 4)
+        assert (rev["trans"] > 0) == (mode in (O.MODE_POSITION, O.MODE_BODY_VEL, O.MODE_ATT_THRUST))
+
+
 # ------------------------------------------------- obstacle pose re-draw --
 ENV_MIN, ENV_MAX = (-5.0, -4.0, 0.0), (5.0, 4.0, 3.0)
 
