@@ -57,20 +57,37 @@ FLOP_PER_VEHICLE_STEP_MIXED = 584.4
 # per step the collision test (position 12, 16 boxes x 40 in; hit byte out)
 # and the reset pass (hit byte in).
 PLAIN_BYTES_PER_VEHICLE_STEP = 301 * 4 + 12 + 16 * 40 + 1 + 1
-HBM_PEAK_GBS = 6794.5  # measured GB300 copy bandwidth (MEASURED_PEAKS.json, hbm_gbs)
+HBM_PEAK_GBS = 6788.3  # measured GB300 copy bandwidth (MEASURED_PEAKS.json, hbm_gbs)
+
+
+def hbm_peak_gbs() -> float:
+    """The machine's measured copy bandwidth (MEASURED_PEAKS.json when present,
+    else the figure it held when these lines were written)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return HBM_PEAK_GBS
+
+
 FLOP_PER_VEHICLE_STEP_PAPER_SHAPE = 528.5
-# GB300 FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2,070 MHz
-SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
-ALU_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+
+
+def alu_peak_tflops(info: dict) -> float:
+    """FP32 CUDA-core peak from a device's own attributes: SMs x FP32 lanes per
+    SM x 2 FLOP per FMA x peak SM clock (ag_query_alu_peak)."""
+    return info["sm_count"] * info["fp32_lanes_per_sm"] * 2 * info["max_sm_clock_khz"] * 1e3 / 1e12
+
+
 # Algorithmic bytes of one fused launch per vehicle: state in+out (13 f32 x 2),
 # motors in+out (4 x 2), body (4), targets (4), mode (1 B), epoch in+out (2 x 4),
 # boxes (16 x 10 f32), collided flag (1 B), reset-list entry (4 B, upper bound)
 BYTES_PER_VEHICLE_LAUNCH = 4 * (26 + 8 + 4 + 4) + 1 + 8 + 4 * 160 + 1 + 4
 # DRAM traffic of one full-size fused launch (1,048,576 envs, 1,000 steps):
 # dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu capture of
-# exactly this launch (796.32 MB + 68.94 MB). It scales with the fleet size
+# exactly this launch (794.64 MB + 68.57 MB). It scales with the fleet size
 # (each env is loaded and stored once per launch), not with the step count.
-TRAFFIC_BYTES_FULL_LAUNCH = 796.32e6 + 68.94e6
+TRAFFIC_BYTES_FULL_LAUNCH = 794.637312e6 + 68.573952e6
 # Algorithmic bytes of one reach-task step per quad: read action 16, goal 12,
 # step counter 4, state 52, motors 16, body 16, epoch 4, mode 1 (121 B);
 # written state 52, motors 16, epoch 4, collided flag 1, command 16,
@@ -79,6 +96,21 @@ TASK_BYTES_PER_ENV_STEP = (16 + 12 + 4 + 52 + 16 + 16 + 4 + 1) + (52 + 16 + 4 + 
 # Algorithmic bytes of one depth frame: the float32 270 x 480 image written
 # (the boxes and poses read are under 1 KB per camera).
 DEPTH_BYTES_PER_FRAME = 270 * 480 * 4
+# Algorithmic FP32 operations of the depth caster (the oracle's ray_box_depth
+# run with the operation-counting scalar, comparisons excluded), by what each
+# part repeats over: per pixel (its ray R d_c), per (camera, box) pair (R_b^T
+# and the camera origin in the box frame), per (pixel, box) pair (the ray in
+# the box frame and the slab intervals). tests/test_bench_constants.py
+# re-derives them.
+DEPTH_FLOP_PER_PIXEL, DEPTH_FLOP_PER_CAMERA_BOX, DEPTH_FLOP_PER_PIXEL_BOX = 21.0, 57.0, 27.0
+# Algorithmic operations of one step of the differentiable rollout (position
+# mode, quadrotor, SIE, one substep, the step's loss term): the forward step
+# and its reverse-mode adjoint (the oracle run with the reverse-counting
+# scalar, every elementary operation's adjoint rule counted). The backward
+# launch's algorithmic work per vehicle-step is one forward recomputation
+# from the checkpoints plus the adjoint.
+FLOP_PER_VEHICLE_STEP_ADJ_FWD = 460.0
+FLOP_PER_VEHICLE_STEP_ADJ_REV = 1217.0
 
 
 def dist_env():
@@ -208,6 +240,13 @@ def time_calls(fl, call, k: int, world: int):
     return max_over_ranks(total_ms / 1e3, world), per
 
 
+def rate_stats(units_per_call: float, per_ms: list[float]) -> dict:
+    """Median and range of per-call rates (units per call over each call's
+    CUDA-event duration)."""
+    rates = sorted(units_per_call / (ms * 1e-3) for ms in per_ms)
+    return {"median": float(np.median(rates)), "range": [rates[0], rates[-1]]}
+
+
 def gpu_arm(args) -> dict | None:
     import torch
     from paper_2305_16510_gb300 import build, workloads as W
@@ -219,6 +258,9 @@ def gpu_arm(args) -> dict | None:
     else:
         torch.cuda.set_device(0)
     build.build()
+    from paper_2305_16510_gb300 import _abi
+    alu = _abi.ag_query_alu_peak(torch.cuda.current_device())
+    alu_peak = alu_peak_tflops(alu)
     w = W.WORKLOADS[WORKLOAD]
     if args.envs:
         w = W.scaled(w, args.envs)
@@ -243,7 +285,6 @@ def gpu_arm(args) -> dict | None:
     out = {}
     # check of the derived ALU peak: an FMA-chain kernel of the library, run
     # after the timed region on the same stream (about 0.2 s)
-    from paper_2305_16510_gb300 import _abi
     fma_chain = _abi.ag_measure_fp32_peak(fl.stream.cuda_stream, iters=10000, reps=5)
 
     # ---- unfused comparison path (same fleet, same call size)
@@ -255,9 +296,9 @@ def gpu_arm(args) -> dict | None:
         plain_value = w.n_envs * C * k_plain * world / secs_p
         out["plain"] = {"value": plain_value, "unit": UNIT, "ms_per_step": secs_p * 1e3 / k_plain,
                         "bytes_per_vehicle_step": PLAIN_BYTES_PER_VEHICLE_STEP,
-                        "hbm_frac": plain_value / world * PLAIN_BYTES_PER_VEHICLE_STEP / 1e9 / HBM_PEAK_GBS,
+                        "hbm_frac": plain_value / world * PLAIN_BYTES_PER_VEHICLE_STEP / 1e9 / hbm_peak_gbs(),
                         "launches_per_step": C * (3 * w.substeps_per_step + 2) + 1,
-                        "fused_over_plain": value / plain_value}
+                        "fused_over_plain": value / plain_value, **rate_stats(w.n_envs * C, per_p)}
 
     # ---- end to end through the C-ABI with host buffers: per call, upload the
     # commands from pinned host memory, step, read the state back
@@ -294,10 +335,13 @@ def gpu_arm(args) -> dict | None:
         fs = make_fleet(ws, inp_s, seed)
         fs.step(100)
         torch.cuda.synchronize()
-        secs_s, _ = time_calls(fs, lambda: fs.step(1000), 3, world)
-        v_s = ws.n_envs * 1000 * 3 * world / secs_s
+        k_s = 5
+        secs_s, per_s = time_calls(fs, lambda: fs.step(1000), k_s, world)
+        v_s = ws.n_envs * 1000 * k_s * world / secs_s
+        st = rate_stats(ws.n_envs * 1000, per_s)
         out["paper_shape"] = {"value": v_s, "unit": UNIT,
-                              "alu_frac": v_s / world * FLOP_PER_VEHICLE_STEP_PAPER_SHAPE / 1e12 / ALU_PEAK_TFLOPS,
+                              "alu_frac": v_s / world * FLOP_PER_VEHICLE_STEP_PAPER_SHAPE / 1e12 / alu_peak,
+                              **st,
                               "workload": "131,072 quads, attitude/body-velocity commands, no obstacles, SIE, "
                                           "1 substep",
                               "paper_value": 3.8e6,
@@ -305,13 +349,13 @@ def gpu_arm(args) -> dict | None:
         fs.close()
     fl.close()
     if "mixed" in parts:
-        out["mixed"] = mixed_part(seed, world)
+        out["mixed"] = mixed_part(seed, world, alu_peak)
     if "depth" in parts:
-        out["depth"] = depth_part(seed, world)
+        out["depth"] = depth_part(seed, world, alu_peak)
     if "task" in parts:
         out["task"] = task_part(seed, world)
     if "adjoint" in parts:
-        out["adjoint"] = adjoint_part(seed, world)
+        out["adjoint"] = adjoint_part(seed, world, alu_peak)
     if "serve" in parts:
         out["serving"] = serving_part(seed)
     if world > 1:
@@ -320,8 +364,8 @@ def gpu_arm(args) -> dict | None:
     if rank != 0:
         return None
     clocks = clk.summary()
-    wtext = WORKLOAD_TEXT if (w.n_envs == 1 << 20 and C == STEPS_PER_CALL) else \
-        f"reduced case of the same recipe: {w.n_envs} envs, {C} steps per call"
+    full_size = w.n_envs == 1 << 20 and C == STEPS_PER_CALL
+    wtext = WORKLOAD_TEXT if full_size else f"reduced case of the same recipe: {w.n_envs} envs, {C} steps per call"
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -330,13 +374,15 @@ def gpu_arm(args) -> dict | None:
                    "substeps_per_step": w.substeps_per_step, "integrator": "rk4", "boxes_per_env": w.n_obstacles,
                    "l2": "no flush: inputs exceed L2 (boxes 671 MB + state 55 MB per call)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / ALU_PEAK_TFLOPS,
-                     "traffic": TRAFFIC_BYTES_FULL_LAUNCH if w.n_envs == 1 << 20 else None,
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / alu_peak,
+                     "traffic": TRAFFIC_BYTES_FULL_LAUNCH if full_size else None,
                      "kernel": "k_fused_step<RK4, quad>", "launch_ms": launch_ms,
                      "flop_per_vehicle_step": FLOP_PER_VEHICLE_STEP,
-                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz (MEASURED_PEAKS has no "
-                                    "FP32 figure)",
+                     "peak_source": (f"derived from the device: {alu['sm_count']} SM x {alu['fp32_lanes_per_sm']} "
+                                     f"FP32 lanes x 2 x {alu['max_sm_clock_khz'] / 1e3:.0f} MHz "
+                                     "(MEASURED_PEAKS has no FP32 figure)"),
+                     "device": alu,
                      "fma_chain_check": {
                          "scalar_tflops": fma_chain["scalar_tflops"], "packed_tflops": fma_chain["packed_tflops"],
                          "frac_of_packed": achieved_tflops / fma_chain["packed_tflops"],
@@ -346,13 +392,14 @@ def gpu_arm(args) -> dict | None:
         "gpu_launches": args.steps,
         "clocks": clocks,
         "resets_last_call": int(n_reset.numel()),
+        **rate_stats(w.n_envs * C, per),
     }
     res.update(out)
     return res
 
 
 # ------------------------------------------------------------- mixed fleet --
-def mixed_part(seed: int, world: int) -> dict:
+def mixed_part(seed: int, world: int, alu_peak: float) -> dict:
     """4,194,304 vehicles (40 % quad, 40 % hexa, 20 % octo), randomised mass
     and inertia, motor lag, drag, body-velocity commands, semi-implicit Euler:
     the 500-step rollout as 10 calls of 50 steps, each followed by a 1 %
@@ -373,42 +420,59 @@ def mixed_part(seed: int, world: int) -> dict:
 
     rollout()
     torch.cuda.synchronize()
-    secs, _ = time_calls(fl, rollout, 3, world)
+    k = 5
+    secs, per = time_calls(fl, rollout, k, world)
     fl.close()
-    v = w.n_envs * 500 * 3 * world / secs
-    return {"value": v, "unit": UNIT, "ms_per_rollout": secs * 1e3 / 3,
-            "alu_frac": v / world * FLOP_PER_VEHICLE_STEP_MIXED / 1e12 / ALU_PEAK_TFLOPS,
+    v = w.n_envs * 500 * k * world / secs
+    st = rate_stats(w.n_envs * 500, per)
+    return {"value": v, "unit": UNIT, "ms_per_rollout": secs * 1e3 / k,
+            "alu_frac": v / world * FLOP_PER_VEHICLE_STEP_MIXED / 1e12 / alu_peak, **st,
             "workload": "4,194,304 vehicles (1,677,722 quad / 1,677,722 hexa / 838,860 octo), mass and inertia "
                         "x U[0.8, 1.2], tau 0.03, drag 0.1, body-velocity targets U[-2, 2]^3, SIE, 500 steps "
                         "as 10 x (50-step ag_step + 1 % ag_reset mask)"}
 
 
 # ------------------------------------------------------------------- depth --
-def depth_part(seed: int, world: int) -> dict:
+def depth_part(seed: int, world: int, alu_peak: float) -> dict:
     """2^10 robots, each a 270 x 480 depth camera (87 deg horizontal field of
     view, 10 m range) ray-cast against its environment's 16 boxes."""
     import math
     import torch
-    from paper_2305_16510_gb300 import workloads as W
+    from paper_2305_16510_gb300 import _abi, workloads as W
     w = W.scaled(W.WORKLOADS[WORKLOAD], 1024)
     inp = W.make_inputs(w, seed)
     fl = make_fleet(w, inp, seed)
     fl.step(10)
-    out = torch.empty((1024, 270, 480), dtype=torch.float32, device="cuda")
+    H, Wd, hfov, rng_max = 270, 480, math.radians(87), 10.0
+    out = torch.empty((1024, H, Wd), dtype=torch.float32, device="cuda")
 
     def render():
-        fl.render_depth(480, 270, math.radians(87), 10.0, out=out)
+        fl.render_depth(Wd, H, hfov, rng_max, out=out)
 
     for _ in range(3):
         render()
     torch.cuda.synchronize()
     k = 20
     secs, per = time_calls(fl, render, k, world)
+    # pixel-box pairs the kernel tests after its conservative culling
+    live = _abi.ag_depth_live_pairs(fl.ctx, Wd, H, hfov, rng_max, None, None, 1024)
     fl.close()
     frames = 1024 * k * world
+    launch_s = float(np.mean(per)) * 1e-3
+    all_pairs = 1024 * H * Wd * w.n_obstacles
+    per_launch = 1024 * (H * Wd * DEPTH_FLOP_PER_PIXEL + w.n_obstacles * DEPTH_FLOP_PER_CAMERA_BOX)
     return {"value": frames / secs, "unit": "depth frames/s", "ms_per_1024_frames": float(np.mean(per)),
-            "pixel_box_pairs_per_s": frames * 270 * 480 * 16 / secs,  # culled pairs included
-            "hbm_frac": 1024 * DEPTH_BYTES_PER_FRAME / (float(np.mean(per)) * 1e-3) / 1e9 / HBM_PEAK_GBS,
+            **rate_stats(1024, per),
+            "pixel_box_pairs_per_s": frames * H * Wd * w.n_obstacles / secs,  # culled pairs included
+            "live_pair_frac": live / all_pairs,
+            "flop": {"per_pixel": DEPTH_FLOP_PER_PIXEL, "per_camera_box": DEPTH_FLOP_PER_CAMERA_BOX,
+                     "per_pixel_box": DEPTH_FLOP_PER_PIXEL_BOX},
+            # the method's work that the kernel performs: every pixel's ray, every camera-box setup
+            # and every live pair's slab test (comparisons and min/max are not counted)
+            "alu_frac": (per_launch + live * DEPTH_FLOP_PER_PIXEL_BOX) / launch_s / 1e12 / alu_peak,
+            # the same with every pair counted, as a test without culling would do (context)
+            "alu_frac_all_pairs": (per_launch + all_pairs * DEPTH_FLOP_PER_PIXEL_BOX) / launch_s / 1e12 / alu_peak,
+            "hbm_frac": 1024 * DEPTH_BYTES_PER_FRAME / launch_s / 1e9 / hbm_peak_gbs(),
             "bound": "issue (ALU pipe: slab min/max and compares), not HBM",
             "workload": "1,024 robots x 270 x 480 depth camera, 16 oriented boxes per environment, 87 deg hfov",
             "paper_value": 1800.0, "paper_hardware": "2x RTX 3090, Isaac Gym camera sensors (graphics renderer)"}
@@ -448,22 +512,24 @@ def task_part(seed: int, world: int) -> dict:
     with torch.cuda.stream(side):
         g.replay()
         torch.cuda.synchronize()
-        secs_g, _ = time_calls(env.fleet, g.replay, k // per_graph, world)
+        secs_g, per_g = time_calls(env.fleet, g.replay, k // per_graph, world)
     env.close()
     return {"value": n * k * world / secs, "unit": "task env-steps/s", "ms_per_step": float(np.mean(per)),
+            **rate_stats(n, per),
             "bytes_per_env_step": TASK_BYTES_PER_ENV_STEP,
             # algorithmic bytes of one launch over its mean CUDA-event duration
-            "hbm_frac": n * TASK_BYTES_PER_ENV_STEP / (float(np.mean(per)) * 1e-3) / 1e9 / HBM_PEAK_GBS,
+            "hbm_frac": n * TASK_BYTES_PER_ENV_STEP / (float(np.mean(per)) * 1e-3) / 1e9 / hbm_peak_gbs(),
             "workload": "reach-a-setpoint, 1,048,576 quads, attitude interface, SIE 1 substep, no obstacles, "
                         "obs [n,13] + reward + done per step", "launches_per_step": 1,
             "cuda_graph": {"value": n * k * world / secs_g, "ms_per_step": secs_g * 1e3 / k,
-                           "steps_per_graph": per_graph}}
+                           "steps_per_graph": per_graph, **rate_stats(n * per_graph, per_g)}}
 
 
 # ----------------------------------------------------------------- adjoint --
-def adjoint_part(seed: int, world: int) -> dict:
+def adjoint_part(seed: int, world: int, alu_peak: float) -> dict:
     """Differentiable rollout at 65,536 quads x 256 steps (position mode, SIE,
-    checkpoint every 32): recorded forward + hand-written adjoint."""
+    checkpoint every 32): recorded forward + hand-written adjoint. Each half
+    is timed with CUDA events on the fleet's stream."""
     import torch
     from paper_2305_16510_gb300 import _abi, workloads as W
     w = W.WORKLOADS["adjoint"]
@@ -475,24 +541,43 @@ def adjoint_part(seed: int, world: int) -> dict:
     gx = torch.empty((13, n), device="cuda")
     gg = torch.empty(12, device="cuda")
     x0, m0 = fl.state().clone(), fl.motors().clone()
+    stream = fl.stream
 
-    def fwd_bwd():
+    def fwd_bwd(ev=None):
         fl.set_state(x0, m0)
+        if ev:
+            ev[0].record(stream)
         _abi.ag_rollout_loss(fl.ctx, H, 1.0, 0.01, goal, loss)
+        if ev:
+            ev[1].record(stream)
         _abi.ag_backward(fl.ctx, None, gx, gg, None)
+        if ev:
+            ev[2].record(stream)
 
     for _ in range(3):
         fwd_bwd()
     torch.cuda.synchronize()
+    k = 20
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(k)]
+    barrier(world)
     t0 = time.perf_counter()
-    k = 10
-    for _ in range(k):
-        fwd_bwd()
+    for e in evs:
+        fwd_bwd(e)
     torch.cuda.synchronize()
     secs = max_over_ranks(time.perf_counter() - t0, world)
     fl.close()
-    return {"value": n * H * k * world / secs, "unit": "vehicle-steps/s (forward + adjoint)",
-            "ms_per_rollout": secs * 1e3 / k,
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    bwd_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    units = n * H
+    fwd_s, bwd_s = float(np.median(fwd_ms)) * 1e-3, float(np.median(bwd_ms)) * 1e-3
+    return {"value": units * k * world / secs, "unit": "vehicle-steps/s (forward + adjoint)",
+            "ms_per_rollout": secs * 1e3 / k, **rate_stats(units, [a + b for a, b in zip(fwd_ms, bwd_ms)]),
+            "record_ms": fwd_s * 1e3, "backward_ms": bwd_s * 1e3,
+            "flop_per_vehicle_step": {"forward": FLOP_PER_VEHICLE_STEP_ADJ_FWD,
+                                      "reverse": FLOP_PER_VEHICLE_STEP_ADJ_FWD + FLOP_PER_VEHICLE_STEP_ADJ_REV},
+            "alu_frac_record": units * FLOP_PER_VEHICLE_STEP_ADJ_FWD / fwd_s / 1e12 / alu_peak,
+            "alu_frac_backward": units * (FLOP_PER_VEHICLE_STEP_ADJ_FWD + FLOP_PER_VEHICLE_STEP_ADJ_REV)
+            / bwd_s / 1e12 / alu_peak,
             "workload": "65,536 quads, position mode, SIE, horizon 256, checkpoint every 32 steps, "
                         "gradients w.r.t. x0 (13/vehicle) and 12 gains"}
 
@@ -501,15 +586,30 @@ def adjoint_part(seed: int, world: int) -> dict:
 SERVE_LAMBDA = 200.0           # requests per second (Poisson arrivals)
 SERVE_REQUESTS = 2200          # 200 warm-up + 2,000 measured
 SERVE_WARMUP = 200
+SERVE_REPLAYS = 3              # replays of the lambda = 200 trace (median and range of p99)
 SERVE_POOL = 1 << 19           # pool of environments requests take slices of
 SERVE_BUDGET = 40 << 30
+# Capacity: the highest arrival rate of a sweep at which a policy keeps up
+# with the offered load (completed work >= 95 % of the offered work rate) with
+# p99 latency at or below SERVE_P99_BOUND_MS. The largest request of the trace
+# (262,144 quads x 2,000 steps) needs about 94 ms of the whole GPU alone.
+SERVE_P99_BOUND_MS = 250.0
+# Rates of the sweep (requests/s) per policy; the highest of each overloads it,
+# so the throughput there is that policy's ceiling.
+SERVE_SWEEP = {"batched": (250.0, 300.0, 350.0, 400.0, 600.0), "one_per_launch": (100.0, 125.0, 150.0, 175.0)}
+SERVE_SWEEP_SECONDS = 4.0      # arrivals per rate of the sweep: about this long, 200 .. 1,600 requests
 
 
-def serve_trace(n_req: int, seed: int = 7):
-    """Seeded request trace: exponential inter-arrivals, fleet log-uniform in
-    [256, 262144], horizon uniform in {50..2000}, obstacles from {0, 8, 32}."""
+def sweep_requests(lam: float) -> int:
+    return int(min(1600, max(200, lam * SERVE_SWEEP_SECONDS)))
+
+
+def serve_trace(n_req: int, seed: int = 7, lam: float = SERVE_LAMBDA):
+    """Seeded request trace: exponential inter-arrivals at rate lam, fleet
+    log-uniform in [256, 262144], horizon uniform in {50..2000}, obstacles from
+    {0, 8, 32}."""
     rng = np.random.default_rng(seed)
-    t = np.cumsum(rng.exponential(1.0 / SERVE_LAMBDA, size=n_req))
+    t = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
     n = np.floor(np.exp(rng.uniform(np.log(256), np.log(262144), size=n_req))).astype(int)
     h = rng.integers(50, 2001, size=n_req)
     obs = rng.choice([0, 8, 32], size=n_req)
@@ -560,16 +660,26 @@ def run_trace(server, pool, trace, warm: int, cap_s: float) -> dict:
     t_begin = trace[warm]["t"]
     t_end = max(done_at[i] for i in meas)
     work = sum(trace[i]["n"] * trace[i]["h"] for i in meas)
+    offered = sum(trace[i]["n"] * trace[i]["h"] for i in range(warm, len(trace))) / \
+        max(trace[-1]["t"] - t_begin, 1e-9)
     L = np.array([lat[i] for i in meas])
     edges = [0, 5, 10, 20, 50, 100, 200, 500, 1000, 2000, np.inf]
     counts, _ = np.histogram(L, bins=edges)
     return {"value": work / (t_end - t_begin), "unit": UNIT, "p50_ms": float(np.percentile(L, 50)),
             "p99_ms": float(np.percentile(L, 99)), "mean_ms": float(L.mean()), "completed": len(meas),
             "measured_of": len(trace) - warm, "submitted": submitted, "window_s": t_end - t_begin,
+            "offered": offered,
             "latency_ms": {"p10": float(np.percentile(L, 10)), "p25": float(np.percentile(L, 25)),
                            "p75": float(np.percentile(L, 75)), "p90": float(np.percentile(L, 90)),
                            "max": float(L.max()),
                            "histogram": {f"{edges[k]}-{edges[k + 1]}": int(counts[k]) for k in range(len(counts))}}}
+
+
+def keeps_up(r: dict) -> bool:
+    """Every measured request completed, the completed work rate is at least
+    95 % of the offered one, and p99 is within the bound."""
+    return (r.get("completed", 0) == r.get("measured_of", -1) and r["value"] >= 0.95 * r["offered"]
+            and r["p99_ms"] <= SERVE_P99_BOUND_MS)
 
 
 def serving_part(seed: int) -> dict:
@@ -585,18 +695,50 @@ def serving_part(seed: int) -> dict:
                         "fleet log-uniform [256, 262144] quads, horizon U{50..2000} steps, modes mixed, "
                         "obstacles {0, 8, 32}, RK4 4 substeps, 40 GB budget, 50 steps per launch"),
            "offered_vehicle_steps_per_s": sum(r["n"] * r["h"] for r in trace) / trace[-1]["t"]}
-    with Server(max_active=1024, chunk_steps=50, hbm_budget_bytes=SERVE_BUDGET) as srv:
-        out["batched"] = run_trace(srv, pool, trace, SERVE_WARMUP, cap_s=120.0)
+    policies = {"batched": 1024, "one_per_launch": 1}
+    with Server(max_active=policies["batched"], chunk_steps=50, hbm_budget_bytes=SERVE_BUDGET) as srv:
+        runs = [run_trace(srv, pool, trace, SERVE_WARMUP, cap_s=120.0) for _ in range(SERVE_REPLAYS)]
         st = srv.stats()
-        out["batched"]["launches"] = int(st.launches)
-        out["batched"]["gpu_busy_s"] = st.gpu_ms / 1e3
-    with Server(max_active=1, chunk_steps=50, hbm_budget_bytes=SERVE_BUDGET) as srv:
-        out["one_per_launch"] = run_trace(srv, pool, trace, SERVE_WARMUP, cap_s=30.0)
+    p99s = sorted(r["p99_ms"] for r in runs if r.get("completed"))
+    mid = sorted(runs, key=lambda r: r.get("p99_ms", np.inf))[len(runs) // 2]   # the replay with the median p99
+    out["batched"] = dict(mid)
+    out["batched"].update({"replays": len(runs), "p99_ms_median": float(np.median(p99s)),
+                           "p99_ms_range": [p99s[0], p99s[-1]],
+                           "p50_ms_range": [min(r["p50_ms"] for r in runs), max(r["p50_ms"] for r in runs)],
+                           "value_range": [min(r["value"] for r in runs), max(r["value"] for r in runs)],
+                           "launches": int(st.launches), "gpu_busy_s": st.gpu_ms / 1e3})
+    with Server(max_active=policies["one_per_launch"], chunk_steps=50, hbm_budget_bytes=SERVE_BUDGET) as srv:
+        out["one_per_launch"] = run_trace(srv, pool, trace, SERVE_WARMUP, cap_s=20.0)
         st = srv.stats()
         out["one_per_launch"]["launches"] = int(st.launches)
     b, o = out["batched"], out["one_per_launch"]
     if b.get("value") and o.get("value"):
         out["batched_over_one_per_launch"] = b["value"] / o["value"]
+    # capacity sweep: shorter traces of the same recipe at higher / lower rates
+    cap = {"p99_bound_ms": SERVE_P99_BOUND_MS, "rule": "completed work >= 95 % of offered and p99 <= bound",
+           "requests_per_rate": f"{SERVE_SWEEP_SECONDS:g} s of arrivals, 200 .. 1,600 requests, first 10 % warm-up"}
+    main = {"batched": b, "one_per_launch": o}
+    for name, rates in SERVE_SWEEP.items():
+        sweep = {f"{SERVE_LAMBDA:g}": {k: main[name].get(k) for k in ("value", "offered", "p50_ms", "p99_ms")} |
+                 {"keeps_up": keeps_up(main[name])}}
+        for lam in rates:                    # a fresh server per rate: no backlog carries over
+            n_req = sweep_requests(lam)
+            tr = serve_trace(n_req, seed=11, lam=lam)
+            with Server(max_active=policies[name], chunk_steps=50, hbm_budget_bytes=SERVE_BUDGET) as srv:
+                r = run_trace(srv, pool, tr, n_req // 10, cap_s=25.0)
+            ok = bool(r.get("completed")) and keeps_up(r)
+            sweep[f"{lam:g}"] = {k: r.get(k) for k in ("value", "offered", "p50_ms", "p99_ms", "completed",
+                                                       "measured_of")} | {"keeps_up": ok}
+        ok_rates = sorted(float(k) for k, v in sweep.items() if v["keeps_up"])
+        # capacity: the highest rate below which every swept rate keeps up
+        best = None
+        for lam in sorted(float(k) for k in sweep):
+            if not sweep[f"{lam:g}"]["keeps_up"]:
+                break
+            best = lam
+        cap[name] = {"req_per_s": best, "ceiling": max(v["value"] or 0.0 for v in sweep.values()),
+                     "rates_kept_up": ok_rates, "sweep": sweep}
+    out["capacity"] = cap
     return out
 
 
@@ -783,6 +925,117 @@ def make_parser() -> argparse.ArgumentParser:
     return ap
 
 
+DETAIL_DIR = os.path.join(ROOT, "gpurun_out")
+
+
+def detail_path(parts: str) -> str:
+    """Side file of a run: bench_detail.json for every part, else named by the parts."""
+    if set(parts.split(",")) == set(PARTS):
+        return os.path.join(DETAIL_DIR, "bench_detail.json")
+    return os.path.join(DETAIL_DIR, "bench_detail_" + "_".join(sorted(parts.split(","))) + ".json")
+
+
+def _sig(x, digits: int = 4):
+    """x rounded to `digits` significant digits (recursively in lists and dicts)."""
+    if isinstance(x, bool) or x is None or isinstance(x, (int, str)):
+        return x
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}")
+    if isinstance(x, (list, tuple)):
+        return [_sig(v, digits) for v in x]
+    if isinstance(x, dict):
+        return {k: _sig(v, digits) for k, v in x.items()}
+    return x
+
+
+def _pick(d: dict | None, *keys):
+    if not d:
+        return None
+    return {k: d[k] for k in keys if k in d}
+
+
+def compact_line(res: dict) -> dict:
+    """The printed JSON line: the contract's keys plus the headline figures of
+    every part, each number to 4 significant digits, short enough (about
+    1.4 KB) to be kept whole by a reader of the output's tail. Everything
+    else (workload texts, latency histograms, the sweep, per-row CPU
+    baselines) goes to the side file."""
+    r = res
+    out = {k: r[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                             "higher_is_better", "scaling", "vs_baseline", "dtype") if k in r}
+    out["data"] = "synthetic"
+    cfg = r["config"]
+    out["config"] = {"workload": (f"{cfg['n_envs']} quads,3 modes,RK4x{cfg['substeps_per_step']},"
+                                  f"{cfg['boxes_per_env']} OBB,{cfg['steps_per_call']} steps/call"),
+                     "l2": "inputs>L2"}
+    rf = r["roofline"]
+    out["roofline"] = {**_pick(rf, "bound", "achieved", "peak", "unit", "frac", "traffic"),
+                       "fma_chain_tflops": rf["fma_chain_check"]["packed_tflops"]}
+    if "cpu_baseline" in r:
+        cb = r["cpu_baseline"]
+        out["cpu_baseline"] = {**_pick(cb, "value", "unit", "cores", "kind"), "sample": cb["sample"].split(" of ")[0]}
+    out["clocks"] = _pick(r["clocks"], "sm_mhz", "sm_max_mhz", "reasons")
+    if "e2e" in r:
+        out["e2e"] = r["e2e"]
+    out["gpu_launches"] = r["gpu_launches"]
+    out["range"] = r["range"]
+    if "plain" in r:
+        out["plain"] = _pick(r["plain"], "value", "fused_over_plain")
+    if "serving" in r:
+        sv = r["serving"]
+        b, o = sv.get("batched", {}), sv.get("one_per_launch", {})
+        cap = sv.get("capacity", {})
+        out["serving"] = {"batched": {**_pick(b, "value", "p50_ms"), "p99_ms": b.get("p99_ms_median"),
+                                      "p99_range": b.get("p99_ms_range")},
+                          "one_per_launch": _pick(o, "value", "p50_ms", "p99_ms"),
+                          "capacity": {"p99_bound_ms": cap.get("p99_bound_ms"),
+                                       "batched": (cap.get("batched") or {}).get("req_per_s"),
+                                       "one_per_launch": (cap.get("one_per_launch") or {}).get("req_per_s"),
+                                       "ceiling": [(cap.get(k) or {}).get("ceiling")
+                                                   for k in ("batched", "one_per_launch")]}}
+    for key in ("mixed", "paper_shape"):
+        if key in r:
+            out[key] = _pick(r[key], "value", "alu_frac", "range")
+    if "depth" in r:
+        out["depth"] = _pick(r["depth"], "value", "alu_frac")
+    if "task" in r:
+        out["task"] = _pick(r["task"], "value", "hbm_frac")
+    if "adjoint" in r:
+        a = r["adjoint"]
+        out["adjoint"] = {"value": a["value"], "alu_record": a["alu_frac_record"],
+                          "alu_backward": a["alu_frac_backward"], "range": a["range"]}
+    head = {k: out[k] for k in list(out)[:list(out).index("range") + 1]}
+    parts = {k: out[k] for k in list(out)[list(out).index("range") + 1:]}
+    return {**_sig(head, 4), **_sig(parts, 3)}
+
+
+def dumps_compact(x) -> str:
+    """JSON with no spaces and floats in %.4g form (exponents without '+' or
+    leading zeros, e.g. 1.373e10): valid JSON, about a third shorter."""
+    if isinstance(x, dict):
+        return "{" + ",".join(json.dumps(str(k)) + ":" + dumps_compact(v) for k, v in x.items()) + "}"
+    if isinstance(x, (list, tuple)):
+        return "[" + ",".join(dumps_compact(v) for v in x) + "]"
+    if isinstance(x, float) and np.isfinite(x):
+        t = f"{x:.4g}"
+        if "e" in t:
+            m, e = t.split("e")
+            t = f"{m}e{int(e)}"
+        return t
+    if isinstance(x, float):
+        return "null"
+    return json.dumps(x)
+
+
+def write_detail(res: dict, path: str) -> None:
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(res, f, indent=1)
+    except OSError as e:
+        print(f"bench: could not write {path}: {e}", file=sys.stderr)
+
+
 def main():
     ap = make_parser()
     args = ap.parse_args()
@@ -794,7 +1047,7 @@ def main():
     if args.impl == "reference":
         out = reference_arm(args)
         if out is not None:
-            print(json.dumps(out), flush=True)
+            print(dumps_compact(out), flush=True)
         return
     out = gpu_arm(args)
     if out is None:
@@ -803,7 +1056,8 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
         out["cpu_baseline"]["rows"] = cpu_baseline_rows(set(args.parts.split(",")))
-    print(json.dumps(out), flush=True)
+    write_detail(out, detail_path(args.parts))
+    print(dumps_compact(compact_line(out)), flush=True)
 
 
 if __name__ == "__main__":

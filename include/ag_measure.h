@@ -1,4 +1,4 @@
-/* ag_measure.h — measurement utility of libaerialgb (not part of the
+/* ag_measure.h — measurement utilities of libaerialgb (not part of the
  * simulation).
  *
  * The fused fleet step (ag_step) is bound by plain FP32 arithmetic on the CUDA
@@ -37,6 +37,41 @@ typedef struct {
  * is NULL or iters or reps (1 .. 100) is out of range; AG_ERR_CUDA when a
  * CUDA call fails (ag_last_error(NULL) gives the message). */
 ag_status ag_measure_fp32_peak(void* cuda_stream, uint32_t iters, uint32_t reps, ag_fp32_peak* out);
+
+typedef struct {
+  uint32_t sm_count;          /* streaming multiprocessors (cudaDevAttrMultiProcessorCount) */
+  uint32_t fp32_lanes_per_sm; /* FP32 FMA lanes per SM of the compute capability (128 on sm_10x) */
+  uint32_t max_sm_clock_khz;  /* peak SM clock (cudaDevAttrClockRate) */
+  uint32_t cc_major, cc_minor;
+  double tflops;              /* sm_count x lanes x 2 FLOP per FMA x clock / 1e12 */
+} ag_alu_peak;
+
+/* The derived FP32 CUDA-core peak of CUDA device `device`, from the device's
+ * own attributes: SM count and peak SM clock as the driver reports them,
+ * FP32 lanes per SM from the compute capability (64 on 6.0, 7.x and 8.0;
+ * 128 on every other capability from 6.1 on). AG_ERR_INVALID for a NULL out
+ * or a capability below 6.0; AG_ERR_CUDA when a query fails. No launch, no
+ * allocation. */
+ag_status ag_query_alu_peak(int device, ag_alu_peak* out);
+
+/* The ray caster of ag_render_depth (include/ag.h; Sec. III depth cameras,
+ * Sec. VII kernel-based ray casting), same arguments and results, with the
+ * slab intervals' three reciprocals per pixel and box correctly rounded
+ * (IEEE division) instead of the fast approximate reciprocal that
+ * ag_render_depth uses. It exists to measure how many pixels the
+ * approximation moves: it is not faster and not otherwise different. */
+ag_status ag_render_depth_ieee(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
+                               const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth);
+
+/* Counts the (pixel, box) pairs that ag_render_depth, with the same
+ * arguments, tests after its conservative culling (a box culled for a 32 x 32
+ * tile is not tested for any pixel of it), into *live_pairs (host). Renders
+ * nothing; synchronises the context's stream. This is the work a launch
+ * performs, against which its ALU fraction is stated. Errors as
+ * ag_render_depth; AG_ERR_INVALID for a NULL live_pairs. */
+ag_status ag_depth_live_pairs(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
+                              const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams,
+                              uint64_t* live_pairs);
 
 #ifdef __cplusplus
 }

@@ -78,6 +78,12 @@ class ag_fp32_peak(ctypes.Structure):
                 ("block", ctypes.c_uint32)]
 
 
+class ag_alu_peak(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_uint32), ("fp32_lanes_per_sm", ctypes.c_uint32),
+                ("max_sm_clock_khz", ctypes.c_uint32), ("cc_major", ctypes.c_uint32), ("cc_minor", ctypes.c_uint32),
+                ("tflops", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -102,6 +108,12 @@ SIGNATURES = {
     "ag_eval_controller": (ctypes.c_int, [_vp, _vp, _vp]),
     "ag_inject_failure": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "ag_measure_fp32_peak": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ag_fp32_peak)]),
+    "ag_query_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ag_alu_peak)]),
+    "ag_render_depth_ieee": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
+                                            ctypes.POINTER(ctypes.c_float * 3), _vp, ctypes.c_uint32, _vp]),
+    "ag_depth_live_pairs": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
+                                           ctypes.POINTER(ctypes.c_float * 3), _vp, ctypes.c_uint32,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
     "ag_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),
     "ag_get_motors": (ctypes.c_int, [_vp, _vp, _vp]),
     "ag_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -224,6 +236,28 @@ def ag_render_depth(ctx: int, width: int, height: int, hfov: float, max_range: f
     _check(rc, "ag_render_depth", ctx)
 
 
+def ag_render_depth_ieee(ctx: int, width: int, height: int, hfov: float, max_range: float, cam_offset, env_ids,
+                         n_cams: int, depth) -> None:
+    """ag_render_depth with correctly rounded reciprocals (include/ag_measure.h)."""
+    off = None if cam_offset is None else (ctypes.c_float * 3)(*cam_offset)
+    rc = lib().ag_render_depth_ieee(ctx, int(width), int(height), float(hfov), float(max_range),
+                                    ctypes.byref(off) if off is not None else None, ptr(env_ids), int(n_cams),
+                                    ptr(depth))
+    _check(rc, "ag_render_depth_ieee", ctx)
+
+
+def ag_depth_live_pairs(ctx: int, width: int, height: int, hfov: float, max_range: float, cam_offset, env_ids,
+                        n_cams: int) -> int:
+    """(pixel, box) pairs ag_render_depth tests after culling (include/ag_measure.h)."""
+    off = None if cam_offset is None else (ctypes.c_float * 3)(*cam_offset)
+    out = ctypes.c_uint64()
+    rc = lib().ag_depth_live_pairs(ctx, int(width), int(height), float(hfov), float(max_range),
+                                   ctypes.byref(off) if off is not None else None, ptr(env_ids), int(n_cams),
+                                   ctypes.byref(out))
+    _check(rc, "ag_depth_live_pairs", ctx)
+    return int(out.value)
+
+
 def ag_set_obstacle_randomization(ctx: int, env_min, env_max, per_box) -> None:
     """per_box: a sequence of ag_box_randomization (one per obstacle) or None to disable."""
     lo = (ctypes.c_float * 3)(*env_min) if env_min is not None else None
@@ -263,6 +297,14 @@ def ag_measure_fp32_peak(stream: int = 0, iters: int = 10000, reps: int = 5, out
     rc = lib().ag_measure_fp32_peak(stream or None, iters, reps, ctypes.byref(r) if out is None else out)
     _check(rc, "ag_measure_fp32_peak", None)
     return {k: getattr(r, k) for k, _ in ag_fp32_peak._fields_}
+
+
+def ag_query_alu_peak(device: int = 0) -> dict:
+    """Derived FP32 CUDA-core peak of a device from its own attributes
+    (include/ag_measure.h)."""
+    r = ag_alu_peak()
+    _check(lib().ag_query_alu_peak(int(device), ctypes.byref(r)), "ag_query_alu_peak", None)
+    return {k: getattr(r, k) for k, _ in ag_alu_peak._fields_}
 
 
 def ag_eval_controller(ctx: int, state, wrench) -> None:

@@ -235,6 +235,7 @@ void free_all(ag_ctx* ctx) {
   free_adjoint(ctx);
   if (ctx->cam_ids) cudaFree(ctx->cam_ids);
   if (ctx->depth_stage) cudaFree(ctx->depth_stage);
+  if (ctx->live_dev) cudaFree(ctx->live_dev);
   if (ctx->eval_state) cudaFree(ctx->eval_state);
   if (ctx->check_dev) cudaFree(ctx->check_dev);
   if (ctx->reach_goals) cudaFree(ctx->reach_goals);

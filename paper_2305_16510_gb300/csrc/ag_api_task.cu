@@ -11,11 +11,15 @@
 
 using namespace agh;
 
-extern "C" {
+namespace {
 
-ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
-                          const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth) {
-  agk::NvtxRange range("ag_render_depth");
+// ag_render_depth and its two measurement variants (ag_measure.h): ieee_div
+// renders with correctly rounded reciprocals; a non-NULL live_pairs (host)
+// renders nothing and receives the number of (pixel, box) pairs the kernel
+// would test after culling (the call then synchronises).
+ag_status render_depth_impl(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
+                            const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth,
+                            int ieee_div, uint64_t* live_pairs) {
   ag_status s = enter(ctx);
   if (s != AG_OK) return s;
   const uint32_t n = ctx->cfg.n_envs;
@@ -23,7 +27,7 @@ ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hf
     return fail_invalid(ctx, "image size must be positive and at most 2^30 pixels");
   if (!(hfov > 0.f && hfov < 3.14159f)) return fail_invalid(ctx, "hfov must lie in (0, pi)");
   if (!(max_range > 0.f)) return fail_invalid(ctx, "max_range must be > 0");
-  if (n_cams == 0 || !depth) return fail_invalid(ctx, "n_cams must be >= 1 and depth non-NULL");
+  if (n_cams == 0 || (!depth && !live_pairs)) return fail_invalid(ctx, "n_cams must be >= 1 and depth non-NULL");
   if (!env_ids && n_cams > n) return fail_invalid(ctx, "n_cams exceeds n_envs");
   if (env_ids && n_cams > n) return fail_invalid(ctx, "at most n_envs cameras per call");
   cudaStream_t st = ctx->stream;
@@ -38,8 +42,11 @@ ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hf
     ids_dev = ctx->cam_ids;
   }
   const size_t count = (size_t)n_cams * width * height;
-  const bool out_on_device = on_device(depth);
+  const bool out_on_device = live_pairs ? true : on_device(depth);
   float* out = depth;
+  if (live_pairs && !ctx->live_dev &&
+      (s = alloc_or_oom(ctx, &ctx->live_dev, 1, "the live-pair counter")) != AG_OK)
+    return s;
   if (!out_on_device) {
     if (count > ctx->depth_stage_cap) {
       if (ctx->depth_stage) { cudaStreamSynchronize(st); cudaFree(ctx->depth_stage); ctx->depth_stage = nullptr; }
@@ -62,10 +69,50 @@ ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hf
   a.inv_f = (float)(std::tan(0.5 * (double)hfov) / (0.5 * width));
   a.max_range = max_range;
   for (int i = 0; i < 3; ++i) a.offset[i] = cam_offset ? cam_offset[i] : 0.f;
+  a.ieee_div = ieee_div;
+  a.live_pairs = nullptr;
+  if (live_pairs) {
+    a.live_pairs = ctx->live_dev;
+    if ((s = check_cuda(ctx, cudaMemsetAsync(ctx->live_dev, 0, sizeof(unsigned long long), st),
+                        "clear live-pair counter")) != AG_OK) return s;
+  }
   if ((s = check_cuda(ctx, agk::launch_render_depth(a, st), "depth launch")) != AG_OK) return s;
+  if (live_pairs) {
+    unsigned long long v = 0;
+    if ((s = check_cuda(ctx, cudaMemcpyAsync(&v, ctx->live_dev, sizeof(v), cudaMemcpyDeviceToHost, st),
+                        "copy live-pair count")) != AG_OK) return s;
+    if ((s = check_cuda(ctx, cudaStreamSynchronize(st), "synchronize")) != AG_OK) return s;
+    *live_pairs = (uint64_t)v;
+    return AG_OK;
+  }
   if (!out_on_device)
     s = check_cuda(ctx, cudaMemcpyAsync(depth, out, count * sizeof(float), cudaMemcpyDeviceToHost, st), "copy depth out");
   return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+ag_status ag_render_depth(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
+                          const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth) {
+  agk::NvtxRange range("ag_render_depth");
+  return render_depth_impl(ctx, width, height, hfov, max_range, cam_offset, env_ids, n_cams, depth, 0, nullptr);
+}
+
+ag_status ag_render_depth_ieee(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
+                               const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth) {
+  agk::NvtxRange range("ag_render_depth_ieee");
+  return render_depth_impl(ctx, width, height, hfov, max_range, cam_offset, env_ids, n_cams, depth, 1, nullptr);
+}
+
+ag_status ag_depth_live_pairs(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
+                              const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams,
+                              uint64_t* live_pairs) {
+  agk::NvtxRange range("ag_depth_live_pairs");
+  if (ctx && !live_pairs) return fail_invalid(ctx, "live_pairs is NULL");
+  return render_depth_impl(ctx, width, height, hfov, max_range, cam_offset, env_ids, n_cams, nullptr, 0,
+                           live_pairs);
 }
 
 void ag_reach_config_default(ag_reach_config* c) {

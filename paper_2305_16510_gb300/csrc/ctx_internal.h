@@ -35,6 +35,7 @@ struct ag_ctx {
   uint32_t* cam_ids;         // [n_envs]
   float* depth_stage;        // device staging when the caller's buffer is on the host
   size_t depth_stage_cap;    // floats
+  unsigned long long* live_dev;  // [1] live-pair counter of ag_depth_live_pairs (allocated on first use)
   float* eval_state;         // [13][n_envs] states of ag_eval_controller (allocated on first use)
   uint32_t* check_dev;       // [1] count of the setters' precondition checks
   // reach-a-setpoint task (allocated at the first ag_reach_begin)

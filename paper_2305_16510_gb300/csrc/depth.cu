@@ -155,6 +155,18 @@ __device__ __forceinline__ uint8_t slab_signs(const float4* rec, const TileRays&
   return f;
 }
 
+// What a launch of k_render_depth does: render with fast reciprocals (the
+// ray caster), render with correctly rounded reciprocals (to measure what the
+// approximation moves), or only count the live (pixel, box) pairs.
+enum DepthMode { kRenderFast = 0, kRenderIeee = 1, kCountLive = 2 };
+
+template <int MODE>
+__device__ __forceinline__ float depth_rcp(float x) {
+  if (MODE == kRenderIeee) return 1.f / x;
+  return __fdividef(1.f, x);
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
   __shared__ float4 recs[AG_MAX_OBSTACLES * 4];
   __shared__ float4 spheres[AG_MAX_OBSTACLES];
@@ -162,6 +174,7 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
   __shared__ uint8_t live_k[kDepthTilesPerBlock][AG_MAX_OBSTACLES];
   __shared__ uint8_t live_f[kDepthTilesPerBlock][AG_MAX_OBSTACLES];
   __shared__ int n_live[kDepthTilesPerBlock];
+  __shared__ uint32_t tile_x0[kDepthTilesPerBlock], tile_y0[kDepthTilesPerBlock];  // pixel origin of each tile
   // block -> (camera, group of kDepthTilesPerBlock consecutive tiles); cameras cam0, cam0 + 1, ...
   const uint32_t tiles_x = (a.width + kDepthTile - 1) / kDepthTile;
   const uint32_t tiles = tiles_x * ((a.height + kDepthTile - 1) / kDepthTile);
@@ -214,13 +227,24 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
         }
         count += __popc(m);
       }
-      if (lane == 0) n_live[w] = count;
+      if (lane == 0) {
+        n_live[w] = count;
+        tile_x0[w] = x0;
+        tile_y0[w] = y0;
+      }
+      if (MODE == kCountLive && lane == 0) {
+        // pixels of tile t times its live boxes
+        const unsigned long long px = (unsigned long long)(x1 - x0 + 1) * (y1 - y0 + 1);
+        atomicAdd(a.live_pairs, px * (unsigned long long)count);
+      }
     }
   }
+  if (MODE == kCountLive) return;
   __syncthreads();
+  float* const out_cam = a.out + (size_t)j * n_pix;
   for (uint32_t t = t_begin; t < t_end; ++t) {
-    const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
     const int tl = (int)(t - t_begin);
+    const uint32_t x0 = tile_x0[tl], y0 = tile_y0[tl];
     const uint32_t col = x0 + tx;
     const float dy = -((float)col + 0.5f - half_w) * a.inv_f;
     float dz[kDepthPix], best[kDepthPix];
@@ -244,9 +268,9 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
         const float near_z = nz ? r3.z : r2.w, far_z = nz ? r2.w : r3.z;
 #pragma unroll
         for (int p = 0; p < kDepthPix; ++p) {
-          const float ix = __fdividef(1.f, fmaf(dz[p], r0.z, cx));
-          const float iy = __fdividef(1.f, fmaf(dz[p], r1.y, cy));
-          const float iz = __fdividef(1.f, fmaf(dz[p], r2.x, cz));
+          const float ix = depth_rcp<MODE>(fmaf(dz[p], r0.z, cx));
+          const float iy = depth_rcp<MODE>(fmaf(dz[p], r1.y, cy));
+          const float iz = depth_rcp<MODE>(fmaf(dz[p], r2.x, cz));
           const float t_in = fmaxf(fmaxf(0.f, near_x * ix), fmaxf(near_y * iy, near_z * iz));
           const float t_out = fminf(fminf(best[p], far_x * ix), fminf(far_y * iy, far_z * iz));
           if (t_in <= t_out) best[p] = t_in;
@@ -255,9 +279,9 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
       }
 #pragma unroll
       for (int p = 0; p < kDepthPix; ++p) {
-        const float ix = __fdividef(1.f, fmaf(dz[p], r0.z, cx));
-        const float iy = __fdividef(1.f, fmaf(dz[p], r1.y, cy));
-        const float iz = __fdividef(1.f, fmaf(dz[p], r2.x, cz));
+        const float ix = depth_rcp<MODE>(fmaf(dz[p], r0.z, cx));
+        const float iy = depth_rcp<MODE>(fmaf(dz[p], r1.y, cy));
+        const float iz = depth_rcp<MODE>(fmaf(dz[p], r2.x, cz));
         const float ax = r2.y * ix, bx = r3.x * ix, ay = r2.z * iy, by = r3.y * iy, az = r2.w * iz, bz = r3.z * iz;
         // only hits in [0, best) matter
         const float t_in = fmaxf(fmaxf(0.f, fminf(ax, bx)), fmaxf(fminf(ay, by), fminf(az, bz)));
@@ -269,7 +293,7 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
 #pragma unroll
       for (int p = 0; p < kDepthPix; ++p) {
         const uint32_t row = y0 + ty + p * kDepthRows;
-        if (row < a.height) a.out[(size_t)j * n_pix + (size_t)row * a.width + col] = best[p];
+        if (row < a.height) out_cam[(size_t)row * a.width + col] = best[p];
       }
     }
   }
@@ -287,7 +311,9 @@ cudaError_t launch_render_depth(const DepthArgs& a_in, cudaStream_t st) {
   for (uint64_t c0 = 0; c0 < a_in.n_cams; c0 += cams_per_launch) {
     const uint64_t nc = a_in.n_cams - c0 < cams_per_launch ? a_in.n_cams - c0 : cams_per_launch;
     a.cam0 = (uint32_t)c0;
-    k_render_depth<<<(unsigned)(nc * groups), kDepthThreads, 0, st>>>(a);
+    if (a.live_pairs) k_render_depth<kCountLive><<<(unsigned)(nc * groups), kDepthThreads, 0, st>>>(a);
+    else if (a.ieee_div) k_render_depth<kRenderIeee><<<(unsigned)(nc * groups), kDepthThreads, 0, st>>>(a);
+    else k_render_depth<kRenderFast><<<(unsigned)(nc * groups), kDepthThreads, 0, st>>>(a);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -99,3 +99,24 @@ extern "C" ag_status ag_measure_fp32_peak(void* cuda_stream, uint32_t iters, uin
   out->block = kBlock;
   return AG_OK;
 }
+
+extern "C" ag_status ag_query_alu_peak(int device, ag_alu_peak* out) {
+  if (!out) return agh::fail_invalid(nullptr, "ag_query_alu_peak: out is NULL");
+  int sms = 0, khz = 0, major = 0, minor = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+  if (e != cudaSuccess) return cuda_fail(e, "ag_query_alu_peak: device query");
+  if (major < 6) return agh::fail_invalid(nullptr, "ag_query_alu_peak: compute capability below 6.0");
+  // FP32 lanes per SM: half-rate FP32 parts (6.0, Volta/Turing 7.x, A100 8.0)
+  // have 64, every later consumer and data-centre part (8.6+, 9.0, 10.x, 12.x) 128
+  const bool lanes64 = (major == 6 && minor == 0) || major == 7 || (major == 8 && minor == 0);
+  out->sm_count = (uint32_t)sms;
+  out->fp32_lanes_per_sm = lanes64 ? 64u : 128u;
+  out->max_sm_clock_khz = (uint32_t)khz;
+  out->cc_major = (uint32_t)major;
+  out->cc_minor = (uint32_t)minor;
+  out->tflops = (double)sms * out->fp32_lanes_per_sm * 2.0 * (double)khz * 1e3 / 1e12;
+  return AG_OK;
+}

@@ -160,3 +160,65 @@ def test_depth_full_size_sampled_cameras():
     ref = O.render_depth(state, boxes, cams, 480, 270, hfov, rng_max)
     _compare(got, ref, 0.002)
     assert (ref < rng_max).mean() > 0.05
+
+
+def _mismatch(a, b):
+    """Fraction of pixels where two float32 images differ by more than 1e-4 relative."""
+    a64, b64 = a.astype(np.float64), b.astype(np.float64)
+    return float((np.abs(a64 - b64) > 1e-4 * np.maximum(1.0, np.abs(b64))).mean())
+
+
+def test_fast_reciprocal_moves_few_pixels():
+    """The kernel's fast reciprocals against the same kernel with correctly
+    rounded ones (ag_render_depth_ieee), on the bench's depth workload (2^10
+    robots, 270 x 480, 16 boxes): the measured mismatch rate must stay within
+    the 0.2 % budget that the oracle comparisons allow, and the correctly
+    rounded variant must agree with the oracle at least as well."""
+    w = W.scaled(W.WORKLOADS["obstacles"], 1024)
+    inp = W.make_inputs(w, 1)
+    fl = gpu_fleet(w, inp, 1)
+    fl.reset(None, 1)
+    fl.step(10)
+    hfov, rng_max = math.radians(87), 10.0
+    fast = _np(fl.render_depth(480, 270, hfov, rng_max))
+    ieee = torch.empty((1024, 270, 480), dtype=torch.float32, device=fl.device)
+    _abi.ag_render_depth_ieee(fl.ctx, 480, 270, hfov, rng_max, None, None, 1024, ieee)
+    ieee = _np(ieee)
+    moved = _mismatch(fast, ieee)
+    exact_equal = float((fast == ieee).mean())
+    cams = np.sort(np.random.default_rng(4).choice(1024, 8, replace=False))
+    ref = O.render_depth(_np(fl.state()), _np(fl.obstacles()), cams, 480, 270, hfov, rng_max)
+    fl.close()
+    bad_fast, bad_ieee = _mismatch(fast[cams], ref), _mismatch(ieee[cams], ref)
+    print(f"fast vs ieee: {100 * moved:.4f} % of pixels beyond 1e-4 rel ({100 * exact_equal:.2f} % bit-equal); "
+          f"vs oracle on 8 cameras: fast {100 * bad_fast:.4f} %, ieee {100 * bad_ieee:.4f} %")
+    assert moved <= 0.002
+    assert bad_ieee <= 0.002 and bad_fast <= 0.002
+    assert bad_ieee <= bad_fast + 1e-4
+
+
+def test_live_pair_count_bounds_and_monotone_in_range():
+    """ag_depth_live_pairs: at most every (pixel, box) pair, more than none when
+    the cameras see boxes, no more at a shorter range, none without boxes, and
+    the same on a repeated call."""
+    w = W.scaled(W.WORKLOADS["obstacles"], 256)
+    inp = W.make_inputs(w, 2)
+    fl = gpu_fleet(w, inp, 2)
+    fl.reset(None, 2)
+    fl.step(5)
+    hfov = math.radians(87)
+    all_pairs = 256 * 270 * 480 * w.n_obstacles
+    live = _abi.ag_depth_live_pairs(fl.ctx, 480, 270, hfov, 10.0, None, None, 256)
+    assert 0 < live < all_pairs
+    assert _abi.ag_depth_live_pairs(fl.ctx, 480, 270, hfov, 10.0, None, None, 256) == live
+    short = _abi.ag_depth_live_pairs(fl.ctx, 480, 270, hfov, 0.5, None, None, 256)
+    assert short <= live
+    # a live pair is needed for every pixel that sees a box
+    img = _np(fl.render_depth(480, 270, hfov, 10.0))
+    assert live >= int((img < 10.0).sum())
+    fl.close()
+    from paper_2305_16510_gb300.fleet import Fleet
+    empty = Fleet(16)
+    empty.reset(None, 3)
+    assert _abi.ag_depth_live_pairs(empty.ctx, 64, 48, hfov, 10.0, None, None, 16) == 0
+    empty.close()
