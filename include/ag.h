@@ -98,7 +98,9 @@ typedef struct {
   float kx[3], kv[3], kR[3], kW[3]; /* diagonal controller gains */
   uint64_t seed;     /* Philox key for resets until ag_reset supplies another */
   uint64_t hbm_budget_bytes; /* 0 = no limit; otherwise ag_create fails with
-                                AG_ERR_OOM if its buffers would exceed it */
+                                AG_ERR_OOM if its buffers would exceed it, and
+                                ag_rollout_loss keeps its whole-horizon tape
+                                within it (else it uses a one-segment tape) */
 } ag_config;
 
 /* Fills *cfg with the defaults of a 1,024-quad fleet: dt 0.01, 1 substep,
@@ -336,7 +338,14 @@ ag_status ag_rollout_loss(ag_ctx* ctx, uint32_t n_steps, float w_pos, float w_om
  * the loss as a function of q_0 / |q_0|. Where the controller meets a
  * degenerate direction (zero commanded acceleration, thrust along the
  * heading, body x axis vertical) the gradient is that of the fallback
- * branch. Returns AG_ERR_STATE if nothing was recorded. */
+ * branch. Returns AG_ERR_STATE if nothing was recorded.
+ * The reverse sweep needs every step's start state again. ag_rollout_loss
+ * allocates a tape of the whole horizon (n_steps x 21 floats per
+ * environment) when it fits in device memory and in hbm_budget_bytes; then
+ * one launch recomputes every checkpoint segment's states into it in
+ * parallel before the sweep. Otherwise the tape holds one segment
+ * (record_every x 21 floats per environment) and the sweep recomputes the
+ * segments one after another. The two agree to float32 rounding. */
 ag_status ag_backward(ag_ctx* ctx, const float* loss_weights, float* grad_x0, float* grad_gains,
                       float* grad_gains_per_env, float* grad_targets);
 

@@ -18,12 +18,16 @@
 // inverts.
 //
 // Memory: the forward kernel stores a checkpoint (state + motors) every K
-// steps. The adjoint kernel walks the segments from the last to the first:
-// it recomputes the segment's K step-start states into a per-vehicle tape,
-// then sweeps them in reverse, recomputing each step's intermediates in
-// registers before back-propagating through it. Per-vehicle gain gradients
-// are summed over the fleet by a deterministic two-level reduction (fixed
-// block order, fixed tree order).
+// steps. The backward pass needs every step's start state again. When a tape
+// of the whole horizon fits (AdjointBuffers::full_tape), one launch with a
+// thread per (vehicle, segment) recomputes every segment's step-start states
+// from its checkpoint into the tape at once, and the reverse sweep then reads
+// them; otherwise the sweep walks the segments from the last to the first and
+// recomputes each segment's states into a one-segment tape itself. Either way
+// the sweep recomputes each step's intermediates in registers before
+// back-propagating through it. Per-vehicle gain gradients are summed over the
+// fleet by a deterministic two-level reduction (fixed block order, fixed tree
+// order).
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -525,7 +529,11 @@ __device__ __forceinline__ void record_mode(const AdjointBuffers& ab, const Step
   }
 }
 
-__global__ void __launch_bounds__(128) k_record(AdjointBuffers ab, StepParams P) {
+// One warp per block: the fleet's warps spread evenly over the SMs (a
+// 65,536-vehicle fleet puts 13 or 14 on each of 152 SMs, where 128-thread
+// blocks would put 12 on some and 16 on others).
+constexpr int kRecordBlock = 32;
+__global__ void __launch_bounds__(kRecordBlock) k_record(AdjointBuffers ab, StepParams P) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ab.n) return;
   const int nr = rotors_of(ab, i);
@@ -534,55 +542,43 @@ __global__ void __launch_bounds__(128) k_record(AdjointBuffers ab, StepParams P)
   else record_mode<8>(ab, P, i);
 }
 
-template <int NROT, int MODE>
-__device__ void adjoint_one(const AdjointBuffers& ab, const StepParams& P, uint32_t i) {
-  const uint32_t n = ab.n;
-  const Body b = body_at(ab.body, n, i);
-  const Gains g = gains_of(P);
-  const Cmd cm = load_cmd(ab, i, MODE);
-  const V3 goal = {ab.p_goal[i], ab.p_goal[n + i], ab.p_goal[2 * n + i]};
-  const float wgt = ab.loss_weights ? ab.loss_weights[i] : 1.f;
+// Adjoint state of one vehicle during the reverse sweep.
+template <int NROT> struct SweepState {
   Adj<NROT> lam;
-  lam.p = lam.v = lam.w = {0.f, 0.f, 0.f};
-  lam.q = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int k = 0; k < NROT; ++k) lam.u[k] = 0.f;
   GainAdj gb;
-  gb.kx = gb.kv = gb.kR = gb.kW = {0.f, 0.f, 0.f};
-  float tb[4] = {0.f, 0.f, 0.f, 0.f};
-  const int H = ab.n_steps, K = ab.K;
-  const int n_seg = (H + K - 1) / K;
-  for (int seg = n_seg - 1; seg >= 0; --seg) {
-    const int t0 = seg * K;
-    const int len = H - t0 < K ? H - t0 : K;
-    Xs<NROT> x;
-    load_x(ab.ckpt + (size_t)seg * 21 * n, ab.ckpt + (size_t)seg * 21 * n + 13 * n, n, i, x);
-    if (seg == 0) normalize(x.q);
-    // recompute the segment's step-start states into the tape
-    for (int t = 0; t < len; ++t) {
-      store_x(ab.tape + (size_t)t * 21 * n, ab.tape + (size_t)t * 21 * n + 13 * n, n, i, x);
-      Step<NROT> S;
-      Xs<NROT> xn;
-      forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
-      x = xn;
-    }
-    // reverse sweep; the next (earlier) tape entry is requested one step ahead
-    Xs<NROT> x_prev;
-    load_x(ab.tape + (size_t)(len - 1) * 21 * n, ab.tape + (size_t)(len - 1) * 21 * n + 13 * n, n, i, x_prev);
-    for (int t = len - 1; t >= 0; --t) {
-      x = x_prev;
-      if (t > 0) load_x(ab.tape + (size_t)(t - 1) * 21 * n, ab.tape + (size_t)(t - 1) * 21 * n + 13 * n, n, i, x_prev);
-      Step<NROT> S;
-      Xs<NROT> xn;
-      forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
-      // this step's loss term acts on x_{t+1}
-      const V3 e = xn.p - goal;
-      lam.p = lam.p + (2.f * ab.w_pos * wgt) * e;
-      lam.w = lam.w + (2.f * ab.w_omega * wgt) * xn.w;
-      backward_step<NROT, MODE>(x, cm, b, g, P, S, lam, gb, tb);
-    }
-  }
-  // the kernel normalised q_0 at load: q_hat = q0 / |q0|
+  float tb[4];
+};
+
+template <int NROT> __device__ __forceinline__ void sweep_init(SweepState<NROT>& z) {
+  z.lam.p = z.lam.v = z.lam.w = {0.f, 0.f, 0.f};
+  z.lam.q = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < NROT; ++k) z.lam.u[k] = 0.f;
+  z.gb.kx = z.gb.kv = z.gb.kR = z.gb.kW = {0.f, 0.f, 0.f};
+  z.tb[0] = z.tb[1] = z.tb[2] = z.tb[3] = 0.f;
+}
+
+// One step of the reverse sweep from its start state x: recompute the step's
+// intermediates, add the step's loss term (it acts on x_{t+1}), back-propagate.
+template <int NROT, int MODE>
+__device__ __forceinline__ void sweep_step(const AdjointBuffers& ab, const StepParams& P, const Xs<NROT>& x,
+                                           const Cmd& cm, const Body& b, const Gains& g, V3 goal, float wgt,
+                                           SweepState<NROT>& z) {
+  Step<NROT> S;
+  Xs<NROT> xn;
+  forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
+  const V3 e = xn.p - goal;
+  z.lam.p = z.lam.p + (2.f * ab.w_pos * wgt) * e;
+  z.lam.w = z.lam.w + (2.f * ab.w_omega * wgt) * xn.w;
+  backward_step<NROT, MODE>(x, cm, b, g, P, S, z.lam, z.gb, z.tb);
+}
+
+// Writes vehicle i's gradients. The kernel normalised q_0 at load
+// (q_hat = q0 / |q0|), so the quaternion adjoint is mapped back through that.
+template <int NROT>
+__device__ __forceinline__ void sweep_finish(const AdjointBuffers& ab, uint32_t i, SweepState<NROT>& z) {
+  const uint32_t n = ab.n;
+  Adj<NROT>& lam = z.lam;
   {
     const Q4 q0 = {ab.ckpt[6 * n + i], ab.ckpt[7 * n + i], ab.ckpt[8 * n + i], ab.ckpt[9 * n + i]};
     const float nq = sqrtf(q0.w * q0.w + q0.x * q0.x + q0.y * q0.y + q0.z * q0.z);
@@ -597,32 +593,145 @@ __device__ void adjoint_one(const AdjointBuffers& ab, const StepParams& P, uint3
   gx[6 * n + i] = lam.q.w; gx[7 * n + i] = lam.q.x; gx[8 * n + i] = lam.q.y; gx[9 * n + i] = lam.q.z;
   gx[10 * n + i] = lam.w.x; gx[11 * n + i] = lam.w.y; gx[12 * n + i] = lam.w.z;
   float* gg = ab.grad_gains_env;
+  const GainAdj& gb = z.gb;
   const float v12[12] = {gb.kx.x, gb.kx.y, gb.kx.z, gb.kv.x, gb.kv.y, gb.kv.z,
                          gb.kR.x, gb.kR.y, gb.kR.z, gb.kW.x, gb.kW.y, gb.kW.z};
 #pragma unroll
   for (int k = 0; k < 12; ++k) gg[k * n + i] = v12[k];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) ab.grad_targets[k * n + i] = tb[k];
+  for (int k = 0; k < 4; ++k) ab.grad_targets[k * n + i] = z.tb[k];
 }
 
 template <int NROT>
-__device__ __forceinline__ void adjoint_mode(const AdjointBuffers& ab, const StepParams& P, uint32_t i) {
-  switch (mode_of(ab, i)) {
-    case kModePosition: adjoint_one<NROT, kModePosition>(ab, P, i); break;
-    case kModeBodyVel: adjoint_one<NROT, kModeBodyVel>(ab, P, i); break;
-    case kModeAttThrust: adjoint_one<NROT, kModeAttThrust>(ab, P, i); break;
-    default: adjoint_one<NROT, kModeWrench>(ab, P, i); break;
+__device__ __forceinline__ float* tape_at(const AdjointBuffers& ab, int t) {
+  return ab.tape + (size_t)t * 21 * ab.n;
+}
+
+// Reverse sweep of vehicle i. full_tape: every step-start state is already on
+// the tape (k_tape); otherwise each segment's states are recomputed here,
+// segment by segment, into the one-segment tape.
+template <int NROT, int MODE, bool FULL_TAPE>
+__device__ void adjoint_one(const AdjointBuffers& ab, const StepParams& P, uint32_t i) {
+  const uint32_t n = ab.n;
+  const Body b = body_at(ab.body, n, i);
+  const Gains g = gains_of(P);
+  const Cmd cm = load_cmd(ab, i, MODE);
+  const V3 goal = {ab.p_goal[i], ab.p_goal[n + i], ab.p_goal[2 * n + i]};
+  const float wgt = ab.loss_weights ? ab.loss_weights[i] : 1.f;
+  SweepState<NROT> z;
+  sweep_init(z);
+  const int H = ab.n_steps, K = ab.K;
+  if (FULL_TAPE) {
+    // the next (earlier) tape entry is requested one step ahead
+    Xs<NROT> x, x_prev;
+    load_x(tape_at<NROT>(ab, H - 1), tape_at<NROT>(ab, H - 1) + 13 * n, n, i, x_prev);
+    for (int t = H - 1; t >= 0; --t) {
+      x = x_prev;
+      if (t > 0) load_x(tape_at<NROT>(ab, t - 1), tape_at<NROT>(ab, t - 1) + 13 * n, n, i, x_prev);
+      sweep_step<NROT, MODE>(ab, P, x, cm, b, g, goal, wgt, z);
+    }
+    sweep_finish(ab, i, z);
+    return;
+  }
+  const int n_seg = (H + K - 1) / K;
+  for (int seg = n_seg - 1; seg >= 0; --seg) {
+    const int t0 = seg * K;
+    const int len = H - t0 < K ? H - t0 : K;
+    Xs<NROT> x;
+    load_x(ab.ckpt + (size_t)seg * 21 * n, ab.ckpt + (size_t)seg * 21 * n + 13 * n, n, i, x);
+    if (seg == 0) normalize(x.q);
+    // recompute the segment's step-start states into the tape
+    for (int t = 0; t < len; ++t) {
+      store_x(tape_at<NROT>(ab, t), tape_at<NROT>(ab, t) + 13 * n, n, i, x);
+      if (t + 1 < len) {
+        Step<NROT> S;
+        Xs<NROT> xn;
+        forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
+        x = xn;
+      }
+    }
+    // reverse sweep; the next (earlier) tape entry is requested one step ahead
+    Xs<NROT> x_prev;
+    load_x(tape_at<NROT>(ab, len - 1), tape_at<NROT>(ab, len - 1) + 13 * n, n, i, x_prev);
+    for (int t = len - 1; t >= 0; --t) {
+      x = x_prev;
+      if (t > 0) load_x(tape_at<NROT>(ab, t - 1), tape_at<NROT>(ab, t - 1) + 13 * n, n, i, x_prev);
+      sweep_step<NROT, MODE>(ab, P, x, cm, b, g, goal, wgt, z);
+    }
+  }
+  sweep_finish(ab, i, z);
+}
+
+// Step-start states of one segment of vehicle i, recomputed from its
+// checkpoint into the whole-horizon tape (tape step t0 + t, t < len).
+template <int NROT, int MODE>
+__device__ void tape_one(const AdjointBuffers& ab, const StepParams& P, uint32_t i, int seg) {
+  const uint32_t n = ab.n;
+  const int t0 = seg * ab.K;
+  const int len = ab.n_steps - t0 < ab.K ? ab.n_steps - t0 : ab.K;
+  const Body b = body_at(ab.body, n, i);
+  const Gains g = gains_of(P);
+  const Cmd cm = load_cmd(ab, i, MODE);
+  Xs<NROT> x;
+  load_x(ab.ckpt + (size_t)seg * 21 * n, ab.ckpt + (size_t)seg * 21 * n + 13 * n, n, i, x);
+  if (seg == 0) normalize(x.q);
+  for (int t = 0; t < len; ++t) {
+    store_x(tape_at<NROT>(ab, t0 + t), tape_at<NROT>(ab, t0 + t) + 13 * n, n, i, x);
+    if (t + 1 < len) {
+      Step<NROT> S;
+      Xs<NROT> xn;
+      forward_step<NROT, MODE>(x, cm, b, g, P, S, xn);
+      x = xn;
+    }
   }
 }
 
-constexpr int kAdjointBlock = 128;
-__global__ void __launch_bounds__(kAdjointBlock, 3) k_adjoint(AdjointBuffers ab, StepParams P) {
+template <int NROT>
+__device__ __forceinline__ void tape_mode(const AdjointBuffers& ab, const StepParams& P, uint32_t i, int seg) {
+  switch (mode_of(ab, i)) {
+    case kModePosition: tape_one<NROT, kModePosition>(ab, P, i, seg); break;
+    case kModeBodyVel: tape_one<NROT, kModeBodyVel>(ab, P, i, seg); break;
+    case kModeAttThrust: tape_one<NROT, kModeAttThrust>(ab, P, i, seg); break;
+    default: tape_one<NROT, kModeWrench>(ab, P, i, seg); break;
+  }
+}
+
+// One thread per (vehicle, segment): thread j handles vehicle j % n of
+// segment j / n, so a warp's loads and stores stay coalesced.
+constexpr int kTapeBlock = 128;
+__global__ void __launch_bounds__(kTapeBlock) k_tape(AdjointBuffers ab, StepParams P, int n_seg) {
+  const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= (uint64_t)ab.n * n_seg) return;
+  const uint32_t i = (uint32_t)(j % ab.n);
+  const int seg = (int)(j / ab.n);
+  const int nr = rotors_of(ab, i);
+  if (nr == 4) tape_mode<4>(ab, P, i, seg);
+  else if (nr == 6) tape_mode<6>(ab, P, i, seg);
+  else tape_mode<8>(ab, P, i, seg);
+}
+
+template <int NROT, bool FULL_TAPE>
+__device__ __forceinline__ void adjoint_mode(const AdjointBuffers& ab, const StepParams& P, uint32_t i) {
+  switch (mode_of(ab, i)) {
+    case kModePosition: adjoint_one<NROT, kModePosition, FULL_TAPE>(ab, P, i); break;
+    case kModeBodyVel: adjoint_one<NROT, kModeBodyVel, FULL_TAPE>(ab, P, i); break;
+    case kModeAttThrust: adjoint_one<NROT, kModeAttThrust, FULL_TAPE>(ab, P, i); break;
+    default: adjoint_one<NROT, kModeWrench, FULL_TAPE>(ab, P, i); break;
+  }
+}
+
+// One warp per block and at most 144 registers: 14 warps fit on an SM, so a
+// 65,536-vehicle fleet (2,048 warps) is resident in one wave on 152 SMs, and
+// single-warp blocks spread the warps evenly (13 or 14 per SM).
+constexpr int kAdjointBlock = 32;
+template <bool FULL_TAPE>
+__global__ void __maxnreg__(144) k_adjoint(AdjointBuffers ab, StepParams P) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ab.n) return;
   const int nr = rotors_of(ab, i);
-  if (nr == 4) adjoint_mode<4>(ab, P, i);
-  else if (nr == 6) adjoint_mode<6>(ab, P, i);
-  else adjoint_mode<8>(ab, P, i);
+  if (nr == 4) adjoint_mode<4, FULL_TAPE>(ab, P, i);
+  else if (nr == 6) adjoint_mode<6, FULL_TAPE>(ab, P, i);
+  else adjoint_mode<8, FULL_TAPE>(ab, P, i);
 }
 
 // Deterministic fleet sum of the 12 per-env gain gradients: each of the
@@ -666,13 +775,22 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const float* parti
 }  // namespace
 
 cudaError_t launch_record(const AdjointBuffers& ab, const StepParams& P, cudaStream_t st) {
-  k_record<<<(ab.n + 127) / 128, 128, 0, st>>>(ab, P);
+  k_record<<<(ab.n + kRecordBlock - 1) / kRecordBlock, kRecordBlock, 0, st>>>(ab, P);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(const AdjointBuffers& ab, const StepParams& P, cudaStream_t st) {
-  k_adjoint<<<(ab.n + kAdjointBlock - 1) / kAdjointBlock, kAdjointBlock, 0, st>>>(ab, P);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (ab.full_tape) {
+    const int n_seg = (ab.n_steps + ab.K - 1) / ab.K;
+    const uint64_t threads = (uint64_t)ab.n * n_seg;
+    k_tape<<<(unsigned)((threads + kTapeBlock - 1) / kTapeBlock), kTapeBlock, 0, st>>>(ab, P, n_seg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const unsigned blocks = (ab.n + kAdjointBlock - 1) / kAdjointBlock;
+  if (ab.full_tape) k_adjoint<true><<<blocks, kAdjointBlock, 0, st>>>(ab, P);
+  else k_adjoint<false><<<blocks, kAdjointBlock, 0, st>>>(ab, P);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 g1(kReduceParts, 12);
   k_reduce_partial<<<g1, kRedThreads, 0, st>>>(ab.grad_gains_env, ab.n, ab.partial, kReduceParts);

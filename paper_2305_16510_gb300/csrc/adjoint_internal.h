@@ -12,7 +12,8 @@ constexpr int kReduceParts = 256;  // first-level blocks of the gain-gradient re
 
 // Device buffers of one recorded rollout and its adjoint. Checkpoint s holds
 // the state (13 rows) and motors (8 rows) at step s*K as [21][n]; the tape
-// holds one segment's K step-start states in the same layout.
+// holds step-start states in the same layout: every step of the horizon when
+// full_tape is set, else one segment's K steps.
 struct AdjointBuffers {
   float* state;                // [13][n] fleet state (advanced by the record)
   float* motors;               // [8][n]
@@ -21,7 +22,7 @@ struct AdjointBuffers {
   const float* targets;        // [4][n] command targets
   const float* p_goal;         // [3][n]
   float* ckpt;                 // [S][21][n]
-  float* tape;                 // [K][21][n]
+  float* tape;                 // [n_steps][21][n] (full_tape) or [K][21][n]
   float* loss;                 // [n]
   uint8_t* saturated;          // [n] some motor hit a clamp during the record
   const float* loss_weights;   // [n] upstream gradient of each env's loss (NULL = 1)
@@ -32,6 +33,7 @@ struct AdjointBuffers {
   float* grad_gains;           // [12]
   uint32_t n, n_quad, n_hexa, n_octo;
   int n_steps, K;
+  int full_tape;               // 1: the tape spans the whole horizon (recomputed by k_tape)
   float w_pos, w_omega;
 };
 

@@ -36,13 +36,46 @@ ag_status ensure_adjoint(ag_ctx* ctx, int n_steps, int K) {
     if (e != cudaSuccess) { cudaGetLastError(); ctx->err = "adjoint buffers do not fit"; return AG_ERR_OOM; }
   }
   if (n_ckpt > ctx->adj_ckpt_cap) {
-    if (a.ckpt) { cudaStreamSynchronize(ctx->stream); cudaFree(a.ckpt); a.ckpt = nullptr; }
+    if (a.ckpt) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(a.ckpt);
+      a.ckpt = nullptr;
+      ctx->bytes -= ctx->adj_ckpt_cap * 21 * n * sizeof(float);
+    }
     e = alloc(ctx, &a.ckpt, n_ckpt * 21 * n);
     if (e != cudaSuccess) { cudaGetLastError(); ctx->adj_ckpt_cap = 0; ctx->err = "checkpoints do not fit"; return AG_ERR_OOM; }
     ctx->adj_ckpt_cap = n_ckpt;
   }
-  if (K > ctx->adj_tape_cap) {
-    if (a.tape) { cudaStreamSynchronize(ctx->stream); cudaFree(a.tape); a.tape = nullptr; }
+  // The tape of step-start states: the whole horizon when it fits (within
+  // hbm_budget_bytes when one is set), so that the backward pass can
+  // recompute every segment in parallel; else one segment of K steps.
+  const size_t step_bytes = 21 * n * sizeof(float);
+  const size_t held = (size_t)ctx->adj_tape_cap * step_bytes;
+  auto free_tape = [&]() {
+    if (a.tape) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(a.tape);
+      a.tape = nullptr;
+      ctx->bytes -= held;
+    }
+    ctx->adj_tape_cap = 0;
+  };
+  if ((size_t)ctx->adj_tape_cap < (size_t)n_steps) {
+    const size_t full_bytes = (size_t)n_steps * step_bytes;
+    const uint64_t budget = ctx->cfg.hbm_budget_bytes;
+    if (budget == 0 || ctx->bytes - held + full_bytes <= budget) {
+      free_tape();
+      if (alloc(ctx, &a.tape, (size_t)n_steps * 21 * n) == cudaSuccess) {
+        ctx->adj_tape_cap = n_steps;
+      } else {
+        cudaGetLastError();  // an out-of-memory cudaMalloc leaves no sticky error
+        a.tape = nullptr;
+      }
+    }
+  }
+  a.full_tape = (size_t)ctx->adj_tape_cap >= (size_t)n_steps ? 1 : 0;
+  if (!a.full_tape && K > ctx->adj_tape_cap) {
+    free_tape();
     e = alloc(ctx, &a.tape, (size_t)K * 21 * n);
     if (e != cudaSuccess) { cudaGetLastError(); ctx->adj_tape_cap = 0; ctx->err = "tape does not fit"; return AG_ERR_OOM; }
     ctx->adj_tape_cap = K;

@@ -357,3 +357,48 @@ def test_autograd_target_gradient_matches_ag_backward():
     np.testing.assert_allclose(_np(tg_t.grad), gt, rtol=1e-6, atol=1e-6 * np.abs(gt).max())
     np.testing.assert_allclose(_np(x0_t.grad), gx, rtol=1e-6, atol=1e-6 * np.abs(gx).max())
     fl.close()
+
+
+def test_whole_horizon_tape_and_one_segment_tape_agree():
+    """ag_rollout_loss keeps a tape of the whole horizon when it fits (the
+    backward pass then recomputes every checkpoint segment in parallel), else
+    one segment's tape (recomputed segment by segment in the sweep). A context
+    whose hbm_budget_bytes leaves no room for the whole-horizon tape takes the
+    second path. The two recompute the same steps in different kernels, where
+    the compiler may contract multiply-adds differently, so they agree to
+    float32 rounding (measured about 1e-6 relative), not bit for bit: each
+    vehicle's gradient within 1e-4 relative, here over every mode and airframe
+    with a horizon that is not a multiple of the checkpoint interval. The loss
+    comes from the same record in both and is identical."""
+    from paper_2305_16510_gb300.fleet import Fleet
+    w = MODES_W
+    inp = _mode_inputs(w, 41, gentle=False)
+    horizon = 100                                   # segments of 32, 32, 32 and 4 steps
+    n = w.n_envs
+    full_tape_bytes = horizon * 21 * n * 4          # 25.8 MB
+    outs = []
+    for budget in (0, 12 << 20):                    # no limit; 12 MiB (the fleet, checkpoints, one segment)
+        fl = Fleet(n, n_hexa=w.n_hexa, n_octo=w.n_octo, drag=w.drag, seed=41, hbm_budget_bytes=budget)
+        fl.set_body(inp.body)
+        fl.set_commands(inp.modes, inp.targets)
+        fl.reset(None, 41)
+        goal = torch.from_numpy(np.ascontiguousarray(inp.targets[0:3])).cuda()
+        loss = torch.empty(n, dtype=torch.float32, device="cuda")
+        gx = torch.empty((13, n), dtype=torch.float32, device="cuda")
+        gg = torch.empty((12,), dtype=torch.float32, device="cuda")
+        gge = torch.empty((12, n), dtype=torch.float32, device="cuda")
+        gt = torch.empty((4, n), dtype=torch.float32, device="cuda")
+        _abi.ag_rollout_loss(fl.ctx, horizon, W_POS, W_OMEGA, goal, loss)
+        _abi.ag_backward(fl.ctx, None, gx, gg, gge, gt)
+        torch.cuda.synchronize()
+        outs.append([_np(t) for t in (loss, gx, gg, gge, gt)])
+        fl.close()
+    assert full_tape_bytes > 12 << 20
+    full, seg = outs
+    np.testing.assert_array_equal(full[0], seg[0])                     # loss
+    for k in (1, 3, 4):                                                # per vehicle: x0, gains, targets
+        diff = np.linalg.norm(full[k] - seg[k], axis=0)
+        ref = np.maximum(np.linalg.norm(seg[k], axis=0), 1e-6)
+        assert np.max(diff / ref) <= 1e-4, (k, np.max(diff / ref))
+    assert np.linalg.norm(full[2] - seg[2]) <= 1e-4 * np.linalg.norm(seg[2])   # fleet gain sum
+    assert np.abs(full[1]).max() > 0
