@@ -30,8 +30,8 @@ constexpr size_t kFusedSmemCap = 200 * 1024;
 // that groups environments of equal rotor count and command mode, so the
 // mode branches of the controller are warp-uniform), or environment i when
 // order is NULL. Each thread stages its environment's boxes once per launch:
-// boxes 0 and 1 in registers, the others in shared memory as float2
-// [pair][field][thread], so a warp's 8-byte loads of one field are
+// boxes 0 and 1 in registers, the others in shared memory as float4
+// [pair][field pair][thread], so a warp's 16-byte loads of two fields are
 // consecutive and conflict-free. A thread reads only what it wrote, so no
 // barrier is needed.
 // BOXES = false (no obstacles) keeps the kernel within 128 registers, so
@@ -43,7 +43,7 @@ constexpr size_t kFusedSmemCap = 200 * 1024;
 template <int INTEG, bool QUAD_ONLY, bool DRAG, bool BOXES>
 __global__ void __launch_bounds__(128, BOXES ? 3 : ((QUAD_ONLY && INTEG == kIntegSIE) ? 7 : 4))
     k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
-  extern __shared__ float2 sm_pairs[];  // [ceil(n_obs / 2) - 1][10][blockDim.x] box pairs 1..
+  extern __shared__ float4 sm_pairs[];  // [ceil(n_obs / 2) - 1][5][blockDim.x] box pairs 1..
   const int B = blockDim.x;
   const uint32_t slot = blockIdx.x * B + threadIdx.x;
   const bool active = slot < fb.n;
@@ -60,17 +60,25 @@ __global__ void __launch_bounds__(128, BOXES ? 3 : ((QUAD_ONLY && INTEG == kInte
       // the slot-ordered pair copy: coalesced 8-byte rows
 #pragma unroll
       for (int f = 0; f < 10; ++f) bx.r[f] = fb.boxes_slot[(size_t)f * fb.n + slot];
-      for (int r = 10; r < pairs * 10; ++r) bx.sm[(r - 10) * B] = fb.boxes_slot[(size_t)r * fb.n + slot];
+      for (int r = 10; r < pairs * 10; r += 2) {
+        const float2 lo = fb.boxes_slot[(size_t)r * fb.n + slot], hi = fb.boxes_slot[(size_t)(r + 1) * fb.n + slot];
+        bx.sm[(r - 10) / 2 * B] = make_float4(lo.x, lo.y, hi.x, hi.y);
+      }
     } else {
       // ungrouped (env == slot): pair up the env-ordered rows here
       bx.reload(fb, slot);
       for (int j = 1; j < pairs; ++j) {
         const int k0 = 2 * j, k1 = 2 * j + 1;
 #pragma unroll
-        for (int f = 0; f < 10; ++f) {
-          const float a = fb.boxes[((size_t)k0 * 10 + f) * fb.n + slot];
-          const float b = k1 < n_obs ? fb.boxes[((size_t)k1 * 10 + f) * fb.n + slot] : box_pad_field(f);
-          bx.sm[((j - 1) * 10 + f) * B] = make_float2(staged_field(f, a), staged_field(f, b));
+        for (int f = 0; f < 10; f += 2) {
+          float v[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {  // a_f, b_f, a_f+1, b_f+1
+            const int k = (c & 1) ? k1 : k0, ff = f + (c >> 1);
+            const float raw = k < n_obs ? fb.boxes[((size_t)k * 10 + ff) * fb.n + slot] : box_pad_field(ff);
+            v[c] = staged_field(ff, raw);
+          }
+          bx.sm[((j - 1) * 5 + f / 2) * B] = make_float4(v[0], v[1], v[2], v[3]);
         }
       }
     }

@@ -129,12 +129,15 @@ __device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float
 }
 
 // RegSmemBoxPairs: the first pair (boxes 0 and 1) in registers, the others
-// in shared memory as float2 [pair - 1][field][thread]. Holding one pair in
-// registers shrinks each thread's shared-memory footprint by a tenth of the
-// 16-box case, which lets one more block reside per SM.
+// in shared memory as float4 [pair - 1][field pair][thread], each float4 two
+// consecutive fields of both boxes, (a_f, b_f, a_f+1, b_f+1): a pair is five
+// 16-byte loads, and a warp's load of one float4 row is 512 consecutive bytes
+// (no bank conflicts). Holding one pair in registers shrinks each thread's
+// shared-memory footprint by a tenth of the 16-box case, which lets one more
+// block reside per SM.
 struct RegSmemBoxPairs {
   float2 r[10];  // pair 0, fields 0..9
-  float2* sm;    // this thread's column of pairs 1..: element ((j - 1) * 10 + f) * B
+  float4* sm;    // this thread's column of pairs 1..: element ((j - 1) * 5 + f / 2) * B
   int B;
   __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
     const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
@@ -142,20 +145,24 @@ struct RegSmemBoxPairs {
     const int pairs = (n_obs + 1) >> 1;
 #pragma unroll 2
     for (int j = 1; j < pairs; ++j) {
-      const float2* f = sm + (size_t)(j - 1) * 10 * B;
-      hit |= pair_hits(px, py, pz, r2, f[0], f[B], f[2 * B], f[3 * B], f[4 * B], f[5 * B], f[6 * B], f[7 * B],
-                       f[8 * B], f[9 * B]);
+      const float4* f = sm + (size_t)(j - 1) * 5 * B;
+      const float4 f01 = f[0], f23 = f[B], f45 = f[2 * B], f67 = f[3 * B], f89 = f[4 * B];
+      hit |= pair_hits(px, py, pz, r2, make_float2(f01.x, f01.y), make_float2(f01.z, f01.w),
+                       make_float2(f23.x, f23.y), make_float2(f23.z, f23.w), make_float2(f45.x, f45.y),
+                       make_float2(f45.z, f45.w), make_float2(f67.x, f67.y), make_float2(f67.z, f67.w),
+                       make_float2(f89.x, f89.y), make_float2(f89.z, f89.w));
     }
     return hit;
   }
   // The shared-memory part, as the target of a re-draw (boxes 2..).
   struct Staged {
-    float2* sm;
+    float4* sm;
     int B;
     __device__ __forceinline__ void set(int k, int f, float v) const {
       if (k < 2) return;
-      float2& e = sm[(size_t)(((k >> 1) - 1) * 10 + f) * B];
-      if (k & 1) e.y = v; else e.x = v;
+      float4& e = sm[(size_t)(((k >> 1) - 1) * 5 + (f >> 1)) * B];
+      const int c = (f & 1) * 2 + (k & 1);  // a_f, b_f, a_f+1, b_f+1
+      if (c == 0) e.x = v; else if (c == 1) e.y = v; else if (c == 2) e.z = v; else e.w = v;
     }
   };
   __device__ __forceinline__ Staged staged() const { return {sm, B}; }
