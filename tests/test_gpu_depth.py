@@ -2,7 +2,9 @@
 
 A pixel whose ray grazes a box silhouette can legitimately be a hit in one
 precision and a miss in the other; such pixels are counted and must stay a
-small minority. Every other pixel must agree to 1e-4 relative.
+small minority (at most 0.01 % of the pixels on the paper-resolution images,
+where none was measured; 0.1 % on the 64-box images; 0.2 % on the small
+images of the edge cases). Every other pixel must agree to 1e-4 relative.
 """
 import math
 
@@ -30,8 +32,10 @@ def _np(t):
     return t.detach().cpu().numpy()
 
 
-def _compare(gpu, orc, max_bad_frac):
+def _compare(gpu, orc, max_bad_frac, check=None, what="pixels beyond 1e-4 relative"):
     close = np.abs(gpu.astype(np.float64) - orc) <= 1e-4 * np.maximum(1.0, orc)
+    if check is not None:
+        check(what, 1.0 - close.mean(), max_bad_frac)
     assert close.mean() >= 1.0 - max_bad_frac, close.mean()
 
 
@@ -87,7 +91,7 @@ def test_depth_without_boxes_is_max_range_everywhere():
     fl.close()
 
 
-def test_depth_paper_resolution_1024_robots_sampled():
+def test_depth_paper_resolution_1024_robots_sampled(within_tolerance):
     # 2^10 robots with 270 x 480 depth cameras (the paper's depth-camera
     # workload); 3 sampled cameras are re-rendered by the oracle
     w = W.Workload("cams", 1024, 4, 1, 16, 1024, 0, 0, mode_mix=(0, 1, 2))
@@ -101,11 +105,11 @@ def test_depth_paper_resolution_1024_robots_sampled():
     st, bx = _np(fl.state()), _np(fl.obstacles())
     for j in (0, 511, 1023):
         ref = O.render_depth(st, bx, [j], 480, 270, math.radians(87), 10.0)
-        _compare(_np(img[j:j + 1]), ref, 0.002)
+        _compare(_np(img[j:j + 1]), ref, 1e-4, within_tolerance, f"camera {j}: pixels beyond 1e-4 relative")
     fl.close()
 
 
-def test_depth_with_the_maximum_box_count():
+def test_depth_with_the_maximum_box_count(within_tolerance):
     # AG_MAX_OBSTACLES boxes per environment, the nearest surface taken over all of them
     n_obs = _abi.AG_MAX_OBSTACLES
     w = W.Workload("cams_many", 4, 1, 0, n_obs, 4, 0, 0)
@@ -115,7 +119,7 @@ def test_depth_with_the_maximum_box_count():
     hfov, rng_max = math.radians(70), 20.0
     img = _np(fl.render_depth(40, 24, hfov, rng_max))
     ref = O.render_depth(_np(fl.state()), _np(fl.obstacles()), np.arange(4), 40, 24, hfov, rng_max)
-    _compare(img, ref, 0.01)
+    _compare(img, ref, 1e-3, within_tolerance)
     assert (ref < rng_max).mean() > 0.3
     # the last box alone decides some pixels: moving it away changes them
     boxes = _np(fl.obstacles()).copy()
@@ -141,7 +145,7 @@ def test_depth_more_cameras_than_a_grid_dimension():
     fl.close()
 
 
-def test_depth_full_size_sampled_cameras():
+def test_depth_full_size_sampled_cameras(within_tolerance):
     """The bench's depth workload (2^10 robots of the obstacle recipe, 16 boxes
     each, after 10 steps, 270 x 480 at 87 deg): 12 sampled cameras are
     rendered again by the oracle, whole."""
@@ -158,7 +162,7 @@ def test_depth_full_size_sampled_cameras():
     got = _np(img[torch.from_numpy(cams).cuda()])
     fl.close()
     ref = O.render_depth(state, boxes, cams, 480, 270, hfov, rng_max)
-    _compare(got, ref, 0.002)
+    _compare(got, ref, 1e-4, within_tolerance)
     assert (ref < rng_max).mean() > 0.05
 
 
@@ -168,12 +172,12 @@ def _mismatch(a, b):
     return float((np.abs(a64 - b64) > 1e-4 * np.maximum(1.0, np.abs(b64))).mean())
 
 
-def test_fast_reciprocal_moves_few_pixels():
+def test_fast_reciprocal_moves_few_pixels(within_tolerance):
     """The kernel's fast reciprocals against the same kernel with correctly
     rounded ones (ag_render_depth_ieee), on the bench's depth workload (2^10
-    robots, 270 x 480, 16 boxes): the measured mismatch rate must stay within
-    the 0.2 % budget that the oracle comparisons allow, and the correctly
-    rounded variant must agree with the oracle at least as well."""
+    robots, 270 x 480, 16 boxes): 3 of the 132.7 million pixels differ by
+    more than 1e-4 relative (2.3e-8), bound 1e-6; against the oracle both
+    variants stay within the 1e-4 budget of the full-size comparisons."""
     w = W.scaled(W.WORKLOADS["obstacles"], 1024)
     inp = W.make_inputs(w, 1)
     fl = gpu_fleet(w, inp, 1)
@@ -192,8 +196,9 @@ def test_fast_reciprocal_moves_few_pixels():
     bad_fast, bad_ieee = _mismatch(fast[cams], ref), _mismatch(ieee[cams], ref)
     print(f"fast vs ieee: {100 * moved:.4f} % of pixels beyond 1e-4 rel ({100 * exact_equal:.2f} % bit-equal); "
           f"vs oracle on 8 cameras: fast {100 * bad_fast:.4f} %, ieee {100 * bad_ieee:.4f} %")
-    assert moved <= 0.002
-    assert bad_ieee <= 0.002 and bad_fast <= 0.002
+    within_tolerance("pixels the fast reciprocal moves beyond 1e-4 relative", moved, 1e-6)
+    within_tolerance("fast vs oracle: pixels beyond 1e-4 relative", bad_fast, 1e-4)
+    within_tolerance("ieee vs oracle: pixels beyond 1e-4 relative", bad_ieee, 1e-4)
     assert bad_ieee <= bad_fast + 1e-4
 
 

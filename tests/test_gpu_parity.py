@@ -2,8 +2,12 @@
 
 Tolerances: the FP32 state after 100 semi-implicit-Euler steps must match
 the oracle within 1e-4 m in position and 1e-4 rad in attitude (the parity
-bar of the fleet-step workload); single-step comparisons use
-abs 2e-5 + rel 2e-6, the float32 rounding of one RK4 step with margin.
+bar of the fleet-step workload). Every other bound sits 5 to 15 times above
+the error measured on its seeded case (each check records both when
+AG_TOLERANCE_REPORT is set), and never above that bar except where noted:
+one step from the same float32 state 2e-6 relative; rollouts of 60 to 100
+steps 1e-5; the 1,000-step full-size rollout 1e-4 (position, relative to
+1 + |p|) and 1e-4 rad.
 Reset draws are compared bit for bit. Collision decisions whose squared
 distance margin lies within 1e-5 m^2 of the radius are near-ties that float32
 and float64 may decide differently; they are counted and excluded.
@@ -93,8 +97,8 @@ def test_parity_position_mode_1024_quads_100_steps(within_tolerance):
     # T1: the parity bar of the 1,024-quad, 100-step workload
     within_tolerance("position [m]", dp.max(), 1e-4)
     within_tolerance("attitude [rad]", dang.max(), 1e-4)
-    within_tolerance("velocity [m/s]", dv.max(), 1e-3)
-    within_tolerance("body rate [rad/s]", dw.max(), 1e-2)
+    within_tolerance("velocity [m/s]", dv.max(), 5e-5)
+    within_tolerance("body rate [rad/s]", dw.max(), 3e-4)
     # the oracle's controller really moved the fleet towards its targets
     assert np.mean(np.abs(orc.state[0:3] - orc.targets[0:3])) < 2.0
 
@@ -116,8 +120,8 @@ def test_parity_each_mode_and_integrator(mode_mix, integ, sub, within_tolerance)
     dp, dv, dang, dw = max_state_errors(_np(fl.state()), orc.state)
     scale = 1.0 + np.max(np.abs(orc.state[0:3]), axis=0)
     # T2
-    within_tolerance("position / (1 + |p|) [m]", np.max(dp / scale), 1e-4)
-    within_tolerance("attitude [rad]", dang.max(), 2e-4)
+    within_tolerance("position / (1 + |p|) [m]", np.max(dp / scale), 1e-5)
+    within_tolerance("attitude [rad]", dang.max(), 5e-5)
 
 
 def test_parity_mixed_rotor_types_drag_and_random_bodies(within_tolerance):
@@ -127,10 +131,10 @@ def test_parity_mixed_rotor_types_drag_and_random_bodies(within_tolerance):
     O.rollout(oracle_world(w), orc, 60, n_threads=8)
     dp, dv, dang, dw = max_state_errors(_np(fl.state()), orc.state)
     # T3
-    within_tolerance("position [m]", dp.max(), 1e-4)
-    within_tolerance("attitude [rad]", dang.max(), 1e-4)
+    within_tolerance("position [m]", dp.max(), 1e-5)
+    within_tolerance("attitude [rad]", dang.max(), 1e-5)
     mot = _np(fl.motors())
-    within_tolerance("motor thrust [N]", np.max(np.abs(mot - orc.motors)), 2e-4)
+    within_tolerance("motor thrust [N]", np.max(np.abs(mot - orc.motors)), 1e-5)
 
 
 def test_wrench_mode_free_fall_and_hover_fixed_point():
@@ -317,8 +321,8 @@ def _teacher_forced_steps(w, seed, n_calls, within_tolerance, plain=False):
         worst_p = max(worst_p, float(np.max(dp / scale)))
         worst_ang = max(worst_ang, float(dang.max()))
     # T4: one step from the same float32 state
-    within_tolerance("position / (1 + |p|) per step [m]", worst_p, 2e-5)
-    within_tolerance("attitude per step [rad]", worst_ang, 2e-5)
+    within_tolerance("position / (1 + |p|) per step [m]", worst_p, 2e-6)
+    within_tolerance("attitude per step [rad]", worst_ang, 2e-6)
     return n_hits, n_ambiguous
 
 
@@ -355,8 +359,8 @@ def test_plain_and_fused_agree(within_tolerance):
     cb, ib = b.events()
     same = (_np(ca) == _np(cb)) & (_np(a.epoch()) == _np(b.epoch()))
     # T5: rare float32 near-ties may differ between the two evaluation orders
-    within_tolerance("fraction of envs whose collisions differ", 1.0 - same.mean(), 0.005)
-    within_tolerance("|fused - plain| / (1e-4 + 1e-5 |x|)", _allclose_ratio(sa[:, same], sb[:, same], 1e-4, 1e-5), 1.0)
+    within_tolerance("fraction of envs whose collisions differ", 1.0 - same.mean(), 0.002)
+    within_tolerance("|fused - plain| / (1e-5 + 1e-6 |x|)", _allclose_ratio(sa[:, same], sb[:, same], 1e-5, 1e-6), 1.0)
     a.close()
     b.close()
 
@@ -391,7 +395,7 @@ def test_one_call_of_many_steps_equals_single_step_calls(within_tolerance):
         b.step(1)
     same = _np(a.epoch()) == _np(b.epoch())
     # T6
-    within_tolerance("fraction of envs whose resets differ", 1.0 - same.mean(), 0.005)
+    within_tolerance("fraction of envs whose resets differ", 1.0 - same.mean(), 0.002)
     within_tolerance("|one call - 12 calls| / (1e-5 + 1e-6 |x|)",
                      _allclose_ratio(_np(a.state())[:, same], _np(b.state())[:, same], 1e-5, 1e-6), 1.0)
     a.close()
@@ -543,13 +547,13 @@ def test_full_size_obstacle_fleet_sampled_against_oracle(within_tolerance):
         c, _ = O.rollout(world, orc, 1, env_ids=idx)    # resets draw with the global env id
         any_hit |= c
     # T7
-    within_tolerance("fraction of sampled envs with a near-tie step", 1.0 - ok.mean(), 0.03)
+    within_tolerance("fraction of sampled envs with a near-tie step", 1.0 - ok.mean(), 0.01)
     np.testing.assert_array_equal(e1[idx][ok], orc.epoch[ok])
     np.testing.assert_array_equal(col[idx][ok], any_hit[ok])
     dp, dv, dang, dw = max_state_errors(s1[:, idx[ok]], orc.state[:, ok])
     scale = 1.0 + np.max(np.abs(orc.state[0:3, ok]), axis=0)
     within_tolerance("position / (1 + |p|) after 1,000 steps [m]", np.max(dp / scale), 1e-4)
-    within_tolerance("attitude after 1,000 steps [rad]", dang.max(), 1e-3)
+    within_tolerance("attitude after 1,000 steps [rad]", dang.max(), 1e-4)
 
 
 def test_full_size_mixed_fleet_with_reset_masks_sampled_against_oracle(within_tolerance):
@@ -592,8 +596,8 @@ def test_full_size_mixed_fleet_with_reset_masks_sampled_against_oracle(within_to
     dp, dv, dang, dw = max_state_errors(s1[:, idx], orc.state)
     # T8
     within_tolerance("position [m]", dp.max(), 1e-4)
-    within_tolerance("attitude [rad]", dang.max(), 1e-4)
-    within_tolerance("motor thrust [N]", np.max(np.abs(mot[:, idx] - orc.motors)), 2e-4)
+    within_tolerance("attitude [rad]", dang.max(), 3e-5)
+    within_tolerance("motor thrust [N]", np.max(np.abs(mot[:, idx] - orc.motors)), 1e-5)
 
 
 def test_injected_failure_is_sticky_and_the_context_still_destroys():
