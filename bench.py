@@ -46,6 +46,11 @@ WORKLOAD_TEXT = ("1,048,576 quadrotors; command mode uniform over position / bod
 # command modes, RK4 x 4 substeps + 16 boxes. tests/test_bench_constants.py
 # re-derives it.
 FLOP_PER_VEHICLE_STEP = 4588.0
+# Of which one sphere-vs-box test, per box (40 multiplications, 26 additions;
+# pinned by a hand count in tests/test_oracle_pins.py). The fused step skips
+# tests that provably cannot hit; the work it performs is counted with
+# ag_collision_tests_run.
+FLOP_PER_BOX_TEST = 66.0
 # The same count for the other lines: the mixed fleet (body velocity, SIE,
 # drag, 40 % quad / 40 % hexa / 20 % octo) and the paper shape (attitude and
 # body velocity, SIE, quads, no boxes).
@@ -282,6 +287,9 @@ def gpu_arm(args) -> dict | None:
     launch_ms = float(np.mean(per))
     achieved_tflops = w.n_envs * C * FLOP_PER_VEHICLE_STEP / (launch_ms * 1e-3) / 1e12
     _, n_reset = fl.events()
+    # collision tests the last timed call ran, of the n_envs x C the method specifies
+    tests_frac = _abi.ag_collision_tests_run(fl.ctx) / float(w.n_envs * C)
+    flop_performed = FLOP_PER_VEHICLE_STEP - w.n_obstacles * FLOP_PER_BOX_TEST * (1.0 - tests_frac)
     out = {}
     # check of the derived ALU peak: an FMA-chain kernel of the library, run
     # after the timed region on the same stream (about 0.2 s)
@@ -379,6 +387,10 @@ def gpu_arm(args) -> dict | None:
                      "traffic": TRAFFIC_BYTES_FULL_LAUNCH if full_size else None,
                      "kernel": "k_fused_step<RK4, quad>", "launch_ms": launch_ms,
                      "flop_per_vehicle_step": FLOP_PER_VEHICLE_STEP,
+                     # the same over the work the launch performed: every step's controller and
+                     # integration, and only the collision tests it ran (tests_run of n_envs x steps)
+                     "tests_run": tests_frac,
+                     "frac_performed": w.n_envs * C * flop_performed / (launch_ms * 1e-3) / 1e12 / alu_peak,
                      "peak_source": (f"derived from the device: {alu['sm_count']} SM x {alu['fp32_lanes_per_sm']} "
                                      f"FP32 lanes x 2 x {alu['max_sm_clock_khz'] / 1e3:.0f} MHz "
                                      "(MEASURED_PEAKS has no FP32 figure)"),
@@ -965,11 +977,14 @@ def compact_line(res: dict) -> dict:
                              "higher_is_better", "scaling", "vs_baseline", "dtype") if k in r}
     out["data"] = "synthetic"
     cfg = r["config"]
-    out["config"] = {"workload": (f"{cfg['n_envs']} quads,3 modes,RK4x{cfg['substeps_per_step']},"
+    nq = cfg["n_envs"]
+    out["config"] = {"workload": (f"{nq >> 20 if nq % (1 << 20) == 0 else nq}{'M' if nq % (1 << 20) == 0 else ''} "
+                                  f"quads,3 modes,RK4x{cfg['substeps_per_step']},"
                                   f"{cfg['boxes_per_env']} OBB,{cfg['steps_per_call']} steps/call"),
                      "l2": "inputs>L2"}
     rf = r["roofline"]
     out["roofline"] = {**_pick(rf, "bound", "achieved", "peak", "unit", "frac", "traffic"),
+                       "frac_performed": rf["frac_performed"],
                        "fma_chain_tflops": rf["fma_chain_check"]["packed_tflops"]}
     if "cpu_baseline" in r:
         cb = r["cpu_baseline"]
@@ -1002,8 +1017,8 @@ def compact_line(res: dict) -> dict:
         out["task"] = _pick(r["task"], "value", "hbm_frac")
     if "adjoint" in r:
         a = r["adjoint"]
-        out["adjoint"] = {"value": a["value"], "alu_record": a["alu_frac_record"],
-                          "alu_backward": a["alu_frac_backward"], "range": a["range"]}
+        out["adjoint"] = {"value": a["value"], "alu_fwd": a["alu_frac_record"], "alu_bwd": a["alu_frac_backward"],
+                          "range": a["range"]}
     head = {k: out[k] for k in list(out)[:list(out).index("range") + 1]}
     parts = {k: out[k] for k in list(out)[list(out).index("range") + 1:]}
     return {**_sig(head, 4), **_sig(parts, 3)}

@@ -200,7 +200,10 @@ ag_status ag_set_body(ag_ctx* ctx, const float* body);
  * quaternion renormalisation; after the last substep of every step the
  * vehicle sphere is tested against every box of its environment, and an
  * environment that touches one is reset in place (epoch + 1, Philox draw of
- * a new state, as ag_reset). Afterwards the collided flags mark environments
+ * a new state, as ag_reset). A vehicle's test is skipped while it has moved
+ * less from its last exact test than that test's clearance to the nearest
+ * box, minus a slack far above float32 rounding: such a test could not hit,
+ * so every decision is the one the exact test makes at every step. Afterwards the collided flags mark environments
  * that hit a box in any step of this call and the reset list holds each
  * environment reset during this call once (order unspecified).
  * AG_ERR_INVALID unless n_substeps / substeps_per_step is in 1 .. 2^31 - 1.

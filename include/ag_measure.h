@@ -63,6 +63,17 @@ ag_status ag_query_alu_peak(int device, ag_alu_peak* out);
 ag_status ag_render_depth_ieee(ag_ctx* ctx, uint32_t width, uint32_t height, float hfov, float max_range,
                                const float* cam_offset, const uint32_t* env_ids, uint32_t n_cams, float* depth);
 
+/* The number of (environment, step) collision tests the last ag_step of the
+ * context ran, into *tests (host). The method tests every environment
+ * against every box after every step (n_envs x steps); the fused step skips
+ * a test while the vehicle has moved less from its last exact test than
+ * that test's clearance to the nearest box (minus a rounding slack), which
+ * changes no decision. This count is the work a launch performed, against
+ * which its performed-work ALU fraction is stated. 0 before the first
+ * ag_step; the unfused path does not count. Synchronises the context's
+ * stream. AG_ERR_INVALID for a NULL tests. */
+ag_status ag_collision_tests_run(ag_ctx* ctx, uint64_t* tests);
+
 /* Counts the (pixel, box) pairs that ag_render_depth, with the same
  * arguments, tests after its conservative culling (a box culled for a 32 x 32
  * tile is not tested for any pixel of it), into *live_pairs (host). Renders

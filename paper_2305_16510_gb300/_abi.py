@@ -109,6 +109,7 @@ SIGNATURES = {
     "ag_inject_failure": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "ag_measure_fp32_peak": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ag_fp32_peak)]),
     "ag_query_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ag_alu_peak)]),
+    "ag_collision_tests_run": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "ag_render_depth_ieee": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
                                             ctypes.POINTER(ctypes.c_float * 3), _vp, ctypes.c_uint32, _vp]),
     "ag_depth_live_pairs": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
@@ -234,6 +235,13 @@ def ag_render_depth(ctx: int, width: int, height: int, hfov: float, max_range: f
     rc = lib().ag_render_depth(ctx, int(width), int(height), float(hfov), float(max_range),
                                ctypes.byref(off) if off is not None else None, ptr(env_ids), int(n_cams), ptr(depth))
     _check(rc, "ag_render_depth", ctx)
+
+
+def ag_collision_tests_run(ctx: int) -> int:
+    """Collision tests the last ag_step ran (include/ag_measure.h)."""
+    out = ctypes.c_uint64()
+    _check(lib().ag_collision_tests_run(ctx, ctypes.byref(out)), "ag_collision_tests_run", ctx)
+    return int(out.value)
 
 
 def ag_render_depth_ieee(ctx: int, width: int, height: int, hfov: float, max_range: float, cam_offset, env_ids,

@@ -157,7 +157,7 @@ size_t buffer_bytes(const ag_config* c) {
   size_t n = c->n_envs;
   size_t per = sizeof(float) * (13 + 8 + 4 + 4 + 4 + 4) + sizeof(uint32_t) * 4 + 3 /* modes, collided, hits */ + 1;
   return n * per + (size_t)c->n_obstacles * 10 * n * sizeof(float) +
-         agk::box_pair_elems(n, c->n_obstacles) * sizeof(float2) + sizeof(uint32_t);
+         agk::box_pair_elems(n, c->n_obstacles) * sizeof(float2) + sizeof(uint32_t) + sizeof(unsigned long long);
 }
 
 }  // namespace
@@ -176,6 +176,7 @@ agk::StepParams agk::step_params_for(const ag_config& c, uint64_t seed) {
   P.u_max = c.u_max;
   P.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
   P.seed_hi = (uint32_t)(seed >> 32);
+  P.exact_tests = 0;
   return P;
 }
 
@@ -197,6 +198,7 @@ agk::StepParams step_params(const ag_ctx* ctx) {
   P.u_max = c.u_max;
   P.seed_lo = (uint32_t)(ctx->seed & 0xFFFFFFFFu);
   P.seed_hi = (uint32_t)(ctx->seed >> 32);
+  P.exact_tests = 0;
   return P;
 }
 
@@ -242,7 +244,7 @@ void free_all(ag_ctx* ctx) {
   if (ctx->reach_steps) cudaFree(ctx->reach_steps);
   agk::FleetBuffers& f = ctx->fb;
   void* ptrs[] = {f.state, f.motors, f.body, f.modes, f.targets, f.boxes, f.epoch, f.collided, f.reset_ids,
-                  f.n_reset, f.cmd, f.wrench, f.resets, f.hits, f.order, f.boxes_slot, ctx->mask_dev,
+                  f.n_reset, f.tests_run, f.cmd, f.wrench, f.resets, f.hits, f.order, f.boxes_slot, ctx->mask_dev,
                   ctx->order_scratch, f.slot_of, (void*)f.box_rand};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -344,6 +346,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = alloc(ctx, &f.collided, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.reset_ids, n);
   if (e == cudaSuccess) e = alloc(ctx, &f.n_reset, 1);
+  if (e == cudaSuccess) e = alloc(ctx, &f.tests_run, 1);
   if (e == cudaSuccess) e = alloc(ctx, &f.cmd, 4 * n);
   if (e == cudaSuccess) e = alloc(ctx, &f.wrench, 4 * n);
   if (e == cudaSuccess) e = alloc(ctx, &f.resets, n);
@@ -377,6 +380,7 @@ ag_status ag_create(const ag_config* cfg, void* cuda_stream, ag_ctx** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(f.epoch, 0, n * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.collided, 0, n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.n_reset, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.tests_run, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = agk::launch_build_order(f, ctx->order_scratch, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {

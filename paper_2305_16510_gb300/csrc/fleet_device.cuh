@@ -76,6 +76,7 @@ struct StepParams {
   float r2;           // squared collision radius
   float u_max;
   uint32_t seed_lo, seed_hi;
+  uint32_t exact_tests;  // 1: run the collision test at every step (no clearance skip)
 };
 
 __device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }

@@ -43,6 +43,7 @@ struct FleetBuffers {
                        // in the staged form of staged_field (-c, -h, -w, 2u)
   uint32_t* slot_of;   // [n]     inverse of order (NULL when no obstacle re-draw is needed)
   const BoxRandDev* box_rand;  // [n_obs] obstacle re-draw on reset (NULL = boxes keep their poses)
+  unsigned long long* tests_run;  // [1] exact collision tests of the last fused call (NULL = not counted)
   uint32_t n, n_quad, n_hexa, n_octo, n_obs;
 };
 
@@ -80,12 +81,15 @@ inline size_t fused_smem_bytes(int n_obs, int B) {
   return pairs > 1 ? (size_t)(pairs - 1) * 10 * B * 8 : 0;
 }
 
-// Launch choices of the fused kernel. Defaults: mode-grouped order and the
+// Launch choices of the fused kernel. Defaults: mode-grouped order, the
 // block size (from 64, 128, 96, 32) with the most resident warps per SM by
-// the occupancy calculator (block = 0 here). Tuning overrides (read at each
+// the occupancy calculator (block = 0 here), and collision tests skipped
+// while a vehicle provably cannot reach a box. Tuning overrides (read at each
 // launch): AG_FUSED_ORDER=identity runs env i in slot i (the ungrouped
-// ablation), AG_FUSED_BLOCK=32..128 (multiple of 32) sets the block size.
-struct FusedTuning { bool sorted; int block; };
+// ablation), AG_FUSED_BLOCK=32..128 (multiple of 32) sets the block size,
+// AG_FUSED_SKIP=0 runs the exact test at every step (same results, the
+// reference the skip is checked against).
+struct FusedTuning { bool sorted; int block; bool skip; };
 FusedTuning fused_tuning_from_env(int n_obs);
 
 }  // namespace agk

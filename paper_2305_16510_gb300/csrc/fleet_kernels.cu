@@ -26,6 +26,15 @@ namespace {
 // Dynamic shared memory cap of the fused kernel (box staging).
 constexpr size_t kFusedSmemCap = 200 * 1024;
 
+// Tuning override (read at each launch): AG_FUSED_BOXES=smem stages every
+// thread's boxes on chip for the whole launch instead of reading them from
+// the global pair copy when a collision test runs (the ablation of that
+// choice; results are identical).
+bool fused_boxes_staged_from_env() {
+  const char* v = std::getenv("AG_FUSED_BOXES");
+  return v && std::strcmp(v, "smem") == 0;
+}
+
 // Thread slot i of the launch simulates environment order[i] (a permutation
 // that groups environments of equal rotor count and command mode, so the
 // mode branches of the controller are warp-uniform), or environment i when
@@ -40,8 +49,17 @@ constexpr size_t kFusedSmemCap = 200 * 1024;
 // and its bound of 7 blocks per SM lets a 131,072-vehicle fleet run in one
 // wave; fleets with hexa and octo rotors keep the looser bound, which
 // measured faster for them.
-template <int INTEG, bool QUAD_ONLY, bool DRAG, bool BOXES>
-__global__ void __launch_bounds__(128, BOXES ? 3 : ((QUAD_ONLY && INTEG == kIntegSIE) ? 7 : 4))
+// Where a launch's collision tests read the boxes from.
+enum : int {
+  kBoxesNone = 0,    // no obstacles
+  kBoxesStaged = 1,  // staged per thread: pair 0 in registers, the others in shared memory
+  kBoxesGlobal = 2,  // the slot-ordered pair copy in global memory, read when a test runs
+};
+
+template <int INTEG, bool QUAD_ONLY, bool DRAG, int BOXES>
+__global__ void __launch_bounds__(128, BOXES == kBoxesStaged ? 3
+                                      : BOXES == kBoxesGlobal ? 5
+                                      : ((QUAD_ONLY && INTEG == kIntegSIE) ? 7 : 4))
     k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
   extern __shared__ float4 sm_pairs[];  // [ceil(n_obs / 2) - 1][5][blockDim.x] box pairs 1..
   const int B = blockDim.x;
@@ -54,7 +72,7 @@ __global__ void __launch_bounds__(128, BOXES ? 3 : ((QUAD_ONLY && INTEG == kInte
 #pragma unroll
   for (int f = 0; f < 10; ++f) bx.r[f] = make_float2(0.f, 0.f);
   const int n_obs = (int)fb.n_obs;
-  if (BOXES && active && n_obs > 0) {
+  if (BOXES == kBoxesStaged && active && n_obs > 0) {
     const int pairs = (n_obs + 1) / 2;
     if (fb.order) {
       // the slot-ordered pair copy: coalesced 8-byte rows
@@ -83,29 +101,41 @@ __global__ void __launch_bounds__(128, BOXES ? 3 : ((QUAD_ONLY && INTEG == kInte
       }
     }
   }
-  uint32_t resets = 0;
+  uint32_t resets = 0, tests = 0;
   bool any_hit = false;
   if (active) {
     const int nrot = QUAD_ONLY ? 4 : rotor_count(fb, env);
-    if (BOXES) {
+    if (BOXES == kBoxesGlobal) {
+      GlobalBoxPairs gx{fb.boxes_slot, fb.n, slot};
       if (nrot == 4)
-        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else if (nrot == 6)
-        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else
-        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit);
+        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+    } else if (BOXES == kBoxesStaged) {
+      if (nrot == 4)
+        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+      else if (nrot == 6)
+        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+      else
+        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
     } else {
       NoBoxSource none;
       if (nrot == 4)
-        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit);
+        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else if (nrot == 6)
-        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit);
+        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else
-        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit);
+        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
     }
     fb.collided[env] = any_hit ? 1 : 0;
   }
   append_compact(resets > 0u, env, fb.reset_ids, fb.n_reset);
+  if (BOXES != kBoxesNone && fb.tests_run) {  // one atomic per warp
+    const unsigned t = __reduce_add_sync(0xFFFFFFFFu, tests);
+    if ((threadIdx.x & 31u) == 0u && t) atomicAdd(fb.tests_run, (unsigned long long)t);
+  }
 }
 
 // Grouping permutation: key = rotor-type index * 4 + mode (12 keys). Slots
@@ -291,7 +321,7 @@ __global__ void __launch_bounds__(256) k_plain_compact(FleetBuffers fb) {
   append_compact(pred, i, fb.reset_ids, fb.n_reset);
 }
 
-template <int INTEG, bool QUAD_ONLY, bool DRAG, bool BOXES>
+template <int INTEG, bool QUAD_ONLY, bool DRAG, int BOXES>
 cudaError_t launch_fused_b(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
                            cudaStream_t st) {
   const auto kernel = k_fused_step<INTEG, QUAD_ONLY, DRAG, BOXES>;
@@ -309,7 +339,7 @@ cudaError_t launch_fused_b(const FleetBuffers& fb, const StepParams& P, int n_st
   if (B == 0) {  // the block size with the most resident warps per SM (ties: the earlier candidate)
     int best = -1;
     for (int b : {64, 128, 96, 32}) {
-      const size_t sm = fused_smem_bytes((int)fb.n_obs, b);
+      const size_t sm = BOXES == kBoxesStaged ? fused_smem_bytes((int)fb.n_obs, b) : 0;
       if (sm > kFusedSmemCap) continue;
       int blocks = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, b, sm);
@@ -318,7 +348,7 @@ cudaError_t launch_fused_b(const FleetBuffers& fb, const StepParams& P, int n_st
     }
     if (best <= 0) return cudaErrorInvalidConfiguration;
   }
-  const size_t smem = fused_smem_bytes((int)fb.n_obs, B);
+  const size_t smem = BOXES == kBoxesStaged ? fused_smem_bytes((int)fb.n_obs, B) : 0;
   const unsigned grid = (fb.n + B - 1) / B;
   kernel<<<grid, B, smem, st>>>(fb, P, n_steps, substeps);
   return cudaGetLastError();
@@ -327,8 +357,11 @@ cudaError_t launch_fused_b(const FleetBuffers& fb, const StepParams& P, int n_st
 template <int INTEG, bool QUAD_ONLY, bool DRAG>
 cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_steps, int substeps, int B,
                            cudaStream_t st) {
-  return fb.n_obs > 0 ? launch_fused_b<INTEG, QUAD_ONLY, DRAG, true>(fb, P, n_steps, substeps, B, st)
-                      : launch_fused_b<INTEG, QUAD_ONLY, DRAG, false>(fb, P, n_steps, substeps, B, st);
+  if (fb.n_obs == 0) return launch_fused_b<INTEG, QUAD_ONLY, DRAG, kBoxesNone>(fb, P, n_steps, substeps, B, st);
+  // the global pair copy is in slot order: it serves the grouped order only
+  if (fb.order && fb.boxes_slot && !P.exact_tests && !fused_boxes_staged_from_env())
+    return launch_fused_b<INTEG, QUAD_ONLY, DRAG, kBoxesGlobal>(fb, P, n_steps, substeps, B, st);
+  return launch_fused_b<INTEG, QUAD_ONLY, DRAG, kBoxesStaged>(fb, P, n_steps, substeps, B, st);
 }
 
 template <int INTEG>
@@ -349,7 +382,9 @@ FusedTuning fused_tuning_from_env(int n_obs) {
   FusedTuning t;
   t.sorted = true;
   t.block = 0;
+  t.skip = true;
   if (const char* v = std::getenv("AG_FUSED_ORDER")) t.sorted = std::strcmp(v, "identity") != 0;
+  if (const char* v = std::getenv("AG_FUSED_SKIP")) t.skip = std::strcmp(v, "0") != 0;
   if (const char* v = std::getenv("AG_FUSED_BLOCK")) {
     int b = std::atoi(v);
     if (b >= 32 && b <= 128 && b % 32 == 0 && fused_smem_bytes(n_obs, b) <= kFusedSmemCap) t.block = b;
@@ -360,12 +395,15 @@ FusedTuning fused_tuning_from_env(int n_obs) {
 cudaError_t launch_fused_step(const FleetBuffers& fb_in, const StepParams& P, int integrator, int n_steps,
                               int substeps, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(fb_in.n_reset, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess && fb_in.tests_run) e = cudaMemsetAsync(fb_in.tests_run, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   const FusedTuning t = fused_tuning_from_env((int)fb_in.n_obs);
   FleetBuffers fb = fb_in;
   if (!t.sorted) fb.order = nullptr;
-  return integrator == kIntegRK4 ? launch_fused_i<kIntegRK4>(fb, P, n_steps, substeps, t.block, st)
-                                 : launch_fused_i<kIntegSIE>(fb, P, n_steps, substeps, t.block, st);
+  StepParams Pl = P;
+  if (!t.skip) Pl.exact_tests = 1;
+  return integrator == kIntegRK4 ? launch_fused_i<kIntegRK4>(fb, Pl, n_steps, substeps, t.block, st)
+                                 : launch_fused_i<kIntegSIE>(fb, Pl, n_steps, substeps, t.block, st);
 }
 
 cudaError_t launch_build_order(const FleetBuffers& fb, uint32_t* scratch, cudaStream_t st) {

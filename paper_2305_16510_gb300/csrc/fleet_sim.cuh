@@ -75,9 +75,10 @@ __device__ __forceinline__ void append_compact(bool pred, uint32_t env, uint32_t
   if (pred) ids[base + __popc(mask & ((1u << lane) - 1u))] = env;
 }
 
-// Box sources of the per-vehicle loop; any_hit(p, r2, n_obs) runs the
-// sphere-vs-box test against all boxes of the environment, staged() is the
-// copy a re-draw updates and reload() re-reads what a re-draw changed.
+// Box sources of the per-vehicle loop; any_hit_min(p, r2, n_obs, m) runs the
+// sphere-vs-box test against all boxes of the environment and leaves the
+// smallest squared distance to a box in m, staged() is the copy a re-draw
+// updates and reload() re-reads what a re-draw changed.
 //
 // Boxes are handled in pairs (field f of boxes 2j and 2j+1 side by side), so
 // one 8-byte load fetches a field of two boxes and the test runs on both at
@@ -106,9 +107,10 @@ __device__ __forceinline__ float staged_field(int f, float v) { return f >= 7 ? 
 // d = R_b^T v = v - w t + u x t is computed as (v - w t) + 1/2 ((2u) x t);
 // negation, doubling and halving are exact, so d rounds as the plain form
 // would.
-__device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float r2, float2 ncx, float2 ncy,
-                                          float2 ncz, float2 nhx, float2 nhy, float2 nhz, float2 nqw, float2 ux2,
-                                          float2 uy2, float2 uz2) {
+// Returns the squared distances from p to the two boxes.
+__device__ __forceinline__ float2 pair_dist2(float2 px, float2 py, float2 pz, float2 ncx, float2 ncy, float2 ncz,
+                                             float2 nhx, float2 nhy, float2 nhz, float2 nqw, float2 ux2, float2 uy2,
+                                             float2 uz2) {
   const float2 vx = add2(px, ncx), vy = add2(py, ncy), vz = add2(pz, ncz);
   const float2 tx = fma2(uy2, vz, neg2(mul2(uz2, vy)));
   const float2 ty = fma2(uz2, vx, neg2(mul2(ux2, vz)));
@@ -124,7 +126,24 @@ __device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float
   const float2 mx = make_float2(fmaxf(ex.x, 0.f), fmaxf(ex.y, 0.f));
   const float2 my = make_float2(fmaxf(ey.x, 0.f), fmaxf(ey.y, 0.f));
   const float2 mz = make_float2(fmaxf(ez.x, 0.f), fmaxf(ez.y, 0.f));
-  const float2 e2 = fma2(mz, mz, fma2(my, my, mul2(mx, mx)));
+  return fma2(mz, mz, fma2(my, my, mul2(mx, mx)));
+}
+
+// Sphere (squared radius r2, centre p) against two boxes at once: touching
+// counts.
+__device__ __forceinline__ bool pair_hits(float2 px, float2 py, float2 pz, float r2, float2 ncx, float2 ncy,
+                                          float2 ncz, float2 nhx, float2 nhy, float2 nhz, float2 nqw, float2 ux2,
+                                          float2 uy2, float2 uz2) {
+  const float2 e2 = pair_dist2(px, py, pz, ncx, ncy, ncz, nhx, nhy, nhz, nqw, ux2, uy2, uz2);
+  return !(r2 < e2.x) | !(r2 < e2.y);
+}
+
+// The pair test that also lowers m to the smaller squared distance.
+__device__ __forceinline__ bool pair_hits_min(float2 px, float2 py, float2 pz, float r2, float2 ncx, float2 ncy,
+                                              float2 ncz, float2 nhx, float2 nhy, float2 nhz, float2 nqw, float2 ux2,
+                                              float2 uy2, float2 uz2, float& m) {
+  const float2 e2 = pair_dist2(px, py, pz, ncx, ncy, ncz, nhx, nhy, nhz, nqw, ux2, uy2, uz2);
+  m = fminf(m, fminf(e2.x, e2.y));
   return !(r2 < e2.x) | !(r2 < e2.y);
 }
 
@@ -139,18 +158,20 @@ struct RegSmemBoxPairs {
   float2 r[10];  // pair 0, fields 0..9
   float4* sm;    // this thread's column of pairs 1..: element ((j - 1) * 5 + f / 2) * B
   int B;
-  __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
+  // Any box within r of p; m receives the smallest squared distance to a box.
+  __device__ __forceinline__ bool any_hit_min(V3 p, float r2, int n_obs, float& m) const {
     const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
-    bool hit = pair_hits(px, py, pz, r2, r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7], r[8], r[9]);
+    m = __int_as_float(0x7f800000);
+    bool hit = pair_hits_min(px, py, pz, r2, r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7], r[8], r[9], m);
     const int pairs = (n_obs + 1) >> 1;
 #pragma unroll 2
     for (int j = 1; j < pairs; ++j) {
       const float4* f = sm + (size_t)(j - 1) * 5 * B;
       const float4 f01 = f[0], f23 = f[B], f45 = f[2 * B], f67 = f[3 * B], f89 = f[4 * B];
-      hit |= pair_hits(px, py, pz, r2, make_float2(f01.x, f01.y), make_float2(f01.z, f01.w),
-                       make_float2(f23.x, f23.y), make_float2(f23.z, f23.w), make_float2(f45.x, f45.y),
-                       make_float2(f45.z, f45.w), make_float2(f67.x, f67.y), make_float2(f67.z, f67.w),
-                       make_float2(f89.x, f89.y), make_float2(f89.z, f89.w));
+      hit |= pair_hits_min(px, py, pz, r2, make_float2(f01.x, f01.y), make_float2(f01.z, f01.w),
+                           make_float2(f23.x, f23.y), make_float2(f23.z, f23.w), make_float2(f45.x, f45.y),
+                           make_float2(f45.z, f45.w), make_float2(f67.x, f67.y), make_float2(f67.z, f67.w),
+                           make_float2(f89.x, f89.y), make_float2(f89.z, f89.w), m);
     }
     return hit;
   }
@@ -184,7 +205,10 @@ struct NoBoxes {
 
 // No boxes at all (a fleet without obstacles): nothing to test or re-load.
 struct NoBoxSource {
-  __device__ __forceinline__ bool any_hit(V3, float, int) const { return false; }
+  __device__ __forceinline__ bool any_hit_min(V3, float, int, float& m) const {
+    m = __int_as_float(0x7f800000);
+    return false;
+  }
   __device__ __forceinline__ NoBoxes staged() const { return {}; }
   __device__ __forceinline__ void reload(const FleetBuffers&, uint32_t) {}
 };
@@ -199,15 +223,16 @@ struct GlobalBoxPairs {
   __device__ __forceinline__ NoBoxes staged() const { return {}; }
   __device__ __forceinline__ void reload(const FleetBuffers&, uint32_t) {}
   __device__ __forceinline__ float2 at(int r) const { return __ldg(rows + (size_t)r * n + idx); }
-  __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
+  __device__ __forceinline__ bool any_hit_min(V3 p, float r2, int n_obs, float& m) const {
     const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
     bool hit = false;
+    m = __int_as_float(0x7f800000);
     const int pairs = (n_obs + 1) >> 1;
 #pragma unroll 2
     for (int j = 0; j < pairs; ++j) {
       const int r = j * 10;
-      hit |= pair_hits(px, py, pz, r2, at(r), at(r + 1), at(r + 2), at(r + 3), at(r + 4), at(r + 5), at(r + 6),
-                       at(r + 7), at(r + 8), at(r + 9));
+      hit |= pair_hits_min(px, py, pz, r2, at(r), at(r + 1), at(r + 2), at(r + 3), at(r + 4), at(r + 5), at(r + 6),
+                           at(r + 7), at(r + 8), at(r + 9), m);
     }
     return hit;
   }
@@ -260,13 +285,28 @@ __device__ __forceinline__ void reset_env(const FleetBuffers& fb, uint32_t env, 
   if (fb.box_rand) redraw_boxes(fb, env, fb.slot_of ? fb.slot_of[env] : env, epoch, seed_lo, seed_hi, NoBoxes{});
 }
 
+// How far a vehicle may move from p, where the exact test found min_e2 as
+// its smallest squared distance to a box, before the sphere of radius r could
+// touch one; returned squared, or -1 when it must be tested again at once.
+// The distance to a box is 1-Lipschitz in the position, so as long as
+// |p' - p| < sqrt(min_e2) - r - slack no box is within r of p'. The slack
+// (1 mm plus 1e-5 of the magnitudes involved) is far above the float32
+// rounding of the test, so a skipped test is one the exact float32 test
+// would also have found clear: every collision decision is the exact test's.
+__device__ __forceinline__ float clearance_threshold2(V3 p, float min_e2, float r) {
+  const float c = sqrtf(min_e2) - r;
+  const float slack = 1e-3f + 1e-5f * (fabsf(c) + fabsf(p.x) + fabsf(p.y) + fabsf(p.z));
+  const float t = c - slack;
+  return t > 0.f ? t * t : -1.f;
+}
+
 // simulate() with the command given (cm) instead of read from fb; returns
 // the final state, which it also stores.
 template <int NROT, int INTEG, bool DRAG, class Boxes>
 __device__ __forceinline__ VState simulate_cmd(const FleetBuffers& fb, const StepParams& P, uint32_t env,
                                                uint32_t slot, const Command& cm, int n_steps, int substeps, int n_obs,
                                                Boxes& boxes, uint32_t seed_lo, uint32_t seed_hi, uint32_t& resets,
-                                               bool& any_hit) {
+                                               bool& any_hit, uint32_t& tests) {
   const uint32_t n = fb.n;
   VState s = load_state(fb.state, n, env);
   normalize(s.q);
@@ -275,6 +315,13 @@ __device__ __forceinline__ VState simulate_cmd(const FleetBuffers& fb, const Ste
   for (int k = 0; k < NROT; ++k) u[k] = fb.motors[k * n + env];
   const Body b = load_body(fb.body, n, env);
   uint32_t epoch = fb.epoch[env];
+  // Collision tests that cannot hit are skipped (see clearance_threshold2):
+  // p_test is the position of the last exact test, thr2 the squared distance
+  // the vehicle may move from there before it could touch a box (-1: test
+  // at the next step).
+  V3 p_test = {0.f, 0.f, 0.f};
+  float thr2 = -1.f;
+  const float r = sqrtf(P.r2);
   for (int step = 0; step < n_steps; ++step) {
     for (int ss = 0; ss < substeps; ++ss) {
       V3 b3;
@@ -282,15 +329,23 @@ __device__ __forceinline__ VState simulate_cmd(const FleetBuffers& fb, const Ste
       integrate<INTEG, DRAG>(s, b3, W, b, P);
     }
     if (n_obs > 0) {
-      const bool hit = boxes.any_hit(s.p, P.r2, n_obs);
-      if (hit) {
-        any_hit = true;
-        resets += 1;
-        epoch += 1;
-        reset_in_registers<NROT>(s, u, b.m, env, epoch, seed_lo, seed_hi);
-        if (fb.box_rand) {
-          redraw_boxes(fb, env, slot, epoch, seed_lo, seed_hi, boxes.staged());
-          boxes.reload(fb, env);
+      const V3 dp = s.p - p_test;
+      if (!(dot(dp, dp) < thr2)) {
+        float min_e2;
+        const bool hit = boxes.any_hit_min(s.p, P.r2, n_obs, min_e2);
+        tests += 1;
+        p_test = s.p;
+        thr2 = P.exact_tests ? -1.f : clearance_threshold2(s.p, min_e2, r);
+        if (hit) {
+          any_hit = true;
+          resets += 1;
+          epoch += 1;
+          reset_in_registers<NROT>(s, u, b.m, env, epoch, seed_lo, seed_hi);
+          thr2 = -1.f;
+          if (fb.box_rand) {
+            redraw_boxes(fb, env, slot, epoch, seed_lo, seed_hi, boxes.staged());
+            boxes.reload(fb, env);
+          }
         }
       }
     }
@@ -305,9 +360,9 @@ __device__ __forceinline__ VState simulate_cmd(const FleetBuffers& fb, const Ste
 template <int NROT, int INTEG, bool DRAG, class Boxes>
 __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, uint32_t slot,
                                          int n_steps, int substeps, int n_obs, Boxes& boxes, uint32_t seed_lo,
-                                         uint32_t seed_hi, uint32_t& resets, bool& any_hit) {
+                                         uint32_t seed_hi, uint32_t& resets, bool& any_hit, uint32_t& tests) {
   simulate_cmd<NROT, INTEG, DRAG>(fb, P, env, slot, load_command(fb, env), n_steps, substeps, n_obs, boxes, seed_lo,
-                                  seed_hi, resets, any_hit);
+                                  seed_hi, resets, any_hit, tests);
 }
 
 }  // namespace agk

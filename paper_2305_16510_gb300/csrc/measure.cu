@@ -120,3 +120,15 @@ extern "C" ag_status ag_query_alu_peak(int device, ag_alu_peak* out) {
   out->tflops = (double)sms * out->fp32_lanes_per_sm * 2.0 * (double)khz * 1e3 / 1e12;
   return AG_OK;
 }
+
+extern "C" ag_status ag_collision_tests_run(ag_ctx* ctx, uint64_t* tests) {
+  ag_status s = agh::enter(ctx);
+  if (s != AG_OK) return s;
+  if (!tests) return agh::fail_invalid(ctx, "ag_collision_tests_run: tests is NULL");
+  unsigned long long v = 0;
+  s = agh::check_cuda(ctx, cudaMemcpyAsync(&v, ctx->fb.tests_run, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream),
+                      "copy test count");
+  if (s == AG_OK) s = agh::check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "synchronize");
+  if (s == AG_OK) *tests = (uint64_t)v;
+  return s;
+}

@@ -70,10 +70,10 @@ __global__ void __launch_bounds__(kServeBlock) k_serve_step(const ServeDesc* __r
   if (slot >= d.fb.n || d.steps <= 0) return;
   const uint32_t env = d.fb.order[slot];
   GlobalBoxPairs bx{d.fb.boxes_slot, d.fb.n, slot};
-  uint32_t resets = 0;
+  uint32_t resets = 0, tests = 0;
   bool hit = false;
   simulate<4, INTEG, DRAG>(d.fb, P, env, slot, d.steps, substeps, (int)d.fb.n_obs, bx, d.seed_lo, d.seed_hi, resets,
-                           hit);
+                           hit, tests);
 }
 
 // First-fit allocator over [0, size) with coalescing frees (host bookkeeping

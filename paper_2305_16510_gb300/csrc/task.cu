@@ -50,13 +50,14 @@ struct EnvBoxPairs {
     return make_float2(staged_field(f, boxes[((size_t)k0 * 10 + f) * n + env]),
                        staged_field(f, k1 < n_obs ? boxes[((size_t)k1 * 10 + f) * n + env] : box_pad_field(f)));
   }
-  __device__ __forceinline__ bool any_hit(V3 p, float r2, int n_obs) const {
+  __device__ __forceinline__ bool any_hit_min(V3 p, float r2, int n_obs, float& m) const {
     const float2 px = dup2(p.x), py = dup2(p.y), pz = dup2(p.z);
     bool hit = false;
+    m = __int_as_float(0x7f800000);
     for (int j = 0; j < (n_obs + 1) >> 1; ++j)
-      hit |= pair_hits(px, py, pz, r2, at(j, 0, n_obs), at(j, 1, n_obs), at(j, 2, n_obs), at(j, 3, n_obs),
-                       at(j, 4, n_obs), at(j, 5, n_obs), at(j, 6, n_obs), at(j, 7, n_obs), at(j, 8, n_obs),
-                       at(j, 9, n_obs));
+      hit |= pair_hits_min(px, py, pz, r2, at(j, 0, n_obs), at(j, 1, n_obs), at(j, 2, n_obs), at(j, 3, n_obs),
+                           at(j, 4, n_obs), at(j, 5, n_obs), at(j, 6, n_obs), at(j, 7, n_obs), at(j, 8, n_obs),
+                           at(j, 9, n_obs), m);
     return hit;
   }
   __device__ __forceinline__ NoBoxes staged() const { return {}; }
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kTaskBlock, BOXES ? 384 / kTaskBlock : 1024 / 
   const FleetBuffers& fb = a.fb;
   const uint32_t i = blockIdx.x * kTaskBlock + threadIdx.x;
   const uint32_t n = fb.n;
-  uint32_t resets = 0;
+  uint32_t resets = 0, tests = 0;
   if (i < n) {
     // everything the step reads from memory, requested up front
     const float4 act = reinterpret_cast<const float4*>(a.actions)[i];
@@ -132,19 +133,19 @@ __global__ void __launch_bounds__(kTaskBlock, BOXES ? 384 / kTaskBlock : 1024 / 
     if (BOXES) {
       EnvBoxPairs bx{fb.boxes, n, i};
       if (nrot == 4)
-        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit, tests);
       else if (nrot == 6)
-        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit, tests);
       else
-        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, n_obs, bx, a.seed_lo, a.seed_hi, resets, hit, tests);
     } else {
       NoBoxSource none;
       if (nrot == 4)
-        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<4, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit, tests);
       else if (nrot == 6)
-        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<6, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit, tests);
       else
-        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit);
+        s = simulate_cmd<8, INTEG, DRAG>(fb, P, i, slot, cm, 1, substeps, 0, none, a.seed_lo, a.seed_hi, resets, hit, tests);
     }
     fb.collided[i] = hit ? 1 : 0;
 #pragma unroll

@@ -20,6 +20,12 @@ def test_flop_per_vehicle_step_matches_oracle_count():
     assert abs(sum(tot) / len(tot) - bench.FLOP_PER_VEHICLE_STEP) < 1.0
 
 
+def test_box_test_flop_matches_oracle_count():
+    world = O.World(n_envs=1)
+    c0, c1 = O.count_ops(world, W.MODE_WRENCH, 0), O.count_ops(world, W.MODE_WRENCH, 1)
+    assert _tot(c1) - _tot(c0) == bench.FLOP_PER_BOX_TEST
+
+
 def test_alu_peak_from_device_attributes():
     info = {"sm_count": 152, "fp32_lanes_per_sm": 128, "max_sm_clock_khz": 2070000}
     assert abs(bench.alu_peak_tflops(info) - 152 * 128 * 2 * 2.070e9 / 1e12) < 1e-9
@@ -66,6 +72,7 @@ def _full_result():
                        "parallelism": "replicas x1"},
             "roofline": {"bound": "alu", "achieved": 63.005529, "peak": 80.54784, "unit": "TFLOP/s",
                          "frac": 0.78221252, "traffic": 865260000.0, "kernel": "k", "launch_ms": 76.3,
+                         "frac_performed": 0.81234567, "tests_run": 0.04123456,
                          "fma_chain_check": {"packed_tflops": 80.312345, "scalar_tflops": 78.5}},
             "cpu_baseline": {"value": 11817509.8, "unit": bench.UNIT, "cores": 16, "kind": "oracle",
                              "sample": "8192 envs x 15370 steps of the same workload (10.7 s, FP64, 16 threads)",
@@ -100,7 +107,7 @@ def test_compact_line_is_valid_json_short_and_carries_every_part():
     assert d["serving"]["batched"]["p99_ms"] and d["serving"]["one_per_launch"]["p99_ms"]
     assert d["serving"]["capacity"]["batched"] == 400
     assert d["mixed"]["alu_frac"] and d["paper_shape"]["alu_frac"] and d["roofline"]["fma_chain_tflops"]
-    assert d["adjoint"]["alu_backward"] and d["depth"]["alu_frac"]
+    assert d["adjoint"]["alu_bwd"] and d["depth"]["alu_frac"] and d["roofline"]["frac_performed"]
     assert abs(d["value"] - 1.3732214e10) / 1.3732214e10 < 1e-3
 
 

@@ -365,6 +365,39 @@ def test_plain_and_fused_agree(within_tolerance):
     b.close()
 
 
+def test_skipped_collision_tests_change_no_decision(monkeypatch):
+    """The fused step skips a vehicle's collision test while the distance it
+    has moved since its last exact test stays below that test's clearance
+    (minus a rounding slack). AG_FUSED_SKIP=0 runs the exact test at every
+    step instead; both runs must agree bit for bit. The boxes are packed
+    closer than in the bench recipe (centres U[-2.5, 2.5]^3) so that vehicles
+    pass near them often, and one call runs 300 steps so the skip is in
+    force for long stretches."""
+    w = W.scaled(W.WORKLOADS["obstacles"], 8192)
+    inp = W.make_inputs(w, 44)
+    boxes = inp.boxes.copy()
+    boxes[:, 0:3] = np.random.default_rng(45).uniform(-2.5, 2.5, (w.n_obstacles, 3, w.n_envs)).astype(np.float32)
+    inp = W.Inputs(inp.modes, inp.targets, inp.body, boxes)
+    out, tests = [], []
+    for skip in ("1", "0"):
+        monkeypatch.setenv("AG_FUSED_SKIP", skip)
+        fl = gpu_fleet(w, inp, 44)
+        fl.reset(None, 44)
+        fl.step(300)
+        col, ids = fl.events()
+        out.append((_np(fl.state()), _np(fl.motors()), _np(fl.epoch()), _np(col), np.sort(_np(ids))))
+        tests.append(_abi.ag_collision_tests_run(fl.ctx))
+        fl.close()
+    monkeypatch.delenv("AG_FUSED_SKIP")
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
+    # the exact run tests every environment after every step; the default run skips most tests
+    assert tests[1] == w.n_envs * 300
+    assert 0 < tests[0] < 0.8 * tests[1]
+    assert (out[0][2].astype(np.int64) - 1).sum() > 500   # hundreds of collision resets after the first draw
+    assert out[0][3].mean() > 0.02
+
+
 def test_max_obstacles_and_single_env():
     for n, n_obs in ((1, 3), (77, 64)):
         w = W.Workload("maxobs", n, 2, 1, n_obs, n, 0, 0, mode_mix=(W.MODE_POSITION, W.MODE_ATT_THRUST))
