@@ -12,19 +12,20 @@
 // the optical axis because d has a unit forward component; max_range when
 // nothing is closer.
 //
-// A block of 256 threads renders up to eight 32 x 32 tiles of one camera's
-// image in turn, four pixels per thread (column tx, rows ty, ty + 8, ty + 16,
-// ty + 24: each warp stores 32 consecutive pixels of a row). Once per block it
+// A block of 128 threads renders up to eight 32 x 32 tiles of one camera's
+// image in turn, eight pixels per thread (column tx, rows ty, ty + 4, ...,
+// ty + 28: each warp stores 32 consecutive pixels of a row). Once per block it
 // turns each box into one 16-float record in shared memory: M = R_b^T R (the
 // camera's axes in the box frame) and the slab bounds lo = -h - o_b,
 // hi = h - o_b (o_b the camera origin in the box frame). Per pixel and box
 // the ray's box-frame direction is then M (1, dy, dz) (six FMAs), followed by
 // three reciprocals and the slab intervals; records are read as four
-// broadcast 16-byte loads and reused for the thread's four pixels.
+// broadcast 16-byte loads and reused for the thread's eight pixels.
 //
-// Once per block, warp w culls for the block's tile w, conservatively, the
-// boxes that no ray of the tile can reach closer than max_range, and lists
-// the live ones (ballot and popc), so the tile's loop visits only those. A
+// Once per block, warp w culls for the block's tiles w and w + 4,
+// conservatively, the boxes that no ray of the tile can reach closer than
+// max_range, and lists the live ones (ballot and popc), so the tile's loop
+// visits only those. A
 // box is culled when its bounding sphere (centre
 // s in the camera frame, radius |h| with a rounding margin) lies beyond
 // max_range along the axis, behind the camera, or outside one of the four
@@ -47,9 +48,9 @@ namespace agk {
 namespace {
 
 constexpr int kDepthTile = 32;                           // tile edge in pixels
-constexpr int kDepthThreads = 256;
-constexpr int kDepthPix = kDepthTile * kDepthTile / kDepthThreads;  // pixels per thread: 4
-constexpr int kDepthRows = kDepthThreads / kDepthTile;             // rows between a thread's pixels: 8
+constexpr int kDepthThreads = 128;
+constexpr int kDepthPix = kDepthTile * kDepthTile / kDepthThreads;  // pixels per thread: 8
+constexpr int kDepthRows = kDepthThreads / kDepthTile;             // rows between a thread's pixels: 4
 constexpr int kDepthTilesPerBlock = 8;                             // tiles of one camera per block
 
 struct CamPose {
@@ -198,10 +199,11 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
     }
   }
   __syncthreads();
-  // ... then warp w culls the boxes for tile w of the block and lists the live ones
-  static_assert(kDepthThreads / 32 == kDepthTilesPerBlock, "one warp per tile");
-  {
-    const uint32_t w = threadIdx.x / 32, lane = threadIdx.x % 32, t = t_begin + w;
+  // ... then warp w culls the boxes for tiles w, w + 4, ... of the block and lists the live ones
+  constexpr uint32_t kWarps = kDepthThreads / 32;
+  static_assert(kDepthTilesPerBlock % kWarps == 0, "whole tiles per warp");
+  for (uint32_t w = threadIdx.x / 32; w < (uint32_t)kDepthTilesPerBlock; w += kWarps) {
+    const uint32_t lane = threadIdx.x % 32, t = t_begin + w;
     if (t < t_end) {
       const uint32_t x0 = (t % tiles_x) * kDepthTile, y0 = (t / tiles_x) * kDepthTile;
       const uint32_t x1 = min(x0 + kDepthTile, a.width) - 1, y1 = min(y0 + kDepthTile, a.height) - 1;
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(kDepthThreads) k_render_depth(DepthArgs a) {
       const int k = live_k[tl][j];
       const uint8_t flags = live_f[tl][j];
       const float4 r0 = recs[4 * k], r1 = recs[4 * k + 1], r2 = recs[4 * k + 2], r3 = recs[4 * k + 3];
-      // the column's part of M (1, dy, dz), shared by the thread's four pixels
+      // the column's part of M (1, dy, dz), shared by the thread's eight pixels
       const float cx = fmaf(dy, r0.y, r0.x), cy = fmaf(dy, r1.x, r0.w), cz = fmaf(dy, r1.w, r1.z);
       if (flags & kFixedSigns) {
         // slab bounds lo = (r2.y, r2.z, r2.w), hi = (r3.x, r3.y, r3.z): near is lo for a positive
