@@ -4,11 +4,11 @@
 // Fused step (the hot path): one thread owns one environment for a whole
 // launch of n_steps steps. Its 13 state words, motor thrusts, body
 // parameters and command live in registers across every substep; its boxes
-// are staged once per launch in shared memory in a [box][field][thread]
-// layout, so a warp reading one field of one box touches 32 consecutive
-// words (no bank conflicts); global memory is touched only at the start and
-// the end of the launch (coalesced structure-of-arrays rows). Collision
-// resets happen in registers; the reset list is built with one
+// are read only when a collision test runs (the first step, then only while
+// the vehicle may be within reach of a box), as coalesced rows of the
+// slot-ordered pair copy; state and command are read at the start and
+// written at the end of the launch (coalesced structure-of-arrays rows).
+// Collision resets happen in registers; the reset list is built with one
 // __ballot_sync + __popc prefix and one atomicAdd per warp.
 #include <atomic>
 #include <cstdint>
@@ -35,20 +35,6 @@ bool fused_boxes_staged_from_env() {
   return v && std::strcmp(v, "smem") == 0;
 }
 
-// Thread slot i of the launch simulates environment order[i] (a permutation
-// that groups environments of equal rotor count and command mode, so the
-// mode branches of the controller are warp-uniform), or environment i when
-// order is NULL. Each thread stages its environment's boxes once per launch:
-// boxes 0 and 1 in registers, the others in shared memory as float4
-// [pair][field pair][thread], so a warp's 16-byte loads of two fields are
-// consecutive and conflict-free. A thread reads only what it wrote, so no
-// barrier is needed.
-// BOXES = false (no obstacles) keeps the kernel within 128 registers, so
-// more warps are resident when there is no staging to pay for. A quad-only
-// semi-implicit-Euler fleet without obstacles needs about 70 (no spills),
-// and its bound of 7 blocks per SM lets a 131,072-vehicle fleet run in one
-// wave; fleets with hexa and octo rotors keep the looser bound, which
-// measured faster for them.
 // Where a launch's collision tests read the boxes from.
 enum : int {
   kBoxesNone = 0,    // no obstacles
@@ -56,6 +42,23 @@ enum : int {
   kBoxesGlobal = 2,  // the slot-ordered pair copy in global memory, read when a test runs
 };
 
+// Thread slot i of the launch simulates environment order[i] (a permutation
+// that groups environments of equal rotor count and command mode, so the
+// mode branches of the controller are warp-uniform), or environment i when
+// order is NULL. A collision test that cannot hit is skipped (simulate_cmd),
+// so tests are rare after the first step; by default a test reads the
+// environment's box pairs from the slot-ordered copy in global memory, which
+// needs no shared memory and leaves the kernel at 96 registers (5 blocks of
+// 128 threads per SM). The staged form keeps each thread's boxes on chip for
+// the launch instead: boxes 0 and 1 in registers, the others in shared memory
+// as float4 [pair][field pair][thread], so a warp's 16-byte loads of two
+// fields are consecutive and conflict-free (a thread reads only what it
+// wrote, so no barrier is needed).
+// Without obstacles the kernel stays within 128 registers. A quad-only
+// semi-implicit-Euler fleet without obstacles needs about 70 (no spills),
+// and its bound of 7 blocks per SM lets a 131,072-vehicle fleet run in one
+// wave; fleets with hexa and octo rotors keep the looser bound, which
+// measured faster for them.
 template <int INTEG, bool QUAD_ONLY, bool DRAG, int BOXES>
 __global__ void __launch_bounds__(128, BOXES == kBoxesStaged ? 3
                                       : BOXES == kBoxesGlobal ? 5
