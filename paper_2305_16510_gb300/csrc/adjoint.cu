@@ -720,12 +720,16 @@ __device__ __forceinline__ void adjoint_mode(const AdjointBuffers& ab, const Ste
   }
 }
 
-// One warp per block and at most 144 registers: 14 warps fit on an SM, so a
-// 65,536-vehicle fleet (2,048 warps) is resident in one wave on 152 SMs, and
-// single-warp blocks spread the warps evenly (13 or 14 per SM).
+// One warp per block and at most 128 registers. Each SM sub-partition holds a
+// quarter of the register file: 128 registers fit four warps per
+// sub-partition, 16 per SM, so a 65,536-vehicle fleet (2,048 warps) is
+// resident in one wave on 152 SMs, and single-warp blocks spread the warps
+// evenly (13 or 14 per SM). The sweep wants about 168 registers, and the cap
+// spills about 1.3 KB per thread; at 144 registers (12 warps per SM) the
+// fleet needed 1.12 waves, which cost more than the spills do.
 constexpr int kAdjointBlock = 32;
 template <bool FULL_TAPE>
-__global__ void __maxnreg__(144) k_adjoint(AdjointBuffers ab, StepParams P) {
+__global__ void __maxnreg__(128) k_adjoint(AdjointBuffers ab, StepParams P) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ab.n) return;
   const int nr = rotors_of(ab, i);
