@@ -48,9 +48,12 @@ enum : int {
 // order is NULL. A collision test that cannot hit is skipped (simulate_cmd),
 // so tests are rare after the first step; by default a test reads the
 // environment's box pairs from the slot-ordered copy in global memory, which
-// needs no shared memory and leaves the kernel at 96 registers (5 blocks of
-// 128 threads per SM). The staged form keeps each thread's boxes on chip for
-// the launch instead: boxes 0 and 1 in registers, the others in shared memory
+// needs no shared memory. Its bound of 3 blocks of 128 threads per SM leads
+// the compiler to 126 registers, which still fit 4 warps per SM
+// sub-partition (16 per SM); bounds of 4 and 5 blocks (105 and 96
+// registers) and of 1 or 2 (157 registers, 12 warps per SM) measured
+// slower. The staged form keeps each thread's boxes on chip for the launch
+// instead: boxes 0 and 1 in registers, the others in shared memory
 // as float4 [pair][field pair][thread], so a warp's 16-byte loads of two
 // fields are consecutive and conflict-free (a thread reads only what it
 // wrote, so no barrier is needed).
@@ -60,9 +63,7 @@ enum : int {
 // wave; fleets with hexa and octo rotors keep the looser bound, which
 // measured faster for them.
 template <int INTEG, bool QUAD_ONLY, bool DRAG, int BOXES>
-__global__ void __launch_bounds__(128, BOXES == kBoxesStaged ? 3
-                                      : BOXES == kBoxesGlobal ? 5
-                                      : ((QUAD_ONLY && INTEG == kIntegSIE) ? 7 : 4))
+__global__ void __launch_bounds__(128, BOXES != kBoxesNone ? 3 : ((QUAD_ONLY && INTEG == kIntegSIE) ? 7 : 4))
     k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
   extern __shared__ float4 sm_pairs[];  // [ceil(n_obs / 2) - 1][5][blockDim.x] box pairs 1..
   const int B = blockDim.x;
