@@ -18,6 +18,7 @@ struct DepthArgs {
   float inv_f;             // tan(hfov / 2) / (width / 2)
   float max_range;
   float offset[3];         // camera position in the body frame
+  int vec_store;           // set by the launcher: width % 4 == 0 and out 16-byte aligned (one float4 per row)
   // Measurement variants (ag_measure.h); both 0 / NULL for ag_render_depth.
   int ieee_div;                    // 1: correctly rounded reciprocals instead of the fast approximation
   unsigned long long* live_pairs;  // non-NULL: count the (pixel, box) pairs left after culling, render nothing

@@ -83,6 +83,24 @@ __device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b
 __device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
 __device__ __forceinline__ V3 operator*(float s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
 __device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// 1/x and 1/sqrt(x) by the hardware approximations with subnormal inputs
+// and results flushed to zero (PTX rcp.approx.ftz.f32, rsqrt.approx.ftz.f32).
+// Used only where x is a squared norm in the normal range: that of a
+// unit-scale quaternion, or one checked against 1e-18 or against the
+// smallest normal float (kMinNormal) first; a squared norm below kMinNormal
+// counts as 0.
+constexpr float kMinNormal = 1.17549435e-38f;  // 2^-126
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ V3 cross(V3 a, V3 b) {
   return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
@@ -141,7 +159,7 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
             -P.kx[2] * (s.p.z - cm.c[2]) - P.kv[2] * s.v.z + kGravity};
     f = b.m * (a.x * R[0][2] + a.y * R[1][2] + a.z * R[2][2]);
     float an2 = dot(a, a);
-    V3 b3d = an2 > 1e-18f ? rsqrtf(an2) * a : V3{0.f, 0.f, 1.f};
+    V3 b3d = an2 > 1e-18f ? rsqrt_ftz(an2) * a : V3{0.f, 0.f, 1.f};
     V3 b1c = {cm.c[3], cm.c[4], 0.f};
     V3 c = cross(b3d, b1c);
     float cn2 = dot(c, c);
@@ -150,7 +168,7 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
       c = cross(b3d, b1c);
       cn2 = dot(c, c);
     }
-    V3 b2d = rsqrtf(cn2) * c;
+    V3 b2d = rsqrt_ftz(cn2) * c;  // cn2 > 1e-18, or near 1 for the perpendicular heading
     V3 b1d = cross(b2d, b3d);
     Rd[0][0] = b1d.x; Rd[0][1] = b2d.x; Rd[0][2] = b3d.x;
     Rd[1][0] = b1d.y; Rd[1][1] = b2d.y; Rd[1][2] = b3d.y;
@@ -160,8 +178,8 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
     // current yaw of the body frame: (cos psi, sin psi) = (R00, R10) / rho
     float rho2 = R[0][0] * R[0][0] + R[1][0] * R[1][0];
     float cpsi = 1.f, spsi = 0.f;
-    if (rho2 > 0.f) {
-      float ir = rsqrtf(rho2);
+    if (rho2 >= kMinNormal) {
+      float ir = rsqrt_ftz(rho2);
       cpsi = R[0][0] * ir;
       spsi = R[1][0] * ir;
     }
@@ -175,11 +193,11 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
       float rxz2 = a.x * a.x + a.z * a.z;
       float an2 = rxz2 + a.y * a.y;
       cphi = 1.f; sphi = 0.f; cth = 1.f; sth = 0.f;
-      if (rxz2 > 0.f) {
-        float irxz = rsqrtf(rxz2);
+      if (rxz2 >= kMinNormal) {
+        float irxz = rsqrt_ftz(rxz2);
         cth = a.z * irxz;
         sth = a.x * irxz;
-        float ian = rsqrtf(an2);
+        float ian = rsqrt_ftz(an2);  // an2 >= rxz2
         cphi = rxz2 * irxz * ian;
         sphi = -a.y * ian;
       } else if (an2 > 0.f) {
@@ -230,14 +248,14 @@ __device__ __forceinline__ Wrench4 allocate(const Wrench4& cmd, float (&u)[NROT]
 // Body z axis of a possibly non-unit quaternion: the homogeneous form over |q|^2.
 __device__ __forceinline__ V3 body_z(const Q4& q) {
   float n2 = q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z;
-  float inv = __fdividef(1.f, n2);
+  float inv = rcp_ftz(n2);
   float inv2 = 2.f * inv;
   return {inv2 * (q.x * q.z + q.w * q.y), inv2 * (q.y * q.z - q.w * q.x),
           inv * (q.w * q.w - q.x * q.x - q.y * q.y + q.z * q.z)};
 }
 
 __device__ __forceinline__ void normalize(Q4& q) {
-  float r = rsqrtf(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+  float r = rsqrt_ftz(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
   q.w *= r; q.x *= r; q.y *= r; q.z *= r;
 }
 
