@@ -63,13 +63,13 @@ template <int NROT> struct Step {
   float rate;        // commanded yaw rate (velocity, attitude): R_d Omega_d = rate e_3
   // position
   V3 a, c, b1c;      // a is also the vehicle-frame acceleration of the velocity mode
-  float an, cn;
+  float ian, icn;    // 1/|a| (0 when |a| <= 1e-9: b3d = e3), 1/|c|
   bool turned;       // heading fallback (b1c turned by 90 degrees) taken
   // current yaw and tilt (velocity, attitude)
   float cps, sps, ir;  // (cos, sin) psi = (R00, R10) * ir; ir = 0 when R00 = R10 = 0
   V3 B[3];             // columns of R_y(theta_d) R_x(phi_d)
   V3 vV;               // velocity in the yaw frame
-  float rxz, anv;      // |(a_x, a_z)|, |a|
+  float irxz, ianv;    // 1/|(a_x, a_z)|, 1/|a| (both 0 when a_x = a_z = 0)
   // allocation and integration
   float pre[NROT];   // A^+ (f, M) before the clamp
   bool pass[NROT];   // 0 < pre < u_max: the clamp passes the gradient
@@ -78,7 +78,7 @@ template <int NROT> struct Step {
   Wrench4 W;         // realised wrench
   V3 vn, wn, pn;
   Q4 qt, qn;
-  float qtn;
+  float iqtn;        // 1/|q_t|
 };
 
 struct Gains { V3 kx, kv, kR, kW; };
@@ -115,27 +115,29 @@ __device__ __forceinline__ void forward_step(const Xs<NROT>& x, const Cmd& cm, c
       S.a = {-g.kx.x * (x.p.x - cm.t[0]) - g.kv.x * x.v.x, -g.kx.y * (x.p.y - cm.t[1]) - g.kv.y * x.v.y,
              -g.kx.z * (x.p.z - cm.t[2]) - g.kv.z * x.v.z + kGravity};
       S.f = b.m * dot(S.a, b3);
-      S.an = sqrtf(dot(S.a, S.a));
-      const V3 b3d = S.an > 1e-9f ? (1.f / S.an) * S.a : V3{0.f, 0.f, 1.f};
+      const float a2 = dot(S.a, S.a);
+      S.ian = a2 > 1e-18f ? rsqrt_ftz(a2) : 0.f;
+      const V3 b3d = S.ian > 0.f ? S.ian * S.a : V3{0.f, 0.f, 1.f};
       S.b1c = {cm.c0, cm.s0, 0.f};
       S.c = cross(b3d, S.b1c);
-      S.cn = sqrtf(dot(S.c, S.c));
-      S.turned = !(S.cn > 1e-9f);
+      float c2 = dot(S.c, S.c);
+      S.turned = !(c2 > 1e-18f);
       if (S.turned) {  // commanded thrust along the heading: use the heading turned by 90 degrees
         S.b1c = {-cm.s0, cm.c0, 0.f};
         S.c = cross(b3d, S.b1c);
-        S.cn = sqrtf(dot(S.c, S.c));
+        c2 = dot(S.c, S.c);  // near 1
       }
-      const V3 b2d = (1.f / S.cn) * S.c;
+      S.icn = rsqrt_ftz(c2);
+      const V3 b2d = S.icn * S.c;
       S.Rd[0] = cross(b2d, b3d);
       S.Rd[1] = b2d;
       S.Rd[2] = b3d;
       S.rate = 0.f;
     } else {
       const float rho2 = S.R[0][0] * S.R[0][0] + S.R[1][0] * S.R[1][0];
-      S.ir = rho2 > 0.f ? rsqrtf(rho2) : 0.f;
-      S.cps = rho2 > 0.f ? S.R[0][0] * S.ir : 1.f;
-      S.sps = rho2 > 0.f ? S.R[1][0] * S.ir : 0.f;
+      S.ir = rho2 >= kMinNormal ? rsqrt_ftz(rho2) : 0.f;
+      S.cps = S.ir > 0.f ? S.R[0][0] * S.ir : 1.f;
+      S.sps = S.ir > 0.f ? S.R[1][0] * S.ir : 0.f;
       float cphi, sphi, cth, sth;
       if (MODE == kModeBodyVel) {
         S.vV = {S.cps * x.v.x + S.sps * x.v.y, -S.sps * x.v.x + S.cps * x.v.y, x.v.z};
@@ -143,15 +145,18 @@ __device__ __forceinline__ void forward_step(const Xs<NROT>& x, const Cmd& cm, c
         const V3 b3V = {S.cps * b3.x + S.sps * b3.y, -S.sps * b3.x + S.cps * b3.y, b3.z};
         S.f = b.m * dot(S.a, b3V);
         const float rxz2 = S.a.x * S.a.x + S.a.z * S.a.z;
-        S.rxz = sqrtf(rxz2);
-        S.anv = sqrtf(rxz2 + S.a.y * S.a.y);
+        const float an2 = rxz2 + S.a.y * S.a.y;
+        S.irxz = 0.f;
+        S.ianv = 0.f;
         cth = 1.f; sth = 0.f; cphi = 1.f; sphi = 0.f;
-        if (rxz2 > 0.f) {
-          cth = S.a.z / S.rxz;
-          sth = S.a.x / S.rxz;
-          cphi = S.rxz / S.anv;
-          sphi = -S.a.y / S.anv;
-        } else if (S.anv > 0.f) {  // a along +-y: phi_d = atan2(-a_y, 0), theta_d = atan2(0, 0) = 0
+        if (rxz2 >= kMinNormal) {
+          S.irxz = rsqrt_ftz(rxz2);
+          S.ianv = rsqrt_ftz(an2);
+          cth = S.a.z * S.irxz;
+          sth = S.a.x * S.irxz;
+          cphi = rxz2 * S.irxz * S.ianv;
+          sphi = -S.a.y * S.ianv;
+        } else if (an2 > 0.f) {  // a along +-y: phi_d = atan2(-a_y, 0), theta_d = atan2(0, 0) = 0
           cphi = 0.f;
           sphi = S.a.y > 0.f ? -1.f : 1.f;
         }
@@ -201,8 +206,8 @@ __device__ __forceinline__ void forward_step(const Xs<NROT>& x, const Cmd& cm, c
   const V3& w = S.wn;
   S.qt = {q.w - hh * (q.x * w.x + q.y * w.y + q.z * w.z), q.x + hh * (q.w * w.x + q.y * w.z - q.z * w.y),
           q.y + hh * (q.w * w.y - q.x * w.z + q.z * w.x), q.z + hh * (q.w * w.z + q.x * w.y - q.y * w.x)};
-  S.qtn = sqrtf(S.qt.w * S.qt.w + S.qt.x * S.qt.x + S.qt.y * S.qt.y + S.qt.z * S.qt.z);
-  const float iq = 1.f / S.qtn;
+  S.iqtn = rsqrt_ftz(S.qt.w * S.qt.w + S.qt.x * S.qt.x + S.qt.y * S.qt.y + S.qt.z * S.qt.z);
+  const float iq = S.iqtn;
   S.qn = {S.qt.w * iq, S.qt.x * iq, S.qt.y * iq, S.qt.z * iq};
   xn.p = S.pn;
   xn.v = S.vn;
@@ -226,10 +231,10 @@ __device__ __forceinline__ void cross_bwd(V3 a, V3 b, V3 ybar, V3& abar, V3& bba
   bbar = bbar + cross(ybar, a);
 }
 
-// y = x / |x| (|x| = n): x_bar += (y_bar - y (y . y_bar)) / n
-__device__ __forceinline__ V3 normalize_bwd(V3 y, float n, V3 ybar) {
+// y = x / |x| (1 / |x| = in): x_bar += in (y_bar - y (y . y_bar))
+__device__ __forceinline__ V3 normalize_bwd(V3 y, float in, V3 ybar) {
   const float d = dot(y, ybar);
-  return (1.f / n) * (ybar - d * y);
+  return in * (ybar - d * y);
 }
 
 // Reverse of forward_step. On entry lam is the adjoint of (x_{t+1}, u_{t+1})
@@ -246,7 +251,7 @@ __device__ __forceinline__ void backward_step(const Xs<NROT>& x, const Cmd& cm, 
   Q4 qtb;
   {
     const float d = S.qn.w * lam.q.w + S.qn.x * lam.q.x + S.qn.y * lam.q.y + S.qn.z * lam.q.z;
-    const float iq = 1.f / S.qtn;
+    const float iq = S.iqtn;
     qtb = {iq * (lam.q.w - d * S.qn.w), iq * (lam.q.x - d * S.qn.x), iq * (lam.q.y - d * S.qn.y),
            iq * (lam.q.z - d * S.qn.z)};
   }
@@ -330,11 +335,11 @@ __device__ __forceinline__ void backward_step(const Xs<NROT>& x, const Cmd& cm, 
       V3 b2db = Rdb[1], b3db = Rdb[2];
       cross_bwd(S.Rd[1], S.Rd[2], Rdb[0], b2db, b3db);
       // b2d = c / |c|,  c = b3d x b1c
-      const V3 cb = normalize_bwd(S.Rd[1], S.cn, b2db);
+      const V3 cb = normalize_bwd(S.Rd[1], S.icn, b2db);
       V3 b1cb = {0.f, 0.f, 0.f};
       cross_bwd(S.Rd[2], S.b1c, cb, b3db, b1cb);
       // b3d = a / |a| (constant e3 in the degenerate case |a| = 0)
-      if (S.an > 1e-9f) ab = ab + normalize_bwd(S.Rd[2], S.an, b3db);
+      if (S.ian > 0.f) ab = ab + normalize_bwd(S.Rd[2], S.ian, b3db);
       // a = -k_x (p - p_d) - k_v v + g e3
       const V3 ex = {x.p.x - cm.t[0], x.p.y - cm.t[1], x.p.z - cm.t[2]};
       pb = pb - V3{g.kx.x * ab.x, g.kx.y * ab.y, g.kx.z * ab.z};
@@ -378,13 +383,13 @@ __device__ __forceinline__ void backward_step(const Xs<NROT>& x, const Cmd& cm, 
         cpb += b3.x * b3Vb.x + b3.y * b3Vb.y;
         spb += b3.y * b3Vb.x - b3.x * b3Vb.y;
         // B from a: B_2 = a/|a|, B_0 = (a_z, 0, -a_x)/|(a_x, a_z)|, B_1 = B_2 x B_0 (constant when a_x = a_z = 0)
-        if (S.rxz > 0.f) {
+        if (S.irxz > 0.f) {
           V3 B2b = Bb[2], B0b = Bb[0];
           cross_bwd(S.B[2], S.B[0], Bb[1], B2b, B0b);
-          const V3 wbar = normalize_bwd(S.B[0], S.rxz, B0b);
+          const V3 wbar = normalize_bwd(S.B[0], S.irxz, B0b);
           ab.z += wbar.x;
           ab.x -= wbar.z;
-          ab = ab + normalize_bwd(S.B[2], S.anv, B2b);
+          ab = ab + normalize_bwd(S.B[2], S.ianv, B2b);
         }
         // a = k_v (v_d - v^V) + g e3
         const V3 vVb = {-g.kv.x * ab.x, -g.kv.y * ab.y, -g.kv.z * ab.z};
