@@ -22,6 +22,12 @@ BUILD_DIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["ag_api.cu", "ag_api_task.cu", "ag_api_adjoint.cu", "ag_api_noalloc.cu", "fleet_kernels.cu",
                 "adjoint.cu", "serve.cu", "depth.cu", "task.cu", "measure.cu"]
+# Translation units whose float arithmetic is written with every fused
+# multiply-add explicit (fmaf, __ffma2_rn): the compiler contracts nothing
+# else, so each kernel that runs the per-vehicle step (fused, unfused,
+# serving, task; each mode-specialised copy) rounds exactly as the source
+# says, and they agree bit for bit.
+NO_CONTRACTION = {"fleet_kernels.cu", "serve.cu", "task.cu", "depth.cu"}
 
 
 def _nvcc() -> str:
@@ -72,7 +78,8 @@ def _compile(verbose: bool) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+        extra = ["-fmad=false"] if src in NO_CONTRACTION else []
+        cmd = [nvcc] + common + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

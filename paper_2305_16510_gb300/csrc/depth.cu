@@ -75,7 +75,7 @@ __device__ __forceinline__ CamPose camera_pose(const DepthArgs& a, uint32_t env)
   rotation(q, c.R);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
-    c.o[i] = st[i * n + env] + c.R[i][0] * a.offset[0] + c.R[i][1] * a.offset[1] + c.R[i][2] * a.offset[2];
+    c.o[i] = st[i * n + env] + fmaf(c.R[i][2], a.offset[2], fmaf(c.R[i][1], a.offset[1], c.R[i][0] * a.offset[0]));
   return c;
 }
 
@@ -89,9 +89,9 @@ __device__ __forceinline__ void box_record(const DepthArgs& a, uint32_t env, con
   float M[3][3], ob[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    ob[i] = Rb[0][i] * v[0] + Rb[1][i] * v[1] + Rb[2][i] * v[2];
+    ob[i] = fmaf(Rb[2][i], v[2], fmaf(Rb[1][i], v[1], Rb[0][i] * v[0]));
 #pragma unroll
-    for (int j = 0; j < 3; ++j) M[i][j] = Rb[0][i] * c.R[0][j] + Rb[1][i] * c.R[1][j] + Rb[2][i] * c.R[2][j];
+    for (int j = 0; j < 3; ++j) M[i][j] = fmaf(Rb[2][i], c.R[2][j], fmaf(Rb[1][i], c.R[1][j], Rb[0][i] * c.R[0][j]));
   }
   const float h[3] = {bx[3 * n], bx[4 * n], bx[5 * n]};
   rec[0] = make_float4(M[0][0], M[0][1], M[0][2], M[1][0]);
@@ -106,9 +106,9 @@ __device__ __forceinline__ float4 box_sphere(const DepthArgs& a, uint32_t env, c
   const uint32_t n = a.n;
   const float* bx = a.boxes + (size_t)k * 10 * n + env;
   const float v[3] = {bx[0] - c.o[0], bx[n] - c.o[1], bx[2 * n] - c.o[2]};
-  const float sx = c.R[0][0] * v[0] + c.R[1][0] * v[1] + c.R[2][0] * v[2];
-  const float sy = c.R[0][1] * v[0] + c.R[1][1] * v[1] + c.R[2][1] * v[2];
-  const float sz = c.R[0][2] * v[0] + c.R[1][2] * v[1] + c.R[2][2] * v[2];
+  const float sx = fmaf(c.R[2][0], v[2], fmaf(c.R[1][0], v[1], c.R[0][0] * v[0]));
+  const float sy = fmaf(c.R[2][1], v[2], fmaf(c.R[1][1], v[1], c.R[0][1] * v[0]));
+  const float sz = fmaf(c.R[2][2], v[2], fmaf(c.R[1][2], v[1], c.R[0][2] * v[0]));
   const float h0 = bx[3 * n], h1 = bx[4 * n], h2 = bx[5 * n];
   const float rho = 1.001f * sqrtf(h0 * h0 + h1 * h1 + h2 * h2) + 1e-4f * (fabsf(sx) + fabsf(sy) + fabsf(sz)) + 1e-6f;
   return make_float4(sx, sy, sz, rho);

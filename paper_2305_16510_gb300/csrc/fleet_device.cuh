@@ -82,7 +82,7 @@ struct StepParams {
 __device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
 __device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
 __device__ __forceinline__ V3 operator*(float s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
-__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)); }
 // 1/x and 1/sqrt(x) by the hardware approximations with subnormal inputs
 // and results flushed to zero (PTX rcp.approx.ftz.f32, rsqrt.approx.ftz.f32).
 // Used only where x is a squared norm in the normal range: that of a
@@ -102,17 +102,25 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
 }
 
 __device__ __forceinline__ V3 cross(V3 a, V3 b) {
-  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+  return {fmaf(a.y, b.z, -(a.z * b.y)), fmaf(a.z, b.x, -(a.x * b.z)), fmaf(a.x, b.y, -(a.y * b.x))};
 }
+// a x b for b = (b.x, b.y, 0)
+__device__ __forceinline__ V3 cross_xy(V3 a, float bx, float by) {
+  return {-(a.z * by), a.z * bx, fmaf(a.x, by, -(a.y * bx))};
+}
+__device__ __forceinline__ float dot4(const Q4& q) { return fmaf(q.z, q.z, fmaf(q.y, q.y, fmaf(q.x, q.x, q.w * q.w))); }
 
-// Rotation matrix of a unit quaternion (body -> world).
+// Rotation matrix of a unit quaternion (body -> world), from the doubled
+// vector part (doubling is exact): R00 = 1 - 2 y^2 - 2 z^2, R01 = 2 (x y - w z), ...
 __device__ __forceinline__ void rotation(const Q4& q, float R[3][3]) {
-  float xx = q.x * q.x, yy = q.y * q.y, zz = q.z * q.z;
-  float xy = q.x * q.y, xz = q.x * q.z, yz = q.y * q.z;
-  float wx = q.w * q.x, wy = q.w * q.y, wz = q.w * q.z;
-  R[0][0] = 1.f - 2.f * (yy + zz); R[0][1] = 2.f * (xy - wz);       R[0][2] = 2.f * (xz + wy);
-  R[1][0] = 2.f * (xy + wz);       R[1][1] = 1.f - 2.f * (xx + zz); R[1][2] = 2.f * (yz - wx);
-  R[2][0] = 2.f * (xz - wy);       R[2][1] = 2.f * (yz + wx);       R[2][2] = 1.f - 2.f * (xx + yy);
+  const float x2 = 2.f * q.x, y2 = 2.f * q.y, z2 = 2.f * q.z;
+  const float wx = q.w * x2, wy = q.w * y2, wz = q.w * z2;
+  R[0][0] = fmaf(-q.y, y2, fmaf(-q.z, z2, 1.f));
+  R[1][1] = fmaf(-q.x, x2, fmaf(-q.z, z2, 1.f));
+  R[2][2] = fmaf(-q.x, x2, fmaf(-q.y, y2, 1.f));
+  R[0][1] = fmaf(q.x, y2, -wz); R[1][0] = fmaf(q.x, y2, wz);
+  R[0][2] = fmaf(q.x, z2, wy);  R[2][0] = fmaf(q.x, z2, -wy);
+  R[1][2] = fmaf(q.y, z2, -wx); R[2][1] = fmaf(q.y, z2, wx);
 }
 
 // Per-launch constants of an environment's command. Trig of commanded angles
@@ -154,18 +162,16 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
   float f;
   if (cm.mode == kModePosition) {
     // Lee 2011: a = -k_x e_x - k_v e_v + g e3, b3d = a/|a|, b2d ~ b3d x b1c, b1d = b2d x b3d
-    V3 a = {-P.kx[0] * (s.p.x - cm.c[0]) - P.kv[0] * s.v.x,
-            -P.kx[1] * (s.p.y - cm.c[1]) - P.kv[1] * s.v.y,
-            -P.kx[2] * (s.p.z - cm.c[2]) - P.kv[2] * s.v.z + kGravity};
-    f = b.m * (a.x * R[0][2] + a.y * R[1][2] + a.z * R[2][2]);
+    V3 a = {fmaf(-P.kx[0], s.p.x - cm.c[0], -(P.kv[0] * s.v.x)),
+            fmaf(-P.kx[1], s.p.y - cm.c[1], -(P.kv[1] * s.v.y)),
+            fmaf(-P.kx[2], s.p.z - cm.c[2], fmaf(-P.kv[2], s.v.z, kGravity))};
+    f = b.m * dot(a, b3);
     float an2 = dot(a, a);
     V3 b3d = an2 > 1e-18f ? rsqrt_ftz(an2) * a : V3{0.f, 0.f, 1.f};
-    V3 b1c = {cm.c[3], cm.c[4], 0.f};
-    V3 c = cross(b3d, b1c);
+    V3 c = cross_xy(b3d, cm.c[3], cm.c[4]);  // b1c = (cos psi_d, sin psi_d, 0)
     float cn2 = dot(c, c);
     if (!(cn2 > 1e-18f)) {
-      b1c = {-cm.c[4], cm.c[3], 0.f};
-      c = cross(b3d, b1c);
+      c = cross_xy(b3d, -cm.c[4], cm.c[3]);  // b1c turned by 90 degrees
       cn2 = dot(c, c);
     }
     V3 b2d = rsqrt_ftz(cn2) * c;  // cn2 > 1e-18, or near 1 for the perpendicular heading
@@ -176,7 +182,7 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
     rate = 0.f;
   } else {
     // current yaw of the body frame: (cos psi, sin psi) = (R00, R10) / rho
-    float rho2 = R[0][0] * R[0][0] + R[1][0] * R[1][0];
+    float rho2 = fmaf(R[1][0], R[1][0], R[0][0] * R[0][0]);
     float cpsi = 1.f, spsi = 0.f;
     if (rho2 >= kMinNormal) {
       float ir = rsqrt_ftz(rho2);
@@ -186,12 +192,12 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
     float cphi, sphi, cth, sth;
     if (cm.mode == kModeBodyVel) {
       // Eq. 6 in the vehicle frame, Eq. 7 thrust, Eqs. 8-9 tilt (algebraic)
-      V3 vV = {cpsi * s.v.x + spsi * s.v.y, -spsi * s.v.x + cpsi * s.v.y, s.v.z};
-      V3 a = {P.kv[0] * (cm.c[0] - vV.x), P.kv[1] * (cm.c[1] - vV.y), P.kv[2] * (cm.c[2] - vV.z) + kGravity};
-      V3 b3V = {cpsi * R[0][2] + spsi * R[1][2], -spsi * R[0][2] + cpsi * R[1][2], R[2][2]};
+      V3 vV = {fmaf(spsi, s.v.y, cpsi * s.v.x), fmaf(cpsi, s.v.y, -(spsi * s.v.x)), s.v.z};
+      V3 a = {P.kv[0] * (cm.c[0] - vV.x), P.kv[1] * (cm.c[1] - vV.y), fmaf(P.kv[2], cm.c[2] - vV.z, kGravity)};
+      V3 b3V = {fmaf(spsi, R[1][2], cpsi * R[0][2]), fmaf(cpsi, R[1][2], -(spsi * R[0][2])), R[2][2]};
       f = b.m * dot(a, b3V);
-      float rxz2 = a.x * a.x + a.z * a.z;
-      float an2 = rxz2 + a.y * a.y;
+      float rxz2 = fmaf(a.z, a.z, a.x * a.x);
+      float an2 = fmaf(a.y, a.y, rxz2);
       cphi = 1.f; sphi = 0.f; cth = 1.f; sth = 0.f;
       if (rxz2 >= kMinNormal) {
         float irxz = rsqrt_ftz(rxz2);
@@ -211,19 +217,25 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
     }
     // Eq. 1: R_d = R_z(psi) R_y(theta_d) R_x(phi_d)
     float b01 = sth * sphi, b02 = sth * cphi, b21 = cth * sphi, b22 = cth * cphi;
-    Rd[0][0] = cpsi * cth;  Rd[0][1] = cpsi * b01 - spsi * cphi; Rd[0][2] = cpsi * b02 + spsi * sphi;
-    Rd[1][0] = spsi * cth;  Rd[1][1] = spsi * b01 + cpsi * cphi; Rd[1][2] = spsi * b02 - cpsi * sphi;
-    Rd[2][0] = -sth;        Rd[2][1] = b21;                      Rd[2][2] = b22;
+    Rd[0][0] = cpsi * cth; Rd[0][1] = fmaf(cpsi, b01, -(spsi * cphi)); Rd[0][2] = fmaf(cpsi, b02, spsi * sphi);
+    Rd[1][0] = spsi * cth; Rd[1][1] = fmaf(spsi, b01, cpsi * cphi);    Rd[1][2] = fmaf(spsi, b02, -(cpsi * sphi));
+    Rd[2][0] = -sth;       Rd[2][1] = b21;                             Rd[2][2] = b22;
   }
-  // Eq. 3: e_R = 1/2 vee(E - E^T), E = R_d^T R (off-diagonal entries only)
-  auto Eij = [&](int i, int j) { return Rd[0][i] * R[0][j] + Rd[1][i] * R[1][j] + Rd[2][i] * R[2][j]; };
-  V3 eR = {0.5f * (Eij(2, 1) - Eij(1, 2)), 0.5f * (Eij(0, 2) - Eij(2, 0)), 0.5f * (Eij(1, 0) - Eij(0, 1))};
+  // Eq. 3: e_R = 1/2 vee(E - E^T), E = R_d^T R (off-diagonal entries only); each component is
+  // E_ij - E_ji = col_i(R_d) . col_j(R) - col_j(R_d) . col_i(R) as one chain of six products, and
+  // its factor 1/2 is exact, so it is applied with the gain below
+  auto dE = [&](int i, int j) {
+    return fmaf(Rd[0][i], R[0][j], fmaf(Rd[1][i], R[1][j], fmaf(Rd[2][i], R[2][j],
+           fmaf(-Rd[0][j], R[0][i], fmaf(-Rd[1][j], R[1][i], -(Rd[2][j] * R[2][i]))))));
+  };
+  const V3 eR2 = {dE(2, 1), dE(0, 2), dE(1, 0)};  // 2 e_R
   // Eq. 4 with R^T R_d Omega_d = rate R^T e_3
-  V3 eW = {s.w.x - rate * R[2][0], s.w.y - rate * R[2][1], s.w.z - rate * R[2][2]};
+  V3 eW = {fmaf(-rate, R[2][0], s.w.x), fmaf(-rate, R[2][1], s.w.y), fmaf(-rate, R[2][2], s.w.z)};
   // Eq. 5's Omega x J Omega in principal axes
   const V3 gyro = {b.gx * (s.w.y * s.w.z), b.gy * (s.w.z * s.w.x), b.gz * (s.w.x * s.w.y)};
-  return {f, -P.kR[0] * eR.x - P.kW[0] * eW.x + gyro.x, -P.kR[1] * eR.y - P.kW[1] * eW.y + gyro.y,
-          -P.kR[2] * eR.z - P.kW[2] * eW.z + gyro.z};
+  return {f, fmaf(-0.5f * P.kR[0], eR2.x, fmaf(-P.kW[0], eW.x, gyro.x)),
+          fmaf(-0.5f * P.kR[1], eR2.y, fmaf(-P.kW[1], eW.y, gyro.y)),
+          fmaf(-0.5f * P.kR[2], eR2.z, fmaf(-P.kW[2], eW.z, gyro.z))};
 }
 
 // Rotor allocation, per-motor clamp to [0, u_max], first-order lag; returns
@@ -234,35 +246,34 @@ __device__ __forceinline__ Wrench4 allocate(const Wrench4& cmd, float (&u)[NROT]
   Wrench4 W = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < NROT; ++i) {
-    float uc = P.Ap[T][i][0] * cmd.f + P.Ap[T][i][1] * cmd.mx + P.Ap[T][i][2] * cmd.my + P.Ap[T][i][3] * cmd.mz;
+    float uc = fmaf(P.Ap[T][i][3], cmd.mz, fmaf(P.Ap[T][i][2], cmd.my, fmaf(P.Ap[T][i][1], cmd.mx, P.Ap[T][i][0] * cmd.f)));
     uc = fminf(fmaxf(uc, 0.f), P.u_max);
-    u[i] = u[i] + P.alpha * (uc - u[i]);
-    W.f += P.A[T][0][i] * u[i];
-    W.mx += P.A[T][1][i] * u[i];
-    W.my += P.A[T][2][i] * u[i];
-    W.mz += P.A[T][3][i] * u[i];
+    u[i] = fmaf(P.alpha, uc - u[i], u[i]);
+    W.f = fmaf(P.A[T][0][i], u[i], W.f);
+    W.mx = fmaf(P.A[T][1][i], u[i], W.mx);
+    W.my = fmaf(P.A[T][2][i], u[i], W.my);
+    W.mz = fmaf(P.A[T][3][i], u[i], W.mz);
   }
   return W;
 }
 
 // Body z axis of a possibly non-unit quaternion: the homogeneous form over |q|^2.
 __device__ __forceinline__ V3 body_z(const Q4& q) {
-  float n2 = q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z;
-  float inv = rcp_ftz(n2);
+  float inv = rcp_ftz(dot4(q));
   float inv2 = 2.f * inv;
-  return {inv2 * (q.x * q.z + q.w * q.y), inv2 * (q.y * q.z - q.w * q.x),
-          inv * (q.w * q.w - q.x * q.x - q.y * q.y + q.z * q.z)};
+  return {inv2 * fmaf(q.x, q.z, q.w * q.y), inv2 * fmaf(q.y, q.z, -(q.w * q.x)),
+          inv * fmaf(q.w, q.w, fmaf(-q.x, q.x, fmaf(-q.y, q.y, q.z * q.z)))};
 }
 
 __device__ __forceinline__ void normalize(Q4& q) {
-  float r = rsqrt_ftz(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+  float r = rsqrt_ftz(dot4(q));
   q.w *= r; q.x *= r; q.y *= r; q.z *= r;
 }
 
 // q (x) (0, w): twice the quaternion rate q' = 1/2 q (x) (0, Omega)
 __device__ __forceinline__ Q4 quat_rate2(const Q4& q, const V3& w) {
-  return {-(q.x * w.x + q.y * w.y + q.z * w.z), q.w * w.x + q.y * w.z - q.z * w.y, q.w * w.y - q.x * w.z + q.z * w.x,
-          q.w * w.z + q.x * w.y - q.y * w.x};
+  return {-fmaf(q.z, w.z, fmaf(q.y, w.y, q.x * w.x)), fmaf(q.w, w.x, fmaf(q.y, w.z, -(q.z * w.y))),
+          fmaf(q.w, w.y, fmaf(q.z, w.x, -(q.x * w.z))), fmaf(q.w, w.z, fmaf(q.x, w.y, -(q.y * w.x)))};
 }
 
 // The rigid-body rates under the wrench held over a substep:
@@ -271,13 +282,13 @@ __device__ __forceinline__ Q4 quat_rate2(const Q4& q, const V3& w) {
 // equations in principal axes).
 template <bool DRAG>
 __device__ __forceinline__ V3 accel(V3 b3, V3 v, float fm, float dm) {
-  V3 a = {fm * b3.x, fm * b3.y, fm * b3.z - kGravity};
-  if (DRAG) a = {a.x - dm * v.x, a.y - dm * v.y, a.z - dm * v.z};
-  return a;
+  if (DRAG)
+    return {fmaf(fm, b3.x, -(dm * v.x)), fmaf(fm, b3.y, -(dm * v.y)), fmaf(fm, b3.z, fmaf(-dm, v.z, -kGravity))};
+  return {fm * b3.x, fm * b3.y, fmaf(fm, b3.z, -kGravity)};
 }
 
 __device__ __forceinline__ V3 ang_accel(V3 w, V3 aw, const Body& b) {
-  return {aw.x - b.ex * (w.y * w.z), aw.y - b.ey * (w.z * w.x), aw.z - b.ez * (w.x * w.y)};
+  return {fmaf(-b.ex, w.y * w.z, aw.x), fmaf(-b.ey, w.z * w.x, aw.y), fmaf(-b.ez, w.x * w.y, aw.z)};
 }
 
 // Semi-implicit Euler: v, Omega from the rates; p, q from the updated
@@ -288,12 +299,12 @@ __device__ __forceinline__ void step_sie(VState& s, V3 b3, const Wrench4& W, con
   const V3 aw = {b.ijx * W.mx, b.ijy * W.my, b.ijz * W.mz};
   const V3 dv = accel<DRAG>(b3, s.v, fm, dm);
   const V3 dw = ang_accel(s.w, aw, b);
-  s.v = s.v + h * dv;
-  s.w = s.w + h * dw;
-  s.p = s.p + h * s.v;
+  s.v = {fmaf(h, dv.x, s.v.x), fmaf(h, dv.y, s.v.y), fmaf(h, dv.z, s.v.z)};
+  s.w = {fmaf(h, dw.x, s.w.x), fmaf(h, dw.y, s.w.y), fmaf(h, dw.z, s.w.z)};
+  s.p = {fmaf(h, s.v.x, s.p.x), fmaf(h, s.v.y, s.p.y), fmaf(h, s.v.z, s.p.z)};
   const float hh = 0.5f * h;
   const Q4 r = quat_rate2(s.q, s.w);
-  s.q = {s.q.w + hh * r.w, s.q.x + hh * r.x, s.q.y + hh * r.y, s.q.z + hh * r.z};
+  s.q = {fmaf(hh, r.w, s.q.w), fmaf(hh, r.x, s.q.x), fmaf(hh, r.y, s.q.y), fmaf(hh, r.z, s.q.z)};
   normalize(s.q);
 }
 
@@ -371,16 +382,19 @@ __device__ __forceinline__ void integrate(VState& s, V3 b3, const Wrench4& W, co
 // hx, hy, hz, unit quaternion qb): p is taken into the box frame by the
 // conjugate rotation v - w t + u x t with t = 2 u x v; the distance to the
 // box is the norm of max(|d| - h, 0) per axis (equal to |d - clamp(d, -h, h)|);
-// touching counts.
+// touching counts. The operations and their order are those of the fused
+// step's paired test (pair_dist2), so both take the same decisions.
 __device__ __forceinline__ bool sphere_hits_box(V3 p, float r2, V3 c, V3 hb, Q4 qb) {
-  V3 v = p - c;
-  V3 u = {qb.x, qb.y, qb.z};
-  V3 t = 2.f * cross(u, v);
-  V3 d = v - qb.w * t + cross(u, t);
-  float ex = fmaxf(fabsf(d.x) - hb.x, 0.f);
-  float ey = fmaxf(fabsf(d.y) - hb.y, 0.f);
-  float ez = fmaxf(fabsf(d.z) - hb.z, 0.f);
-  return !(r2 < ex * ex + ey * ey + ez * ez);
+  const V3 v = p - c;
+  const V3 u2 = {2.f * qb.x, 2.f * qb.y, 2.f * qb.z};
+  const V3 t = cross(u2, v);                  // 2 u x v
+  const V3 ut2 = cross(u2, t);                // 2 (u x t)
+  const V3 d = {fmaf(0.5f, ut2.x, fmaf(-qb.w, t.x, v.x)), fmaf(0.5f, ut2.y, fmaf(-qb.w, t.y, v.y)),
+                fmaf(0.5f, ut2.z, fmaf(-qb.w, t.z, v.z))};
+  const float ex = fmaxf(fabsf(d.x) - hb.x, 0.f);
+  const float ey = fmaxf(fabsf(d.y) - hb.y, 0.f);
+  const float ez = fmaxf(fabsf(d.z) - hb.z, 0.f);
+  return !(r2 < fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
 }
 
 }  // namespace agk

@@ -63,7 +63,8 @@ enum : int {
 // wave; fleets with hexa and octo rotors keep the looser bound, which
 // measured faster for them.
 template <int INTEG, bool QUAD_ONLY, bool DRAG, int BOXES>
-__global__ void __launch_bounds__(128, BOXES != kBoxesNone ? 3 : ((QUAD_ONLY && INTEG == kIntegSIE) ? 7 : 4))
+__global__ void __launch_bounds__(128, BOXES == kBoxesGlobal ? 4
+                                       : (BOXES == kBoxesStaged ? 3 : ((QUAD_ONLY && INTEG == kIntegSIE) ? 7 : 4)))
     k_fused_step(FleetBuffers fb, StepParams P, int n_steps, int substeps) {
   extern __shared__ float4 sm_pairs[];  // [ceil(n_obs / 2) - 1][5][blockDim.x] box pairs 1..
   const int B = blockDim.x;
@@ -112,14 +113,14 @@ __global__ void __launch_bounds__(128, BOXES != kBoxesNone ? 3 : ((QUAD_ONLY && 
     if (BOXES == kBoxesGlobal) {
       GlobalBoxPairs gx{fb.boxes_slot, fb.n, slot};
       if (nrot == 4)
-        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+        simulate<4, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else if (nrot == 6)
         simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else
         simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
     } else if (BOXES == kBoxesStaged) {
       if (nrot == 4)
-        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+        simulate<4, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else if (nrot == 6)
         simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(128, BOXES != kBoxesNone ? 3 : ((QUAD_ONLY && 
     } else {
       NoBoxSource none;
       if (nrot == 4)
-        simulate<4, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+        simulate<4, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else if (nrot == 6)
         simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else
@@ -363,7 +364,7 @@ cudaError_t launch_fused_t(const FleetBuffers& fb, const StepParams& P, int n_st
                            cudaStream_t st) {
   if (fb.n_obs == 0) return launch_fused_b<INTEG, QUAD_ONLY, DRAG, kBoxesNone>(fb, P, n_steps, substeps, B, st);
   // the global pair copy is in slot order: it serves the grouped order only
-  if (fb.order && fb.boxes_slot && !P.exact_tests && !fused_boxes_staged_from_env())
+  if (fb.order && fb.boxes_slot && !fused_boxes_staged_from_env())
     return launch_fused_b<INTEG, QUAD_ONLY, DRAG, kBoxesGlobal>(fb, P, n_steps, substeps, B, st);
   return launch_fused_b<INTEG, QUAD_ONLY, DRAG, kBoxesStaged>(fb, P, n_steps, substeps, B, st);
 }

@@ -300,13 +300,17 @@ __device__ __forceinline__ float clearance_threshold2(V3 p, float min_e2, float 
   return t > 0.f ? t * t : -1.f;
 }
 
-// simulate() with the command given (cm) instead of read from fb; returns
-// the final state, which it also stores.
-template <int NROT, int INTEG, bool DRAG, class Boxes>
+// simulate() with the command given (cm_in) instead of read from fb; returns
+// the final state, which it also stores. MODE >= 0: every calling thread's
+// command mode is MODE; the mode is then a constant of the compiled loop,
+// and the controller's branches on it fold away.
+template <int NROT, int INTEG, bool DRAG, class Boxes, int MODE = -1>
 __device__ __forceinline__ VState simulate_cmd(const FleetBuffers& fb, const StepParams& P, uint32_t env,
-                                               uint32_t slot, const Command& cm, int n_steps, int substeps, int n_obs,
+                                               uint32_t slot, const Command& cm_in, int n_steps, int substeps, int n_obs,
                                                Boxes& boxes, uint32_t seed_lo, uint32_t seed_hi, uint32_t& resets,
                                                bool& any_hit, uint32_t& tests) {
+  Command cm = cm_in;
+  if (MODE >= 0) cm.mode = MODE;
   const uint32_t n = fb.n;
   VState s = load_state(fb.state, n, env);
   normalize(s.q);
@@ -357,12 +361,43 @@ __device__ __forceinline__ VState simulate_cmd(const FleetBuffers& fb, const Ste
   return s;
 }
 
-template <int NROT, int INTEG, bool DRAG, class Boxes>
+// With BY_MODE and the grouped thread order (fb.order: warps of one rotor
+// count and command mode), a group of threads that run together and share
+// one command mode (position, body velocity, attitude + thrust) runs the
+// steps compiled for that mode, in which the controller's branches on the
+// mode are folded away; other threads run the branching form. Every fused
+// multiply-add of the step is explicit (fmaf) and the files that include
+// this header are compiled without contraction, so both forms round
+// identically and the choice changes no result.
+template <int NROT, int INTEG, bool DRAG, bool BY_MODE = false, class Boxes>
 __device__ __forceinline__ void simulate(const FleetBuffers& fb, const StepParams& P, uint32_t env, uint32_t slot,
                                          int n_steps, int substeps, int n_obs, Boxes& boxes, uint32_t seed_lo,
                                          uint32_t seed_hi, uint32_t& resets, bool& any_hit, uint32_t& tests) {
-  simulate_cmd<NROT, INTEG, DRAG>(fb, P, env, slot, load_command(fb, env), n_steps, substeps, n_obs, boxes, seed_lo,
-                                  seed_hi, resets, any_hit, tests);
+  const Command cm = load_command(fb, env);
+  bool uniform = false;
+  if (BY_MODE && fb.order) {
+    const unsigned group = __activemask();
+    uniform = __match_any_sync(group, cm.mode) == group;
+  }
+  if (uniform) {
+    if (cm.mode == kModePosition) {
+      simulate_cmd<NROT, INTEG, DRAG, Boxes, kModePosition>(fb, P, env, slot, cm, n_steps, substeps, n_obs, boxes,
+                                                           seed_lo, seed_hi, resets, any_hit, tests);
+      return;
+    }
+    if (cm.mode == kModeBodyVel) {
+      simulate_cmd<NROT, INTEG, DRAG, Boxes, kModeBodyVel>(fb, P, env, slot, cm, n_steps, substeps, n_obs, boxes,
+                                                          seed_lo, seed_hi, resets, any_hit, tests);
+      return;
+    }
+    if (cm.mode == kModeAttThrust) {
+      simulate_cmd<NROT, INTEG, DRAG, Boxes, kModeAttThrust>(fb, P, env, slot, cm, n_steps, substeps, n_obs, boxes,
+                                                            seed_lo, seed_hi, resets, any_hit, tests);
+      return;
+    }
+  }
+  simulate_cmd<NROT, INTEG, DRAG>(fb, P, env, slot, cm, n_steps, substeps, n_obs, boxes, seed_lo, seed_hi, resets,
+                                  any_hit, tests);
 }
 
 }  // namespace agk

@@ -108,7 +108,13 @@ def test_served_request_matches_the_oracle(pool):
     assert np.all(ep == 1)
 
 
-def test_served_request_matches_the_context_path(pool):
+def test_served_request_matches_the_context_path(pool, monkeypatch):
+    """A served request against the same fleet stepped through the context
+    (two 50-step ag_step calls), in both thread orders of the context. The
+    server's kernel, the fused kernel's branching loop (identity order) and
+    its loops compiled per command mode (grouped order) are separate
+    programs; every fused multiply-add of the step is explicit and nothing
+    else is contracted, so all of them must agree bit for bit."""
     rp, inp = pool
     from harness import gpu_fleet
     n, seed, off = 2500, 9, 5000
@@ -117,16 +123,21 @@ def test_served_request_matches_the_context_path(pool):
     w = W.Workload("ctx", n, 4, 1, 32, n, 0, 0)
     sub = W.Inputs(inp.modes[off:off + n].copy(), np.ascontiguousarray(inp.targets[:, off:off + n]),
                    W.body(w, np.random.default_rng(0)), np.ascontiguousarray(inp.boxes[:, :, off:off + n]))
-    fl = gpu_fleet(w, sub, seed)
-    fl.reset(None, seed)
-    fl.step(50)
-    fl.step(50)
-    st_ctx = fl.state().cpu().numpy()
-    ep_ctx = fl.epoch().cpu().numpy().astype(np.uint32)
-    fl.close()
-    assert np.mean(ep_ctx > 1) > 0.01                  # collisions happened
-    np.testing.assert_array_equal(ep, ep_ctx)
-    np.testing.assert_allclose(st, st_ctx, rtol=1e-6, atol=1e-6)
+    for order in ("identity", "grouped"):
+        if order == "identity":
+            monkeypatch.setenv("AG_FUSED_ORDER", "identity")
+        else:
+            monkeypatch.delenv("AG_FUSED_ORDER")
+        fl = gpu_fleet(w, sub, seed)
+        fl.reset(None, seed)
+        fl.step(50)
+        fl.step(50)
+        st_ctx = fl.state().cpu().numpy()
+        ep_ctx = fl.epoch().cpu().numpy().astype(np.uint32)
+        fl.close()
+        assert np.mean(ep_ctx > 1) > 0.01                  # collisions happened
+        np.testing.assert_array_equal(ep, ep_ctx, err_msg=order)
+        np.testing.assert_array_equal(st, st_ctx, err_msg=order)
 
 
 def test_admission_stays_within_the_hbm_budget(pool):
