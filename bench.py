@@ -90,10 +90,10 @@ def alu_peak_tflops(info: dict) -> float:
 BYTES_PER_VEHICLE_LAUNCH = 4 * (26 + 8 + 4 + 4) + 1 + 8 + 4 * 160 + 1 + 4
 # DRAM traffic of one full-size fused launch (1,048,576 envs, 1,000 steps):
 # dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu capture of
-# exactly this launch (797.82 MB + 68.00 MB). It scales with the fleet size
+# exactly this launch (796.43 MB + 68.02 MB). It scales with the fleet size
 # (each env is loaded and stored once per launch; the rare collision tests
 # after the first re-read a few boxes), not with the step count.
-TRAFFIC_BYTES_FULL_LAUNCH = 797.820672e6 + 67.997696e6
+TRAFFIC_BYTES_FULL_LAUNCH = 796.430080e6 + 68.015872e6
 # Algorithmic bytes of one reach-task step per quad: read action 16, goal 12,
 # step counter 4, state 52, motors 16, body 16, epoch 4, mode 1 (121 B);
 # written state 52, motors 16, epoch 4, collided flag 1, command 16,
@@ -486,7 +486,8 @@ def depth_part(seed: int, world: int, alu_peak: float) -> dict:
             # the same with every pair counted, as a test without culling would do (context)
             "alu_frac_all_pairs": (per_launch + all_pairs * DEPTH_FLOP_PER_PIXEL_BOX) / launch_s / 1e12 / alu_peak,
             "hbm_frac": 1024 * DEPTH_BYTES_PER_FRAME / launch_s / 1e9 / hbm_peak_gbs(),
-            "bound": "issue (ALU pipe: slab min/max and compares), not HBM",
+            "bound": "instruction issue (slab min/max on the ALU pipe, reciprocals on XU) above the HBM write "
+                     "floor of the image",
             "workload": "1,024 robots x 270 x 480 depth camera, 16 oriented boxes per environment, 87 deg hfov",
             "paper_value": 1800.0, "paper_hardware": "2x RTX 3090, Isaac Gym camera sensors (graphics renderer)"}
 
