@@ -48,10 +48,10 @@ enum : int {
 // order is NULL. A collision test that cannot hit is skipped (simulate_cmd),
 // so tests are rare after the first step; by default a test reads the
 // environment's box pairs from the slot-ordered copy in global memory, which
-// needs no shared memory. Its bound of 3 blocks of 128 threads per SM leads
-// the compiler to 126 registers, which still fit 4 warps per SM
-// sub-partition (16 per SM); bounds of 4 and 5 blocks (105 and 96
-// registers) and of 1 or 2 (157 registers, 12 warps per SM) measured
+// needs no shared memory. Quad threads of one command mode run the loop
+// compiled for that mode (simulate). The bound of 4 blocks of 128 threads
+// per SM holds the kernel at 128 registers, 4 warps per SM sub-partition
+// (16 per SM); a bound of 3 (140 registers, 12 warps per SM) measured
 // slower. The staged form keeps each thread's boxes on chip for the launch
 // instead: boxes 0 and 1 in registers, the others in shared memory
 // as float4 [pair][field pair][thread], so a warp's 16-byte loads of two
