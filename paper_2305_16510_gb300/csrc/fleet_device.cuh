@@ -257,12 +257,13 @@ __device__ __forceinline__ Wrench4 allocate(const Wrench4& cmd, float (&u)[NROT]
   return W;
 }
 
-// Body z axis of a possibly non-unit quaternion: the homogeneous form over |q|^2.
+// Body z axis of a possibly non-unit quaternion: the homogeneous form over
+// |q|^2, 2 (xz + wy, yz - wx, .) / |q|^2, with its third component written
+// as 1 - 2 (x^2 + y^2) / |q|^2 (w^2 + z^2 = |q|^2 - x^2 - y^2).
 __device__ __forceinline__ V3 body_z(const Q4& q) {
-  float inv = rcp_ftz(dot4(q));
-  float inv2 = 2.f * inv;
+  const float inv2 = 2.f * rcp_ftz(dot4(q));
   return {inv2 * fmaf(q.x, q.z, q.w * q.y), inv2 * fmaf(q.y, q.z, -(q.w * q.x)),
-          inv * fmaf(q.w, q.w, fmaf(-q.x, q.x, fmaf(-q.y, q.y, q.z * q.z)))};
+          fmaf(-inv2, fmaf(q.x, q.x, q.y * q.y), 1.f)};
 }
 
 __device__ __forceinline__ void normalize(Q4& q) {
@@ -313,10 +314,11 @@ __device__ __forceinline__ void step_sie(VState& s, V3 b3, const Wrench4& W, con
 //
 // The state travels as seven FP32 pairs, (vx vy) (vz wx) (wy wz) (qw qx)
 // (qy qz) (px py) (pz -), and each stage's rates in the same order as
-// (v' | Omega' | q' | p'), with q' = q (x) (0, Omega / 2). Every stage state
-// x + c k and every accumulation s + 2 k is then one packed FMA per pair
-// (__ffma2_rn); halving Omega and the step weights is exact, so each product
-// equals that of the scalar form.
+// (v' | Omega' | 2 q' | p'), with 2 q' = q (x) (0, Omega): the quaternion's
+// factor 1/2 goes into its pairs' stage and step weights instead. Every
+// stage state x + c k and every accumulation s + 2 k is then one packed FMA
+// per pair (__ffma2_rn); halving a weight is exact, so each product equals
+// that of the scalar form.
 template <bool DRAG>
 __device__ __forceinline__ void rk4_rates(const float2 (&y)[7], V3 b3, float fm, float dm, V3 aw, const Body& b,
                                           float2 (&k)[7]) {
@@ -324,7 +326,7 @@ __device__ __forceinline__ void rk4_rates(const float2 (&y)[7], V3 b3, float fm,
   const Q4 q = {y[3].x, y[3].y, y[4].x, y[4].y};
   const V3 a = accel<DRAG>(b3, v, fm, dm);
   const V3 al = ang_accel(w, aw, b);
-  const Q4 r = quat_rate2(q, {0.5f * w.x, 0.5f * w.y, 0.5f * w.z});
+  const Q4 r = quat_rate2(q, w);  // twice the quaternion rate
   k[0] = make_float2(a.x, a.y);
   k[1] = make_float2(a.z, al.x);
   k[2] = make_float2(al.y, al.z);
@@ -348,21 +350,22 @@ __device__ __forceinline__ void step_rk4(VState& s, V3 b3, const Wrench4& W, con
   for (int i = 0; i < 7; ++i) acc[i] = k[i];
   // stages 2 and 3 at t + h/2, stage 4 at t + h, each from the previous stage's rates
   const float2 c2 = make_float2(0.5f * h, 0.5f * h), c4 = make_float2(h, h), two = make_float2(2.f, 2.f);
+  const float2 c2q = make_float2(0.25f * h, 0.25f * h), c4q = make_float2(0.5f * h, 0.5f * h);
 #pragma unroll
   for (int st = 0; st < 3; ++st) {
-    const float2 c = st < 2 ? c2 : c4;
+    const float2 c = st < 2 ? c2 : c4, cq = st < 2 ? c2q : c4q;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) y[i] = __ffma2_rn(c, k[i], x[i]);  // v, Omega, q (p is not needed)
+    for (int i = 0; i < 5; ++i) y[i] = __ffma2_rn(i >= 3 ? cq : c, k[i], x[i]);  // v, Omega, q (p is not needed)
     rk4_rates<DRAG>(y, body_z({y[3].x, y[3].y, y[4].x, y[4].y}), fm, dm, aw, b, k);
 #pragma unroll
     for (int i = 0; i < 7; ++i) acc[i] = st < 2 ? __ffma2_rn(two, k[i], acc[i]) : __fadd2_rn(k[i], acc[i]);
   }
   // x + h/6 (k1 + 2 k2 + 2 k3 + k4)
   const float h6 = h * (1.f / 6.f);
-  const float2 c6 = make_float2(h6, h6);
+  const float2 c6 = make_float2(h6, h6), c6q = make_float2(0.5f * h6, 0.5f * h6);
   float2 xn[7];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) xn[i] = __ffma2_rn(c6, acc[i], x[i]);
+  for (int i = 0; i < 7; ++i) xn[i] = __ffma2_rn(i == 3 || i == 4 ? c6q : c6, acc[i], x[i]);
   s.v = {xn[0].x, xn[0].y, xn[1].x};
   s.w = {xn[1].y, xn[2].x, xn[2].y};
   s.q = {xn[3].x, xn[3].y, xn[4].x, xn[4].y};
