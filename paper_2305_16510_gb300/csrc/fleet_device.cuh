@@ -288,6 +288,19 @@ __device__ __forceinline__ V3 accel(V3 b3, V3 v, float fm, float dm) {
   return {fm * b3.x, fm * b3.y, fmaf(fm, b3.z, -kGravity)};
 }
 
+// v' of an RK4 stage whose quaternion q need not be unit, with the body z
+// axis b3(q) = (2 (xz + wy), 2 (yz - wx), |q|^2 - 2 (x^2 + y^2)) / |q|^2
+// folded in: with s = 2 fm / |q|^2, v' = (s (xz + wy), s (yz - wx),
+// (fm - g) - s (x^2 + y^2)) - (c/m) v. fm2 = 2 fm and fmg = fm - g are taken
+// once per substep.
+template <bool DRAG>
+__device__ __forceinline__ V3 accel_q(const Q4& q, V3 v, float fm2, float fmg, float dm) {
+  const float s = fm2 * rcp_ftz(dot4(q));
+  const float px = fmaf(q.x, q.z, q.w * q.y), py = fmaf(q.y, q.z, -(q.w * q.x)), pz = fmaf(q.x, q.x, q.y * q.y);
+  if (DRAG) return {fmaf(s, px, -(dm * v.x)), fmaf(s, py, -(dm * v.y)), fmaf(-s, pz, fmaf(-dm, v.z, fmg))};
+  return {s * px, s * py, fmaf(-s, pz, fmg)};
+}
+
 __device__ __forceinline__ V3 ang_accel(V3 w, V3 aw, const Body& b) {
   return {fmaf(-b.ex, w.y * w.z, aw.x), fmaf(-b.ey, w.z * w.x, aw.y), fmaf(-b.ez, w.x * w.y, aw.z)};
 }
@@ -310,7 +323,8 @@ __device__ __forceinline__ void step_sie(VState& s, V3 b3, const Wrench4& W, con
 }
 
 // Classic RK4 on (p, v, q, Omega) with the wrench held over the stages;
-// renormalise q. The first stage uses the start attitude's b3 (unit q).
+// renormalise q. The first stage uses the start attitude's b3 (unit q), the
+// others the body z axis of their stage quaternion (accel_q).
 //
 // The state travels as seven FP32 pairs, (vx vy) (vz wx) (wy wz) (qw qx)
 // (qy qz) (px py) (pz -), and each stage's rates in the same order as
@@ -319,12 +333,10 @@ __device__ __forceinline__ void step_sie(VState& s, V3 b3, const Wrench4& W, con
 // stage state x + c k and every accumulation s + 2 k is then one packed FMA
 // per pair (__ffma2_rn); halving a weight is exact, so each product equals
 // that of the scalar form.
-template <bool DRAG>
-__device__ __forceinline__ void rk4_rates(const float2 (&y)[7], V3 b3, float fm, float dm, V3 aw, const Body& b,
-                                          float2 (&k)[7]) {
+// The rates of stage state y given its v' (a).
+__device__ __forceinline__ void rk4_rates(const float2 (&y)[7], V3 a, V3 aw, const Body& b, float2 (&k)[7]) {
   const V3 v = {y[0].x, y[0].y, y[1].x}, w = {y[1].y, y[2].x, y[2].y};
   const Q4 q = {y[3].x, y[3].y, y[4].x, y[4].y};
-  const V3 a = accel<DRAG>(b3, v, fm, dm);
   const V3 al = ang_accel(w, aw, b);
   const Q4 r = quat_rate2(q, w);  // twice the quaternion rate
   k[0] = make_float2(a.x, a.y);
@@ -345,10 +357,11 @@ __device__ __forceinline__ void step_rk4(VState& s, V3 b3, const Wrench4& W, con
                        make_float2(s.p.z, 0.f)};
   float2 k[7], acc[7], y[7];
   // stage 1; acc collects k1 + 2 k2 + 2 k3 + k4
-  rk4_rates<DRAG>(x, b3, fm, dm, aw, b, k);
+  rk4_rates(x, accel<DRAG>(b3, s.v, fm, dm), aw, b, k);
 #pragma unroll
   for (int i = 0; i < 7; ++i) acc[i] = k[i];
   // stages 2 and 3 at t + h/2, stage 4 at t + h, each from the previous stage's rates
+  const float fm2 = 2.f * fm, fmg = fm - kGravity;
   const float2 c2 = make_float2(0.5f * h, 0.5f * h), c4 = make_float2(h, h), two = make_float2(2.f, 2.f);
   const float2 c2q = make_float2(0.25f * h, 0.25f * h), c4q = make_float2(0.5f * h, 0.5f * h);
 #pragma unroll
@@ -356,7 +369,7 @@ __device__ __forceinline__ void step_rk4(VState& s, V3 b3, const Wrench4& W, con
     const float2 c = st < 2 ? c2 : c4, cq = st < 2 ? c2q : c4q;
 #pragma unroll
     for (int i = 0; i < 5; ++i) y[i] = __ffma2_rn(i >= 3 ? cq : c, k[i], x[i]);  // v, Omega, q (p is not needed)
-    rk4_rates<DRAG>(y, body_z({y[3].x, y[3].y, y[4].x, y[4].y}), fm, dm, aw, b, k);
+    rk4_rates(y, accel_q<DRAG>({y[3].x, y[3].y, y[4].x, y[4].y}, {y[0].x, y[0].y, y[1].x}, fm2, fmg, dm), aw, b, k);
 #pragma unroll
     for (int i = 0; i < 7; ++i) acc[i] = st < 2 ? __ffma2_rn(two, k[i], acc[i]) : __fadd2_rn(k[i], acc[i]);
   }
