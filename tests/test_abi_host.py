@@ -167,3 +167,22 @@ def test_config_validation_follows_the_documented_rules(lib):
         _abi.ag_destroy(ctx)
 
     check()
+
+
+def test_step_sources_compile_without_implicit_contraction():
+    """Every file that compiles the per-vehicle step (the fused kernels and
+    their per-mode loops, the unfused stages, the serving kernel, the task
+    step) writes its fused multiply-adds out and is compiled with
+    -fmad=false, so that each compiled copy rounds as the source says and
+    the copies agree bit for bit; a new file that includes the step's
+    headers must join them."""
+    import os
+    import re
+    from paper_2305_16510_gb300 import build
+    for src in build.CUDA_SOURCES:
+        text = open(os.path.join(build.CSRC, src)).read()
+        includes = set(re.findall(r'#include "([^"]+)"', text))
+        runs_step = "fleet_sim.cuh" in includes or ("fleet_device.cuh" in includes and "simulate" in text)
+        if runs_step:
+            assert src in build.NO_CONTRACTION, src
+    assert {"fleet_kernels.cu", "serve.cu", "task.cu"} <= build.NO_CONTRACTION
