@@ -103,11 +103,11 @@ __device__ __forceinline__ void write_obs(const ReachArgs& a, const float* stage
 // step (controller, allocation, integration, collision test and reset, as in
 // the fused fleet step), then reach_tail. Every environment shares the task's
 // command mode, so warps are mode-uniform without a grouping permutation.
-// Without boxes the step is memory-latency bound: 32 warps per SM at 64
-// registers, with a few bytes of spills, beat fewer warps without. With boxes
-// it keeps 12 warps per SM (170 registers).
+// Without boxes the step is memory-latency bound: a bound of 14 blocks (28
+// warps) per SM measured best, against 16 blocks (64 registers, more spills)
+// and 20 (48 registers). With boxes it keeps 12 warps per SM (170 registers).
 template <int INTEG, bool DRAG, bool BOXES>
-__global__ void __launch_bounds__(kTaskBlock, BOXES ? 384 / kTaskBlock : 1024 / kTaskBlock)
+__global__ void __launch_bounds__(kTaskBlock, BOXES ? 384 / kTaskBlock : 896 / kTaskBlock)
     k_reach_step(ReachArgs a, StepParams P, int substeps) {
   __shared__ float stage[kTaskBlock * kObs];  // odd row length: conflict-free
   const FleetBuffers& fb = a.fb;
