@@ -428,8 +428,11 @@ ag_status ag_reach_observe(ag_ctx* ctx, float* obs);
  * they finish. A finished request's final state and reset epochs are kept
  * on the host until ag_server_wait collects them. Chunk boundaries are
  * counted from each request's own first launch, so a request's result is
- * bit-identical alone or in any mix. max_active = 1 makes the same loop run
- * one request per launch (the unbatched comparison point). Physics settings
+ * bit-identical alone or in any mix, and to ag_step calls of chunk_steps
+ * steps each on the same inputs (every fused multiply-add of the step is
+ * explicit in the source, so both kernels round alike). max_active = 1
+ * makes the same loop run one request per launch (the unbatched comparison
+ * point). Physics settings
  * (integrator, substeps, dt, gains, motor model, radius) come from `physics`;
  * its fleet-size fields are ignored. */
 #define AG_SERVER_MAX_ACTIVE 4096
