@@ -26,14 +26,19 @@
 //     mode, where Omega_d = 0);
 //   * the first derivative evaluation of a substep reuses the controller's
 //     R e_3 (q is unit there: it was renormalised after the last substep);
-//   * the body z axis of a non-unit quaternion (RK4 stages) is the
+//   * the body z axis of a non-unit quaternion (RK4 stages 2-4) is the
 //     homogeneous quaternion form divided by |q|^2, which equals the axis of
-//     q / |q| exactly;
+//     q / |q| exactly, and is folded into the stage's acceleration (accel_q);
 //   * with the diagonal inertia, Omega x J Omega is written in principal
 //     axes, ((Jz - Jy) wy wz, (Jx - Jz) wz wx, (Jy - Jx) wx wy), and J^-1 M is
 //     formed once per substep (the wrench is held over the RK4 stages);
 //   * the factor 1/2 of q' = 1/2 q (x) (0, Omega) is folded into the RK4
-//     stage weights (multiplications by powers of two are exact).
+//     stage weights of the quaternion and into the semi-implicit Euler step
+//     (multiplications by powers of two are exact);
+//   * 1/x and 1/sqrt(x) of squared norms use the hardware approximations
+//     (rcp_ftz, rsqrt_ftz), and every fused multiply-add is explicit (the
+//     including files are compiled without contraction), so each compiled
+//     copy of the step rounds alike.
 #pragma once
 
 #include <cstdint>
