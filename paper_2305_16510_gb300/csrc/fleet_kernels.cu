@@ -48,7 +48,7 @@ enum : int {
 // order is NULL. A collision test that cannot hit is skipped (simulate_cmd),
 // so tests are rare after the first step; by default a test reads the
 // environment's box pairs from the slot-ordered copy in global memory, which
-// needs no shared memory. Quad threads of one command mode run the loop
+// needs no shared memory. Threads of one command mode run the loop
 // compiled for that mode (simulate). The bound of 4 blocks of 128 threads
 // per SM holds the kernel at 128 registers, 4 warps per SM sub-partition
 // (16 per SM); a bound of 3 (140 registers, 12 warps per SM) measured
@@ -115,24 +115,24 @@ __global__ void __launch_bounds__(128, BOXES == kBoxesGlobal ? 4
       if (nrot == 4)
         simulate<4, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else if (nrot == 6)
-        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+        simulate<6, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else
-        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+        simulate<8, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, n_obs, gx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
     } else if (BOXES == kBoxesStaged) {
       if (nrot == 4)
         simulate<4, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else if (nrot == 6)
-        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+        simulate<6, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else
-        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+        simulate<8, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, n_obs, bx, P.seed_lo, P.seed_hi, resets, any_hit, tests);
     } else {
       NoBoxSource none;
       if (nrot == 4)
         simulate<4, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else if (nrot == 6)
-        simulate<6, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+        simulate<6, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
       else
-        simulate<8, INTEG, DRAG>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
+        simulate<8, INTEG, DRAG, true>(fb, P, env, slot, n_steps, substeps, 0, none, P.seed_lo, P.seed_hi, resets, any_hit, tests);
     }
     fb.collided[env] = any_hit ? 1 : 0;
   }
