@@ -177,6 +177,7 @@ agk::StepParams agk::step_params_for(const ag_config& c, uint64_t seed) {
   P.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
   P.seed_hi = (uint32_t)(seed >> 32);
   P.exact_tests = 0;
+  agk::pair_rotor_matrices(P);
   return P;
 }
 
@@ -199,6 +200,7 @@ agk::StepParams step_params(const ag_ctx* ctx) {
   P.seed_lo = (uint32_t)(ctx->seed & 0xFFFFFFFFu);
   P.seed_hi = (uint32_t)(ctx->seed >> 32);
   P.exact_tests = 0;
+  agk::pair_rotor_matrices(P);
   return P;
 }
 

@@ -75,6 +75,9 @@ struct StepParams {
   float kx[3], kv[3], kR[3], kW[3];
   float A[3][4][8];   // wrench = A u for quad (0), hexa (1), octo (2)
   float Ap[3][8][4];  // pseudo-inverse of A (FP64-computed, stored float32)
+  // the same in the pair layout of the packed allocation (pair_rotor_matrices):
+  float2 Ap2[3][4][4];  // (Ap[2j][k], Ap[2j + 1][k]): motors 2j and 2j + 1
+  float2 A2[3][2][8];   // (A[0][i], A[1][i]) and (A[2][i], A[3][i]): (f, M_x) and (M_y, M_z) of motor i
   float h;            // substep length
   float alpha;        // motor lag factor 1 - exp(-h / tau)
   float drag;
@@ -83,6 +86,18 @@ struct StepParams {
   uint32_t seed_lo, seed_hi;
   uint32_t exact_tests;  // 1: run the collision test at every step (no clearance skip)
 };
+
+// Fills the pair layout of the allocation matrices from A and Ap.
+inline void pair_rotor_matrices(StepParams& P) {
+  for (int t = 0; t < 3; ++t) {
+    for (int j = 0; j < 4; ++j)
+      for (int k = 0; k < 4; ++k) P.Ap2[t][j][k] = make_float2(P.Ap[t][2 * j][k], P.Ap[t][2 * j + 1][k]);
+    for (int i = 0; i < 8; ++i) {
+      P.A2[t][0][i] = make_float2(P.A[t][0][i], P.A[t][1][i]);
+      P.A2[t][1][i] = make_float2(P.A[t][2][i], P.A[t][3][i]);
+    }
+  }
+}
 
 __device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
 __device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
@@ -244,22 +259,33 @@ __device__ __forceinline__ Wrench4 controller(const VState& s, const Command& cm
 }
 
 // Rotor allocation, per-motor clamp to [0, u_max], first-order lag; returns
-// the realised wrench A u.
+// the realised wrench A u. Two motors travel as one FP32 pair through the
+// allocation and the lag, and the wrench accumulates as the pairs (f, M_x)
+// and (M_y, M_z), in packed FMAs (__ffma2_rn) that round each lane as the
+// scalar form would, in the same order.
 template <int NROT>
 __device__ __forceinline__ Wrench4 allocate(const Wrench4& cmd, float (&u)[NROT], const StepParams& P) {
   constexpr int T = NROT == 4 ? 0 : (NROT == 6 ? 1 : 2);
-  Wrench4 W = {0.f, 0.f, 0.f, 0.f};
+  const float2 f2 = make_float2(cmd.f, cmd.f), mx2 = make_float2(cmd.mx, cmd.mx);
+  const float2 my2 = make_float2(cmd.my, cmd.my), mz2 = make_float2(cmd.mz, cmd.mz);
+  const float2 alpha2 = make_float2(P.alpha, P.alpha);
+  float2 Wa = make_float2(0.f, 0.f), Wb = make_float2(0.f, 0.f);  // (f, M_x), (M_y, M_z)
 #pragma unroll
-  for (int i = 0; i < NROT; ++i) {
-    float uc = fmaf(P.Ap[T][i][3], cmd.mz, fmaf(P.Ap[T][i][2], cmd.my, fmaf(P.Ap[T][i][1], cmd.mx, P.Ap[T][i][0] * cmd.f)));
-    uc = fminf(fmaxf(uc, 0.f), P.u_max);
-    u[i] = fmaf(P.alpha, uc - u[i], u[i]);
-    W.f = fmaf(P.A[T][0][i], u[i], W.f);
-    W.mx = fmaf(P.A[T][1][i], u[i], W.mx);
-    W.my = fmaf(P.A[T][2][i], u[i], W.my);
-    W.mz = fmaf(P.A[T][3][i], u[i], W.mz);
+  for (int j = 0; j < NROT / 2; ++j) {
+    float2 uc = __ffma2_rn(P.Ap2[T][j][3], mz2,
+                           __ffma2_rn(P.Ap2[T][j][2], my2, __ffma2_rn(P.Ap2[T][j][1], mx2, __fmul2_rn(P.Ap2[T][j][0], f2))));
+    uc = make_float2(fminf(fmaxf(uc.x, 0.f), P.u_max), fminf(fmaxf(uc.y, 0.f), P.u_max));
+    float2 uu = make_float2(u[2 * j], u[2 * j + 1]);
+    uu = __ffma2_rn(alpha2, __fadd2_rn(uc, make_float2(-uu.x, -uu.y)), uu);
+    u[2 * j] = uu.x;
+    u[2 * j + 1] = uu.y;
+    const float2 u0 = make_float2(uu.x, uu.x), u1 = make_float2(uu.y, uu.y);
+    Wa = __ffma2_rn(P.A2[T][0][2 * j], u0, Wa);
+    Wb = __ffma2_rn(P.A2[T][1][2 * j], u0, Wb);
+    Wa = __ffma2_rn(P.A2[T][0][2 * j + 1], u1, Wa);
+    Wb = __ffma2_rn(P.A2[T][1][2 * j + 1], u1, Wb);
   }
-  return W;
+  return {Wa.x, Wa.y, Wb.x, Wb.y};
 }
 
 // Body z axis of a possibly non-unit quaternion: the homogeneous form over
