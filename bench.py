@@ -90,10 +90,10 @@ def alu_peak_tflops(info: dict) -> float:
 BYTES_PER_VEHICLE_LAUNCH = 4 * (26 + 8 + 4 + 4) + 1 + 8 + 4 * 160 + 1 + 4
 # DRAM traffic of one full-size fused launch (1,048,576 envs, 1,000 steps):
 # dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu capture of
-# exactly this launch (797.28 MB + 68.10 MB). It scales with the fleet size
+# exactly this launch (797.11 MB + 68.19 MB). It scales with the fleet size
 # (each env is loaded and stored once per launch; the rare collision tests
 # after the first re-read a few boxes), not with the step count.
-TRAFFIC_BYTES_FULL_LAUNCH = 797.280256e6 + 68.103168e6
+TRAFFIC_BYTES_FULL_LAUNCH = 797.112064e6 + 68.190976e6
 # Algorithmic bytes of one reach-task step per quad: read action 16, goal 12,
 # step counter 4, state 52, motors 16, body 16, epoch 4, mode 1 (121 B);
 # written state 52, motors 16, epoch 4, collided flag 1, command 16,
