@@ -50,7 +50,7 @@ enum : int {
 // environment's box pairs from the slot-ordered copy in global memory, which
 // needs no shared memory. Threads of one command mode run the loop
 // compiled for that mode (simulate). The bound of 4 blocks of 128 threads
-// per SM holds the kernel to 126 registers, 4 warps per SM sub-partition
+// per SM holds the kernel under 128 registers, 4 warps per SM sub-partition
 // (16 per SM); a bound of 3 (140 registers, 12 warps per SM) measured
 // slower. The staged form keeps each thread's boxes on chip for the launch
 // instead: boxes 0 and 1 in registers, the others in shared memory
