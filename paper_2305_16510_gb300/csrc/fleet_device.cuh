@@ -344,12 +344,22 @@ __device__ __forceinline__ void step_sie(VState& s, V3 b3, const Wrench4& W, con
   const V3 aw = {b.ijx * W.mx, b.ijy * W.my, b.ijz * W.mz};
   const V3 dv = accel<DRAG>(b3, s.v, fm, dm);
   const V3 dw = ang_accel(s.w, aw, b);
-  s.v = {fmaf(h, dv.x, s.v.x), fmaf(h, dv.y, s.v.y), fmaf(h, dv.z, s.v.z)};
-  s.w = {fmaf(h, dw.x, s.w.x), fmaf(h, dw.y, s.w.y), fmaf(h, dw.z, s.w.z)};
-  s.p = {fmaf(h, s.v.x, s.p.x), fmaf(h, s.v.y, s.p.y), fmaf(h, s.v.z, s.p.z)};
+  // the updates as FP32 pairs (v_x v_y) (v_z w_x) (w_y w_z) (p_x p_y) (q_w q_x) (q_y q_z), each lane
+  // rounded as the scalar fmaf
+  const float2 h2 = make_float2(h, h);
+  const float2 vxy = __ffma2_rn(h2, make_float2(dv.x, dv.y), make_float2(s.v.x, s.v.y));
+  const float2 vzwx = __ffma2_rn(h2, make_float2(dv.z, dw.x), make_float2(s.v.z, s.w.x));
+  const float2 wyz = __ffma2_rn(h2, make_float2(dw.y, dw.z), make_float2(s.w.y, s.w.z));
+  s.v = {vxy.x, vxy.y, vzwx.x};
+  s.w = {vzwx.y, wyz.x, wyz.y};
+  const float2 pxy = __ffma2_rn(h2, vxy, make_float2(s.p.x, s.p.y));
+  s.p = {pxy.x, pxy.y, fmaf(h, s.v.z, s.p.z)};
   const float hh = 0.5f * h;
+  const float2 hh2 = make_float2(hh, hh);
   const Q4 r = quat_rate2(s.q, s.w);
-  s.q = {fmaf(hh, r.w, s.q.w), fmaf(hh, r.x, s.q.x), fmaf(hh, r.y, s.q.y), fmaf(hh, r.z, s.q.z)};
+  const float2 qwx = __ffma2_rn(hh2, make_float2(r.w, r.x), make_float2(s.q.w, s.q.x));
+  const float2 qyz = __ffma2_rn(hh2, make_float2(r.y, r.z), make_float2(s.q.y, s.q.z));
+  s.q = {qwx.x, qwx.y, qyz.x, qyz.y};
   normalize(s.q);
 }
 
